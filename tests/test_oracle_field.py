@@ -1,0 +1,122 @@
+"""Pins of the oracle's whole-field results against closed forms and exact integrals."""
+import math
+
+import numpy as np
+import pytest
+
+import meshgen
+from oracle.integrals import tet_uniform, triangle_linear
+from oracle.nearfield import boundary_geometry
+from oracle.paim import AimGrid
+from oracle.problem import OracleProblem
+
+
+@pytest.fixture(scope="module")
+def film():
+    m = meshgen.film_cell(10, 10, 2)
+    return OracleProblem(m.xyz, m.tets, m.periods, grid=(16, 16, 8), near_boxes=3)
+
+
+def test_film_in_plane_magnetisation_has_no_field(film):
+    # m along x: no volume charge, surface charges only on periodic faces, which pair
+    mx = meshgen.m_uniform(film.Np, (1, 0, 0))
+    assert np.abs(film.charges(mx)).max() < 1e-12 * film.Ms * 1e-18
+    assert np.abs(film.h_ms(mx, "paim")).max() < 1e-12 * film.Ms
+    assert np.abs(film.h_ms(mx, "direct")).max() < 1e-12 * film.Ms
+
+
+def test_film_demag_factor_nzz_is_one(film):
+    mz = meshgen.m_uniform(film.Np, (0, 0, 1))
+    H = film.h_ms(mz, "direct")
+    Hz = (H[:, 2] * film.V).sum() / film.V.sum() / film.Ms
+    assert abs(Hz + 1.0) < 0.03          # discretisation error of the nodal-charge model (~2.5% at 2 layers)
+    assert np.abs(H[:, :2]).max() < 0.03 * film.Ms
+
+
+def test_moments_add_up_to_charges(film):
+    m = meshgen.m_random(film.Np, 7)
+    q = film.charges(m)
+    assert np.abs(film.moments(m) - q).max() < 1e-12 * np.abs(q).max()
+    assert abs(q.sum()) < 1e-13 * np.abs(q).sum()
+
+
+def test_filled_3d_cell_has_no_field():
+    c = meshgen.cube_cell(4, jitter=0.2, seed=3)
+    pb = OracleProblem(c.xyz, c.tets, c.periods, grid=(8, 8, 8), near_boxes=2)
+    for d in ((0, 0, 1), (1, 1, 0)):
+        m = meshgen.m_uniform(pb.Np, d)
+        assert np.abs(pb.h_ms(m, "direct")).max() < 1e-12 * pb.Ms
+        assert np.abs(pb.h_ms(m, "paim")).max() < 1e-12 * pb.Ms
+
+
+def test_prism_demag_factors():
+    p = meshgen.prism_cell(5, 5, 6, jitter=0.1, seed=2)
+    pb = OracleProblem(p.xyz, p.tets, p.periods)
+    mz = meshgen.m_uniform(pb.Np, (0, 0, 1))
+    assert np.abs(pb.h_ms(mz, "direct")).max() < 1e-12 * pb.Ms
+    for d in (0, 1):
+        e = np.zeros(3)
+        e[d] = 1
+        H = pb.h_ms(meshgen.m_uniform(pb.Np, e), "direct")
+        mean = (H[:, d] * pb.V).sum() / pb.V.sum() / pb.Ms
+        assert abs(mean + 0.5) < 0.03
+
+
+def test_free_space_all_near_equals_exact_potential():
+    # with every element near, O1 is the exact potential of the P1 charge distribution
+    xyz, tets = meshgen.kuhn_box(3, 3, 2, 1e-9, jitter=0.15, seed=2)
+    pb = OracleProblem(xyz, tets, (0, 0, 0), near_elem_factor=100.0)
+    M = pb.Ms * meshgen.m_random(pb.Np, 5)
+    u1 = pb.potential_direct(M / pb.Ms)
+    rho = -np.einsum("tjd,tjd->t", pb.grad, M[pb.lca[pb.tets]])
+    nrm, _ = boundary_geometry(xyz, pb.tri)
+    sig = np.einsum("fjd,fd->fj", M[pb.lca[pb.tri]], nrm)
+    u = np.array([np.sum(rho * tet_uniform(np.repeat(r[None], pb.tets.shape[0], 0), xyz[pb.tets]))
+                  + np.sum(sig * triangle_linear(np.repeat(r[None], pb.tri.shape[0], 0), xyz[pb.tri]))
+                  for r in pb.pos_f])
+    assert np.abs(u1 - u).max() < 1e-12 * np.abs(u).max()
+
+
+def test_fft_convolution_equals_grid_sum():
+    rng = np.random.default_rng(0)
+    for periods, dims in (((0, 0, 0), (8, 7, 9)), ((2.0, 0, 0), (8, 7, 8)), ((2.0, 2.0, 0), (8, 8, 7)),
+                          ((0, 0, 2.0), (7, 8, 8)), ((2.0, 2.0, 2.0), (8, 8, 8))):
+        pos = rng.uniform(0, 1.9, size=(30, 3))
+        g = AimGrid(pos, periods, dims, 3)
+        K = g.kernel_table()
+        Q = rng.normal(size=dims)
+        U1 = g.convolve(Q, np.fft.rfftn(K).real)
+        U2 = g.convolve_direct(Q, K)
+        assert np.abs(U1 - U2).max() < 1e-12 * np.abs(U2).max()
+
+
+@pytest.mark.slow
+def test_paim_method_error_vs_direct():
+    m = meshgen.film_cell(10, 10, 2)
+    pb = OracleProblem(m.xyz, m.tets, m.periods, grid=(16, 16, 8), near_boxes=3)
+    mr = meshgen.m_random(pb.Np, 3)
+    H1 = pb.h_ms(mr, "direct")
+    H2 = pb.h_ms(mr, "paim")
+    err = np.linalg.norm(H2 - H1) / np.linalg.norm(H1)
+    assert err < 2e-3
+    # and a coarser near zone is measurably worse (the correction is doing the work)
+    pb2 = OracleProblem(m.xyz, m.tets, m.periods, grid=(16, 16, 8), near_boxes=1)
+    err1 = np.linalg.norm(pb2.h_ms(mr, "paim") - H1) / np.linalg.norm(H1)
+    assert err1 > 3 * err
+
+
+@pytest.mark.slow
+def test_fold_translation_invariance():
+    # translating a touching 1D cell so it straddles the cell boundary changes nothing at O1
+    p = meshgen.prism_cell(4, 4, 6, jitter=0.15, seed=5)
+    m0 = None
+    Hs = []
+    for shift in (0.0, 0.37):
+        xyz = p.xyz.copy()
+        xyz[:, 2] += shift * p.periods[2]
+        pb = OracleProblem(xyz, p.tets, p.periods, grid=(12, 12, 12), near_boxes=3)
+        if m0 is None:
+            m0 = meshgen.m_random(pb.Np, 11)
+        Hs.append((pb.h_ms(m0, "direct"), pb.h_ms(m0, "paim")))
+    assert np.linalg.norm(Hs[1][0] - Hs[0][0]) / np.linalg.norm(Hs[0][0]) < 1e-10
+    assert np.linalg.norm(Hs[1][1] - Hs[0][1]) / np.linalg.norm(Hs[0][1]) < 5e-3
