@@ -1,0 +1,172 @@
+/*
+ * pmfem.h -- C-ABI of the periodic micromagnetic FEM effective-field library (libpmfem.so).
+ *
+ * What it computes (Ai, Duan, Lomakin, "Periodic micromagnetic finite element method"):
+ *   H_eff = H_ex + H_ms + H_ap                                   (Eq. 3, no anisotropy)
+ *   H_ex  : periodized P1 Laplacian, Eqs. 7-12
+ *   H_ms  : charges (Eq. 14a) -> projection onto a uniform grid (BAIM step 1) -> FFT
+ *           convolution with the periodic Green's function of Eq. 15 (step 2) ->
+ *           interpolation (step 3) -> near-field precorrection (step 4, Eq. 14c) ->
+ *           periodized gradient (Eq. 14d)
+ *   LLG   : Eq. 2 / Eq. 6, integrated by classical RK4 with renormalisation.
+ * Units are SI (metres, A/m, J/m, seconds); magnetisation arguments are unit vectors m
+ * (M = Ms m is applied inside).
+ *
+ * Conventions shared by every call
+ *   - Every function returns int: 0 on success, a negative PMFEM_E* code on failure.
+ *     pmfem_last_error(h) gives a message for the last failing call on that handle.
+ *   - Handles are opaque.  The library owns all device memory it allocates; the caller
+ *     owns every buffer it passes in.  Host arrays passed in are copied before the call
+ *     returns and may be freed afterwards.
+ *   - "device" pointers are CUDA device (or managed) addresses; "host" pointers are CPU
+ *     addresses (pinned memory makes the host-buffer calls faster but is not required).
+ *   - stream is a cudaStream_t passed as void*; NULL selects the library's own stream.
+ *     Calls that take a stream enqueue work and return without synchronising, except
+ *     where stated.
+ *   - Unknown ordering: the N' unknowns are the ancestors of the periodic pairing
+ *     (Sec. 2.2), numbered by increasing original node index; pmfem_lca_map gives the
+ *     unknown of every original node.  Field/state arrays are N' x 3, row-major.
+ *   - Precision (pmfem_set_precision) fixes the element type T of field/state buffers:
+ *     PMFEM_FP64 -> double; PMFEM_FP32 and PMFEM_BF16SPLIT -> float.
+ *   - Set-up (create_mesh, set_aim, set_periodicity) runs on the host and does not touch
+ *     the GPU; device buffers are allocated on the first call that needs them.
+ */
+#ifndef PMFEM_H
+#define PMFEM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pmfem_state* pmfem_t;
+
+/* status codes */
+#define PMFEM_OK          0
+#define PMFEM_EINVAL     -1   /* bad argument (size, NULL, out-of-range value)          */
+#define PMFEM_ENOMEM     -2   /* host or device allocation failed                       */
+#define PMFEM_ECUDA      -3   /* a CUDA runtime call failed (no GPU, launch failure)    */
+#define PMFEM_EMESH      -4   /* invalid mesh: bad index, degenerate tetrahedron,
+                                 unpaired node on a touching periodic face               */
+#define PMFEM_ENONFINITE -5   /* NaN/Inf met in an input or a result (device check)      */
+#define PMFEM_ETIMEOUT   -6   /* a bounded device wait ran out                          */
+#define PMFEM_ESTATE     -7   /* call out of order (e.g. field before set_periodicity)  */
+
+/* precision modes */
+#define PMFEM_FP64      0
+#define PMFEM_FP32      1
+#define PMFEM_BF16SPLIT 2     /* BF16 storage of operator values and grid buffers,
+                                 FP32 arithmetic and accumulation                       */
+
+/* field component bitmask for pmfem_field */
+#define PMFEM_EX 1
+#define PMFEM_MS 2
+#define PMFEM_AP 4
+#define PMFEM_ALL 7
+
+/* Library version string and the last error message of a handle (never NULL). */
+const char* pmfem_version(void);
+const char* pmfem_last_error(pmfem_t h);
+
+/*
+ * Create a mesh handle (Sec. 2.2 discrete formulation, P1 tetrahedra, Eq. 4).
+ *   xyz   host, N x 3 doubles, node coordinates in metres
+ *   tets  host, T x 4 int32, node indices in [0, N); negatively oriented tetrahedra
+ *         are re-oriented, tetrahedra with 6|V| <= 1e-12 * (longest edge)^3 -> EMESH
+ *   Ms    saturation magnetisation [A/m] (> 0); A exchange stiffness [J/m] (>= 0);
+ *   alpha Gilbert damping (>= 0).
+ * The handle starts non-periodic with default AIM settings; *out is NULL on failure.
+ */
+int pmfem_create_mesh(pmfem_t* out, const double* xyz, int64_t N, const int32_t* tets, int64_t T,
+                      double Ms, double A, double alpha);
+
+/*
+ * AIM grid and near-zone settings (Sec. 3.2, Eq. 16, Eq. 17).  Call before
+ * pmfem_set_periodicity; 0 selects the default for each argument.
+ *   Nx, Ny, Nz   grid points per axis.  A periodic axis uses Delta = L / N and an FFT of
+ *                length N; a non-periodic axis uses Delta = D / (N - 1 - 2m) with
+ *                m = ceil((p+1)/2) halo cells and an FFT of length 2N.  Every FFT length
+ *                must be a power of two between 4 and 1024.  Default: about 2 grid points
+ *                per mean edge length, rounded up to a power of two.
+ *   order_p      Lagrange stencil order, 2..5 ((p+1)^3 points per node); default 3.
+ *   near_boxes   Chebyshev radius in grid cells of the point-pair precorrection; default 3.
+ *   near_elem_factor  radius of the exact element correction in mean edge lengths; 0 keeps
+ *                only elements touching the observer node (default 0).
+ */
+int pmfem_set_aim(pmfem_t h, int Nx, int Ny, int Nz, int order_p, int near_boxes, double near_elem_factor);
+
+/*
+ * Periods L1, L2, L3 [m] along x, y, z (Eq. 1 / Eq. 5): L > 0 makes the axis periodic,
+ * 0 leaves it open; any subset of axes may be periodic.  Runs the whole host set-up in
+ * FP64: PBC pairing and LCA (tolerance 1e-9 min L), the protruding fold of Eq. 18, the
+ * periodized operators, the grid, the PGF spectrum (Eq. 15, Ewald-type sums) and the
+ * precorrection matrices.  EMESH when a node on a touching periodic face has no partner.
+ * May be called again (with new periods) to redo the set-up.
+ */
+int pmfem_set_periodicity(pmfem_t h, double L1, double L2, double L3);
+
+int pmfem_set_precision(pmfem_t h, int mode);                       /* PMFEM_FP64 | FP32 | BF16SPLIT */
+int pmfem_set_applied_field(pmfem_t h, double Hx, double Hy, double Hz);   /* A/m, uniform       */
+
+/* Number of unknowns N' (Sec. 2.2) and the node -> unknown map (host, N int32). */
+int pmfem_num_unknowns(pmfem_t h, int64_t* n_unknowns);
+int pmfem_lca_map(pmfem_t h, int32_t* host_out);
+
+/*
+ * One effective-field evaluation (Eq. 3).
+ *   m      device, N' x 3 T, unit vectors (read only)
+ *   H      device, N' x 3 T, written in A/m (may not alias m)
+ *   components  bitmask of PMFEM_EX | PMFEM_MS | PMFEM_AP
+ * Enqueued on stream; a non-finite m sets a device flag reported as ENONFINITE by the
+ * next pmfem_sync.
+ */
+int pmfem_field(pmfem_t h, const void* m, void* H, int components, void* stream);
+
+/* Same as pmfem_field with host buffers (N' x 3 T each): copies in, evaluates, copies
+ * out and synchronises the stream before returning. */
+int pmfem_field_host(pmfem_t h, const void* m_host, void* H_host, int components, void* stream);
+
+/* Internal magnetisation state (checkpoint / resume), device N' x 3 T; set_m copies in,
+ * get_m copies out.  set_m normalises nothing: pass unit vectors. */
+int pmfem_set_m(pmfem_t h, const void* m, void* stream);
+int pmfem_get_m(pmfem_t h, void* m, void* stream);
+
+/*
+ * nsteps classical RK4 steps of size dt [s] of Eq. 2 on the internal state, each with
+ * four field evaluations and m <- m/|m| at the end of the step (norm taken in FP64).
+ * dt <= 0 or nsteps < 0 -> EINVAL.
+ */
+int pmfem_llg_step(pmfem_t h, double dt, int nsteps, void* stream);
+
+/* Wait for all work of the handle; returns ENONFINITE / ETIMEOUT if a device check fired
+ * since the previous sync (the flag is then cleared). */
+int pmfem_sync(pmfem_t h);
+int pmfem_destroy(pmfem_t h);
+
+/*
+ * Introspection of the host set-up (for tests and tools; host pointers, FP64).
+ *   which: 0 exchange  K'_nk  = -(2A/(mu0 Ms)) K_nk / V_n                       (1 comp)
+ *          1 charges   W'_nk  = Ms (W^q)_nk                                      (3 comp)
+ *          2 near-element E'_nk = Ms E_nk on the adjacency pattern               (3 comp)
+ *          3 gradient  G'_nk  = -(W^q)_kn / (4 pi V_n)                           (3 comp)
+ *          4 point precorrection C_nk                                             (1 comp)
+ *          5 near-element entries outside the adjacency pattern                   (3 comp)
+ *   info gives rows, nnz and components; export fills rowptr (rows+1), col (nnz) and
+ *   vals (nnz x comp, row-major).
+ */
+int pmfem_operator_info(pmfem_t h, int which, int64_t* rows, int64_t* nnz, int* comps);
+int pmfem_operator_export(pmfem_t h, int which, int32_t* rowptr, int32_t* col, double* vals);
+
+/* Grid of Eq. 16 as set up: dims[3], fft[3], origin[3], delta[3] (host). */
+int pmfem_grid_info(pmfem_t h, int32_t* dims, int32_t* fft, double* origin, double* delta);
+/* PGF spectrum (Eq. 15 on the grid, transformed), reduced by symmetry:
+ * (fft[0]/2+1) x (fft[1]/2+1) x (fft[2]/2+1) doubles, x fastest, unscaled. */
+int pmfem_export_spectrum(pmfem_t h, double* out);
+/* Folded unknown positions of Eq. 18 (host, N' x 3 doubles). */
+int pmfem_folded_positions(pmfem_t h, double* out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PMFEM_H */

@@ -1,0 +1,205 @@
+"""ctypes binding of libpmfem (include/pmfem.h): same names, argument marshalling only.
+
+Device buffers may be torch CUDA tensors (their data_ptr() is passed) or raw integer
+addresses; host buffers are NumPy arrays or pinned torch CPU tensors.  Streams may be
+torch.cuda.Stream objects, raw cudaStream_t integers, or None (library stream).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+PMFEM_FP64, PMFEM_FP32, PMFEM_BF16SPLIT = 0, 1, 2
+PMFEM_EX, PMFEM_MS, PMFEM_AP, PMFEM_ALL = 1, 2, 4, 7
+
+_ERRORS = {-1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "EMESH", -5: "ENONFINITE", -6: "ETIMEOUT", -7: "ESTATE"}
+
+_c = ctypes
+_vp, _i32, _i64, _dbl = _c.c_void_p, _c.c_int32, _c.c_int64, _c.c_double
+_pi32, _pi64, _pdbl = _c.POINTER(_c.c_int32), _c.POINTER(_c.c_int64), _c.POINTER(_c.c_double)
+
+# name -> (restype, argtypes); every exported symbol of include/pmfem.h
+SIGNATURES = {
+    "pmfem_version": (_c.c_char_p, []),
+    "pmfem_last_error": (_c.c_char_p, [_vp]),
+    "pmfem_create_mesh": (_c.c_int, [_c.POINTER(_vp), _vp, _i64, _vp, _i64, _dbl, _dbl, _dbl]),
+    "pmfem_set_aim": (_c.c_int, [_vp, _c.c_int, _c.c_int, _c.c_int, _c.c_int, _c.c_int, _dbl]),
+    "pmfem_set_periodicity": (_c.c_int, [_vp, _dbl, _dbl, _dbl]),
+    "pmfem_set_precision": (_c.c_int, [_vp, _c.c_int]),
+    "pmfem_set_applied_field": (_c.c_int, [_vp, _dbl, _dbl, _dbl]),
+    "pmfem_num_unknowns": (_c.c_int, [_vp, _pi64]),
+    "pmfem_lca_map": (_c.c_int, [_vp, _vp]),
+    "pmfem_field": (_c.c_int, [_vp, _vp, _vp, _c.c_int, _vp]),
+    "pmfem_field_host": (_c.c_int, [_vp, _vp, _vp, _c.c_int, _vp]),
+    "pmfem_set_m": (_c.c_int, [_vp, _vp, _vp]),
+    "pmfem_get_m": (_c.c_int, [_vp, _vp, _vp]),
+    "pmfem_llg_step": (_c.c_int, [_vp, _dbl, _c.c_int, _vp]),
+    "pmfem_sync": (_c.c_int, [_vp]),
+    "pmfem_destroy": (_c.c_int, [_vp]),
+    "pmfem_operator_info": (_c.c_int, [_vp, _c.c_int, _pi64, _pi64, _c.POINTER(_c.c_int)]),
+    "pmfem_operator_export": (_c.c_int, [_vp, _c.c_int, _vp, _vp, _vp]),
+    "pmfem_grid_info": (_c.c_int, [_vp, _vp, _vp, _vp, _vp]),
+    "pmfem_export_spectrum": (_c.c_int, [_vp, _vp]),
+    "pmfem_folded_positions": (_c.c_int, [_vp, _vp]),
+}
+SYMBOLS = tuple(SIGNATURES)
+
+_LIB = None
+LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libpmfem.so")
+
+
+def load_library(path: str | None = None):
+    """Load libpmfem.so (raises when it has not been built; there is no fallback)."""
+    global _LIB
+    if _LIB is None:
+        p = path or LIB_PATH
+        if not os.path.exists(p):
+            raise RuntimeError(f"{p} is missing: build it with __graft_entry__.build() "
+                               "(paper_2409_13958_gb300._build.build()); there is no CPU fallback")
+        lib = ctypes.CDLL(p)
+        for name, (res, args) in SIGNATURES.items():
+            f = getattr(lib, name)
+            f.restype = res
+            f.argtypes = args
+        _LIB = lib
+    return _LIB
+
+
+class PmfemError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{_ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+def _addr(x) -> int | None:
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return int(x.data_ptr())
+    if isinstance(x, np.ndarray):
+        if not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("host arrays must be C-contiguous")
+        return int(x.ctypes.data)
+    raise TypeError(f"cannot take the address of {type(x)}")
+
+
+def _stream(s) -> int | None:
+    if s is None:
+        return None
+    if isinstance(s, int):
+        return s
+    return int(s.cuda_stream)
+
+
+class Pmfem:
+    """One periodic unit cell (a pmfem_t handle)."""
+
+    def __init__(self, handle):
+        self._lib = load_library()
+        self.h = handle
+
+    def _ck(self, rc: int):
+        if rc != 0:
+            msg = self._lib.pmfem_last_error(self.h).decode()
+            raise PmfemError(rc, msg)
+
+    # ------------------------------------------------------------------ set-up
+    @classmethod
+    def create_mesh(cls, xyz, tets, Ms: float, A: float, alpha: float) -> "Pmfem":
+        lib = load_library()
+        xyz = np.ascontiguousarray(xyz, dtype=np.float64)
+        tets = np.ascontiguousarray(tets, dtype=np.int32)
+        h = _vp()
+        rc = lib.pmfem_create_mesh(ctypes.byref(h), xyz.ctypes.data, xyz.shape[0], tets.ctypes.data,
+                                   tets.shape[0], Ms, A, alpha)
+        if rc != 0:
+            raise PmfemError(rc, lib.pmfem_last_error(None).decode())
+        return cls(h)
+
+    def set_aim(self, Nx=0, Ny=0, Nz=0, order_p=0, near_boxes=0, near_elem_factor=0.0):
+        self._ck(self._lib.pmfem_set_aim(self.h, Nx, Ny, Nz, order_p, near_boxes, near_elem_factor))
+
+    def set_periodicity(self, L1=0.0, L2=0.0, L3=0.0):
+        self._ck(self._lib.pmfem_set_periodicity(self.h, L1, L2, L3))
+
+    def set_precision(self, mode: int):
+        self._ck(self._lib.pmfem_set_precision(self.h, mode))
+
+    def set_applied_field(self, Hx=0.0, Hy=0.0, Hz=0.0):
+        self._ck(self._lib.pmfem_set_applied_field(self.h, Hx, Hy, Hz))
+
+    def num_unknowns(self) -> int:
+        n = _i64()
+        self._ck(self._lib.pmfem_num_unknowns(self.h, ctypes.byref(n)))
+        return int(n.value)
+
+    def lca_map(self, n_nodes: int) -> np.ndarray:
+        out = np.empty(n_nodes, dtype=np.int32)
+        self._ck(self._lib.pmfem_lca_map(self.h, out.ctypes.data))
+        return out
+
+    # ------------------------------------------------------------------ compute
+    def field(self, m, H, components: int = PMFEM_ALL, stream=None):
+        self._ck(self._lib.pmfem_field(self.h, _addr(m), _addr(H), components, _stream(stream)))
+
+    def field_host(self, m_host, H_host, components: int = PMFEM_ALL, stream=None):
+        self._ck(self._lib.pmfem_field_host(self.h, _addr(m_host), _addr(H_host), components, _stream(stream)))
+
+    def set_m(self, m, stream=None):
+        self._ck(self._lib.pmfem_set_m(self.h, _addr(m), _stream(stream)))
+
+    def get_m(self, m, stream=None):
+        self._ck(self._lib.pmfem_get_m(self.h, _addr(m), _stream(stream)))
+
+    def llg_step(self, dt: float, nsteps: int = 1, stream=None):
+        self._ck(self._lib.pmfem_llg_step(self.h, dt, nsteps, _stream(stream)))
+
+    def sync(self):
+        self._ck(self._lib.pmfem_sync(self.h))
+
+    def destroy(self):
+        if self.h:
+            self._lib.pmfem_destroy(self.h)
+            self.h = None
+
+    # ------------------------------------------------------------------ introspection
+    def operator_export(self, which: int):
+        rows, nnz, comps = _i64(), _i64(), _c.c_int()
+        self._ck(self._lib.pmfem_operator_info(self.h, which, ctypes.byref(rows), ctypes.byref(nnz),
+                                                 ctypes.byref(comps)))
+        rp = np.empty(rows.value + 1, dtype=np.int32)
+        col = np.empty(nnz.value, dtype=np.int32)
+        vals = np.empty((nnz.value, comps.value), dtype=np.float64)
+        self._ck(self._lib.pmfem_operator_export(self.h, which, rp.ctypes.data, col.ctypes.data, vals.ctypes.data))
+        return rp, col, vals
+
+    def grid_info(self):
+        dims = np.zeros(3, np.int32)
+        fft = np.zeros(3, np.int32)
+        origin = np.zeros(3)
+        delta = np.zeros(3)
+        self._ck(self._lib.pmfem_grid_info(self.h, dims.ctypes.data, fft.ctypes.data, origin.ctypes.data,
+                                           delta.ctypes.data))
+        return dims, fft, origin, delta
+
+    def export_spectrum(self) -> np.ndarray:
+        dims, fft, _, _ = self.grid_info()
+        shape = (fft[2] // 2 + 1, fft[1] // 2 + 1, fft[0] // 2 + 1)   # z, y, x (x fastest)
+        out = np.empty(shape, dtype=np.float64)
+        self._ck(self._lib.pmfem_export_spectrum(self.h, out.ctypes.data))
+        return out
+
+    def folded_positions(self) -> np.ndarray:
+        out = np.empty((self.num_unknowns(), 3), dtype=np.float64)
+        self._ck(self._lib.pmfem_folded_positions(self.h, out.ctypes.data))
+        return out
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass

@@ -1,0 +1,467 @@
+// C-ABI of libpmfem (declared in include/pmfem.h).
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/pmfem.h"
+#include "device.hpp"
+#include "internal.hpp"
+
+using namespace pmfem;
+
+struct pmfem_state {
+  Setup s;
+  Error err;
+  int prec = PMFEM_FP64;
+  double hap[3] = {0, 0, 0};
+  // device side
+  bool dev_ready = false;
+  int dev_prec = -1;
+  cudaStream_t stream = nullptr;
+  std::vector<void*> allocs;
+  DevOps<double> d64;
+  DevOps<float> d32;
+  void* m = nullptr;      // internal state N' x 3
+  void* mA = nullptr;     // RK stage buffers
+  void* mB = nullptr;
+  void* acc = nullptr;
+  void* hbuf = nullptr;   // field output for host-buffer calls
+  int* flag = nullptr;
+};
+
+namespace {
+
+thread_local std::string g_create_error;
+const double kGammaE = 1.76085963023e11;   // electron gyromagnetic ratio, rad/(s T)
+
+int fail(pmfem_t h, int code, const std::string& msg) {
+  if (h) h->err = {code, msg};
+  else g_create_error = msg;
+  return code;
+}
+
+#define PMFEM_CK(h, x)                                                                    \
+  do {                                                                                    \
+    cudaError_t e_ = (x);                                                                 \
+    if (e_ != cudaSuccess) return fail(h, ECUDA_, std::string(#x) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+void free_device(pmfem_t h) {
+  for (void* p : h->allocs) cudaFree(p);
+  h->allocs.clear();
+  h->d64 = DevOps<double>();
+  h->d32 = DevOps<float>();
+  h->m = h->mA = h->mB = h->acc = h->hbuf = nullptr;
+  h->flag = nullptr;
+  h->dev_ready = false;
+  h->dev_prec = -1;
+}
+
+int dalloc(pmfem_t h, void** p, size_t bytes) {
+  *p = nullptr;
+  if (bytes == 0) bytes = 16;
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    return fail(h, e == cudaErrorMemoryAllocation ? ENOMEM_ : ECUDA_,
+                std::string("cudaMalloc failed: ") + cudaGetErrorString(e));
+  }
+  h->allocs.push_back(*p);
+  return OK;
+}
+
+template <typename X>
+int upload(pmfem_t h, const X* src, size_t n, const X** out) {
+  void* p;
+  int rc = dalloc(h, &p, n * sizeof(X));
+  if (rc) return rc;
+  if (n) PMFEM_CK(h, cudaMemcpy(p, src, n * sizeof(X), cudaMemcpyHostToDevice));
+  *out = (const X*)p;
+  return OK;
+}
+
+template <typename T>
+int upload_conv(pmfem_t h, const double* src, size_t n, size_t stride, size_t off, double scale, const T** out) {
+  std::vector<T> tmp(n);
+  for (size_t i = 0; i < n; ++i) tmp[i] = (T)(src[i * stride + off] * scale);
+  return upload(h, tmp.data(), n, out);
+}
+
+template <typename T>
+int build_device(pmfem_t h, DevOps<T>& d) {
+  using C2 = typename Vec2<T>::type;
+  const Setup& s = h->s;
+  int rc;
+  d.Np = s.Np;
+  d.nnz = (int64_t)s.col.size();
+  d.nnzC = s.C.nnz();
+  d.nnzX = s.Ex.nnz();
+  d.p = s.p;
+  for (int a = 0; a < 3; ++a) {
+    d.dims[a] = s.dims[a];
+    d.fft[a] = s.fft[a];
+    d.periodic[a] = s.periodic[a];
+  }
+  if ((rc = upload(h, s.rowptr.data(), s.rowptr.size(), &d.rowptr))) return rc;
+  if ((rc = upload(h, s.col.data(), s.col.size(), &d.col))) return rc;
+  for (int c = 0; c < 3; ++c) {
+    if ((rc = upload_conv<T>(h, s.Wq.data(), d.nnz, 3, c, 1.0, &d.wq[c]))) return rc;
+    if ((rc = upload_conv<T>(h, s.Ea.data(), d.nnz, 3, c, 1.0, &d.ea[c]))) return rc;
+    if ((rc = upload_conv<T>(h, s.Gr.data(), d.nnz, 3, c, 1.0, &d.gr[c]))) return rc;
+  }
+  if ((rc = upload_conv<T>(h, s.Kp.data(), d.nnz, 1, 0, 1.0, &d.kp))) return rc;
+  if ((rc = upload(h, s.C.rowptr.data(), s.C.rowptr.size(), &d.rowptrC))) return rc;
+  if ((rc = upload(h, s.C.col.data(), s.C.col.size(), &d.colC))) return rc;
+  if ((rc = upload_conv<T>(h, s.C.vals.data(), s.C.vals.size(), 1, 0, 1.0, &d.valC))) return rc;
+  if ((rc = upload(h, s.Ex.rowptr.data(), s.Ex.rowptr.size(), &d.rowptrX))) return rc;
+  if ((rc = upload(h, s.Ex.col.data(), s.Ex.col.size(), &d.colX))) return rc;
+  if ((rc = upload_conv<T>(h, s.Ex.vals.data(), s.Ex.vals.size(), 1, 0, 1.0, &d.valX))) return rc;
+  if ((rc = upload(h, s.base.data(), s.base.size(), &d.base))) return rc;
+  if ((rc = upload_conv<T>(h, s.frac.data(), s.frac.size(), 1, 0, 1.0, &d.frac))) return rc;
+  const double scale = 1.0 / ((double)s.fft[0] * s.fft[1] * s.fft[2]);
+  if ((rc = upload_conv<T>(h, s.ghat.data(), s.ghat.size(), 1, 0, scale, &d.ghat))) return rc;
+  for (int a = 0; a < 3; ++a) {
+    const int F = s.fft[a];
+    std::vector<C2> tw(F / 2);
+    for (int j = 0; j < F / 2; ++j) {
+      double ang = 2.0 * kPi * j / F;
+      tw[j].x = (T)std::cos(ang);
+      tw[j].y = (T)(-std::sin(ang));
+    }
+    if ((rc = upload(h, tw.data(), tw.size(), &d.tw[a]))) return rc;
+  }
+  void* p;
+  const int64_t ngrid = (int64_t)s.dims[0] * s.dims[1] * s.dims[2];
+  const int64_t ncb = (int64_t)(s.fft[0] / 2 + 1) * s.fft[1] * s.fft[2];
+  if ((rc = dalloc(h, &p, s.Np * sizeof(T)))) return rc;
+  d.q = (T*)p;
+  if ((rc = dalloc(h, &p, s.Np * sizeof(T)))) return rc;
+  d.e = (T*)p;
+  if ((rc = dalloc(h, &p, s.Np * sizeof(T)))) return rc;
+  d.u = (T*)p;
+  if ((rc = dalloc(h, &p, ngrid * sizeof(T)))) return rc;
+  d.grid = (T*)p;
+  if ((rc = dalloc(h, &p, ncb * sizeof(C2)))) return rc;
+  d.cbuf = (C2*)p;
+  const size_t sb = 3 * (size_t)s.Np * sizeof(T);
+  if ((rc = dalloc(h, &h->m, sb))) return rc;
+  if ((rc = dalloc(h, &h->mA, sb))) return rc;
+  if ((rc = dalloc(h, &h->mB, sb))) return rc;
+  if ((rc = dalloc(h, &h->acc, sb))) return rc;
+  if ((rc = dalloc(h, &h->hbuf, sb))) return rc;
+  if ((rc = dalloc(h, &p, sizeof(int)))) return rc;
+  h->flag = (int*)p;
+  d.flag = h->flag;
+  PMFEM_CK(h, cudaMemset(h->flag, 0, sizeof(int)));
+  PMFEM_CK(h, cudaMemset(h->m, 0, sb));
+  return OK;
+}
+
+int ensure_device(pmfem_t h) {
+  if (!h->s.ready) return fail(h, ESTATE_, "call pmfem_set_periodicity before using the GPU");
+  if (h->dev_ready && h->dev_prec == h->prec) return OK;
+  free_device(h);
+  if (!h->stream) PMFEM_CK(h, cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking));
+  int rc = (h->prec == PMFEM_FP64) ? build_device(h, h->d64) : build_device(h, h->d32);
+  if (rc) {
+    free_device(h);
+    return rc;
+  }
+  h->dev_prec = h->prec;
+  h->dev_ready = true;
+  return OK;
+}
+
+template <typename T>
+void enqueue_eval(pmfem_t h, DevOps<T>& d, const T* m, T* H, int comps, const RkArgs& rk, cudaStream_t st) {
+  if (comps & PMFEM_MS) {
+    cudaMemsetAsync(d.grid, 0, sizeof(T) * (size_t)d.dims[0] * d.dims[1] * d.dims[2], st);
+    launch_charges(d, m, st);
+    launch_anterp(d, st);
+    launch_fft_conv(d, st);
+    launch_interp(d, m, st);
+  }
+  launch_field(d, m, H, comps, h->hap[0], h->hap[1], h->hap[2], rk, st);
+}
+
+int check_launch(pmfem_t h) {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(h, ECUDA_, std::string("kernel launch failed: ") + cudaGetErrorString(e));
+  return OK;
+}
+
+template <typename T>
+int run_llg(pmfem_t h, DevOps<T>& d, double dt, int nsteps, cudaStream_t st) {
+  const double gam = kMu0 * kGammaE / (1.0 + h->s.alpha * h->s.alpha);
+  T* m = (T*)h->m;
+  T* A = (T*)h->mA;
+  T* B = (T*)h->mB;
+  for (int n = 0; n < nsteps; ++n) {
+    RkArgs rk;
+    rk.m0 = m;
+    rk.acc = h->acc;
+    rk.gam = gam;
+    rk.alpha = h->s.alpha;
+    rk.mode = 1;
+    rk.cdt = 0.5 * dt, rk.bw = 1.0, rk.acc_init = 1, rk.mnext = A;
+    enqueue_eval(h, d, m, (T*)nullptr, PMFEM_ALL, rk, st);
+    rk.cdt = 0.5 * dt, rk.bw = 2.0, rk.acc_init = 0, rk.mnext = B;
+    enqueue_eval(h, d, (const T*)A, (T*)nullptr, PMFEM_ALL, rk, st);
+    rk.cdt = dt, rk.bw = 2.0, rk.acc_init = 0, rk.mnext = A;
+    enqueue_eval(h, d, (const T*)B, (T*)nullptr, PMFEM_ALL, rk, st);
+    rk.mode = 2;
+    rk.dt6 = dt / 6.0;
+    enqueue_eval(h, d, (const T*)A, (T*)nullptr, PMFEM_ALL, rk, st);
+    int rc = check_launch(h);
+    if (rc) return rc;
+  }
+  return OK;
+}
+
+size_t elem_size(pmfem_t h) { return h->prec == PMFEM_FP64 ? sizeof(double) : sizeof(float); }
+
+}  // namespace
+
+extern "C" {
+
+const char* pmfem_version(void) { return "pmfem 0.1 (sm_103a)"; }
+
+const char* pmfem_last_error(pmfem_t h) {
+  if (!h) return g_create_error.c_str();
+  return h->err.msg.c_str();
+}
+
+int pmfem_create_mesh(pmfem_t* out, const double* xyz, int64_t N, const int32_t* tets, int64_t T, double Ms,
+                      double A, double alpha) {
+  if (!out) return fail(nullptr, EINVAL_, "out is NULL");
+  *out = nullptr;
+  if (!xyz || !tets || N < 4 || T < 1) return fail(nullptr, EINVAL_, "need xyz, tets, N >= 4 and T >= 1");
+  if (!(Ms > 0) || !(A >= 0) || !(alpha >= 0) || !std::isfinite(Ms) || !std::isfinite(A) || !std::isfinite(alpha))
+    return fail(nullptr, EINVAL_, "need Ms > 0, A >= 0, alpha >= 0 (finite)");
+  pmfem_state* h = nullptr;
+  try {
+    h = new pmfem_state();
+    h->s.N = N;
+    h->s.T = T;
+    h->s.xyz.assign(xyz, xyz + 3 * N);
+    h->s.tets.assign(tets, tets + 4 * T);
+    h->s.Ms = Ms;
+    h->s.A = A;
+    h->s.alpha = alpha;
+    Error err;
+    int rc = setup_validate_mesh(h->s, err);
+    if (rc) {
+      delete h;
+      return fail(nullptr, rc, err.msg);
+    }
+  } catch (const std::bad_alloc&) {
+    delete h;
+    return fail(nullptr, ENOMEM_, "host allocation failed");
+  }
+  *out = h;
+  return OK;
+}
+
+int pmfem_set_aim(pmfem_t h, int Nx, int Ny, int Nz, int order_p, int near_boxes, double near_elem_factor) {
+  if (!h) return EINVAL_;
+  int d[3] = {Nx, Ny, Nz};
+  for (int a = 0; a < 3; ++a)
+    if (d[a] < 0 || (d[a] > 0 && d[a] < 4) || d[a] > 1024) return fail(h, EINVAL_, "grid sizes must be 0 or in [4, 1024]");
+  if (order_p != 0 && (order_p < 2 || order_p > 5)) return fail(h, EINVAL_, "order_p must be 0 or in [2, 5]");
+  if (near_boxes < 0 || near_boxes > 8) return fail(h, EINVAL_, "near_boxes must be in [0, 8]");
+  if (!(near_elem_factor >= 0) || !std::isfinite(near_elem_factor) || near_elem_factor > 10)
+    return fail(h, EINVAL_, "near_elem_factor must be in [0, 10]");
+  for (int a = 0; a < 3; ++a) h->s.dims_req[a] = d[a];
+  h->s.p = order_p ? order_p : 3;
+  h->s.near_boxes = near_boxes ? near_boxes : 3;
+  h->s.near_elem_factor = near_elem_factor;
+  h->s.ready = false;
+  free_device(h);
+  return OK;
+}
+
+int pmfem_set_periodicity(pmfem_t h, double L1, double L2, double L3) {
+  if (!h) return EINVAL_;
+  double L[3] = {L1, L2, L3};
+  for (int a = 0; a < 3; ++a)
+    if (!(L[a] >= 0) || !std::isfinite(L[a])) return fail(h, EINVAL_, "periods must be finite and >= 0");
+  for (int a = 0; a < 3; ++a) h->s.L[a] = L[a];
+  free_device(h);
+  try {
+    Error err;
+    int rc = run_setup(h->s, err);
+    if (rc) return fail(h, rc, err.msg);
+  } catch (const std::bad_alloc&) {
+    return fail(h, ENOMEM_, "host allocation failed during set-up");
+  }
+  return OK;
+}
+
+int pmfem_set_precision(pmfem_t h, int mode) {
+  if (!h) return EINVAL_;
+  if (mode != PMFEM_FP64 && mode != PMFEM_FP32) return fail(h, EINVAL_, "precision mode must be PMFEM_FP64 or PMFEM_FP32");
+  h->prec = mode;
+  return OK;
+}
+
+int pmfem_set_applied_field(pmfem_t h, double Hx, double Hy, double Hz) {
+  if (!h) return EINVAL_;
+  if (!std::isfinite(Hx) || !std::isfinite(Hy) || !std::isfinite(Hz)) return fail(h, EINVAL_, "applied field not finite");
+  h->hap[0] = Hx;
+  h->hap[1] = Hy;
+  h->hap[2] = Hz;
+  return OK;
+}
+
+int pmfem_num_unknowns(pmfem_t h, int64_t* n) {
+  if (!h || !n) return EINVAL_;
+  if (!h->s.ready) return fail(h, ESTATE_, "call pmfem_set_periodicity first");
+  *n = h->s.Np;
+  return OK;
+}
+
+int pmfem_lca_map(pmfem_t h, int32_t* out) {
+  if (!h || !out) return EINVAL_;
+  if (!h->s.ready) return fail(h, ESTATE_, "call pmfem_set_periodicity first");
+  std::memcpy(out, h->s.lca.data(), sizeof(int32_t) * h->s.N);
+  return OK;
+}
+
+int pmfem_field(pmfem_t h, const void* m, void* H, int components, void* stream) {
+  if (!h) return EINVAL_;
+  if (!m || !H || m == H) return fail(h, EINVAL_, "m and H must be distinct device pointers");
+  if (components <= 0 || components > PMFEM_ALL) return fail(h, EINVAL_, "components must be a non-empty PMFEM_EX|MS|AP mask");
+  int rc = ensure_device(h);
+  if (rc) return rc;
+  cudaStream_t st = stream ? (cudaStream_t)stream : h->stream;
+  RkArgs none;
+  if (h->dev_prec == PMFEM_FP64) enqueue_eval(h, h->d64, (const double*)m, (double*)H, components, none, st);
+  else enqueue_eval(h, h->d32, (const float*)m, (float*)H, components, none, st);
+  return check_launch(h);
+}
+
+int pmfem_field_host(pmfem_t h, const void* m_host, void* H_host, int components, void* stream) {
+  if (!h) return EINVAL_;
+  if (!m_host || !H_host) return fail(h, EINVAL_, "NULL host buffer");
+  int rc = ensure_device(h);
+  if (rc) return rc;
+  cudaStream_t st = stream ? (cudaStream_t)stream : h->stream;
+  const size_t bytes = 3 * (size_t)h->s.Np * elem_size(h);
+  PMFEM_CK(h, cudaMemcpyAsync(h->mA, m_host, bytes, cudaMemcpyHostToDevice, st));
+  rc = pmfem_field(h, h->mA, h->hbuf, components, st);
+  if (rc) return rc;
+  PMFEM_CK(h, cudaMemcpyAsync(H_host, h->hbuf, bytes, cudaMemcpyDeviceToHost, st));
+  PMFEM_CK(h, cudaStreamSynchronize(st));
+  return OK;
+}
+
+int pmfem_set_m(pmfem_t h, const void* m, void* stream) {
+  if (!h || !m) return EINVAL_;
+  int rc = ensure_device(h);
+  if (rc) return rc;
+  cudaStream_t st = stream ? (cudaStream_t)stream : h->stream;
+  PMFEM_CK(h, cudaMemcpyAsync(h->m, m, 3 * (size_t)h->s.Np * elem_size(h), cudaMemcpyDeviceToDevice, st));
+  return OK;
+}
+
+int pmfem_get_m(pmfem_t h, void* m, void* stream) {
+  if (!h || !m) return EINVAL_;
+  int rc = ensure_device(h);
+  if (rc) return rc;
+  cudaStream_t st = stream ? (cudaStream_t)stream : h->stream;
+  PMFEM_CK(h, cudaMemcpyAsync(m, h->m, 3 * (size_t)h->s.Np * elem_size(h), cudaMemcpyDeviceToDevice, st));
+  return OK;
+}
+
+int pmfem_llg_step(pmfem_t h, double dt, int nsteps, void* stream) {
+  if (!h) return EINVAL_;
+  if (!(dt > 0) || !std::isfinite(dt) || nsteps < 0) return fail(h, EINVAL_, "need dt > 0 and nsteps >= 0");
+  int rc = ensure_device(h);
+  if (rc) return rc;
+  cudaStream_t st = stream ? (cudaStream_t)stream : h->stream;
+  return h->dev_prec == PMFEM_FP64 ? run_llg(h, h->d64, dt, nsteps, st) : run_llg(h, h->d32, dt, nsteps, st);
+}
+
+int pmfem_sync(pmfem_t h) {
+  if (!h) return EINVAL_;
+  if (!h->dev_ready) return OK;
+  PMFEM_CK(h, cudaDeviceSynchronize());
+  int flag = 0;
+  PMFEM_CK(h, cudaMemcpy(&flag, h->flag, sizeof(int), cudaMemcpyDeviceToHost));
+  if (flag) {
+    PMFEM_CK(h, cudaMemset(h->flag, 0, sizeof(int)));
+    return fail(h, ENONFINITE_, (flag & FLAG_NONFINITE_IN) ? "non-finite magnetisation input"
+                                                          : "non-finite field result");
+  }
+  return OK;
+}
+
+int pmfem_destroy(pmfem_t h) {
+  if (!h) return OK;
+  free_device(h);
+  if (h->stream) cudaStreamDestroy(h->stream);
+  delete h;
+  return OK;
+}
+
+int pmfem_operator_info(pmfem_t h, int which, int64_t* rows, int64_t* nnz, int* comps) {
+  if (!h || !rows || !nnz || !comps) return EINVAL_;
+  if (!h->s.ready) return fail(h, ESTATE_, "call pmfem_set_periodicity first");
+  const Setup& s = h->s;
+  *rows = s.Np;
+  switch (which) {
+    case 0: *nnz = (int64_t)s.col.size(); *comps = 1; break;
+    case 1: case 2: case 3: *nnz = (int64_t)s.col.size(); *comps = 3; break;
+    case 4: *nnz = s.C.nnz(); *comps = 1; break;
+    case 5: *nnz = s.Ex.nnz(); *comps = 3; break;
+    default: return fail(h, EINVAL_, "which must be in 0..5");
+  }
+  return OK;
+}
+
+int pmfem_operator_export(pmfem_t h, int which, int32_t* rowptr, int32_t* col, double* vals) {
+  int64_t rows, nnz;
+  int comps;
+  int rc = pmfem_operator_info(h, which, &rows, &nnz, &comps);
+  if (rc) return rc;
+  if (!rowptr || !col || !vals) return fail(h, EINVAL_, "NULL output");
+  const Setup& s = h->s;
+  const std::vector<int32_t>& rp = which == 4 ? s.C.rowptr : which == 5 ? s.Ex.rowptr : s.rowptr;
+  const std::vector<int32_t>& cl = which == 4 ? s.C.col : which == 5 ? s.Ex.col : s.col;
+  const std::vector<double>& v = which == 0 ? s.Kp : which == 1 ? s.Wq : which == 2 ? s.Ea : which == 3 ? s.Gr
+                                 : which == 4 ? s.C.vals : s.Ex.vals;
+  std::memcpy(rowptr, rp.data(), sizeof(int32_t) * rp.size());
+  std::memcpy(col, cl.data(), sizeof(int32_t) * cl.size());
+  std::memcpy(vals, v.data(), sizeof(double) * v.size());
+  return OK;
+}
+
+int pmfem_grid_info(pmfem_t h, int32_t* dims, int32_t* fft, double* origin, double* delta) {
+  if (!h || !dims || !fft || !origin || !delta) return EINVAL_;
+  if (!h->s.ready) return fail(h, ESTATE_, "call pmfem_set_periodicity first");
+  for (int a = 0; a < 3; ++a) {
+    dims[a] = h->s.dims[a];
+    fft[a] = h->s.fft[a];
+    origin[a] = h->s.origin[a];
+    delta[a] = h->s.delta[a];
+  }
+  return OK;
+}
+
+int pmfem_export_spectrum(pmfem_t h, double* out) {
+  if (!h || !out) return EINVAL_;
+  if (!h->s.ready) return fail(h, ESTATE_, "call pmfem_set_periodicity first");
+  std::memcpy(out, h->s.ghat.data(), sizeof(double) * h->s.ghat.size());
+  return OK;
+}
+
+int pmfem_folded_positions(pmfem_t h, double* out) {
+  if (!h || !out) return EINVAL_;
+  if (!h->s.ready) return fail(h, ESTATE_, "call pmfem_set_periodicity first");
+  std::memcpy(out, h->s.pos_f.data(), sizeof(double) * h->s.pos_f.size());
+  return OK;
+}
+
+}  // extern "C"

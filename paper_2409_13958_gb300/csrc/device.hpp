@@ -1,0 +1,74 @@
+// Device-side data of one handle and the kernel launchers (internal to libpmfem).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+
+namespace pmfem {
+
+template <typename T> struct Vec2;
+template <> struct Vec2<double> { using type = double2; };
+template <> struct Vec2<float> { using type = float2; };
+
+// Operator values, grid set-up and work buffers of one precision, all device memory.
+template <typename T>
+struct DevOps {
+  using C2 = typename Vec2<T>::type;
+  int64_t Np = 0, nnz = 0, nnzC = 0, nnzX = 0;
+  int p = 3;
+  int dims[3] = {0, 0, 0}, fft[3] = {0, 0, 0};
+  bool periodic[3] = {false, false, false};
+  // adjacency pattern (shared by charges, near-element, gradient and exchange values)
+  const int32_t* rowptr = nullptr;
+  const int32_t* col = nullptr;
+  const T* wq[3] = {nullptr, nullptr, nullptr};   // Ms W^q
+  const T* ea[3] = {nullptr, nullptr, nullptr};   // Ms E (touching elements)
+  const T* gr[3] = {nullptr, nullptr, nullptr};   // -(W^q)^T / (4 pi V)
+  const T* kp = nullptr;                          // exchange, scaled
+  // point precorrection C and near-element entries outside the pattern
+  const int32_t* rowptrC = nullptr;
+  const int32_t* colC = nullptr;
+  const T* valC = nullptr;
+  const int32_t* rowptrX = nullptr;
+  const int32_t* colX = nullptr;
+  const T* valX = nullptr;                        // nnzX x 3
+  // stencils and spectrum
+  const int32_t* base = nullptr;                  // Np x 3
+  const T* frac = nullptr;                        // Np x 3
+  const T* ghat = nullptr;                        // (F0/2+1)(F1/2+1)(F2/2+1), scaled by 1/(F0 F1 F2)
+  const C2* tw[3] = {nullptr, nullptr, nullptr};  // exp(-2 pi i j / F_a), j < F_a / 2
+  // work buffers
+  T* q = nullptr;
+  T* e = nullptr;
+  T* u = nullptr;
+  T* grid = nullptr;                              // N0 N1 N2 real (Q, then U)
+  C2* cbuf = nullptr;                             // F2 x F1 x (F0/2+1) complex
+  int* flag = nullptr;                            // device error word
+};
+
+// error word bits
+enum : int { FLAG_NONFINITE_IN = 1, FLAG_NONFINITE_OUT = 2 };
+
+// RK4 epilogue of the field kernel (mode 0: plain field output)
+struct RkArgs {
+  int mode = 0;            // 0 none, 1 intermediate stage, 2 final combination + renormalise
+  const void* m0 = nullptr;   // state at the start of the step
+  void* mnext = nullptr;      // stage input for the next evaluation (mode 1)
+  void* acc = nullptr;        // running sum of b_i k_i
+  double cdt = 0;          // m_next = m0 + cdt * k
+  double bw = 0;           // acc (+)= bw * k
+  int acc_init = 0;        // 1: acc = bw k, 0: acc += bw k
+  double dt6 = 0;          // final: m0 + dt6 (acc + k)
+  double gam = 0;          // gamma0 / (1 + alpha^2)
+  double alpha = 0;
+};
+
+template <typename T> void launch_charges(const DevOps<T>& d, const T* m, cudaStream_t st);
+template <typename T> void launch_anterp(const DevOps<T>& d, cudaStream_t st);
+template <typename T> void launch_fft_conv(const DevOps<T>& d, cudaStream_t st);
+template <typename T> void launch_interp(const DevOps<T>& d, const T* m, cudaStream_t st);
+template <typename T>
+void launch_field(const DevOps<T>& d, const T* m, T* H, int comps, double hx, double hy, double hz,
+                  const RkArgs& rk, cudaStream_t st);
+
+}  // namespace pmfem

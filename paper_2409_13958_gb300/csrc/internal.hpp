@@ -1,0 +1,125 @@
+// Internal declarations of libpmfem: host set-up state and helpers.
+// Not part of the public ABI (see include/pmfem.h).
+#pragma once
+
+#include <array>
+#include <cstdint>
+#include <functional>
+#include <string>
+#include <vector>
+
+namespace pmfem {
+
+constexpr double kPi = 3.14159265358979323846;
+constexpr double kMu0 = 4e-7 * kPi;
+
+// status codes (mirror of pmfem.h)
+enum Status : int { OK = 0, EINVAL_ = -1, ENOMEM_ = -2, ECUDA_ = -3, EMESH_ = -4,
+                    ENONFINITE_ = -5, ETIMEOUT_ = -6, ESTATE_ = -7 };
+
+struct Error {
+  int code = 0;
+  std::string msg;
+};
+
+// Compressed sparse rows with `comps` values per entry (row-major per entry).
+struct Csr {
+  int64_t rows = 0;
+  int comps = 1;
+  std::vector<int32_t> rowptr;  // rows + 1
+  std::vector<int32_t> col;
+  std::vector<double> vals;     // nnz * comps
+  int64_t nnz() const { return (int64_t)col.size(); }
+};
+
+struct Setup {
+  // ---- mesh and material
+  int64_t N = 0, T = 0;
+  std::vector<double> xyz;      // N x 3
+  std::vector<int32_t> tets;    // T x 4, positively oriented
+  double Ms = 0, A = 0, alpha = 0;
+  // ---- AIM settings (0 = default)
+  int dims_req[3] = {0, 0, 0};
+  int p = 3;
+  int near_boxes = 3;
+  double near_elem_factor = 0.0;
+  // ---- periodicity
+  double L[3] = {0, 0, 0};
+  bool periodic[3] = {false, false, false};
+  // ---- pairing (Sec. 2.2)
+  int64_t Np = 0;
+  std::vector<int32_t> lca;     // N: node -> unknown
+  std::vector<int32_t> roots;   // Np: unknown -> node
+  std::vector<double> pos_f;    // Np x 3 folded positions (Eq. 18)
+  double r0[3] = {0, 0, 0};
+  // ---- local operators on the adjacency pattern (Eqs. 8-12, 14a, 14d)
+  std::vector<int32_t> rowptr, col;  // adjacency of unknowns (shared pattern)
+  std::vector<double> V;             // lumped nodal volumes
+  std::vector<double> Kp;            // nnz    exchange, scaled
+  std::vector<double> Wq;            // nnz*3  charges, scaled by Ms
+  std::vector<double> Ea;            // nnz*3  near-element correction, scaled by Ms
+  std::vector<double> Gr;            // nnz*3  gradient, scaled by -1/(4 pi V_n)
+  Csr C;                             // point precorrection (step 4)
+  Csr Ex;                            // near-element entries outside the adjacency pattern
+  // ---- boundary and sizes
+  std::vector<int32_t> bfaces;       // F x 3 original node indices, outward orientation
+  double mean_edge = 0;
+  // ---- grid (Eq. 16)
+  int dims[3] = {0, 0, 0};
+  int fft[3] = {0, 0, 0};
+  double origin[3] = {0, 0, 0};
+  double delta[3] = {0, 0, 0};
+  std::vector<int32_t> base;         // Np x 3 unwrapped stencil start
+  std::vector<double> frac;          // Np x 3 local coordinate s = t - base
+  std::vector<double> ghat;          // (F0/2+1)(F1/2+1)(F2/2+1), x fastest, unscaled
+  bool ready = false;
+};
+
+// set-up stages (host, FP64); each returns a Status and fills err on failure
+int setup_validate_mesh(Setup& s, Error& err);
+int setup_pairing(Setup& s, Error& err);
+int setup_operators(Setup& s, Error& err);
+int setup_grid(Setup& s, Error& err);
+int setup_spectrum(Setup& s, Error& err);
+int setup_precorrection(Setup& s, Error& err);
+int setup_near_elements(Setup& s, Error& err);
+int run_setup(Setup& s, Error& err);
+
+// periodic Green's function of Eq. 15 (k0 = 0), Ewald-type evaluation
+class PeriodicGreen {
+ public:
+  PeriodicGreen(const double L[3], double eta_scale = 1.0);
+  double operator()(double x, double y, double z) const;  // r not on the lattice
+  double reg0() const { return reg0_; }                     // lim (G^p - 1/r)
+  int dim() const { return dim_; }
+ private:
+  double g3(double x, double y, double z) const;
+  double g2(double x, double y, double z) const;
+  double g1(double x, double y, double z) const;
+  double real_space(double x, double y, double z, bool skip_origin) const;
+  void min_image(double& x, double& y, double& z) const;
+  int dim_ = 0;
+  int ax_[3] = {0, 1, 2};          // periodic axes first, then the open ones
+  double L_[3] = {0, 0, 0};
+  bool per_[3] = {false, false, false};
+  double eta_ = 0;
+  int nimg_[3] = {0, 0, 0};
+  std::vector<std::array<double, 4>> kvec_;   // (kx, ky, kz, coefficient)
+  std::vector<double> gl_u_, gl_w_;           // Gauss-Legendre on [0, 1]
+  double reg0_ = 0;
+};
+
+// exact potential integrals (Sec. 3.2 near correction)
+// int_tri phi_j / |r - r'| dS' for the three hat functions of triangle (a, b, c)
+void tri_hat_potentials(const double r[3], const double a[3], const double b[3], const double c[3],
+                        double out[3]);
+// int_tet dV' / |r - r'|
+double tet_potential(const double r[3], const double X[4][3]);
+
+// small thread pool helper: f(begin, end) over [0, n) split in chunks
+void parallel_for(int64_t n, const std::function<void(int64_t, int64_t)>& f, int64_t min_chunk = 256);
+
+// tetrahedron volume and barycentric gradients
+double tet_grads(const double X[4][3], double g[4][3]);
+
+}  // namespace pmfem

@@ -1,0 +1,174 @@
+"""GPU parity: the CUDA path through the C-ABI against the FP64 CPU oracle (O2).
+
+Tolerances (relative L2 over all N' x 3 components): FP64 <= 1e-10, FP32 <= 1e-5.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import meshgen
+from oracle.llg import rk4_step
+from oracle.problem import OracleProblem
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = {0: 1e-10, 1: 1e-5}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+def _shifted_prism():
+    p = meshgen.prism_cell(5, 5, 8, jitter=0.15, seed=5)
+    xyz = p.xyz.copy()
+    xyz[:, 2] += 0.37 * p.periods[2] + 0.2 * xyz[:, 0]        # protruding 1D cell
+    return meshgen.Mesh(xyz, p.tets, p.periods)
+
+
+CASES = {
+    # name: (mesh factory, grid, p, near_boxes, near_elem_factor)
+    "film_20x20x2": (lambda: meshgen.film_cell(20, 20, 2), (32, 32, 8), 3, 3, 0.0),
+    "cube_3d": (lambda: meshgen.cube_cell(6, jitter=0.2, seed=4), (16, 16, 16), 3, 2, 0.0),
+    "prism_1d_protruding": (_shifted_prism, (16, 16, 32), 3, 3, 0.0),
+    "sphere_3d_nt": (lambda: meshgen.sphere_lattice(target_nodes=2500, seed=7), (16, 16, 16), 3, 2, 0.0),
+    "free_space": (lambda: meshgen.Mesh(*meshgen.kuhn_box(6, 5, 4, 1e-9, jitter=0.2, seed=6), (0.0, 0.0, 0.0)),
+                   (16, 16, 16), 3, 2, 0.0),
+    "film_p2_near_radius": (lambda: meshgen.film_cell(9, 7, 3, seed=8), (16, 16, 16), 2, 2, 1.0),
+    "film_p5": (lambda: meshgen.film_cell(9, 7, 3, seed=9), (16, 16, 16), 5, 2, 0.0),
+}
+
+_cache = {}
+
+
+def _problem(name):
+    if name not in _cache:
+        mk, grid, p, nb, f = CASES[name]
+        mesh = mk()
+        ob = OracleProblem(mesh.xyz, mesh.tets, mesh.periods, Ms=8e5, A=1.3e-11, alpha=0.02,
+                           H_ap=(2e3, -1e3, 5e2), grid=grid, p=p, near_boxes=nb, near_elem_factor=f)
+        _cache[name] = (mesh, ob, grid, p, nb, f)
+    return _cache[name]
+
+
+def _lib(mesh, grid, p, nb, f, prec):
+    from paper_2409_13958_gb300 import Pmfem
+    h = Pmfem.create_mesh(mesh.xyz, mesh.tets, 8e5, 1.3e-11, 0.02)
+    h.set_aim(*grid, p, nb, f)
+    h.set_periodicity(*mesh.periods)
+    h.set_precision(prec)
+    h.set_applied_field(2e3, -1e3, 5e2)
+    return h
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_field_parity(name, prec):
+    from paper_2409_13958_gb300 import PMFEM_EX, PMFEM_MS, PMFEM_AP, PMFEM_ALL
+    mesh, ob, grid, p, nb, f = _problem(name)
+    h = _lib(mesh, grid, p, nb, f, prec)
+    dt = torch.float64 if prec == 0 else torch.float32
+    m = meshgen.m_random(ob.Np, seed=11)
+    mt = torch.tensor(m, dtype=dt, device="cuda")
+    H = torch.empty_like(mt)
+    for comps, ref in ((PMFEM_MS, ob.h_ms(m, "paim")), (PMFEM_EX, ob.h_ex(m)),
+                       (PMFEM_ALL, ob.h_eff(m, "paim"))):
+        H.fill_(float("nan"))
+        h.field(mt, H, comps)
+        h.sync()
+        err = _rel(H.double().cpu().numpy(), ref)
+        assert err <= TOL[prec], (name, prec, comps, err)
+    H.fill_(0)
+    h.field(mt, H, PMFEM_AP)
+    h.sync()
+    assert np.allclose(H.double().cpu().numpy(), np.array([2e3, -1e3, 5e2])[None, :], rtol=1e-7)
+    h.destroy()
+
+
+def test_field_host_buffers_match_device():
+    mesh, ob, grid, p, nb, f = _problem("film_20x20x2")
+    h = _lib(mesh, grid, p, nb, f, 0)
+    m = np.ascontiguousarray(meshgen.m_tilted(ob.Np, 5.0, seed=1))
+    Hh = np.empty_like(m)
+    h.field_host(m, Hh)
+    mt = torch.tensor(m, device="cuda")
+    H = torch.empty_like(mt)
+    h.field(mt, H)
+    h.sync()
+    assert _rel(Hh, H.cpu().numpy()) < 1e-13
+    assert _rel(Hh, ob.h_eff(m, "paim")) < 1e-10
+    h.destroy()
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_rk4_trajectory(prec):
+    mesh, ob, grid, p, nb, f = _problem("cube_3d")
+    h = _lib(mesh, grid, p, nb, f, prec)
+    m0 = meshgen.m_random(ob.Np, seed=3)
+    dt = 5e-15
+    nsteps = 10
+    dtype = torch.float64 if prec == 0 else torch.float32
+    h.set_m(torch.tensor(m0, dtype=dtype, device="cuda"))
+    h.llg_step(dt, nsteps)
+    out = torch.empty((ob.Np, 3), dtype=dtype, device="cuda")
+    h.get_m(out)
+    h.sync()
+    m = m0.copy()
+    for _ in range(nsteps):
+        m = rk4_step(m, dt, lambda x: ob.h_eff(x, "paim"), ob.alpha)
+    got = out.double().cpu().numpy()
+    assert _rel(got, m) < (1e-10 if prec == 0 else 1e-5)
+    assert np.abs(np.linalg.norm(got, axis=1) - 1).max() < (1e-14 if prec == 0 else 1e-6)
+    assert _rel(got, m0) > 1e-4        # the state moved
+    h.destroy()
+
+
+def test_checkpoint_resume():
+    mesh, ob, grid, p, nb, f = _problem("cube_3d")
+    h = _lib(mesh, grid, p, nb, f, 0)
+    m0 = torch.tensor(meshgen.m_random(ob.Np, seed=4), device="cuda")
+    h.set_m(m0)
+    h.llg_step(5e-15, 4)
+    full = torch.empty_like(m0)
+    h.get_m(full)
+    h.set_m(m0)
+    h.llg_step(5e-15, 2)
+    mid = torch.empty_like(m0)
+    h.get_m(mid)
+    h.sync()
+    g = _lib(mesh, grid, p, nb, f, 0)          # a fresh handle resumes from the checkpoint
+    g.set_m(mid)
+    g.llg_step(5e-15, 2)
+    res = torch.empty_like(m0)
+    g.get_m(res)
+    g.sync()
+    assert _rel(res.cpu().numpy(), full.cpu().numpy()) < 1e-13
+    h.destroy()
+    g.destroy()
+
+
+def test_nonfinite_input_is_reported():
+    from paper_2409_13958_gb300 import PmfemError
+    mesh, ob, grid, p, nb, f = _problem("cube_3d")
+    h = _lib(mesh, grid, p, nb, f, 0)
+    m = torch.tensor(meshgen.m_random(ob.Np, seed=5), device="cuda")
+    m[7, 1] = float("nan")
+    H = torch.empty_like(m)
+    h.field(m, H)
+    with pytest.raises(PmfemError) as e:
+        h.sync()
+    assert e.value.code == -5
+    m[7, 1] = 0.0
+    h.field(m, H)
+    h.sync()                                   # the flag was cleared
+    h.destroy()

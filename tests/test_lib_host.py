@@ -1,0 +1,182 @@
+"""CPU tests of libpmfem: exported symbols, error conventions, and the host set-up
+(pairing, fold, operators, grid, spectrum, precorrection) against the oracle.
+
+No test here launches a kernel: set-up runs on the host and the device is only touched
+by calls that need it.
+"""
+import math
+import os
+import re
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+import meshgen
+from oracle.problem import OracleProblem
+
+pmf = pytest.importorskip("paper_2409_13958_gb300")
+from paper_2409_13958_gb300 import binding as B  # noqa: E402
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_2409_13958_gb300 import _build
+    _build.build()
+    B.load_library()
+
+
+def test_every_declared_symbol_is_exported():
+    hdr = open(os.path.join(ROOT, "include", "pmfem.h")).read()
+    declared = set(re.findall(r"\b(pmfem_[a-z0-9_]+)\s*\(", hdr))
+    assert declared == set(B.SYMBOLS)
+    lib = B.load_library()
+    for name in declared:
+        assert hasattr(lib, name)
+    assert b"sm_103a" in lib.pmfem_version()
+
+
+def _mk(mesh, periods=None, grid=(0, 0, 0), p=3, nb=3, f=0.0, Ms=8e5, A=1.3e-11):
+    h = B.Pmfem.create_mesh(mesh.xyz, mesh.tets, Ms, A, 0.02)
+    h.set_aim(*grid, p, nb, f)
+    h.set_periodicity(*(mesh.periods if periods is None else periods))
+    return h
+
+
+def test_error_conventions():
+    m = meshgen.film_cell(4, 4, 2)
+    bad = m.tets.copy()
+    bad[0, 0] = m.n_nodes + 5
+    with pytest.raises(B.PmfemError) as e:
+        B.Pmfem.create_mesh(m.xyz, bad, 8e5, 1e-11, 0.02)
+    assert e.value.code == -4
+    deg = m.tets.copy()
+    deg[0, 1] = deg[0, 0]
+    with pytest.raises(B.PmfemError) as e:
+        B.Pmfem.create_mesh(m.xyz, deg, 8e5, 1e-11, 0.02)
+    assert e.value.code == -4
+    with pytest.raises(B.PmfemError) as e:
+        B.Pmfem.create_mesh(m.xyz, m.tets, -1.0, 1e-11, 0.02)
+    assert e.value.code == -1
+    h = B.Pmfem.create_mesh(m.xyz, m.tets, 8e5, 1e-11, 0.02)
+    with pytest.raises(B.PmfemError) as e:
+        h.num_unknowns()
+    assert e.value.code == -7
+    with pytest.raises(B.PmfemError) as e:
+        h.field(1 << 20, 2 << 20)            # before set-up: refused without touching memory
+    assert e.value.code == -7
+    with pytest.raises(B.PmfemError) as e:
+        h.set_aim(3, 8, 8, 3, 3, 0.0)
+    assert e.value.code == -1
+    with pytest.raises(B.PmfemError) as e:
+        h.set_periodicity(-1.0, 0, 0)
+    assert e.value.code == -1
+    h.set_aim(8, 8, 8, 3, 2, 0.0)
+    h.set_periodicity(*m.periods)
+    with pytest.raises(B.PmfemError) as e:
+        h.llg_step(-1e-13, 1)
+    assert e.value.code == -1
+    with pytest.raises(B.PmfemError) as e:
+        h.field(1 << 20, 1 << 20)            # aliasing m and H
+    assert e.value.code == -1
+    with pytest.raises(B.PmfemError) as e:
+        h.set_precision(7)
+    assert e.value.code == -1
+    # a node on a touching face without its partner
+    xyz = m.xyz.copy()
+    moved = np.nonzero(np.isclose(xyz[:, 0], m.periods[0]) & (xyz[:, 1] > 1e-9) & (xyz[:, 1] < 3e-9))[0][0]
+    xyz[moved, 1] += 0.3e-9
+    h2 = B.Pmfem.create_mesh(xyz, m.tets, 8e5, 1e-11, 0.02)
+    with pytest.raises(B.PmfemError) as e:
+        h2.set_periodicity(*m.periods)
+    assert e.value.code == -4
+
+
+def _csr(rp, col, vals, n):
+    return sp.csr_matrix((vals, col, rp), shape=(n, n))
+
+
+def _close(a, b, rtol):
+    d = abs(a - b).max() if (a - b).nnz else 0.0
+    scale = max(abs(b).max(), 1e-300)
+    return d <= rtol * scale, d / scale
+
+
+CASES = {
+    "film": (lambda: meshgen.film_cell(10, 10, 2), None, (16, 16, 8), 3, 3, 0.0),
+    "film_p2_f1": (lambda: meshgen.film_cell(8, 8, 2, seed=3), None, (16, 16, 8), 2, 2, 1.0),
+    "cube": (lambda: meshgen.cube_cell(5, jitter=0.2, seed=4), None, (16, 16, 16), 3, 2, 0.0),
+    "prism_shifted": (lambda: _shifted_prism(), None, (16, 16, 16), 3, 3, 0.0),
+    "free": (lambda: meshgen.Mesh(*meshgen.kuhn_box(4, 3, 3, 1e-9, jitter=0.2, seed=6), (0.0, 0.0, 0.0)),
+             None, (16, 16, 16), 3, 2, 0.5),
+}
+
+
+def _shifted_prism():
+    p = meshgen.prism_cell(4, 4, 6, jitter=0.15, seed=5)
+    xyz = p.xyz.copy()
+    xyz[:, 2] += 0.37 * p.periods[2]
+    xyz[:, 2] += 0.2 * xyz[:, 0]                # shear: the cell protrudes past its period
+    return meshgen.Mesh(xyz, p.tets, p.periods)
+
+
+@pytest.mark.parametrize("case", sorted(CASES))
+def test_host_setup_matches_oracle(case):
+    mk, per, grid, p, nb, f = CASES[case]
+    mesh = mk()
+    Ms, A = 8e5, 1.3e-11
+    h = _mk(mesh, per, grid, p, nb, f, Ms, A)
+    ob = OracleProblem(mesh.xyz, mesh.tets, mesh.periods, Ms=Ms, A=A, grid=grid, p=p, near_boxes=nb,
+                       near_elem_factor=f)
+    n = ob.Np
+    assert h.num_unknowns() == n
+    assert np.array_equal(h.lca_map(mesh.n_nodes), ob.lca)
+    assert np.array_equal(h.folded_positions(), ob.pos_f)
+    # exchange
+    rp, col, v = h.operator_export(0)
+    Kref = sp.csr_matrix(-(2 * A / (4e-7 * math.pi * Ms)) * sp.diags(1 / ob.V) @ ob.K)
+    ok, err = _close(_csr(rp, col, v[:, 0], n), Kref, 1e-12)
+    assert ok, err
+    # charges, gradient, near elements
+    rp, col, W = h.operator_export(1)
+    _, _, G = h.operator_export(3)
+    _, _, Ea = h.operator_export(2)
+    rpx, colx, Ex = h.operator_export(5)
+    for d in range(3):
+        ok, err = _close(_csr(rp, col, W[:, d], n), Ms * ob.Wq[d], 1e-12)
+        assert ok, ("Wq", d, err)
+        Gref = sp.csr_matrix(-(sp.diags(1 / (4 * math.pi * ob.V)) @ ob.Wq[d].T))
+        ok, err = _close(_csr(rp, col, G[:, d], n), Gref, 1e-12)
+        assert ok, ("grad", d, err)
+        Elib = _csr(rp, col, Ea[:, d], n) + _csr(rpx, colx, Ex[:, d], n)
+        ok, err = _close(Elib, Ms * ob.E[d], 1e-11)
+        assert ok, ("E", d, err)
+    if f == 0.0:
+        assert colx.size == 0              # touching elements stay on the adjacency pattern
+    # grid and spectrum
+    dims, fft, origin, delta = h.grid_info()
+    assert tuple(dims) == ob.grid.dims and tuple(fft) == tuple(ob.grid.fft)
+    assert np.array_equal(origin, ob.grid.origin) and np.array_equal(delta, ob.grid.delta)
+    spec = h.export_spectrum()                                   # (z, y, x) reduced, unscaled
+    ref = np.fft.fftn(ob.Ktab)[: fft[0] // 2 + 1, : fft[1] // 2 + 1, : fft[2] // 2 + 1]
+    assert np.abs(ref.imag).max() < 1e-10 * np.abs(ref.real).max()
+    assert np.abs(spec.transpose(2, 1, 0) - ref.real).max() < 1e-11 * np.abs(ref.real).max()
+    # point precorrection
+    rp, col, v = h.operator_export(4)
+    ok, err = _close(_csr(rp, col, v[:, 0], n), ob.C, 1e-11)
+    assert ok, ("C", err)
+
+
+def test_set_aim_defaults_and_validation():
+    m = meshgen.film_cell(10, 10, 2)
+    h = B.Pmfem.create_mesh(m.xyz, m.tets, 8e5, 1.3e-11, 0.02)
+    h.set_periodicity(*m.periods)
+    dims, fft, origin, delta = h.grid_info()
+    for a in range(3):
+        assert fft[a] & (fft[a] - 1) == 0 and 4 <= fft[a] <= 1024
+    h.set_aim(12, 16, 8, 3, 3, 0.0)             # 12 is not a power of two on a periodic axis
+    with pytest.raises(B.PmfemError) as e:
+        h.set_periodicity(*m.periods)
+    assert e.value.code == -1
