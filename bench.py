@@ -1,0 +1,464 @@
+#!/usr/bin/env python
+"""Benchmark: node-field-evaluations per second of the periodic FEM effective field.
+
+Workload (one RK4 LLG step = four field evaluations + stage updates + renormalisation):
+a 1D-periodic (z, period 100 nm) wire of radius 20 nm with seeded bumps and a shear so
+the cell protrudes past its period, ~1M nodes, graded 1:3, AIM grid 128 x 128 x 256
+(FFT 256^3), p = 3, near_boxes = 3, vortex initial magnetisation, permalloy-like
+material.  Synthetic and seeded; operator data is several GB, far larger than L2, so
+every step streams it from HBM.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
+Under torchrun each rank runs an independent replica ("replicas only": one mesh does not
+shard); value = all ranks' node-field-evaluations / max-over-ranks time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "node-field-evals/s at 1M nodes vs plain FP64 GPU; HBM roofline %; rel-L2 vs FP64"
+UNIT = "node-field-evals/s"
+GAMMA0 = 4e-7 * math.pi * 1.76085963023e11
+MS, AEX, ALPHA = 8e5, 1.3e-11, 0.02
+WIRE = dict(L=100e-9, R=20e-9, seed=0)
+GRID = (128, 128, 256)
+P_ORDER, NEAR_BOXES, NEAR_ELEM = 3, 3, 0.0
+KERNELS = ("charges", "projection", "fft_x_fwd", "fft_y_fwd", "fft_z_conv", "fft_y_inv", "fft_x_inv",
+           "interp_precorr", "gradient_exchange", "grid_clear")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--nodes", type=int, default=1_000_000)
+    ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison leg")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the cpu_baseline leg")
+    ap.add_argument("--out", default=None, help="also write the JSON line to this file")
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------ distributed plumbing
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class Dist:
+    def __init__(self, world, local):
+        import torch
+        self.world = world
+        self.torch = torch
+        self.pg = None
+        if world > 1:
+            import torch.distributed as td
+            td.init_process_group("nccl", device_id=torch.device("cuda", local))
+            self.td = td
+            self.pg = True
+
+    def barrier(self):
+        if self.pg:
+            self.td.barrier()
+
+    def max(self, x: float) -> float:
+        if not self.pg:
+            return x
+        t = self.torch.tensor([x], dtype=self.torch.float64, device="cuda")
+        self.td.all_reduce(t, op=self.td.ReduceOp.MAX)
+        return float(t.item())
+
+    def close(self):
+        if self.pg:
+            self.td.destroy_process_group()
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.path = tempfile.mktemp(prefix="pmfem_clocks_", suffix=".csv")
+        self.idx = gpu_index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, power, reasons = [], [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+                power.append(float(parts[3]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        os.unlink(self.path)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "power_w_max": max(power) if power else None, "reasons": sorted(reasons)}
+
+
+# ------------------------------------------------------------------ workload
+def make_mesh(nodes: int):
+    import meshgen
+    return meshgen.wire_cell(L=WIRE["L"], R=WIRE["R"], target_nodes=nodes, seed=WIRE["seed"])
+
+
+def scaled_grid(nodes: int):
+    """Grid for a smaller sample of the wire with the same node-per-cell density."""
+    f = (nodes / 1_000_000) ** (1.0 / 3.0)
+    g = []
+    for n in GRID:
+        k = max(8, int(round(n * f)))
+        g.append(1 << int(round(math.log2(k))))
+    return tuple(g)
+
+
+def initial_m(pos):
+    import meshgen
+    return meshgen.m_vortex(pos, core=5e-9, centre=(0.0, 0.0))
+
+
+def stable_dt(K_rowabs_max: float) -> float:
+    lam = GAMMA0 * (K_rowabs_max + MS)     # Gershgorin bound of the exchange operator + demag scale
+    return min(1e-13, 2.5 / lam)
+
+
+def alg_bytes(name: str, s: int, sz: dict) -> float:
+    """Algorithmic bytes of one launch: every operand read once, every result written once."""
+    Np, nnz, nC, nX = sz["Np"], sz["nnz"], sz["nnzC"], sz["nnzX"]
+    N0, N1, N2 = sz["dims"]
+    F0, F1, F2 = sz["fft"]
+    Hx, H1, H2 = F0 // 2 + 1, F1 // 2 + 1, F2 // 2 + 1
+    G = N0 * N1 * N2
+    idx = 4 * (Np + 1) + 4 * nnz
+    if name == "charges":
+        return idx + 6 * s * nnz + 3 * s * Np + 2 * s * Np
+    if name == "projection":
+        return 12 * Np + 3 * s * Np + s * Np + 2 * s * G
+    if name == "fft_x_fwd":
+        return s * G + 2 * s * Hx * N1 * N2
+    if name == "fft_y_fwd":
+        return 2 * s * Hx * N1 * N2 + 2 * s * Hx * F1 * N2
+    if name == "fft_z_conv":
+        return 2 * 2 * s * Hx * F1 * N2 + s * Hx * H1 * H2
+    if name == "fft_y_inv":
+        return 2 * s * Hx * F1 * N2 + 2 * s * Hx * N1 * N2
+    if name == "fft_x_inv":
+        return 2 * s * Hx * N1 * N2 + s * G
+    if name == "interp_precorr":
+        return (12 + 3 * s) * Np + s * G + 4 * (Np + 1) + (4 + s) * nC + 4 * (Np + 1) + (4 + 3 * s) * nX \
+            + 3 * s * Np * (nX > 0) + 3 * s * Np
+    if name == "gradient_exchange":
+        # RK stage epilogue averaged over the four stages: m_s, m0 read; m_next / m0 written; acc
+        return idx + 4 * s * nnz + s * Np + 3 * s * Np + 3 * s * Np + 3 * s * Np + 4.5 * s * Np
+    if name == "grid_clear":
+        return s * G
+    raise KeyError(name)
+
+
+def src_hash() -> str:
+    h = hashlib.sha1()
+    d = os.path.join(ROOT, "paper_2409_13958_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        if f.endswith((".cu", ".cpp", ".hpp")):
+            h.update(open(os.path.join(d, f), "rb").read())
+    return h.hexdigest()[:12]
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def ncu_traffic(kernel: str):
+    """DRAM bytes per launch from a committed ncu capture, if taken on the current sources."""
+    p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p))
+    if d.get("src_hash") != src_hash():
+        return None
+    e = d.get("kernels", {}).get(kernel)
+    return None if e is None else float(e["bytes_per_launch_full"])
+
+
+# ------------------------------------------------------------------ CPU oracle leg
+def oracle_sample(nodes: int):
+    from oracle.problem import OracleProblem
+    mesh = make_mesh(nodes)
+    grid = scaled_grid(nodes)
+    ob = OracleProblem(mesh.xyz, mesh.tets, mesh.periods, Ms=MS, A=AEX, alpha=ALPHA, grid=grid, p=P_ORDER,
+                       near_boxes=NEAR_BOXES, near_elem_factor=NEAR_ELEM)
+    return ob, grid
+
+
+def time_oracle(ob, budget_s: float, steps: int | None = None, warmup: int = 0):
+    """Time oracle RK4 steps (4 O2 field evaluations each) on the host."""
+    from oracle.llg import rk4_step
+    m = initial_m(ob.pos_f)
+    dt = 1e-14
+    field = lambda x: ob.h_eff(x, "paim")
+    for _ in range(warmup):
+        m = rk4_step(m, dt, field, ob.alpha)
+    n = 0
+    t0 = time.perf_counter()
+    while True:
+        m = rk4_step(m, dt, field, ob.alpha)
+        n += 1
+        el = time.perf_counter() - t0
+        if (steps is not None and n >= steps) or (steps is None and el >= budget_s):
+            break
+    return n, el
+
+
+def cpu_cores_used() -> int:
+    try:
+        import threadpoolctl
+        info = threadpoolctl.threadpool_info()
+        return max([i.get("num_threads", 1) for i in info] + [1])
+    except Exception:
+        return 1
+
+
+def run_reference(args):
+    rank, world, local = dist_env()
+    if rank != 0:
+        return 0
+    sample_nodes = 6000
+    t0 = time.time()
+    ob, grid = oracle_sample(sample_nodes)
+    setup_s = time.time() - t0
+    n, el = time_oracle(ob, 0, steps=args.steps, warmup=args.warmup)
+    value = ob.Np * 4 * n / el
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / n, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "wire-1d-periodic-protruding", "sample_nodes": int(ob.Np), "grid": list(grid),
+                   "p": P_ORDER, "near_boxes": NEAR_BOXES, "oracle_setup_s": round(setup_s, 1)},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cpu_cores_used(), "kind": "oracle",
+                         "sample": f"oracle O2 (NumPy/SciPy FP64) RK4 steps on a {ob.Np}-unknown wire of the same "
+                                   f"geometry, grid {grid}; set-up excluded"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    if args.out:
+        open(args.out, "w").write(json.dumps(line) + "\n")
+    return 0
+
+
+# ------------------------------------------------------------------ GPU leg
+def run_native(args):
+    import torch
+    from paper_2409_13958_gb300 import Pmfem, PMFEM_FP32, PMFEM_FP64, PMFEM_ALL
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = Dist(world, local)
+    import __graft_entry__
+    if rank == 0:
+        __graft_entry__.build()
+    dist.barrier()
+    __graft_entry__.build()
+
+    t0 = time.time()
+    mesh = make_mesh(args.nodes)
+    t_mesh = time.time() - t0
+    t0 = time.time()
+    h = Pmfem.create_mesh(mesh.xyz, mesh.tets, MS, AEX, ALPHA)
+    h.set_aim(*GRID, P_ORDER, NEAR_BOXES, NEAR_ELEM)
+    h.set_periodicity(0.0, 0.0, WIRE["L"])
+    t_setup = time.time() - t0
+    Np = h.num_unknowns()
+    pos = h.folded_positions()
+    m0 = initial_m(pos)
+    sizes = {"Np": Np}
+    for w, key in ((0, "nnz"), (4, "nnzC"), (5, "nnzX")):
+        rp, col, vals = h.operator_export(w)
+        sizes[key] = int(col.size)
+        if w == 0:
+            rowabs = np.add.reduceat(np.abs(vals[:, 0]), rp[:-1]) if col.size else np.zeros(1)
+    dims, fft, origin, delta = h.grid_info()
+    sizes["dims"], sizes["fft"] = [int(x) for x in dims], [int(x) for x in fft]
+    dt = stable_dt(float(rowabs.max()))
+
+    stream = torch.cuda.current_stream()
+    h.set_precision(PMFEM_FP32)
+    m_dev = torch.tensor(m0, dtype=torch.float32, device="cuda")
+    h.set_m(m_dev, stream)
+    for _ in range(max(3, args.warmup)):
+        h.llg_step(dt, 1, stream)
+    torch.cuda.synchronize()
+    dist.barrier()
+    h.profile(True)
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    torch.cuda.synchronize()
+    dist.barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        h.llg_step(dt, 1, stream)
+    e1.record(stream)
+    e1.synchronize()
+    torch.cuda.synchronize()
+    dist.barrier()
+    ck = clocks.stop()
+    prof = h.profile_read()
+    h.profile(False)
+    h.sync()
+    ms = dist.max(e0.elapsed_time(e1))
+    value = world * Np * 4 * args.steps / (ms * 1e-3)
+
+    # end to end through the public API with pinned host buffers, copies in the timed region
+    k2 = max(3, min(args.steps, 10))
+    m_host = torch.empty((Np, 3), dtype=torch.float32, pin_memory=True)
+    h.get_m(m_dev, stream)
+    m_host.copy_(m_dev)
+    torch.cuda.synchronize()
+    dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(k2):
+        m_dev.copy_(m_host, non_blocking=True)
+        h.set_m(m_dev, stream)
+        h.llg_step(dt, 1, stream)
+        h.get_m(m_dev, stream)
+        m_host.copy_(m_dev, non_blocking=True)
+        stream.synchronize()
+    e2e_s = dist.max(time.perf_counter() - t0)
+    e2e_value = world * Np * 4 * k2 / e2e_s
+    step_bytes = Np * 3 * 4
+
+    # accuracy and speed against the plain FP64 GPU path
+    mt32 = torch.tensor(m0, dtype=torch.float32, device="cuda")
+    H32 = torch.empty_like(mt32)
+    h.field(mt32, H32, PMFEM_ALL, stream)
+    h.sync()
+    H32 = H32.double().cpu().numpy()
+    fp64 = {}
+    if not args.no_fp64:
+        h.set_precision(PMFEM_FP64)
+        mt64 = torch.tensor(m0, dtype=torch.float64, device="cuda")
+        H64 = torch.empty_like(mt64)
+        h.field(mt64, H64, PMFEM_ALL, stream)
+        h.sync()
+        H64 = H64.cpu().numpy()
+        h.set_m(mt64, stream)
+        for _ in range(2):
+            h.llg_step(dt, 1, stream)
+        torch.cuda.synchronize()
+        k64 = max(2, args.steps // 5)
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        for _ in range(k64):
+            h.llg_step(dt, 1, stream)
+        f1.record(stream)
+        f1.synchronize()
+        ms64 = dist.max(f0.elapsed_time(f1))
+        fp64 = {"value": world * Np * 4 * k64 / (ms64 * 1e-3), "ms_per_step": ms64 / k64, "steps": k64,
+                "fp32_field_rel_l2_vs_fp64": float(np.linalg.norm(H32 - H64) / np.linalg.norm(H64))}
+        fp64["fp32_speedup"] = value / fp64["value"]
+    h.destroy()
+
+    # roofline of the dominant kernel
+    peak, peak_kind = measured_peaks()
+    per = {k: {"launches": c, "ms_total": t, "share": 0.0} for k, (c, t) in prof.items() if c}
+    tot = sum(v["ms_total"] for k, v in per.items() if k != "grid_clear") or 1.0
+    for k, v in per.items():
+        v["share"] = v["ms_total"] / tot
+        v["us_per_launch"] = 1e3 * v["ms_total"] / v["launches"]
+        v["alg_gbs"] = alg_bytes(k, 4, sizes) / (v["ms_total"] / v["launches"] * 1e-3) / 1e9
+    dom = max((k for k in per if k != "grid_clear"), key=lambda k: per[k]["ms_total"])
+    dom_bytes = alg_bytes(dom, 4, sizes)
+    achieved = per[dom]["alg_gbs"]
+    launches = sum(v["launches"] for k, v in per.items() if k != "grid_clear")
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "wire-1d-periodic-protruding-1M", "nodes": int(mesh.n_nodes), "unknowns": int(Np),
+                   "tets": int(mesh.n_tets), "grid": [int(x) for x in dims], "fft": [int(x) for x in fft],
+                   "p": P_ORDER, "near_boxes": NEAR_BOXES, "near_elem_factor": NEAR_ELEM, "precision": "fp32",
+                   "step": "one RK4 LLG step = 4 field evaluations", "dt_s": dt,
+                   "nnz_adjacency": sizes["nnz"], "nnz_precorrection": sizes["nnzC"],
+                   "l2": "inputs larger than L2 (operator data streamed every evaluation)",
+                   "parallelism": f"replicas x{world}", "setup_s": round(t_setup, 1), "mesh_s": round(t_mesh, 1)},
+        "clocks": ck,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": step_bytes, "d2h_bytes_per_step": step_bytes,
+                "steps": k2},
+        "gpu_launches": launches,
+        "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "peak_kind": peak_kind, "alg_bytes_per_launch": dom_bytes,
+                     "traffic": ncu_traffic(dom)},
+        "fp64": fp64 or None,
+        "kernels": per,
+    }
+    if rank == 0 and not args.no_cpu:
+        ob, grid = oracle_sample(6000)
+        n, el = time_oracle(ob, 15.0)
+        line["cpu_baseline"] = {"value": ob.Np * 4 * n / el, "unit": UNIT, "cores": cpu_cores_used(), "kind": "oracle",
+                                "sample": f"{n} oracle O2 RK4 steps (NumPy/SciPy FP64) on a {ob.Np}-unknown wire of "
+                                          f"the same geometry, grid {grid}; set-up excluded"}
+    dist.close()
+    if rank == 0:
+        print(json.dumps(line))
+        if args.out:
+            open(args.out, "w").write(json.dumps(line) + "\n")
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_native(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

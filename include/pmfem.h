@@ -139,6 +139,18 @@ int pmfem_get_m(pmfem_t h, void* m, void* stream);
  */
 int pmfem_llg_step(pmfem_t h, double dt, int nsteps, void* stream);
 
+/*
+ * Per-launch timing for measurement.  pmfem_profile(h, 1) starts recording a CUDA event
+ * pair around every kernel the handle launches (on the stream it launches on) and clears
+ * the totals; 0 stops recording.  pmfem_profile_read synchronises the device and writes,
+ * for kernel ids 0..n-1, the launch counts and the summed event time in ms since the last
+ * pmfem_profile(h, 1).  Ids: 0 charges, 1 projection, 2 FFT x forward, 3 FFT y forward,
+ * 4 FFT z + spectral multiply, 5 FFT y inverse, 6 FFT x inverse, 7 interpolation +
+ * precorrection, 8 gradient + exchange (+ RK4 stage), 9 grid clear.
+ */
+int pmfem_profile(pmfem_t h, int enable);
+int pmfem_profile_read(pmfem_t h, int64_t* counts, double* total_ms, int n);
+
 /* Wait for all work of the handle; returns ENONFINITE / ETIMEOUT if a device check fired
  * since the previous sync (the flag is then cleared). */
 int pmfem_sync(pmfem_t h);

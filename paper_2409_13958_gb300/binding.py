@@ -36,6 +36,8 @@ SIGNATURES = {
     "pmfem_set_m": (_c.c_int, [_vp, _vp, _vp]),
     "pmfem_get_m": (_c.c_int, [_vp, _vp, _vp]),
     "pmfem_llg_step": (_c.c_int, [_vp, _dbl, _c.c_int, _vp]),
+    "pmfem_profile": (_c.c_int, [_vp, _c.c_int]),
+    "pmfem_profile_read": (_c.c_int, [_vp, _vp, _vp, _c.c_int]),
     "pmfem_sync": (_c.c_int, [_vp]),
     "pmfem_destroy": (_c.c_int, [_vp]),
     "pmfem_operator_info": (_c.c_int, [_vp, _c.c_int, _pi64, _pi64, _c.POINTER(_c.c_int)]),
@@ -157,6 +159,19 @@ class Pmfem:
 
     def llg_step(self, dt: float, nsteps: int = 1, stream=None):
         self._ck(self._lib.pmfem_llg_step(self.h, dt, nsteps, _stream(stream)))
+
+    KERNELS = ("charges", "projection", "fft_x_fwd", "fft_y_fwd", "fft_z_conv", "fft_y_inv", "fft_x_inv",
+               "interp_precorr", "gradient_exchange", "grid_clear")
+
+    def profile(self, enable: bool = True):
+        self._ck(self._lib.pmfem_profile(self.h, 1 if enable else 0))
+
+    def profile_read(self) -> dict:
+        n = len(self.KERNELS)
+        counts = np.zeros(n, dtype=np.int64)
+        ms = np.zeros(n, dtype=np.float64)
+        self._ck(self._lib.pmfem_profile_read(self.h, counts.ctypes.data, ms.ctypes.data, n))
+        return {k: (int(c), float(t)) for k, c, t in zip(self.KERNELS, counts, ms)}
 
     def sync(self):
         self._ck(self._lib.pmfem_sync(self.h))

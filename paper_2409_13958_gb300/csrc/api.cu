@@ -29,6 +29,16 @@ struct pmfem_state {
   void* acc = nullptr;
   void* hbuf = nullptr;   // field output for host-buffer calls
   int* flag = nullptr;
+  // per-launch timing (pmfem_profile)
+  bool prof_on = false;
+  std::vector<cudaEvent_t> ev_pool;
+  size_t ev_next = 0;
+  struct Rec { int id; cudaEvent_t a, b; };
+  std::vector<Rec> recs;
+  int open_id[KID_COUNT] = {};
+  cudaEvent_t open_ev[KID_COUNT] = {};
+  int64_t prof_count[KID_COUNT] = {};
+  double prof_ms[KID_COUNT] = {};
 };
 
 namespace {
@@ -47,6 +57,32 @@ int fail(pmfem_t h, int code, const std::string& msg) {
     cudaError_t e_ = (x);                                                                 \
     if (e_ != cudaSuccess) return fail(h, ECUDA_, std::string(#x) + ": " + cudaGetErrorString(e_)); \
   } while (0)
+
+void prof_hook(void* ctx, int id, int phase, cudaStream_t st) {
+  pmfem_t h = (pmfem_t)ctx;
+  if (h->ev_next >= h->ev_pool.size()) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) return;
+    h->ev_pool.push_back(e);
+  }
+  cudaEvent_t e = h->ev_pool[h->ev_next++];
+  cudaEventRecord(e, st);
+  if (phase == 0) {
+    h->open_ev[id] = e;
+  } else {
+    h->recs.push_back({id, h->open_ev[id], e});
+  }
+}
+
+void apply_prof(pmfem_t h) {
+  ProfHook hk;
+  if (h->prof_on) {
+    hk.fn = prof_hook;
+    hk.ctx = h;
+  }
+  h->d64.prof = hk;
+  h->d32.prof = hk;
+}
 
 void free_device(pmfem_t h) {
   for (void* p : h->allocs) cudaFree(p);
@@ -171,13 +207,16 @@ int ensure_device(pmfem_t h) {
   }
   h->dev_prec = h->prec;
   h->dev_ready = true;
+  apply_prof(h);
   return OK;
 }
 
 template <typename T>
 void enqueue_eval(pmfem_t h, DevOps<T>& d, const T* m, T* H, int comps, const RkArgs& rk, cudaStream_t st) {
   if (comps & PMFEM_MS) {
+    d.prof.begin(KID_MEMSET, st);
     cudaMemsetAsync(d.grid, 0, sizeof(T) * (size_t)d.dims[0] * d.dims[1] * d.dims[2], st);
+    d.prof.end(KID_MEMSET, st);
     launch_charges(d, m, st);
     launch_anterp(d, st);
     launch_fft_conv(d, st);
@@ -398,9 +437,48 @@ int pmfem_sync(pmfem_t h) {
   return OK;
 }
 
+int pmfem_profile(pmfem_t h, int enable) {
+  if (!h) return EINVAL_;
+  h->prof_on = enable != 0;
+  h->recs.clear();
+  h->ev_next = 0;
+  for (int i = 0; i < KID_COUNT; ++i) {
+    h->prof_count[i] = 0;
+    h->prof_ms[i] = 0;
+  }
+  if (h->prof_on && h->ev_pool.size() < 4096) {
+    while (h->ev_pool.size() < 4096) {
+      cudaEvent_t e;
+      PMFEM_CK(h, cudaEventCreate(&e));
+      h->ev_pool.push_back(e);
+    }
+  }
+  apply_prof(h);
+  return OK;
+}
+
+int pmfem_profile_read(pmfem_t h, int64_t* counts, double* total_ms, int n) {
+  if (!h || !counts || !total_ms || n <= 0) return EINVAL_;
+  PMFEM_CK(h, cudaDeviceSynchronize());
+  for (auto& r : h->recs) {
+    float ms = 0;
+    PMFEM_CK(h, cudaEventElapsedTime(&ms, r.a, r.b));
+    h->prof_count[r.id] += 1;
+    h->prof_ms[r.id] += ms;
+  }
+  h->recs.clear();
+  h->ev_next = 0;
+  for (int i = 0; i < n; ++i) {
+    counts[i] = i < KID_COUNT ? h->prof_count[i] : 0;
+    total_ms[i] = i < KID_COUNT ? h->prof_ms[i] : 0.0;
+  }
+  return OK;
+}
+
 int pmfem_destroy(pmfem_t h) {
   if (!h) return OK;
   free_device(h);
+  for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
   if (h->stream) cudaStreamDestroy(h->stream);
   delete h;
   return OK;

@@ -10,6 +10,20 @@ template <typename T> struct Vec2;
 template <> struct Vec2<double> { using type = double2; };
 template <> struct Vec2<float> { using type = float2; };
 
+// Optional per-launch timing: the handle records a CUDA event pair around each kernel.
+enum KernelId : int { KID_CHARGES = 0, KID_ANTERP, KID_FFT_X_FWD, KID_FFT_Y_FWD, KID_FFT_Z_CONV, KID_FFT_Y_INV,
+                      KID_FFT_X_INV, KID_INTERP, KID_FIELD, KID_MEMSET, KID_COUNT };
+struct ProfHook {
+  void (*fn)(void* ctx, int id, int phase, cudaStream_t st) = nullptr;
+  void* ctx = nullptr;
+  void begin(int id, cudaStream_t st) const {
+    if (fn) fn(ctx, id, 0, st);
+  }
+  void end(int id, cudaStream_t st) const {
+    if (fn) fn(ctx, id, 1, st);
+  }
+};
+
 // Operator values, grid set-up and work buffers of one precision, all device memory.
 template <typename T>
 struct DevOps {
@@ -44,6 +58,7 @@ struct DevOps {
   T* grid = nullptr;                              // N0 N1 N2 real (Q, then U)
   C2* cbuf = nullptr;                             // F2 x F1 x (F0/2+1) complex
   int* flag = nullptr;                            // device error word
+  ProfHook prof;
 };
 
 // error word bits

@@ -204,35 +204,45 @@ void launch_fft_conv(const DevOps<T>& d, cudaStream_t st) {
   const int Hx = F0 / 2 + 1;
   // 1. x forward
   {
+    d.prof.begin(KID_FFT_X_FWD, st);
     const int BL = lines_per_block<C2>(F0);
     const int64_t nl = (int64_t)N1 * N2;
     k_fft_x_fwd<T, C2><<<(unsigned)((nl + BL - 1) / BL), kThreads, 2 * BL * F0 * sizeof(C2), st>>>(
         d.grid, d.cbuf, N0, N1, N2, F0, F1, BL, d.tw[0]);
+    d.prof.end(KID_FFT_X_FWD, st);
   }
   // 2. y forward on the populated planes
   {
+    d.prof.begin(KID_FFT_Y_FWD, st);
     const int BL = lines_per_block<C2>(F1);
     const unsigned nb = (unsigned)(((Hx + BL - 1) / BL) * N2);
     k_fft_y<C2><<<nb, kThreads, 2 * BL * F1 * sizeof(C2), st>>>(d.cbuf, Hx, F1, N2, N1, F1, BL, false, d.tw[1]);
+    d.prof.end(KID_FFT_Y_FWD, st);
   }
   // 3. z forward, spectral multiply, z inverse
   {
+    d.prof.begin(KID_FFT_Z_CONV, st);
     const int BL = lines_per_block<C2>(F2);
     const unsigned nb = (unsigned)(((Hx + BL - 1) / BL) * F1);
     k_fft_z_conv<T, C2><<<nb, kThreads, 2 * BL * F2 * sizeof(C2), st>>>(d.cbuf, Hx, F1, F2, N2, BL, d.ghat, d.tw[2]);
+    d.prof.end(KID_FFT_Z_CONV, st);
   }
   // 4. y inverse, keep y < N1
   {
+    d.prof.begin(KID_FFT_Y_INV, st);
     const int BL = lines_per_block<C2>(F1);
     const unsigned nb = (unsigned)(((Hx + BL - 1) / BL) * N2);
     k_fft_y<C2><<<nb, kThreads, 2 * BL * F1 * sizeof(C2), st>>>(d.cbuf, Hx, F1, N2, F1, N1, BL, true, d.tw[1]);
+    d.prof.end(KID_FFT_Y_INV, st);
   }
   // 5. x inverse (complex to real) into the grid buffer
   {
+    d.prof.begin(KID_FFT_X_INV, st);
     const int BL = lines_per_block<C2>(F0);
     const int64_t nl = (int64_t)N1 * N2;
     k_fft_x_inv<T, C2><<<(unsigned)((nl + BL - 1) / BL), kThreads, 2 * BL * F0 * sizeof(C2), st>>>(
         d.cbuf, d.grid, N0, N1, N2, F0, F1, BL, d.tw[0]);
+    d.prof.end(KID_FFT_X_INV, st);
   }
 }
 

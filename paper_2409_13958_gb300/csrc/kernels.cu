@@ -217,13 +217,16 @@ inline unsigned blocks_for(int64_t threads) { return (unsigned)((threads + kBloc
 
 template <typename T>
 void launch_charges(const DevOps<T>& d, const T* m, cudaStream_t st) {
+  d.prof.begin(KID_CHARGES, st);
   k_charges<T><<<blocks_for(d.Np * kG), kBlock, 0, st>>>(d.Np, d.rowptr, d.col, d.wq[0], d.wq[1], d.wq[2], d.ea[0],
                                                          d.ea[1], d.ea[2], m, d.q, d.e, d.flag);
+  d.prof.end(KID_CHARGES, st);
 }
 
 template <typename T>
 void launch_anterp(const DevOps<T>& d, cudaStream_t st) {
   const unsigned nb = blocks_for(d.Np);
+  d.prof.begin(KID_ANTERP, st);
 #define PMFEM_ANTERP(PP)                                                                                \
   k_anterp<T, PP><<<nb, kBlock, 0, st>>>(d.Np, d.base, d.frac, d.q, d.grid, d.dims[0], d.dims[1], d.dims[2], \
                                          d.periodic[0], d.periodic[1], d.periodic[2])
@@ -234,11 +237,13 @@ void launch_anterp(const DevOps<T>& d, cudaStream_t st) {
     default: PMFEM_ANTERP(6); break;
   }
 #undef PMFEM_ANTERP
+  d.prof.end(KID_ANTERP, st);
 }
 
 template <typename T>
 void launch_interp(const DevOps<T>& d, const T* m, cudaStream_t st) {
   const unsigned nb = blocks_for(d.Np * kG);
+  d.prof.begin(KID_INTERP, st);
 #define PMFEM_INTERP(PP)                                                                                          \
   k_interp<T, PP><<<nb, kBlock, 0, st>>>(d.Np, d.base, d.frac, d.grid, d.dims[0], d.dims[1], d.dims[2],          \
                                          d.periodic[0], d.periodic[1], d.periodic[2], d.rowptrC, d.colC, d.valC, \
@@ -250,6 +255,7 @@ void launch_interp(const DevOps<T>& d, const T* m, cudaStream_t st) {
     default: PMFEM_INTERP(6); break;
   }
 #undef PMFEM_INTERP
+  d.prof.end(KID_INTERP, st);
 }
 
 template <typename T>
@@ -261,6 +267,7 @@ void launch_field(const DevOps<T>& d, const T* m, T* H, int comps, double hx, do
   T* m0 = (T*)rk.m0;
   T* mn = (T*)rk.mnext;
   T* acc = (T*)rk.acc;
+  d.prof.begin(KID_FIELD, st);
   if (rk.mode == 0)
     k_field<T, 0><<<nb, kBlock, 0, st>>>(d.Np, d.rowptr, d.col, d.gr[0], d.gr[1], d.gr[2], d.kp, d.u, m, H, use_ms,
                                          use_ex, ax, ay, az, m0, mn, acc, (T)rk.cdt, (T)rk.bw, rk.acc_init,
@@ -273,6 +280,7 @@ void launch_field(const DevOps<T>& d, const T* m, T* H, int comps, double hx, do
     k_field<T, 2><<<nb, kBlock, 0, st>>>(d.Np, d.rowptr, d.col, d.gr[0], d.gr[1], d.gr[2], d.kp, d.u, m, H, use_ms,
                                          use_ex, ax, ay, az, m0, mn, acc, (T)rk.cdt, (T)rk.bw, rk.acc_init,
                                          (T)rk.dt6, (T)rk.gam, (T)rk.alpha, d.flag);
+  d.prof.end(KID_FIELD, st);
 }
 
 #define PMFEM_INSTANTIATE(T)                                                                        \
