@@ -187,8 +187,10 @@ def alg_bytes(name: str, s: int, sz: dict) -> float:
     if name == "fft_x_inv":
         return 2 * s * Hx * N1 * N2 + s * G
     if name == "interp_precorr":
-        return (12 + 3 * s) * Np + s * G + 4 * (Np + 1) + (4 + s) * nC + 4 * (Np + 1) + (4 + 3 * s) * nX \
-            + 3 * s * Np * (nX > 0) + 3 * s * Np
+        # stencil (base + fractions), grid U once, C (rowptr, col, value), q and e once, u written,
+        # plus the near-element entries beyond the adjacency pattern (and m) when present
+        return (12 + 3 * s) * Np + s * G + 4 * (Np + 1) + (4 + s) * nC + 3 * s * Np \
+            + ((4 * (Np + 1) + (4 + 3 * s) * nX + 3 * s * Np) if nX else 0)
     if name == "gradient_exchange":
         # RK stage epilogue averaged over the four stages: m_s, m0 read; m_next / m0 written; acc
         return idx + 4 * s * nnz + s * Np + 3 * s * Np + 3 * s * Np + 3 * s * Np + 4.5 * s * Np
@@ -326,7 +328,8 @@ def run_native(args):
     sizes["dims"], sizes["fft"] = [int(x) for x in dims], [int(x) for x in fft]
     dt = stable_dt(float(rowabs.max()))
 
-    stream = torch.cuda.current_stream()
+    stream = torch.cuda.Stream()          # explicit stream: every launch and event goes on it
+    torch.cuda.set_stream(stream)
     h.set_precision(PMFEM_FP32)
     m_dev = torch.tensor(m0, dtype=torch.float32, device="cuda")
     h.set_m(m_dev, stream)

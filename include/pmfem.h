@@ -20,7 +20,8 @@
  *     returns and may be freed afterwards.
  *   - "device" pointers are CUDA device (or managed) addresses; "host" pointers are CPU
  *     addresses (pinned memory makes the host-buffer calls faster but is not required).
- *   - stream is a cudaStream_t passed as void*; NULL selects the library's own stream.
+ *   - stream is a cudaStream_t passed as void*; NULL selects the library's own stream,
+ *     which is a blocking stream (ordered with the legacy default stream).
  *     Calls that take a stream enqueue work and return without synchronising, except
  *     where stated.
  *   - Unknown ordering: the N' unknowns are the ancestors of the periodic pairing

@@ -160,8 +160,8 @@ int build_device(pmfem_t h, DevOps<T>& d) {
   if ((rc = upload_conv<T>(h, s.ghat.data(), s.ghat.size(), 1, 0, scale, &d.ghat))) return rc;
   for (int a = 0; a < 3; ++a) {
     const int F = s.fft[a];
-    std::vector<C2> tw(F / 2);
-    for (int j = 0; j < F / 2; ++j) {
+    std::vector<C2> tw(F);
+    for (int j = 0; j < F; ++j) {
       double ang = 2.0 * kPi * j / F;
       tw[j].x = (T)std::cos(ang);
       tw[j].y = (T)(-std::sin(ang));
@@ -199,7 +199,8 @@ int ensure_device(pmfem_t h) {
   if (!h->s.ready) return fail(h, ESTATE_, "call pmfem_set_periodicity before using the GPU");
   if (h->dev_ready && h->dev_prec == h->prec) return OK;
   free_device(h);
-  if (!h->stream) PMFEM_CK(h, cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking));
+  // a blocking stream: work on it is ordered with the legacy default stream (handle 0)
+  if (!h->stream) PMFEM_CK(h, cudaStreamCreate(&h->stream));
   int rc = (h->prec == PMFEM_FP64) ? build_device(h, h->d64) : build_device(h, h->d32);
   if (rc) {
     free_device(h);

@@ -50,7 +50,7 @@ struct DevOps {
   const int32_t* base = nullptr;                  // Np x 3
   const T* frac = nullptr;                        // Np x 3
   const T* ghat = nullptr;                        // (F0/2+1)(F1/2+1)(F2/2+1), scaled by 1/(F0 F1 F2)
-  const C2* tw[3] = {nullptr, nullptr, nullptr};  // exp(-2 pi i j / F_a), j < F_a / 2
+  const C2* tw[3] = {nullptr, nullptr, nullptr};  // exp(-2 pi i j / F_a), j < F_a
   // work buffers
   T* q = nullptr;
   T* e = nullptr;

@@ -1,249 +1,392 @@
 // BAIM step 2 on sm_103a: U = IFFT( Ghat . FFT(Q) ) over the grid of Eq. 16.
 // Periodic axes are transformed circularly at their own length; open axes are zero-padded
-// to twice their length (linear convolution).  Five passes over a complex half-spectrum
-// buffer laid out [z][y][kx] (kx = 0..F0/2):
+// to twice their length (linear convolution), and zero inputs are never read.  Five passes
+// over a complex half-spectrum buffer laid out [z][y][kx] (kx = 0..F0/2):
 //   1. x: real-to-complex on the N1 x N2 populated rows (inputs beyond N0 are zero)
-//   2. y: forward on the populated z planes, inputs beyond N1 are zero
+//   2. y: forward on the populated z planes (inputs beyond N1 are zero)
 //   3. z: forward (inputs beyond N2 zero), multiply by the real PGF spectrum, inverse,
-//         keep z < N2
+//         keep z < N2 -- one kernel, the spectrum never leaves registers
 //   4. y: inverse on the populated z planes, keep y < N1
 //   5. x: complex-to-real on the kept rows, keep x < N0
-// Each line transform is an in-shared-memory Stockham radix-2 (autosort) FFT; a block
-// takes BL lines that are adjacent in memory so that loads and stores coalesce.
+//
+// Line transform of length F = R1 * R2 (R1 >= R2, powers of two), two-factor form:
+//   forward  X[k1 + R1 k2] = sum_n2 W_R2^{n2 k2} W_F^{n2 k1} sum_n1 x[R2 n1 + n2] W_R1^{n1 k1}
+//   inverse  y[a + R2 b]   = sum_k1 W_R1^{-b k1} W_F^{-a k1} sum_k2 X[k1 + R1 k2] W_R2^{-a k2}
+// Every small DFT runs on a register array (radix-2, fully unrolled); the single
+// transpose between the two factors goes through padded shared memory.  A block holds
+// LB lines; in strided passes consecutive threads take consecutive lines (adjacent kx),
+// so each global access of a warp is one contiguous segment.
+#include <utility>
+
 #include "device.hpp"
 
 namespace pmfem {
 namespace {
-
-constexpr int kThreads = 256;
-constexpr int kSmemBudget = 96 * 1024;
 
 template <typename C2> __device__ __forceinline__ C2 cadd(C2 a, C2 b) { return {a.x + b.x, a.y + b.y}; }
 template <typename C2> __device__ __forceinline__ C2 csub(C2 a, C2 b) { return {a.x - b.x, a.y - b.y}; }
 template <typename C2> __device__ __forceinline__ C2 cmul(C2 a, C2 b) {
   return {a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x};
 }
-
-// BL lines of length F in x (line-major); returns the buffer holding the result.
-template <typename C2>
-__device__ C2* fft_lines(C2* x, C2* y, int F, int BL, const C2* __restrict__ tw, bool inverse) {
-  const int H = F >> 1;
-  for (int s = 1, m = F; m > 1; s <<= 1, m >>= 1) {
-    const int half = m >> 1;
-    for (int b = threadIdx.x; b < BL * H; b += blockDim.x) {
-      const int l = b / H, i = b - l * H;
-      const int p = i / s, q = i - p * s;
-      C2* xl = x + l * F;
-      C2* yl = y + l * F;
-      const C2 a = xl[q + s * p], c = xl[q + s * (p + half)];
-      C2 w = tw[p * s];
-      if (inverse) w.y = -w.y;
-      yl[q + s * 2 * p] = cadd(a, c);
-      yl[q + s * (2 * p + 1)] = cmul(csub(a, c), w);
-    }
-    __syncthreads();
-    C2* t = x;
-    x = y;
-    y = t;
-  }
-  return x;
+template <typename C2> __device__ __forceinline__ C2 conjif(C2 w, bool inv) {
+  if (inv) w.y = -w.y;
+  return w;
 }
 
-template <typename T, typename C2>
-__global__ void __launch_bounds__(kThreads) k_fft_x_fwd(const T* __restrict__ Q, C2* __restrict__ cb, int N0, int N1,
-                                                       int N2, int F0, int F1, int BL, const C2* __restrict__ tw) {
-  extern __shared__ unsigned char smem_raw[];
-  C2* x = reinterpret_cast<C2*>(smem_raw);
-  C2* y = x + BL * F0;
-  const int64_t nlines = (int64_t)N1 * N2;
-  const int64_t L0 = (int64_t)blockIdx.x * BL;
-  for (int idx = threadIdx.x; idx < BL * F0; idx += blockDim.x) {
-    const int l = idx / F0, j = idx - l * F0;
-    const int64_t L = L0 + l;
-    T v = 0;
-    if (L < nlines && j < N0) v = Q[j + (int64_t)N0 * L];
-    x[idx] = {v, T(0)};
-  }
-  __syncthreads();
-  C2* r = fft_lines(x, y, F0, BL, tw, false);
-  const int Hx = F0 / 2 + 1;
-  for (int idx = threadIdx.x; idx < BL * Hx; idx += blockDim.x) {
-    const int l = idx / Hx, k = idx - l * Hx;
-    const int64_t L = L0 + l;
-    if (L < nlines) {
-      const int64_t yy = L % N1, zz = L / N1;
-      cb[k + (int64_t)Hx * (yy + (int64_t)F1 * zz)] = r[l * F0 + k];
-    }
-  }
+__host__ __device__ constexpr int ilog2(int n) { return n <= 1 ? 0 : 1 + ilog2(n / 2); }
+__host__ __device__ constexpr int bitrev(int i, int bits) {
+  int r = 0;
+  for (int b = 0; b < bits; ++b) r |= ((i >> b) & 1) << (bits - 1 - b);
+  return r;
 }
 
-template <typename C2>
-__global__ void __launch_bounds__(kThreads) k_fft_y(C2* __restrict__ cb, int Hx, int F1, int nz, int n_in, int n_out,
-                                                   int BL, bool inverse, const C2* __restrict__ tw) {
-  extern __shared__ unsigned char smem_raw[];
-  C2* x = reinterpret_cast<C2*>(smem_raw);
-  C2* y = x + BL * F1;
-  const int kxb = (Hx + BL - 1) / BL;
-  const int z = blockIdx.x / kxb;
-  const int kx0 = (blockIdx.x - z * kxb) * BL;
-  C2* plane = cb + (int64_t)Hx * F1 * z;
-  for (int idx = threadIdx.x; idx < BL * F1; idx += blockDim.x) {
-    const int j = idx / BL, l = idx - j * BL;
-    C2 v = {0, 0};
-    if (kx0 + l < Hx && j < n_in) v = plane[kx0 + l + (int64_t)Hx * j];
-    x[l * F1 + j] = v;
-  }
-  __syncthreads();
-  C2* r = fft_lines(x, y, F1, BL, tw, inverse);
-  for (int idx = threadIdx.x; idx < BL * n_out; idx += blockDim.x) {
-    const int j = idx / BL, l = idx - j * BL;
-    if (kx0 + l < Hx) plane[kx0 + l + (int64_t)Hx * j] = r[l * F1 + j];
+// bit-reversal permutation with compile-time indices (keeps the array in registers)
+template <int R, int I, typename C2>
+__device__ __forceinline__ void swap_rev(C2 (&v)[R]) {
+  constexpr int J = bitrev(I, ilog2(R));
+  if constexpr (J > I) {
+    C2 t = v[I];
+    v[I] = v[J];
+    v[J] = t;
   }
 }
-
-template <typename T, typename C2>
-__global__ void __launch_bounds__(kThreads) k_fft_z_conv(C2* __restrict__ cb, int Hx, int F1, int F2, int N2, int BL,
-                                                        const T* __restrict__ ghat, const C2* __restrict__ tw) {
-  extern __shared__ unsigned char smem_raw[];
-  C2* x = reinterpret_cast<C2*>(smem_raw);
-  C2* y = x + BL * F2;
-  const int kxb = (Hx + BL - 1) / BL;
-  const int ky = blockIdx.x / kxb;
-  const int kx0 = (blockIdx.x - ky * kxb) * BL;
-  const int64_t zs = (int64_t)Hx * F1;
-  C2* col0 = cb + kx0 + (int64_t)Hx * ky;
-  for (int idx = threadIdx.x; idx < BL * F2; idx += blockDim.x) {
-    const int j = idx / BL, l = idx - j * BL;
-    C2 v = {0, 0};
-    if (kx0 + l < Hx && j < N2) v = col0[l + zs * j];
-    x[l * F2 + j] = v;
-  }
-  __syncthreads();
-  C2* r = fft_lines(x, y, F2, BL, tw, false);
-  C2* o = (r == x) ? y : x;
-  const int H1 = F1 / 2 + 1;
-  const int iy = ky <= F1 - ky ? ky : F1 - ky;
-  for (int idx = threadIdx.x; idx < BL * F2; idx += blockDim.x) {
-    const int l = idx / F2, j = idx - l * F2;
-    const int kx = kx0 + l < Hx ? kx0 + l : Hx - 1;
-    const int iz = j <= F2 - j ? j : F2 - j;
-    const T g = ghat[kx + (int64_t)Hx * (iy + (int64_t)H1 * iz)];
-    r[idx].x *= g;
-    r[idx].y *= g;
-  }
-  __syncthreads();
-  C2* s = fft_lines(r, o, F2, BL, tw, true);
-  for (int idx = threadIdx.x; idx < BL * N2; idx += blockDim.x) {
-    const int j = idx / BL, l = idx - j * BL;
-    if (kx0 + l < Hx) col0[l + zs * j] = s[l * F2 + j];
-  }
+template <int R, typename C2, int... I>
+__device__ __forceinline__ void bit_reverse(C2 (&v)[R], std::integer_sequence<int, I...>) {
+  (swap_rev<R, I>(v), ...);
 }
 
-template <typename T, typename C2>
-__global__ void __launch_bounds__(kThreads) k_fft_x_inv(const C2* __restrict__ cb, T* __restrict__ U, int N0, int N1,
-                                                       int N2, int F0, int F1, int BL, const C2* __restrict__ tw) {
-  extern __shared__ unsigned char smem_raw[];
-  C2* x = reinterpret_cast<C2*>(smem_raw);
-  C2* y = x + BL * F0;
-  const int64_t nlines = (int64_t)N1 * N2;
-  const int64_t L0 = (int64_t)blockIdx.x * BL;
-  const int Hx = F0 / 2 + 1;
-  for (int idx = threadIdx.x; idx < BL * F0; idx += blockDim.x) {
-    const int l = idx / F0, j = idx - l * F0;
-    const int64_t L = L0 + l;
-    C2 v = {0, 0};
-    if (L < nlines) {
-      const int64_t yy = L % N1, zz = L / N1;
-      const C2* row = cb + (int64_t)Hx * (yy + (int64_t)F1 * zz);
-      if (j < Hx) {
-        v = row[j];
-      } else {
-        v = row[F0 - j];
-        v.y = -v.y;
+// radix-2 butterfly stages of length LEN, 2 LEN, ..., R (compile-time recursion)
+template <int R, int LEN, typename C2>
+__device__ __forceinline__ void dft_stages(C2 (&v)[R], const C2* __restrict__ tw, int step, bool inv) {
+  if constexpr (LEN <= R) {
+    constexpr int half = LEN / 2;
+#pragma unroll
+    for (int i = 0; i < R; i += LEN) {
+#pragma unroll
+      for (int k = 0; k < half; ++k) {
+        C2 u = v[i + k], t = v[i + k + half];
+        if (k != 0) t = cmul(t, conjif(__ldg(&tw[k * (R / LEN) * step]), inv));
+        v[i + k] = cadd(u, t);
+        v[i + k + half] = csub(u, t);
       }
     }
-    x[idx] = v;
-  }
-  __syncthreads();
-  C2* r = fft_lines(x, y, F0, BL, tw, true);
-  for (int idx = threadIdx.x; idx < BL * N0; idx += blockDim.x) {
-    const int l = idx / N0, j = idx - l * N0;
-    const int64_t L = L0 + l;
-    if (L < nlines) U[j + (int64_t)N0 * L] = r[l * F0 + j].x;
+    dft_stages<R, 2 * LEN>(v, tw, step, inv);
   }
 }
 
-template <typename C2>
-int lines_per_block(int F) {
-  int bl = kSmemBudget / (2 * F * (int)sizeof(C2));
-  int p = 1;
-  while (p * 2 <= bl && p * 2 <= 32) p *= 2;
-  return p;
+// In-register DFT of size R, natural order in and out.  tw holds exp(-2 pi i j / F) for
+// j < F and step = F / R, so W_R^j = tw[j * step].
+template <int R, typename C2>
+__device__ __forceinline__ void dft(C2 (&v)[R], const C2* __restrict__ tw, int step, bool inv) {
+  bit_reverse<R>(v, std::make_integer_sequence<int, R>{});
+  dft_stages<R, 2>(v, tw, step, inv);
+}
+
+// line geometry shared by the passes
+template <int F_> struct Fac {
+  static constexpr int F = F_;
+  static constexpr int R1 = 1 << ((ilog2(F_) + 1) / 2);
+  static constexpr int R2 = F_ / R1;
+  static constexpr int IPT = R1 / R2;           // step-2 items per thread (1 or 2)
+  static constexpr int LS = R1 * (R2 + 1) + 1;  // padded shared-memory line stride
+};
+
+// Forward transform of the LB lines a block holds.  ld(l, idx) returns element idx of
+// line l (zero outside the populated range).  On return thread (l, j) holds, for items
+// i < IPT with k1 = j + R2 i, X[k1 + R1 k2] in out[i][k2].
+template <int F, int LB, bool LINE_FAST, typename C2, typename Load>
+__device__ __forceinline__ void line_forward(C2* S, const C2* __restrict__ tw, Load ld, int l, int j,
+                                             C2 (&out)[Fac<F>::IPT][Fac<F>::R2]) {
+  using FF = Fac<F>;
+  C2 a[FF::R1];
+#pragma unroll
+  for (int n1 = 0; n1 < FF::R1; ++n1) a[n1] = ld(l, FF::R2 * n1 + j);
+  dft<FF::R1>(a, tw, FF::R2, false);
+#pragma unroll
+  for (int k1 = 1; k1 < FF::R1; ++k1) a[k1] = cmul(a[k1], __ldg(&tw[j * k1]));
+  C2* Sl = S + l * FF::LS;
+#pragma unroll
+  for (int k1 = 0; k1 < FF::R1; ++k1) Sl[k1 * (FF::R2 + 1) + j] = a[k1];
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < FF::IPT; ++i) {
+    const int k1 = j + FF::R2 * i;
+#pragma unroll
+    for (int n2 = 0; n2 < FF::R2; ++n2) out[i][n2] = Sl[k1 * (FF::R2 + 1) + n2];
+    dft<FF::R2>(out[i], tw, FF::R1, false);
+  }
+}
+
+// Inverse transform from the layout line_forward leaves; st(l, idx, value) stores
+// element idx of the result.  Unnormalised.
+template <int F, int LB, bool LINE_FAST, typename C2, typename Store>
+__device__ __forceinline__ void line_inverse(C2* S, const C2* __restrict__ tw, Store st, int l, int j,
+                                             C2 (&in)[Fac<F>::IPT][Fac<F>::R2]) {
+  using FF = Fac<F>;
+  C2* Sl = S + l * FF::LS;
+  __syncthreads();   // S may still be read by the forward step of another thread
+#pragma unroll
+  for (int i = 0; i < FF::IPT; ++i) {
+    const int k1 = j + FF::R2 * i;
+    dft<FF::R2>(in[i], tw, FF::R1, true);
+#pragma unroll
+    for (int a = 0; a < FF::R2; ++a) {
+      C2 z = in[i][a];
+      if (a != 0 && k1 != 0) z = cmul(z, conjif(__ldg(&tw[a * k1]), true));
+      Sl[k1 * (FF::R2 + 1) + a] = z;
+    }
+  }
+  __syncthreads();
+  C2 c[FF::R1];
+#pragma unroll
+  for (int k1 = 0; k1 < FF::R1; ++k1) c[k1] = Sl[k1 * (FF::R2 + 1) + j];
+  dft<FF::R1>(c, tw, FF::R2, true);
+#pragma unroll
+  for (int b = 0; b < FF::R1; ++b) st(l, j + FF::R2 * b, c[b]);
+}
+
+template <bool LINE_FAST, int LB, int R2>
+__device__ __forceinline__ void thread_line(int& l, int& j) {
+  const int t = threadIdx.x;
+  if (LINE_FAST) {
+    l = t % LB;
+    j = t / LB;
+  } else {
+    l = t / R2;
+    j = t % R2;
+  }
+}
+
+// ---------------------------------------------------------------- pass 1: x forward
+template <typename T, typename C2, int F, int LB>
+__global__ void __launch_bounds__(LB * Fac<F>::R2) k_fft_x_fwd(const T* __restrict__ Q, C2* __restrict__ cb, int N0,
+                                                             int N1, int N2, int F1, const C2* __restrict__ tw) {
+  using FF = Fac<F>;
+  extern __shared__ unsigned char smem_raw[];
+  C2* S = reinterpret_cast<C2*>(smem_raw);
+  int l, j;
+  thread_line<false, LB, FF::R2>(l, j);
+  const int64_t nlines = (int64_t)N1 * N2;
+  const int64_t L = (int64_t)blockIdx.x * LB + l;
+  const bool ok = L < nlines;
+  const T* row = Q + (int64_t)N0 * (ok ? L : 0);
+  auto ld = [&](int, int idx) -> C2 {
+    T v = (ok && idx < N0) ? row[idx] : T(0);
+    return C2{v, T(0)};
+  };
+  C2 X[FF::IPT][FF::R2];
+  line_forward<F, LB, false>(S, tw, ld, l, j, X);
+  if (!ok) return;
+  const int Hx = F / 2 + 1;
+  const int64_t yy = L % N1, zz = L / N1;
+  C2* out = cb + (int64_t)Hx * (yy + (int64_t)F1 * zz);
+#pragma unroll
+  for (int i = 0; i < FF::IPT; ++i)
+#pragma unroll
+    for (int k2 = 0; k2 < FF::R2; ++k2) {
+      const int k = j + FF::R2 * i + FF::R1 * k2;
+      if (k < Hx) out[k] = X[i][k2];
+    }
+}
+
+// ---------------------------------------------------------------- passes 2, 4: y
+template <typename C2, int F, int LB, bool INV>
+__global__ void __launch_bounds__(LB * Fac<F>::R2) k_fft_y(C2* __restrict__ cb, int Hx, int n_in, int n_out,
+                                                         const C2* __restrict__ tw) {
+  using FF = Fac<F>;
+  extern __shared__ unsigned char smem_raw[];
+  C2* S = reinterpret_cast<C2*>(smem_raw);
+  int l, j;
+  thread_line<true, LB, FF::R2>(l, j);
+  const int kxb = (Hx + LB - 1) / LB;
+  const int z = blockIdx.x / kxb;
+  const int kx = (blockIdx.x - z * kxb) * LB + l;
+  const bool ok = kx < Hx;
+  C2* col = cb + (int64_t)Hx * F * z + (ok ? kx : 0);
+  C2 X[FF::IPT][FF::R2];
+  if (!INV) {
+    auto ld = [&](int, int idx) -> C2 { return (ok && idx < n_in) ? col[(int64_t)Hx * idx] : C2{0, 0}; };
+    line_forward<F, LB, true>(S, tw, ld, l, j, X);
+    if (!ok) return;
+#pragma unroll
+    for (int i = 0; i < FF::IPT; ++i)
+#pragma unroll
+      for (int k2 = 0; k2 < FF::R2; ++k2) col[(int64_t)Hx * (j + FF::R2 * i + FF::R1 * k2)] = X[i][k2];
+  } else {
+    // the inverse starts from the k1 + R1 k2 layout: load it directly
+#pragma unroll
+    for (int i = 0; i < FF::IPT; ++i)
+#pragma unroll
+      for (int k2 = 0; k2 < FF::R2; ++k2)
+        X[i][k2] = ok ? col[(int64_t)Hx * (j + FF::R2 * i + FF::R1 * k2)] : C2{0, 0};
+    auto st = [&](int, int idx, C2 v) {
+      if (ok && idx < n_out) col[(int64_t)Hx * idx] = v;
+    };
+    line_inverse<F, LB, true>(S, tw, st, l, j, X);
+  }
+}
+
+// ---------------------------------------------------------------- pass 3: z convolution
+template <typename T, typename C2, int F, int LB>
+__global__ void __launch_bounds__(LB * Fac<F>::R2) k_fft_z_conv(C2* __restrict__ cb, int Hx, int F1, int N2,
+                                                              const T* __restrict__ ghat, const C2* __restrict__ tw) {
+  using FF = Fac<F>;
+  extern __shared__ unsigned char smem_raw[];
+  C2* S = reinterpret_cast<C2*>(smem_raw);
+  int l, j;
+  thread_line<true, LB, FF::R2>(l, j);
+  const int kxb = (Hx + LB - 1) / LB;
+  const int ky = blockIdx.x / kxb;
+  const int kx = (blockIdx.x - ky * kxb) * LB + l;
+  const bool ok = kx < Hx;
+  const int64_t zs = (int64_t)Hx * F1;
+  C2* col = cb + (int64_t)Hx * ky + (ok ? kx : 0);
+  auto ld = [&](int, int idx) -> C2 { return (ok && idx < N2) ? col[zs * idx] : C2{0, 0}; };
+  C2 X[FF::IPT][FF::R2];
+  line_forward<F, LB, true>(S, tw, ld, l, j, X);
+  // spectral multiply by the real, even PGF spectrum (reduced by symmetry in every axis)
+  const int H1 = F1 / 2 + 1;
+  const int iy = ky <= F1 - ky ? ky : F1 - ky;
+  const T* g = ghat + (ok ? kx : 0) + (int64_t)Hx * iy;
+  const int64_t gs = (int64_t)Hx * H1;
+#pragma unroll
+  for (int i = 0; i < FF::IPT; ++i)
+#pragma unroll
+    for (int k2 = 0; k2 < FF::R2; ++k2) {
+      const int kz = j + FF::R2 * i + FF::R1 * k2;
+      const int iz = kz <= F - kz ? kz : F - kz;
+      const T gv = ok ? __ldg(&g[gs * iz]) : T(0);
+      X[i][k2].x *= gv;
+      X[i][k2].y *= gv;
+    }
+  auto st = [&](int, int idx, C2 v) {
+    if (ok && idx < N2) col[zs * idx] = v;
+  };
+  line_inverse<F, LB, true>(S, tw, st, l, j, X);
+}
+
+// ---------------------------------------------------------------- pass 5: x inverse (C2R)
+template <typename T, typename C2, int F, int LB>
+__global__ void __launch_bounds__(LB * Fac<F>::R2) k_fft_x_inv(const C2* __restrict__ cb, T* __restrict__ U, int N0,
+                                                             int N1, int N2, int F1, const C2* __restrict__ tw) {
+  using FF = Fac<F>;
+  extern __shared__ unsigned char smem_raw[];
+  C2* S = reinterpret_cast<C2*>(smem_raw);
+  int l, j;
+  thread_line<false, LB, FF::R2>(l, j);
+  const int64_t nlines = (int64_t)N1 * N2;
+  const int64_t L = (int64_t)blockIdx.x * LB + l;
+  const bool ok = L < nlines;
+  const int Hx = F / 2 + 1;
+  const int64_t yy = ok ? L % N1 : 0, zz = ok ? L / N1 : 0;
+  const C2* row = cb + (int64_t)Hx * (yy + (int64_t)F1 * zz);
+  C2 X[FF::IPT][FF::R2];
+#pragma unroll
+  for (int i = 0; i < FF::IPT; ++i)
+#pragma unroll
+    for (int k2 = 0; k2 < FF::R2; ++k2) {
+      const int k = j + FF::R2 * i + FF::R1 * k2;
+      C2 v = {0, 0};
+      if (ok) {
+        if (k < Hx) {
+          v = row[k];
+        } else {
+          v = row[F - k];   // Hermitian symmetry of a real signal
+          v.y = -v.y;
+        }
+      }
+      X[i][k2] = v;
+    }
+  T* out = U + (int64_t)N0 * (ok ? L : 0);
+  auto st = [&](int, int idx, C2 v) {
+    if (ok && idx < N0) out[idx] = v.x;
+  };
+  line_inverse<F, LB, false>(S, tw, st, l, j, X);
 }
 
 template <typename K>
-void allow_smem(K kernel) {
-  cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBudget);
+void set_smem(K kernel, size_t bytes) {
+  if (bytes > 48 * 1024) cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
+
+// line counts per block: strided passes want 128-byte rows of adjacent lines
+template <typename T> struct Lines { static constexpr int STRIDED = sizeof(T) == 4 ? 16 : 8; };
+
+template <typename T, int F>
+struct Passes {
+  using C2 = typename Vec2<T>::type;
+  using FF = Fac<F>;
+  static constexpr int LBX = (256 / FF::R2) > 0 ? (256 / FF::R2) : 1;   // contiguous passes
+  static constexpr int LBS = Lines<T>::STRIDED;
+  static size_t smem(int lb) { return (size_t)lb * FF::LS * sizeof(C2); }
+
+  static void x_fwd(const DevOps<T>& d, cudaStream_t st) {
+    const int64_t nl = (int64_t)d.dims[1] * d.dims[2];
+    const size_t sm = smem(LBX);
+    set_smem(k_fft_x_fwd<T, C2, F, LBX>, sm);
+    k_fft_x_fwd<T, C2, F, LBX><<<(unsigned)((nl + LBX - 1) / LBX), LBX * FF::R2, sm, st>>>(
+        d.grid, d.cbuf, d.dims[0], d.dims[1], d.dims[2], d.fft[1], d.tw[0]);
+  }
+  static void x_inv(const DevOps<T>& d, cudaStream_t st) {
+    const int64_t nl = (int64_t)d.dims[1] * d.dims[2];
+    const size_t sm = smem(LBX);
+    set_smem(k_fft_x_inv<T, C2, F, LBX>, sm);
+    k_fft_x_inv<T, C2, F, LBX><<<(unsigned)((nl + LBX - 1) / LBX), LBX * FF::R2, sm, st>>>(
+        d.cbuf, d.grid, d.dims[0], d.dims[1], d.dims[2], d.fft[1], d.tw[0]);
+  }
+  static void y(const DevOps<T>& d, bool inv, cudaStream_t st) {
+    const int Hx = d.fft[0] / 2 + 1;
+    const unsigned nb = (unsigned)(((Hx + LBS - 1) / LBS) * d.dims[2]);
+    const size_t sm = smem(LBS);
+    if (!inv) {
+      set_smem(k_fft_y<C2, F, LBS, false>, sm);
+      k_fft_y<C2, F, LBS, false><<<nb, LBS * FF::R2, sm, st>>>(d.cbuf, Hx, d.dims[1], F, d.tw[1]);
+    } else {
+      set_smem(k_fft_y<C2, F, LBS, true>, sm);
+      k_fft_y<C2, F, LBS, true><<<nb, LBS * FF::R2, sm, st>>>(d.cbuf, Hx, F, d.dims[1], d.tw[1]);
+    }
+  }
+  static void z(const DevOps<T>& d, cudaStream_t st) {
+    const int Hx = d.fft[0] / 2 + 1;
+    const unsigned nb = (unsigned)(((Hx + LBS - 1) / LBS) * d.fft[1]);
+    const size_t sm = smem(LBS);
+    set_smem(k_fft_z_conv<T, C2, F, LBS>, sm);
+    k_fft_z_conv<T, C2, F, LBS><<<nb, LBS * FF::R2, sm, st>>>(d.cbuf, Hx, d.fft[1], d.dims[2], d.ghat, d.tw[2]);
+  }
+};
+
+#define PMFEM_FFT_DISPATCH(F, CALL)                     \
+  switch (F) {                                          \
+    case 4: Passes<T, 4>::CALL; break;                  \
+    case 8: Passes<T, 8>::CALL; break;                  \
+    case 16: Passes<T, 16>::CALL; break;                \
+    case 32: Passes<T, 32>::CALL; break;                \
+    case 64: Passes<T, 64>::CALL; break;                \
+    case 128: Passes<T, 128>::CALL; break;              \
+    case 256: Passes<T, 256>::CALL; break;              \
+    case 512: Passes<T, 512>::CALL; break;              \
+    default: Passes<T, 1024>::CALL; break;              \
+  }
 
 }  // namespace
 
 template <typename T>
 void launch_fft_conv(const DevOps<T>& d, cudaStream_t st) {
-  using C2 = typename Vec2<T>::type;
-  static bool attr_done = false;
-  if (!attr_done) {
-    allow_smem(k_fft_x_fwd<T, C2>);
-    allow_smem(k_fft_y<C2>);
-    allow_smem(k_fft_z_conv<T, C2>);
-    allow_smem(k_fft_x_inv<T, C2>);
-    attr_done = true;
-  }
-  const int N0 = d.dims[0], N1 = d.dims[1], N2 = d.dims[2];
-  const int F0 = d.fft[0], F1 = d.fft[1], F2 = d.fft[2];
-  const int Hx = F0 / 2 + 1;
-  // 1. x forward
-  {
-    d.prof.begin(KID_FFT_X_FWD, st);
-    const int BL = lines_per_block<C2>(F0);
-    const int64_t nl = (int64_t)N1 * N2;
-    k_fft_x_fwd<T, C2><<<(unsigned)((nl + BL - 1) / BL), kThreads, 2 * BL * F0 * sizeof(C2), st>>>(
-        d.grid, d.cbuf, N0, N1, N2, F0, F1, BL, d.tw[0]);
-    d.prof.end(KID_FFT_X_FWD, st);
-  }
-  // 2. y forward on the populated planes
-  {
-    d.prof.begin(KID_FFT_Y_FWD, st);
-    const int BL = lines_per_block<C2>(F1);
-    const unsigned nb = (unsigned)(((Hx + BL - 1) / BL) * N2);
-    k_fft_y<C2><<<nb, kThreads, 2 * BL * F1 * sizeof(C2), st>>>(d.cbuf, Hx, F1, N2, N1, F1, BL, false, d.tw[1]);
-    d.prof.end(KID_FFT_Y_FWD, st);
-  }
-  // 3. z forward, spectral multiply, z inverse
-  {
-    d.prof.begin(KID_FFT_Z_CONV, st);
-    const int BL = lines_per_block<C2>(F2);
-    const unsigned nb = (unsigned)(((Hx + BL - 1) / BL) * F1);
-    k_fft_z_conv<T, C2><<<nb, kThreads, 2 * BL * F2 * sizeof(C2), st>>>(d.cbuf, Hx, F1, F2, N2, BL, d.ghat, d.tw[2]);
-    d.prof.end(KID_FFT_Z_CONV, st);
-  }
-  // 4. y inverse, keep y < N1
-  {
-    d.prof.begin(KID_FFT_Y_INV, st);
-    const int BL = lines_per_block<C2>(F1);
-    const unsigned nb = (unsigned)(((Hx + BL - 1) / BL) * N2);
-    k_fft_y<C2><<<nb, kThreads, 2 * BL * F1 * sizeof(C2), st>>>(d.cbuf, Hx, F1, N2, F1, N1, BL, true, d.tw[1]);
-    d.prof.end(KID_FFT_Y_INV, st);
-  }
-  // 5. x inverse (complex to real) into the grid buffer
-  {
-    d.prof.begin(KID_FFT_X_INV, st);
-    const int BL = lines_per_block<C2>(F0);
-    const int64_t nl = (int64_t)N1 * N2;
-    k_fft_x_inv<T, C2><<<(unsigned)((nl + BL - 1) / BL), kThreads, 2 * BL * F0 * sizeof(C2), st>>>(
-        d.cbuf, d.grid, N0, N1, N2, F0, F1, BL, d.tw[0]);
-    d.prof.end(KID_FFT_X_INV, st);
-  }
+  d.prof.begin(KID_FFT_X_FWD, st);
+  PMFEM_FFT_DISPATCH(d.fft[0], x_fwd(d, st));
+  d.prof.end(KID_FFT_X_FWD, st);
+  d.prof.begin(KID_FFT_Y_FWD, st);
+  PMFEM_FFT_DISPATCH(d.fft[1], y(d, false, st));
+  d.prof.end(KID_FFT_Y_FWD, st);
+  d.prof.begin(KID_FFT_Z_CONV, st);
+  PMFEM_FFT_DISPATCH(d.fft[2], z(d, st));
+  d.prof.end(KID_FFT_Z_CONV, st);
+  d.prof.begin(KID_FFT_Y_INV, st);
+  PMFEM_FFT_DISPATCH(d.fft[1], y(d, true, st));
+  d.prof.end(KID_FFT_Y_INV, st);
+  d.prof.begin(KID_FFT_X_INV, st);
+  PMFEM_FFT_DISPATCH(d.fft[0], x_inv(d, st));
+  d.prof.end(KID_FFT_X_INV, st);
 }
 
 template void launch_fft_conv<double>(const DevOps<double>&, cudaStream_t);
