@@ -37,7 +37,7 @@ WIRE = dict(L=100e-9, R=20e-9, seed=0)
 GRID = (128, 128, 256)
 P_ORDER, NEAR_BOXES, NEAR_ELEM = 3, 3, 0.0
 KERNELS = ("charges", "projection", "fft_x_fwd", "fft_y_fwd", "fft_z_conv", "fft_y_inv", "fft_x_inv",
-           "interp_precorr", "gradient_exchange", "grid_clear")
+           "interp_precorr", "gradient_exchange", "grid_clear", "permute")
 
 
 def parse():

@@ -23,11 +23,13 @@ struct pmfem_state {
   std::vector<void*> allocs;
   DevOps<double> d64;
   DevOps<float> d32;
-  void* m = nullptr;      // internal state N' x 3
-  void* mA = nullptr;     // RK stage buffers
+  void* m = nullptr;      // internal state, N' 4-vectors in the internal order
+  void* mA = nullptr;     // RK stage buffers (4-vectors)
   void* mB = nullptr;
   void* acc = nullptr;
-  void* hbuf = nullptr;   // field output for host-buffer calls
+  void* mF = nullptr;     // permuted input of pmfem_field (4-vectors)
+  void* hin = nullptr;    // N' x 3 user-order staging for the host-buffer calls
+  void* hout = nullptr;
   int* flag = nullptr;
   // per-launch timing (pmfem_profile)
   bool prof_on = false;
@@ -89,7 +91,7 @@ void free_device(pmfem_t h) {
   h->allocs.clear();
   h->d64 = DevOps<double>();
   h->d32 = DevOps<float>();
-  h->m = h->mA = h->mB = h->acc = h->hbuf = nullptr;
+  h->m = h->mA = h->mB = h->acc = h->mF = h->hin = h->hout = nullptr;
   h->flag = nullptr;
   h->dev_ready = false;
   h->dev_prec = -1;
@@ -129,33 +131,47 @@ template <typename T>
 int build_device(pmfem_t h, DevOps<T>& d) {
   using C2 = typename Vec2<T>::type;
   const Setup& s = h->s;
+  Layout L;
+  {
+    Error err;
+    int rc = build_layout(s, L, anterp_smem_budget(), sizeof(T), err);
+    if (rc) return fail(h, rc, err.msg);
+  }
   int rc;
   d.Np = s.Np;
-  d.nnz = (int64_t)s.col.size();
-  d.nnzC = s.C.nnz();
-  d.nnzX = s.Ex.nnz();
+  d.nnz = (int64_t)L.col.size();
+  d.nnzC = (int64_t)L.cval.size();
+  d.nnzX = L.Ex.nnz();
   d.p = s.p;
+  d.nb = s.near_boxes;
+  d.TY = L.TY;
+  d.TZ = L.TZ;
+  d.pl = L.pl;
+  d.pr = L.pr;
+  d.tiled = L.tiled;
   for (int a = 0; a < 3; ++a) {
     d.dims[a] = s.dims[a];
     d.fft[a] = s.fft[a];
     d.periodic[a] = s.periodic[a];
   }
-  if ((rc = upload(h, s.rowptr.data(), s.rowptr.size(), &d.rowptr))) return rc;
-  if ((rc = upload(h, s.col.data(), s.col.size(), &d.col))) return rc;
+  if ((rc = upload(h, L.perm.data(), L.perm.size(), &d.perm))) return rc;
+  if ((rc = upload(h, L.rowptr.data(), L.rowptr.size(), &d.rowptr))) return rc;
+  if ((rc = upload(h, L.col.data(), L.col.size(), &d.col))) return rc;
   for (int c = 0; c < 3; ++c) {
-    if ((rc = upload_conv<T>(h, s.Wq.data(), d.nnz, 3, c, 1.0, &d.wq[c]))) return rc;
-    if ((rc = upload_conv<T>(h, s.Ea.data(), d.nnz, 3, c, 1.0, &d.ea[c]))) return rc;
-    if ((rc = upload_conv<T>(h, s.Gr.data(), d.nnz, 3, c, 1.0, &d.gr[c]))) return rc;
+    if ((rc = upload_conv<T>(h, L.Wq.data(), d.nnz, 3, c, 1.0, &d.wq[c]))) return rc;
+    if ((rc = upload_conv<T>(h, L.Ea.data(), d.nnz, 3, c, 1.0, &d.ea[c]))) return rc;
+    if ((rc = upload_conv<T>(h, L.Gr.data(), d.nnz, 3, c, 1.0, &d.gr[c]))) return rc;
   }
-  if ((rc = upload_conv<T>(h, s.Kp.data(), d.nnz, 1, 0, 1.0, &d.kp))) return rc;
-  if ((rc = upload(h, s.C.rowptr.data(), s.C.rowptr.size(), &d.rowptrC))) return rc;
-  if ((rc = upload(h, s.C.col.data(), s.C.col.size(), &d.colC))) return rc;
-  if ((rc = upload_conv<T>(h, s.C.vals.data(), s.C.vals.size(), 1, 0, 1.0, &d.valC))) return rc;
-  if ((rc = upload(h, s.Ex.rowptr.data(), s.Ex.rowptr.size(), &d.rowptrX))) return rc;
-  if ((rc = upload(h, s.Ex.col.data(), s.Ex.col.size(), &d.colX))) return rc;
-  if ((rc = upload_conv<T>(h, s.Ex.vals.data(), s.Ex.vals.size(), 1, 0, 1.0, &d.valX))) return rc;
-  if ((rc = upload(h, s.base.data(), s.base.size(), &d.base))) return rc;
-  if ((rc = upload_conv<T>(h, s.frac.data(), s.frac.size(), 1, 0, 1.0, &d.frac))) return rc;
+  if ((rc = upload_conv<T>(h, L.Kp.data(), d.nnz, 1, 0, 1.0, &d.kp))) return rc;
+  if ((rc = upload(h, L.box.data(), L.box.size(), &d.box))) return rc;
+  if ((rc = upload(h, L.bstart.data(), L.bstart.size(), &d.bstart))) return rc;
+  if ((rc = upload(h, L.cptr.data(), L.cptr.size(), &d.cptr))) return rc;
+  if ((rc = upload_conv<T>(h, L.cval.data(), L.cval.size(), 1, 0, 1.0, &d.cval))) return rc;
+  if ((rc = upload(h, L.Ex.rowptr.data(), L.Ex.rowptr.size(), &d.rowptrX))) return rc;
+  if ((rc = upload(h, L.Ex.col.data(), L.Ex.col.size(), &d.colX))) return rc;
+  if ((rc = upload_conv<T>(h, L.Ex.vals.data(), L.Ex.vals.size(), 1, 0, 1.0, &d.valX))) return rc;
+  if ((rc = upload(h, L.base.data(), L.base.size(), &d.base))) return rc;
+  if ((rc = upload_conv<T>(h, L.frac.data(), L.frac.size(), 1, 0, 1.0, &d.frac))) return rc;
   const double scale = 1.0 / ((double)s.fft[0] * s.fft[1] * s.fft[2]);
   if ((rc = upload_conv<T>(h, s.ghat.data(), s.ghat.size(), 1, 0, scale, &d.ghat))) return rc;
   for (int a = 0; a < 3; ++a) {
@@ -181,17 +197,20 @@ int build_device(pmfem_t h, DevOps<T>& d) {
   d.grid = (T*)p;
   if ((rc = dalloc(h, &p, ncb * sizeof(C2)))) return rc;
   d.cbuf = (C2*)p;
-  const size_t sb = 3 * (size_t)s.Np * sizeof(T);
-  if ((rc = dalloc(h, &h->m, sb))) return rc;
-  if ((rc = dalloc(h, &h->mA, sb))) return rc;
-  if ((rc = dalloc(h, &h->mB, sb))) return rc;
-  if ((rc = dalloc(h, &h->acc, sb))) return rc;
-  if ((rc = dalloc(h, &h->hbuf, sb))) return rc;
+  const size_t sv = (size_t)s.Np * sizeof(V4<T>);
+  const size_t su = 3 * (size_t)s.Np * sizeof(T);
+  if ((rc = dalloc(h, &h->m, sv))) return rc;
+  if ((rc = dalloc(h, &h->mA, sv))) return rc;
+  if ((rc = dalloc(h, &h->mB, sv))) return rc;
+  if ((rc = dalloc(h, &h->acc, sv))) return rc;
+  if ((rc = dalloc(h, &h->mF, sv))) return rc;
+  if ((rc = dalloc(h, &h->hin, su))) return rc;
+  if ((rc = dalloc(h, &h->hout, su))) return rc;
   if ((rc = dalloc(h, &p, sizeof(int)))) return rc;
   h->flag = (int*)p;
   d.flag = h->flag;
   PMFEM_CK(h, cudaMemset(h->flag, 0, sizeof(int)));
-  PMFEM_CK(h, cudaMemset(h->m, 0, sb));
+  PMFEM_CK(h, cudaMemset(h->m, 0, sv));
   return OK;
 }
 
@@ -213,7 +232,7 @@ int ensure_device(pmfem_t h) {
 }
 
 template <typename T>
-void enqueue_eval(pmfem_t h, DevOps<T>& d, const T* m, T* H, int comps, const RkArgs& rk, cudaStream_t st) {
+void enqueue_eval(pmfem_t h, DevOps<T>& d, const V4<T>* m, T* H, int comps, const RkArgs& rk, cudaStream_t st) {
   if (comps & PMFEM_MS) {
     d.prof.begin(KID_MEMSET, st);
     cudaMemsetAsync(d.grid, 0, sizeof(T) * (size_t)d.dims[0] * d.dims[1] * d.dims[2], st);
@@ -235,9 +254,9 @@ int check_launch(pmfem_t h) {
 template <typename T>
 int run_llg(pmfem_t h, DevOps<T>& d, double dt, int nsteps, cudaStream_t st) {
   const double gam = kMu0 * kGammaE / (1.0 + h->s.alpha * h->s.alpha);
-  T* m = (T*)h->m;
-  T* A = (T*)h->mA;
-  T* B = (T*)h->mB;
+  V4<T>* m = (V4<T>*)h->m;
+  V4<T>* A = (V4<T>*)h->mA;
+  V4<T>* B = (V4<T>*)h->mB;
   for (int n = 0; n < nsteps; ++n) {
     RkArgs rk;
     rk.m0 = m;
@@ -246,14 +265,14 @@ int run_llg(pmfem_t h, DevOps<T>& d, double dt, int nsteps, cudaStream_t st) {
     rk.alpha = h->s.alpha;
     rk.mode = 1;
     rk.cdt = 0.5 * dt, rk.bw = 1.0, rk.acc_init = 1, rk.mnext = A;
-    enqueue_eval(h, d, m, (T*)nullptr, PMFEM_ALL, rk, st);
+    enqueue_eval(h, d, (const V4<T>*)m, (T*)nullptr, PMFEM_ALL, rk, st);
     rk.cdt = 0.5 * dt, rk.bw = 2.0, rk.acc_init = 0, rk.mnext = B;
-    enqueue_eval(h, d, (const T*)A, (T*)nullptr, PMFEM_ALL, rk, st);
+    enqueue_eval(h, d, (const V4<T>*)A, (T*)nullptr, PMFEM_ALL, rk, st);
     rk.cdt = dt, rk.bw = 2.0, rk.acc_init = 0, rk.mnext = A;
-    enqueue_eval(h, d, (const T*)B, (T*)nullptr, PMFEM_ALL, rk, st);
+    enqueue_eval(h, d, (const V4<T>*)B, (T*)nullptr, PMFEM_ALL, rk, st);
     rk.mode = 2;
     rk.dt6 = dt / 6.0;
-    enqueue_eval(h, d, (const T*)A, (T*)nullptr, PMFEM_ALL, rk, st);
+    enqueue_eval(h, d, (const V4<T>*)A, (T*)nullptr, PMFEM_ALL, rk, st);
     int rc = check_launch(h);
     if (rc) return rc;
   }
@@ -377,8 +396,13 @@ int pmfem_field(pmfem_t h, const void* m, void* H, int components, void* stream)
   if (rc) return rc;
   cudaStream_t st = stream ? (cudaStream_t)stream : h->stream;
   RkArgs none;
-  if (h->dev_prec == PMFEM_FP64) enqueue_eval(h, h->d64, (const double*)m, (double*)H, components, none, st);
-  else enqueue_eval(h, h->d32, (const float*)m, (float*)H, components, none, st);
+  if (h->dev_prec == PMFEM_FP64) {
+    launch_perm_in(h->d64, (const double*)m, (V4<double>*)h->mF, st);
+    enqueue_eval(h, h->d64, (const V4<double>*)h->mF, (double*)H, components, none, st);
+  } else {
+    launch_perm_in(h->d32, (const float*)m, (V4<float>*)h->mF, st);
+    enqueue_eval(h, h->d32, (const V4<float>*)h->mF, (float*)H, components, none, st);
+  }
   return check_launch(h);
 }
 
@@ -389,10 +413,10 @@ int pmfem_field_host(pmfem_t h, const void* m_host, void* H_host, int components
   if (rc) return rc;
   cudaStream_t st = stream ? (cudaStream_t)stream : h->stream;
   const size_t bytes = 3 * (size_t)h->s.Np * elem_size(h);
-  PMFEM_CK(h, cudaMemcpyAsync(h->mA, m_host, bytes, cudaMemcpyHostToDevice, st));
-  rc = pmfem_field(h, h->mA, h->hbuf, components, st);
+  PMFEM_CK(h, cudaMemcpyAsync(h->hin, m_host, bytes, cudaMemcpyHostToDevice, st));
+  rc = pmfem_field(h, h->hin, h->hout, components, st);
   if (rc) return rc;
-  PMFEM_CK(h, cudaMemcpyAsync(H_host, h->hbuf, bytes, cudaMemcpyDeviceToHost, st));
+  PMFEM_CK(h, cudaMemcpyAsync(H_host, h->hout, bytes, cudaMemcpyDeviceToHost, st));
   PMFEM_CK(h, cudaStreamSynchronize(st));
   return OK;
 }
@@ -402,8 +426,9 @@ int pmfem_set_m(pmfem_t h, const void* m, void* stream) {
   int rc = ensure_device(h);
   if (rc) return rc;
   cudaStream_t st = stream ? (cudaStream_t)stream : h->stream;
-  PMFEM_CK(h, cudaMemcpyAsync(h->m, m, 3 * (size_t)h->s.Np * elem_size(h), cudaMemcpyDeviceToDevice, st));
-  return OK;
+  if (h->dev_prec == PMFEM_FP64) launch_perm_in(h->d64, (const double*)m, (V4<double>*)h->m, st);
+  else launch_perm_in(h->d32, (const float*)m, (V4<float>*)h->m, st);
+  return check_launch(h);
 }
 
 int pmfem_get_m(pmfem_t h, void* m, void* stream) {
@@ -411,8 +436,9 @@ int pmfem_get_m(pmfem_t h, void* m, void* stream) {
   int rc = ensure_device(h);
   if (rc) return rc;
   cudaStream_t st = stream ? (cudaStream_t)stream : h->stream;
-  PMFEM_CK(h, cudaMemcpyAsync(m, h->m, 3 * (size_t)h->s.Np * elem_size(h), cudaMemcpyDeviceToDevice, st));
-  return OK;
+  if (h->dev_prec == PMFEM_FP64) launch_perm_out(h->d64, (const V4<double>*)h->m, (double*)m, st);
+  else launch_perm_out(h->d32, (const V4<float>*)h->m, (float*)m, st);
+  return check_launch(h);
 }
 
 int pmfem_llg_step(pmfem_t h, double dt, int nsteps, void* stream) {
@@ -432,6 +458,7 @@ int pmfem_sync(pmfem_t h) {
   PMFEM_CK(h, cudaMemcpy(&flag, h->flag, sizeof(int), cudaMemcpyDeviceToHost));
   if (flag) {
     PMFEM_CK(h, cudaMemset(h->flag, 0, sizeof(int)));
+    if (flag & FLAG_LAYOUT) return fail(h, EINVAL_, "precorrection layout check failed on the device");
     return fail(h, ENONFINITE_, (flag & FLAG_NONFINITE_IN) ? "non-finite magnetisation input"
                                                           : "non-finite field result");
   }

@@ -10,9 +10,15 @@ template <typename T> struct Vec2;
 template <> struct Vec2<double> { using type = double2; };
 template <> struct Vec2<float> { using type = float2; };
 
+// internal magnetisation / state vectors: (x, y, z, pad), one aligned load per gather
+template <typename T>
+struct alignas(4 * sizeof(T)) V4 {
+  T x, y, z, w;
+};
+
 // Optional per-launch timing: the handle records a CUDA event pair around each kernel.
 enum KernelId : int { KID_CHARGES = 0, KID_ANTERP, KID_FFT_X_FWD, KID_FFT_Y_FWD, KID_FFT_Z_CONV, KID_FFT_Y_INV,
-                      KID_FFT_X_INV, KID_INTERP, KID_FIELD, KID_MEMSET, KID_COUNT };
+                      KID_FFT_X_INV, KID_INTERP, KID_FIELD, KID_MEMSET, KID_PERM, KID_COUNT };
 struct ProfHook {
   void (*fn)(void* ctx, int id, int phase, cudaStream_t st) = nullptr;
   void* ctx = nullptr;
@@ -24,14 +30,18 @@ struct ProfHook {
   }
 };
 
-// Operator values, grid set-up and work buffers of one precision, all device memory.
+// Operator values, grid set-up and work buffers of one precision, all device memory,
+// in the internal (box-sorted) order of the unknowns.
 template <typename T>
 struct DevOps {
   using C2 = typename Vec2<T>::type;
   int64_t Np = 0, nnz = 0, nnzC = 0, nnzX = 0;
-  int p = 3;
+  int p = 3, nb = 3;
   int dims[3] = {0, 0, 0}, fft[3] = {0, 0, 0};
   bool periodic[3] = {false, false, false};
+  int TY = 1, TZ = 1, pl = 1, pr = 2;
+  bool tiled = false;
+  const int32_t* perm = nullptr;                  // internal -> user unknown
   // adjacency pattern (shared by charges, near-element, gradient and exchange values)
   const int32_t* rowptr = nullptr;
   const int32_t* col = nullptr;
@@ -39,10 +49,12 @@ struct DevOps {
   const T* ea[3] = {nullptr, nullptr, nullptr};   // Ms E (touching elements)
   const T* gr[3] = {nullptr, nullptr, nullptr};   // -(W^q)^T / (4 pi V)
   const T* kp = nullptr;                          // exchange, scaled
-  // point precorrection C and near-element entries outside the pattern
-  const int32_t* rowptrC = nullptr;
-  const int32_t* colC = nullptr;
-  const T* valC = nullptr;
+  // point precorrection: values only, sources enumerated from the box structure
+  const int32_t* box = nullptr;                   // Np x 3
+  const int32_t* bstart = nullptr;                // boxes + 1
+  const int64_t* cptr = nullptr;                  // Np + 1
+  const T* cval = nullptr;
+  // near-element entries beyond the pattern
   const int32_t* rowptrX = nullptr;
   const int32_t* colX = nullptr;
   const T* valX = nullptr;                        // nnzX x 3
@@ -62,7 +74,7 @@ struct DevOps {
 };
 
 // error word bits
-enum : int { FLAG_NONFINITE_IN = 1, FLAG_NONFINITE_OUT = 2 };
+enum : int { FLAG_NONFINITE_IN = 1, FLAG_NONFINITE_OUT = 2, FLAG_LAYOUT = 4 };
 
 // RK4 epilogue of the field kernel (mode 0: plain field output)
 struct RkArgs {
@@ -78,12 +90,17 @@ struct RkArgs {
   double alpha = 0;
 };
 
-template <typename T> void launch_charges(const DevOps<T>& d, const T* m, cudaStream_t st);
+// m_user: N' x 3 in the C-ABI unknown order; m: internal 4-vectors
+template <typename T> void launch_perm_in(const DevOps<T>& d, const T* m_user, V4<T>* m, cudaStream_t st);
+template <typename T> void launch_perm_out(const DevOps<T>& d, const V4<T>* m, T* m_user, cudaStream_t st);
+template <typename T> void launch_charges(const DevOps<T>& d, const V4<T>* m, cudaStream_t st);
 template <typename T> void launch_anterp(const DevOps<T>& d, cudaStream_t st);
 template <typename T> void launch_fft_conv(const DevOps<T>& d, cudaStream_t st);
-template <typename T> void launch_interp(const DevOps<T>& d, const T* m, cudaStream_t st);
+template <typename T> void launch_interp(const DevOps<T>& d, const V4<T>* m, cudaStream_t st);
+// mode 0 writes H in the C-ABI order (N' x 3); RK modes update internal 4-vector buffers
 template <typename T>
-void launch_field(const DevOps<T>& d, const T* m, T* H, int comps, double hx, double hy, double hz,
+void launch_field(const DevOps<T>& d, const V4<T>* m, T* H_user, int comps, double hx, double hy, double hz,
                   const RkArgs& rk, cudaStream_t st);
+size_t anterp_smem_budget();
 
 }  // namespace pmfem

@@ -72,8 +72,33 @@ struct Setup {
   std::vector<int32_t> base;         // Np x 3 unwrapped stencil start
   std::vector<double> frac;          // Np x 3 local coordinate s = t - base
   std::vector<double> ghat;          // (F0/2+1)(F1/2+1)(F2/2+1), x fastest, unscaled
+  std::vector<int32_t> box;          // Np x 3 grid box of each unknown (folded position)
   bool ready = false;
 };
+
+// Device-side layout: unknowns re-ordered by grid box so that the precorrection sources
+// of a row are a few contiguous node ranges and projection works tile by tile.
+// Box order: tiles of TY rows x TZ planes (y, z); inside a tile z, then y, then x fastest.
+struct Layout {
+  int TY = 1, TZ = 1;
+  int pl = 1, pr = 2;                // stencil reach below / above a node's box
+  bool tiled = false;                // tile-local projection fits in shared memory
+  std::vector<int32_t> perm;         // internal -> user unknown
+  std::vector<int32_t> box;          // Np x 3, internal order
+  std::vector<int32_t> bstart;       // (boxes + 1): first internal node of each box
+  std::vector<int32_t> rowptr, col;  // adjacency, internal numbering
+  std::vector<double> Wq, Ea, Gr, Kp;
+  std::vector<int32_t> base;
+  std::vector<double> frac;
+  std::vector<int64_t> cptr;         // Np + 1: start of each row's precorrection values
+  std::vector<double> cval;          // values in (dz, dy, x-segment, node) order
+  Csr Ex;                            // near-element entries beyond the pattern, internal
+  int64_t box_index(int x, int y, int z, const int N[3]) const {
+    const int ty = y / TY, yi = y % TY, tz = z / TZ, zi = z % TZ;
+    return ((((int64_t)tz * (N[1] / TY) + ty) * TZ + zi) * TY + yi) * N[0] + x;
+  }
+};
+int build_layout(const Setup& s, Layout& L, size_t smem_budget, size_t elem_bytes, Error& err);
 
 // set-up stages (host, FP64); each returns a Status and fills err on failure
 int setup_validate_mesh(Setup& s, Error& err);

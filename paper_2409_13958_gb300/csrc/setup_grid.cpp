@@ -164,6 +164,7 @@ int setup_precorrection(Setup& s, Error& err) {
       b = std::max<int64_t>(0, std::min<int64_t>(b, s.dims[a] - 1));
       box[3 * u + a] = (int32_t)b;
     }
+  s.box = box;
   const int64_t nbox = (int64_t)N0 * N1 * N2;
   std::vector<int64_t> bptr(nbox + 1, 0);
   auto lin = [&](int64_t x, int64_t y, int64_t z) { return x + (int64_t)N0 * (y + (int64_t)N1 * z); };
