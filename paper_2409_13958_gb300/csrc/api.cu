@@ -134,7 +134,7 @@ int build_device(pmfem_t h, DevOps<T>& d) {
   Layout L;
   {
     Error err;
-    int rc = build_layout(s, L, anterp_smem_budget(), sizeof(T), err);
+    int rc = build_layout(s, L, 96 * 1024, sizeof(T), err);
     if (rc) return fail(h, rc, err.msg);
   }
   int rc;
@@ -148,25 +148,32 @@ int build_device(pmfem_t h, DevOps<T>& d) {
   d.TZ = L.TZ;
   d.pl = L.pl;
   d.pr = L.pr;
-  d.tiled = L.tiled;
   for (int a = 0; a < 3; ++a) {
     d.dims[a] = s.dims[a];
     d.fft[a] = s.fft[a];
     d.periodic[a] = s.periodic[a];
   }
+  const size_t ns = L.col_s.size();
   if ((rc = upload(h, L.perm.data(), L.perm.size(), &d.perm))) return rc;
-  if ((rc = upload(h, L.rowptr.data(), L.rowptr.size(), &d.rowptr))) return rc;
-  if ((rc = upload(h, L.col.data(), L.col.size(), &d.col))) return rc;
+  if ((rc = upload(h, L.len.data(), L.len.size(), &d.len))) return rc;
+  if ((rc = upload(h, L.sell_off.data(), L.sell_off.size(), &d.sell_off))) return rc;
+  if ((rc = upload(h, L.col_s.data(), ns, &d.col))) return rc;
   for (int c = 0; c < 3; ++c) {
-    if ((rc = upload_conv<T>(h, L.Wq.data(), d.nnz, 3, c, 1.0, &d.wq[c]))) return rc;
-    if ((rc = upload_conv<T>(h, L.Ea.data(), d.nnz, 3, c, 1.0, &d.ea[c]))) return rc;
-    if ((rc = upload_conv<T>(h, L.Gr.data(), d.nnz, 3, c, 1.0, &d.gr[c]))) return rc;
+    if ((rc = upload_conv<T>(h, L.Wq_s.data() + c * ns, ns, 1, 0, 1.0, &d.wq[c]))) return rc;
+    if ((rc = upload_conv<T>(h, L.Ea_s.data() + c * ns, ns, 1, 0, 1.0, &d.ea[c]))) return rc;
+    if ((rc = upload_conv<T>(h, L.Gr_s.data() + c * ns, ns, 1, 0, 1.0, &d.gr[c]))) return rc;
   }
-  if ((rc = upload_conv<T>(h, L.Kp.data(), d.nnz, 1, 0, 1.0, &d.kp))) return rc;
+  if ((rc = upload_conv<T>(h, L.Kp_s.data(), ns, 1, 0, 1.0, &d.kp))) return rc;
   if ((rc = upload(h, L.box.data(), L.box.size(), &d.box))) return rc;
   if ((rc = upload(h, L.bstart.data(), L.bstart.size(), &d.bstart))) return rc;
-  if ((rc = upload(h, L.cptr.data(), L.cptr.size(), &d.cptr))) return rc;
-  if ((rc = upload_conv<T>(h, L.cval.data(), L.cval.size(), 1, 0, 1.0, &d.cval))) return rc;
+  if ((rc = upload(h, L.csell_off.data(), L.csell_off.size(), &d.csell_off))) return rc;
+  if ((rc = upload_conv<T>(h, L.cval_s.data(), L.cval_s.size(), 1, 0, 1.0, &d.cval))) return rc;
+  if ((rc = upload(h, L.psell_off.data(), L.psell_off.size(), &d.psell_off))) return rc;
+  if ((rc = upload_conv<T>(h, L.pw_s.data(), L.pw_s.size(), 1, 0, 1.0, &d.pw))) return rc;
+  d.nx_exc = (int64_t)L.xnode.size();
+  if ((rc = upload(h, L.xnode.data(), L.xnode.size(), &d.xnode))) return rc;
+  if ((rc = upload(h, L.xgrid.data(), L.xgrid.size(), &d.xgrid))) return rc;
+  if ((rc = upload_conv<T>(h, L.xw.data(), L.xw.size(), 1, 0, 1.0, &d.xw))) return rc;
   if ((rc = upload(h, L.Ex.rowptr.data(), L.Ex.rowptr.size(), &d.rowptrX))) return rc;
   if ((rc = upload(h, L.Ex.col.data(), L.Ex.col.size(), &d.colX))) return rc;
   if ((rc = upload_conv<T>(h, L.Ex.vals.data(), L.Ex.vals.size(), 1, 0, 1.0, &d.valX))) return rc;
@@ -234,9 +241,6 @@ int ensure_device(pmfem_t h) {
 template <typename T>
 void enqueue_eval(pmfem_t h, DevOps<T>& d, const V4<T>* m, T* H, int comps, const RkArgs& rk, cudaStream_t st) {
   if (comps & PMFEM_MS) {
-    d.prof.begin(KID_MEMSET, st);
-    cudaMemsetAsync(d.grid, 0, sizeof(T) * (size_t)d.dims[0] * d.dims[1] * d.dims[2], st);
-    d.prof.end(KID_MEMSET, st);
     launch_charges(d, m, st);
     launch_anterp(d, st);
     launch_fft_conv(d, st);

@@ -40,20 +40,28 @@ struct DevOps {
   int dims[3] = {0, 0, 0}, fft[3] = {0, 0, 0};
   bool periodic[3] = {false, false, false};
   int TY = 1, TZ = 1, pl = 1, pr = 2;
-  bool tiled = false;
   const int32_t* perm = nullptr;                  // internal -> user unknown
-  // adjacency pattern (shared by charges, near-element, gradient and exchange values)
-  const int32_t* rowptr = nullptr;
+  // adjacency pattern (shared by charges, near-element, gradient and exchange values) in
+  // SELL-32: element j of row i at sell_off[i/32] + 32 j + i%32
+  const int32_t* len = nullptr;
+  const int64_t* sell_off = nullptr;
   const int32_t* col = nullptr;
   const T* wq[3] = {nullptr, nullptr, nullptr};   // Ms W^q
   const T* ea[3] = {nullptr, nullptr, nullptr};   // Ms E (touching elements)
   const T* gr[3] = {nullptr, nullptr, nullptr};   // -(W^q)^T / (4 pi V)
   const T* kp = nullptr;                          // exchange, scaled
-  // point precorrection: values only, sources enumerated from the box structure
+  // point precorrection: values only (SELL-32), sources enumerated from the box structure
   const int32_t* box = nullptr;                   // Np x 3
   const int32_t* bstart = nullptr;                // boxes + 1
-  const int64_t* cptr = nullptr;                  // Np + 1
+  const int64_t* csell_off = nullptr;
   const T* cval = nullptr;
+  // projection gather weights (SELL-32 over grid points) and the exception list
+  const int64_t* psell_off = nullptr;
+  const T* pw = nullptr;
+  int64_t nx_exc = 0;
+  const int32_t* xnode = nullptr;
+  const int64_t* xgrid = nullptr;
+  const T* xw = nullptr;
   // near-element entries beyond the pattern
   const int32_t* rowptrX = nullptr;
   const int32_t* colX = nullptr;
@@ -101,6 +109,6 @@ template <typename T> void launch_interp(const DevOps<T>& d, const V4<T>* m, cud
 template <typename T>
 void launch_field(const DevOps<T>& d, const V4<T>* m, T* H_user, int comps, double hx, double hy, double hz,
                   const RkArgs& rk, cudaStream_t st);
-size_t anterp_smem_budget();
+
 
 }  // namespace pmfem

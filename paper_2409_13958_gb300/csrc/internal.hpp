@@ -93,6 +93,23 @@ struct Layout {
   std::vector<int64_t> cptr;         // Np + 1: start of each row's precorrection values
   std::vector<double> cval;          // values in (dz, dy, x-segment, node) order
   Csr Ex;                            // near-element entries beyond the pattern, internal
+  // SELL-32 copies for one-thread-per-row kernels: element j of row i sits at
+  // off[i / 32] + 32 j + i % 32 (rows of a chunk padded to the chunk's longest row)
+  std::vector<int64_t> sell_off;     // chunks + 1, adjacency
+  std::vector<int32_t> len;          // Np adjacency row lengths
+  std::vector<int32_t> col_s;        // padded with the row's own index
+  std::vector<double> Wq_s, Ea_s, Gr_s, Kp_s;   // SoA per component: [comp][padded nnz]
+  std::vector<int64_t> csell_off;    // chunks + 1, precorrection values
+  std::vector<double> cval_s;
+  // projection as a gather: grid point g (natural grid order) sums w * q over the nodes of
+  // the box rows [g - pr, g + pl]^2 (y, z) and boxes [gx - pr, gx + pl]; weights SELL-32
+  // over grid points; nodes whose stencil does not start at box - pl go to an exception
+  // list added with atomics afterwards
+  std::vector<int64_t> psell_off;    // grid chunks + 1
+  std::vector<double> pw_s;
+  std::vector<int32_t> xnode;        // exceptions: node, grid index, weight
+  std::vector<int64_t> xgrid;
+  std::vector<double> xw;
   int64_t box_index(int x, int y, int z, const int N[3]) const {
     const int ty = y / TY, yi = y % TY, tz = z / TZ, zi = z % TZ;
     return ((((int64_t)tz * (N[1] / TY) + ty) * TZ + zi) * TY + yi) * N[0] + x;

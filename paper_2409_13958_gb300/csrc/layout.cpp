@@ -201,6 +201,144 @@ int build_layout(const Setup& s, Layout& L, size_t smem_budget, size_t elem_byte
       err = {EINVAL_, "precorrection layout does not cover row " + std::to_string(i)};
       return EINVAL_;
     }
+  // SELL-32 copies
+  const int64_t nch = (Np + 31) / 32;
+  L.len.resize(Np);
+  for (int64_t i = 0; i < Np; ++i) L.len[i] = L.rowptr[i + 1] - L.rowptr[i];
+  L.sell_off.assign(nch + 1, 0);
+  L.csell_off.assign(nch + 1, 0);
+  for (int64_t c = 0; c < nch; ++c) {
+    int64_t w = 0, wc = 0;
+    for (int64_t i = 32 * c; i < std::min<int64_t>(Np, 32 * c + 32); ++i) {
+      w = std::max<int64_t>(w, L.len[i]);
+      wc = std::max<int64_t>(wc, L.cptr[i + 1] - L.cptr[i]);
+    }
+    L.sell_off[c + 1] = L.sell_off[c] + 32 * w;
+    L.csell_off[c + 1] = L.csell_off[c] + 32 * wc;
+  }
+  const int64_t ns = L.sell_off[nch], ncs = L.csell_off[nch];
+  L.col_s.assign(ns, 0);
+  L.Wq_s.assign(3 * ns, 0.0);
+  L.Ea_s.assign(3 * ns, 0.0);
+  L.Gr_s.assign(3 * ns, 0.0);
+  L.Kp_s.assign(ns, 0.0);
+  L.cval_s.assign(ncs, 0.0);
+  parallel_for(nch, [&](int64_t b, int64_t e) {
+    for (int64_t c = b; c < e; ++c) {
+      const int64_t w = (L.sell_off[c + 1] - L.sell_off[c]) / 32;
+      for (int64_t i = 32 * c; i < std::min<int64_t>(Np, 32 * c + 32); ++i) {
+        const int64_t lane = i - 32 * c;
+        for (int64_t j = 0; j < w; ++j) {
+          const int64_t o = L.sell_off[c] + 32 * j + lane;
+          if (j < L.len[i]) {
+            const int64_t q = L.rowptr[i] + j;
+            L.col_s[o] = L.col[q];
+            L.Kp_s[o] = L.Kp[q];
+            for (int d = 0; d < 3; ++d) {
+              L.Wq_s[d * ns + o] = L.Wq[3 * q + d];
+              L.Ea_s[d * ns + o] = L.Ea[3 * q + d];
+              L.Gr_s[d * ns + o] = L.Gr[3 * q + d];
+            }
+          } else {
+            L.col_s[o] = (int32_t)i;
+          }
+        }
+        for (int64_t j = 0; j < L.cptr[i + 1] - L.cptr[i]; ++j)
+          L.cval_s[L.csell_off[c] + 32 * j + lane] = L.cval[L.cptr[i] + j];
+      }
+    }
+  }, 256);
+
+  // projection gather weights
+  auto lagr = [&](double sv, int i) {
+    double v = 1.0;
+    for (int j = 0; j <= p; ++j)
+      if (j != i) v *= (sv - j) / (double)(i - j);
+    return v;
+  };
+  std::vector<char> regular(Np, 1);
+  for (int64_t i = 0; i < Np; ++i)
+    for (int a = 0; a < 3; ++a) {
+      const int d = L.base[3 * i + a] - (L.box[3 * i + a] - L.pl);
+      if (!(d == 0 || (p % 2 == 0 && d == 1))) regular[i] = 0;
+    }
+  auto for_pull = [&](int gx, int gy, int gz, auto&& fn) {
+    for (int bz = gz - L.pr; bz <= gz + L.pl; ++bz) {
+      int z = bz;
+      if (!wrap_axis(z, N[2], s.periodic[2])) continue;
+      for (int by = gy - L.pr; by <= gy + L.pl; ++by) {
+        int y = by;
+        if (!wrap_axis(y, N[1], s.periodic[1])) continue;
+        int lo = gx - L.pr, hi = gx + L.pl, lo2 = 0, hi2 = -1;
+        if (!s.periodic[0]) {
+          lo = std::max(lo, 0);
+          hi = std::min(hi, N[0] - 1);
+        } else if (lo < 0) {
+          lo2 = 0, hi2 = hi, lo = lo + N[0], hi = N[0] - 1;
+        } else if (hi >= N[0]) {
+          lo2 = 0, hi2 = hi - N[0], hi = N[0] - 1;
+        }
+        if (lo <= hi) fn(L.bstart[L.box_index(lo, y, z, N)], L.bstart[L.box_index(hi, y, z, N) + 1]);
+        if (lo2 <= hi2) fn(L.bstart[L.box_index(lo2, y, z, N)], L.bstart[L.box_index(hi2, y, z, N) + 1]);
+      }
+    }
+  };
+  const int64_t G = (int64_t)N[0] * N[1] * N[2];
+  const int64_t gch = (G + 31) / 32;
+  std::vector<int32_t> glen(G);
+  parallel_for(G, [&](int64_t b, int64_t e) {
+    for (int64_t g = b; g < e; ++g) {
+      int64_t n = 0;
+      for_pull((int)(g % N[0]), (int)((g / N[0]) % N[1]), (int)(g / ((int64_t)N[0] * N[1])),
+               [&](int64_t k0, int64_t k1) { n += k1 - k0; });
+      glen[g] = (int32_t)n;
+    }
+  }, 4096);
+  L.psell_off.assign(gch + 1, 0);
+  for (int64_t c = 0; c < gch; ++c) {
+    int64_t w = 0;
+    for (int64_t g = 32 * c; g < std::min<int64_t>(G, 32 * c + 32); ++g) w = std::max<int64_t>(w, glen[g]);
+    L.psell_off[c + 1] = L.psell_off[c] + 32 * w;
+  }
+  L.pw_s.assign(L.psell_off[gch], 0.0);
+  parallel_for(G, [&](int64_t b, int64_t e) {
+    for (int64_t g = b; g < e; ++g) {
+      const int gc[3] = {(int)(g % N[0]), (int)((g / N[0]) % N[1]), (int)(g / ((int64_t)N[0] * N[1]))};
+      int64_t o = L.psell_off[g / 32] + (g % 32);
+      for_pull(gc[0], gc[1], gc[2], [&](int64_t k0, int64_t k1) {
+        for (int64_t k = k0; k < k1; ++k, o += 32) {
+          if (!regular[k]) continue;
+          double w = 1.0;
+          for (int a = 0; a < 3; ++a) {
+            int i = gc[a] - L.base[3 * k + a];
+            if (s.periodic[a]) i = ((i % N[a]) + N[a]) % N[a];
+            if (i < 0 || i > p) {
+              w = 0.0;
+              break;
+            }
+            w *= lagr(L.frac[3 * k + a], i);
+          }
+          L.pw_s[o] = w;
+        }
+      });
+    }
+  }, 4096);
+  L.xnode.clear();
+  L.xgrid.clear();
+  L.xw.clear();
+  for (int64_t k = 0; k < Np; ++k) {
+    if (regular[k]) continue;
+    for (int c = 0; c <= p; ++c)
+      for (int bj = 0; bj <= p; ++bj)
+        for (int ai = 0; ai <= p; ++ai) {
+          int gi[3] = {L.base[3 * k] + ai, L.base[3 * k + 1] + bj, L.base[3 * k + 2] + c};
+          for (int a = 0; a < 3; ++a)
+            if (s.periodic[a]) gi[a] = ((gi[a] % N[a]) + N[a]) % N[a];
+          L.xnode.push_back((int32_t)k);
+          L.xgrid.push_back(gi[0] + (int64_t)N[0] * (gi[1] + (int64_t)N[1] * gi[2]));
+          L.xw.push_back(lagr(L.frac[3 * k], ai) * lagr(L.frac[3 * k + 1], bj) * lagr(L.frac[3 * k + 2], c));
+        }
+  }
   return OK;
 }
 

@@ -38,15 +38,15 @@ int setup_grid(Setup& s, Error& err) {
       double span = s.periodic[a] ? s.L[a] : (hi - lo);
       N = (int)std::ceil(2.0 * span / s.mean_edge);
       if (!s.periodic[a]) N += 1 + 2 * m;
-      N = std::max(N, s.periodic[a] ? 2 * s.near_boxes + 2 : 2 * m + 2);
+      N = std::max(N, s.periodic[a] ? std::max(2 * s.near_boxes + 2, s.p + 2) : 2 * m + 2);
       N = next_pow2(N);
       if (!s.periodic[a]) N = std::max(4, N);
       N = std::min(N, s.periodic[a] ? 1024 : 512);
     }
     s.dims[a] = N;
     if (s.periodic[a]) {
-      if (N < 2 * s.near_boxes + 2) {
-        err = {EINVAL_, "periodic grid axis needs N >= 2*near_boxes + 2"};
+      if (N < 2 * s.near_boxes + 2 || N < s.p + 2) {
+        err = {EINVAL_, "periodic grid axis needs N >= 2*near_boxes + 2 and N >= p + 2"};
         return EINVAL_;
       }
       s.delta[a] = s.L[a] / N;
