@@ -168,8 +168,12 @@ int build_device(pmfem_t h, DevOps<T>& d) {
   if ((rc = upload(h, L.bstart.data(), L.bstart.size(), &d.bstart))) return rc;
   if ((rc = upload(h, L.csell_off.data(), L.csell_off.size(), &d.csell_off))) return rc;
   if ((rc = upload_conv<T>(h, L.cval_s.data(), L.cval_s.size(), 1, 0, 1.0, &d.cval))) return rc;
+  if ((rc = upload(h, L.ccol_s.data(), L.ccol_s.size(), &d.ccol))) return rc;
+  if ((rc = upload(h, L.clen.data(), L.clen.size(), &d.clen))) return rc;
   if ((rc = upload(h, L.psell_off.data(), L.psell_off.size(), &d.psell_off))) return rc;
   if ((rc = upload_conv<T>(h, L.pw_s.data(), L.pw_s.size(), 1, 0, 1.0, &d.pw))) return rc;
+  if ((rc = upload(h, L.pcol_s.data(), L.pcol_s.size(), &d.pcol))) return rc;
+  if ((rc = upload(h, L.plen.data(), L.plen.size(), &d.plen))) return rc;
   d.nx_exc = (int64_t)L.xnode.size();
   if ((rc = upload(h, L.xnode.data(), L.xnode.size(), &d.xnode))) return rc;
   if ((rc = upload(h, L.xgrid.data(), L.xgrid.size(), &d.xgrid))) return rc;

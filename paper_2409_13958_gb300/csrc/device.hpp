@@ -54,9 +54,13 @@ struct DevOps {
   const int32_t* box = nullptr;                   // Np x 3
   const int32_t* bstart = nullptr;                // boxes + 1
   const int64_t* csell_off = nullptr;
+  const int32_t* clen = nullptr;
+  const int32_t* ccol = nullptr;
   const T* cval = nullptr;
   // projection gather weights (SELL-32 over grid points) and the exception list
   const int64_t* psell_off = nullptr;
+  const int32_t* plen = nullptr;
+  const int32_t* pcol = nullptr;
   const T* pw = nullptr;
   int64_t nx_exc = 0;
   const int32_t* xnode = nullptr;

@@ -100,12 +100,16 @@ struct Layout {
   std::vector<int32_t> col_s;        // padded with the row's own index
   std::vector<double> Wq_s, Ea_s, Gr_s, Kp_s;   // SoA per component: [comp][padded nnz]
   std::vector<int64_t> csell_off;    // chunks + 1, precorrection values
+  std::vector<int32_t> clen;         // Np row lengths
+  std::vector<int32_t> ccol_s;       // source node of each value (padding: the row itself)
   std::vector<double> cval_s;
   // projection as a gather: grid point g (natural grid order) sums w * q over the nodes of
   // the box rows [g - pr, g + pl]^2 (y, z) and boxes [gx - pr, gx + pl]; weights SELL-32
   // over grid points; nodes whose stencil does not start at box - pl go to an exception
   // list added with atomics afterwards
   std::vector<int64_t> psell_off;    // grid chunks + 1
+  std::vector<int32_t> plen;         // G entries per grid point
+  std::vector<int32_t> pcol_s;       // node of each weight (padding: node 0, weight 0)
   std::vector<double> pw_s;
   std::vector<int32_t> xnode;        // exceptions: node, grid index, weight
   std::vector<int64_t> xgrid;

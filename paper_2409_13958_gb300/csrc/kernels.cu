@@ -7,8 +7,8 @@
 // at the boundary); sparse rows in SELL-32, one thread per row, so that at every step j
 // the 32 threads of a warp read 32 consecutive values (one 128-byte segment in FP32) and
 // each thread has many independent loads in flight.  The projection is a gather: each
-// grid point sums over the nodes of its neighbouring box rows, so there are no atomics
-// (except for a short exception list) and the result is bitwise reproducible.
+// grid point sums over the nodes whose stencil covers it, so there are no atomics (except
+// for a short exception list) and the field is bitwise reproducible.
 #include <cmath>
 #include <cstdio>
 
@@ -47,42 +47,7 @@ __device__ __forceinline__ int wrap(int i, int N, bool per) {
   return i;
 }
 
-__device__ __forceinline__ bool wrap_in(int& v, int N, bool per) {
-  if (per) {
-    if (v < 0) v += N;
-    if (v >= N) v -= N;
-    return true;
-  }
-  return v >= 0 && v < N;
-}
 
-// linear index of the first box of box row (y, z) in the tiled box order
-__device__ __forceinline__ int64_t row_box(int y, int z, int N0, int N1, int TY, int TZ) {
-  return ((((int64_t)(z / TZ) * (N1 / TY) + y / TY) * TZ + z % TZ) * TY + y % TY) * N0;
-}
-
-// node ranges of the boxes [bx - a, bx + b] of one box row (two ranges after a periodic wrap)
-__device__ __forceinline__ void x_ranges(const int32_t* __restrict__ bstart, int64_t rb, int bx, int a, int b,
-                                         int N0, bool per, int& a0, int& a1, int& c0, int& c1) {
-  int lo = bx - a, hi = bx + b, lo2 = 0, hi2 = -1;
-  if (!per) {
-    lo = lo < 0 ? 0 : lo;
-    hi = hi > N0 - 1 ? N0 - 1 : hi;
-  } else if (lo < 0) {
-    lo2 = 0, hi2 = hi, lo = lo + N0, hi = N0 - 1;
-  } else if (hi >= N0) {
-    lo2 = 0, hi2 = hi - N0, hi = N0 - 1;
-  }
-  a0 = a1 = c0 = c1 = 0;
-  if (lo <= hi) {
-    a0 = bstart[rb + lo];
-    a1 = bstart[rb + hi + 1];
-  }
-  if (lo2 <= hi2) {
-    c0 = bstart[rb + lo2];
-    c1 = bstart[rb + hi2 + 1];
-  }
-}
 
 // ---------------------------------------------------------------- boundary permutations
 template <typename T>
@@ -136,38 +101,21 @@ __global__ void __launch_bounds__(kBlock) k_charges(int64_t Np, const int32_t* _
 }
 
 // ---------------------------------------------------------------- projection (step 1)
-// Grid point g receives from every node whose stencil covers it; those nodes lie in the
-// boxes [g - pr, g + pl] along each axis, i.e. (p+1)^2 box rows of (p+1) boxes.  The
-// stencil weights are precomputed in the same enumeration order.
+// Q = P^T q as a gather: grid point g (one thread, SELL-32 over grid points) sums w q over
+// the nodes whose stencil covers it (the nodes of the boxes [g - pr, g + pl] per axis,
+// enumerated at set-up).  No atomics: every grid value has one writer.
 template <typename T>
-__global__ void __launch_bounds__(kBlock) k_project(int N0, int N1, int N2, bool p0, bool p1, bool p2, int TY, int TZ,
-                                                   int pl, int pr, const int32_t* __restrict__ bstart,
-                                                   const int64_t* __restrict__ poff, const T* __restrict__ pw,
-                                                   const T* __restrict__ q, T* __restrict__ grid, int* flag) {
+__global__ void __launch_bounds__(kBlock) k_project(int64_t G, const int32_t* __restrict__ plen,
+                                                   const int64_t* __restrict__ poff, const int32_t* __restrict__ pcol,
+                                                   const T* __restrict__ pw, const T* __restrict__ q,
+                                                   T* __restrict__ grid) {
   const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int64_t G = (int64_t)N0 * N1 * N2;
   if (g >= G) return;
-  const int gx = (int)(g % N0), gy = (int)((g / N0) % N1), gz = (int)(g / ((int64_t)N0 * N1));
+  const int n = plen[g];
   int64_t o = poff[g >> 5] + (g & 31);
-  const int64_t o_end = poff[(g >> 5) + 1];
   T acc = 0;
-  for (int bz = gz - pr; bz <= gz + pl; ++bz) {
-    int z = bz;
-    if (!wrap_in(z, N2, p2)) continue;
-    for (int by = gy - pr; by <= gy + pl; ++by) {
-      int y = by;
-      if (!wrap_in(y, N1, p1)) continue;
-      int a0, a1, c0, c1;
-      x_ranges(bstart, row_box(y, z, N0, N1, TY, TZ), gx, pr, pl, N0, p0, a0, a1, c0, c1);
-      if (o + 32 * (int64_t)((a1 - a0) + (c1 - c0)) > o_end + 31) {   // layout disagreement
-        atomicOr(flag, FLAG_LAYOUT);
-        bz = gz + pl + 1;
-        break;
-      }
-      for (int k = a0; k < a1; ++k, o += 32) acc += pw[o] * q[k];
-      for (int k = c0; k < c1; ++k, o += 32) acc += pw[o] * q[k];
-    }
-  }
+#pragma unroll 4
+  for (int j = 0; j < n; ++j, o += 32) acc += pw[o] * q[pcol[o]];
   grid[g] = acc;
 }
 
@@ -182,14 +130,14 @@ __global__ void __launch_bounds__(kBlock) k_project_exc(int64_t n, const int32_t
 }
 
 // ---------------------------------------------------------------- interpolation + precorrection
-// One thread per observer row.  Precorrection sources are the nodes of the (2 nb + 1)^2
-// neighbouring box rows (contiguous node ranges); the row's values are stored in SELL-32
-// in (dz, dy, x-range, node) order, the order the host layout uses.
+// One thread per observer row: the (p+1)^3 stencil gathers from the grid potential, then
+// the row of the point precorrection (sources: the nodes of the boxes within near_boxes).
 template <typename T, int P>
 __global__ void __launch_bounds__(kBlock) k_interp(
     int64_t Np, const int32_t* __restrict__ box, const int32_t* __restrict__ base, const T* __restrict__ frac,
-    const T* __restrict__ U, int N0, int N1, int N2, bool p0, bool p1, bool p2, int nb, int TY, int TZ,
-    const int32_t* __restrict__ bstart, const int64_t* __restrict__ coff, const T* __restrict__ cval,
+    const T* __restrict__ U, int N0, int N1, int N2, bool p0, bool p1, bool p2,
+    const int32_t* __restrict__ clen, const int64_t* __restrict__ coff, const int32_t* __restrict__ ccol,
+    const T* __restrict__ cval,
     const int32_t* __restrict__ rowptrX, const int32_t* __restrict__ colX, const T* __restrict__ valX,
     const T* __restrict__ q, const T* __restrict__ e, const V4<T>* __restrict__ m, T* __restrict__ u, int* flag) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -217,27 +165,11 @@ __global__ void __launch_bounds__(kBlock) k_interp(
       }
     }
   }
-  {  // step 4: point precorrection over the neighbouring box rows
-    const int bx = box[3 * i], by = box[3 * i + 1], bz = box[3 * i + 2];
+  {  // step 4: point precorrection (SELL-32 row)
+    const int n = clen[i];
     int64_t o = coff[i >> 5] + (i & 31);
-    const int64_t o_end = coff[(i >> 5) + 1];
-    for (int dz = -nb; dz <= nb; ++dz) {
-      int z = bz + dz;
-      if (!wrap_in(z, N2, p2)) continue;
-      for (int dy = -nb; dy <= nb; ++dy) {
-        int y = by + dy;
-        if (!wrap_in(y, N1, p1)) continue;
-        int a0, a1, c0, c1;
-        x_ranges(bstart, row_box(y, z, N0, N1, TY, TZ), bx, nb, nb, N0, p0, a0, a1, c0, c1);
-        if (o + 32 * (int64_t)((a1 - a0) + (c1 - c0)) > o_end + 31) {   // layout disagreement
-          atomicOr(flag, FLAG_LAYOUT);
-          dz = nb + 1;
-          break;
-        }
-        for (int k = a0; k < a1; ++k, o += 32) acc += cval[o] * q[k];
-        for (int k = c0; k < c1; ++k, o += 32) acc += cval[o] * q[k];
-      }
-    }
+#pragma unroll 4
+    for (int j = 0; j < n; ++j, o += 32) acc += cval[o] * q[ccol[o]];
   }
   // near-element entries beyond the adjacency pattern
   for (int32_t p = rowptrX[i]; p < rowptrX[i + 1]; ++p) {
@@ -359,9 +291,7 @@ template <typename T>
 void launch_anterp(const DevOps<T>& d, cudaStream_t st) {
   d.prof.begin(KID_ANTERP, st);
   const int64_t G = (int64_t)d.dims[0] * d.dims[1] * d.dims[2];
-  k_project<T><<<blocks_for(G), kBlock, 0, st>>>(d.dims[0], d.dims[1], d.dims[2], d.periodic[0], d.periodic[1],
-                                                 d.periodic[2], d.TY, d.TZ, d.pl, d.pr, d.bstart, d.psell_off, d.pw,
-                                                 d.q, d.grid, d.flag);
+  k_project<T><<<blocks_for(G), kBlock, 0, st>>>(G, d.plen, d.psell_off, d.pcol, d.pw, d.q, d.grid);
   if (d.nx_exc > 0)
     k_project_exc<T><<<blocks_for(d.nx_exc), kBlock, 0, st>>>(d.nx_exc, d.xnode, d.xgrid, d.xw, d.q, d.grid);
   d.prof.end(KID_ANTERP, st);
@@ -373,9 +303,8 @@ void launch_interp(const DevOps<T>& d, const V4<T>* m, cudaStream_t st) {
   d.prof.begin(KID_INTERP, st);
 #define PMFEM_INTERP(PP)                                                                                      \
   k_interp<T, PP><<<nb, kBlock, 0, st>>>(d.Np, d.box, d.base, d.frac, d.grid, d.dims[0], d.dims[1], d.dims[2], \
-                                         d.periodic[0], d.periodic[1], d.periodic[2], d.nb, d.TY, d.TZ,          \
-                                         d.bstart, d.csell_off, d.cval, d.rowptrX, d.colX, d.valX, d.q, d.e, m,  \
-                                         d.u, d.flag)
+                                         d.periodic[0], d.periodic[1], d.periodic[2], d.clen, d.csell_off,       \
+                                         d.ccol, d.cval, d.rowptrX, d.colX, d.valX, d.q, d.e, m, d.u, d.flag)
   switch (d.p) {
     case 2: PMFEM_INTERP(3); break;
     case 3: PMFEM_INTERP(4); break;

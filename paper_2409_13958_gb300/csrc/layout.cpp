@@ -223,6 +223,9 @@ int build_layout(const Setup& s, Layout& L, size_t smem_budget, size_t elem_byte
   L.Gr_s.assign(3 * ns, 0.0);
   L.Kp_s.assign(ns, 0.0);
   L.cval_s.assign(ncs, 0.0);
+  L.ccol_s.assign(ncs, 0);
+  L.clen.resize(Np);
+  for (int64_t i = 0; i < Np; ++i) L.clen[i] = (int32_t)(L.cptr[i + 1] - L.cptr[i]);
   parallel_for(nch, [&](int64_t b, int64_t e) {
     for (int64_t c = b; c < e; ++c) {
       const int64_t w = (L.sell_off[c + 1] - L.sell_off[c]) / 32;
@@ -243,8 +246,15 @@ int build_layout(const Setup& s, Layout& L, size_t smem_budget, size_t elem_byte
             L.col_s[o] = (int32_t)i;
           }
         }
-        for (int64_t j = 0; j < L.cptr[i + 1] - L.cptr[i]; ++j)
-          L.cval_s[L.csell_off[c] + 32 * j + lane] = L.cval[L.cptr[i] + j];
+        const int64_t cw = (L.csell_off[c + 1] - L.csell_off[c]) / 32;
+        int64_t j = 0;
+        for_segments(i, [&](int64_t k0, int64_t k1) {
+          for (int64_t k = k0; k < k1; ++k, ++j) {
+            L.cval_s[L.csell_off[c] + 32 * j + lane] = L.cval[L.cptr[i] + j];
+            L.ccol_s[L.csell_off[c] + 32 * j + lane] = (int32_t)k;
+          }
+        });
+        for (; j < cw; ++j) L.ccol_s[L.csell_off[c] + 32 * j + lane] = (int32_t)i;
       }
     }
   }, 256);
@@ -301,12 +311,15 @@ int build_layout(const Setup& s, Layout& L, size_t smem_budget, size_t elem_byte
     L.psell_off[c + 1] = L.psell_off[c] + 32 * w;
   }
   L.pw_s.assign(L.psell_off[gch], 0.0);
+  L.pcol_s.assign(L.psell_off[gch], 0);
+  L.plen = glen;
   parallel_for(G, [&](int64_t b, int64_t e) {
     for (int64_t g = b; g < e; ++g) {
       const int gc[3] = {(int)(g % N[0]), (int)((g / N[0]) % N[1]), (int)(g / ((int64_t)N[0] * N[1]))};
       int64_t o = L.psell_off[g / 32] + (g % 32);
       for_pull(gc[0], gc[1], gc[2], [&](int64_t k0, int64_t k1) {
         for (int64_t k = k0; k < k1; ++k, o += 32) {
+          L.pcol_s[o] = (int32_t)k;
           if (!regular[k]) continue;
           double w = 1.0;
           for (int a = 0; a < 3; ++a) {
