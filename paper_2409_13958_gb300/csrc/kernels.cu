@@ -92,9 +92,9 @@ __global__ void __launch_bounds__(kBlock) k_charges(int64_t Np, const int32_t* _
   T aq = 0, ae = 0;
 #pragma unroll 4
   for (int j = 0; j < n; ++j, o += 32) {
-    const V4<T> mk = m[col[o]];
-    aq += wx[o] * mk.x + wy[o] * mk.y + wz[o] * mk.z;
-    ae += ex[o] * mk.x + ey[o] * mk.y + ez[o] * mk.z;
+    const V4<T> mk = m[__ldcs(col + o)];
+    aq += __ldcs(wx + o) * mk.x + __ldcs(wy + o) * mk.y + __ldcs(wz + o) * mk.z;
+    ae += __ldcs(ex + o) * mk.x + __ldcs(ey + o) * mk.y + __ldcs(ez + o) * mk.z;
   }
   q[i] = aq;
   e[i] = ae;
@@ -115,7 +115,7 @@ __global__ void __launch_bounds__(kBlock) k_project(int64_t G, const int32_t* __
   int64_t o = poff[g >> 5] + (g & 31);
   T acc = 0;
 #pragma unroll 4
-  for (int j = 0; j < n; ++j, o += 32) acc += pw[o] * q[pcol[o]];
+  for (int j = 0; j < n; ++j, o += 32) acc += __ldcs(pw + o) * __ldg(q + __ldcs(pcol + o));
   grid[g] = acc;
 }
 
@@ -160,7 +160,7 @@ __global__ void __launch_bounds__(kBlock) k_interp(
         const T* rowp = U + (int64_t)N0 * (wrap(b1 + b, N1, p1) + zo);
         T s = 0;
 #pragma unroll
-        for (int a = 0; a < P; ++a) s += w0[a] * rowp[ix[a]];
+        for (int a = 0; a < P; ++a) s += w0[a] * __ldg(rowp + ix[a]);
         acc += w2[c] * w1[b] * s;
       }
     }
@@ -169,7 +169,7 @@ __global__ void __launch_bounds__(kBlock) k_interp(
     const int n = clen[i];
     int64_t o = coff[i >> 5] + (i & 31);
 #pragma unroll 4
-    for (int j = 0; j < n; ++j, o += 32) acc += cval[o] * q[ccol[o]];
+    for (int j = 0; j < n; ++j, o += 32) acc += __ldcs(cval + o) * __ldg(q + __ldcs(ccol + o));
   }
   // near-element entries beyond the adjacency pattern
   for (int32_t p = rowptrX[i]; p < rowptrX[i + 1]; ++p) {
@@ -203,27 +203,27 @@ __global__ void __launch_bounds__(kBlock) k_field(int64_t Np, const int32_t* __r
   if (use_ms && use_ex) {
 #pragma unroll 4
     for (int j = 0; j < n; ++j, o += 32) {
-      const int32_t k = col[o];
-      const T du = u[k] - un;
+      const int32_t k = __ldcs(col + o);
+      const T du = __ldg(u + k) - un;
       const V4<T> mk = m[k];
-      const T c = kp[o];
-      ax += gx[o] * du + c * (mk.x - mn.x);
-      ay += gy[o] * du + c * (mk.y - mn.y);
-      az += gz[o] * du + c * (mk.z - mn.z);
+      const T c = __ldcs(kp + o);
+      ax += __ldcs(gx + o) * du + c * (mk.x - mn.x);
+      ay += __ldcs(gy + o) * du + c * (mk.y - mn.y);
+      az += __ldcs(gz + o) * du + c * (mk.z - mn.z);
     }
   } else if (use_ms) {
 #pragma unroll 4
     for (int j = 0; j < n; ++j, o += 32) {
-      const T du = u[col[o]] - un;
-      ax += gx[o] * du;
-      ay += gy[o] * du;
-      az += gz[o] * du;
+      const T du = __ldg(u + __ldcs(col + o)) - un;
+      ax += __ldcs(gx + o) * du;
+      ay += __ldcs(gy + o) * du;
+      az += __ldcs(gz + o) * du;
     }
   } else if (use_ex) {
 #pragma unroll 4
     for (int j = 0; j < n; ++j, o += 32) {
-      const V4<T> mk = m[col[o]];
-      const T c = kp[o];
+      const V4<T> mk = m[__ldcs(col + o)];
+      const T c = __ldcs(kp + o);
       ax += c * (mk.x - mn.x);
       ay += c * (mk.y - mn.y);
       az += c * (mk.z - mn.z);
