@@ -128,6 +128,32 @@ int upload_conv(pmfem_t h, const double* src, size_t n, size_t stride, size_t of
 }
 
 template <typename T>
+int upload_sell(pmfem_t h, const SellMatrix& M, DevSell<T>& D) {
+  int rc;
+  D.rows = M.rows;
+  D.col16 = M.col16;
+  bool identity = true;
+  for (int64_t t = 0; t < M.rows && identity; ++t) identity = M.map[t] == t;
+  if (!identity && (rc = upload(h, M.map.data(), M.map.size(), &D.map))) return rc;
+  if ((rc = upload(h, M.len.data(), M.len.size(), &D.len))) return rc;
+  if ((rc = upload(h, M.base.data(), M.base.size(), &D.base))) return rc;
+  if ((rc = upload(h, M.off.data(), M.off.size(), &D.off))) return rc;
+  if (M.col16) {
+    const int16_t* p16;
+    if ((rc = upload(h, M.d16.data(), M.d16.size(), &p16))) return rc;
+    D.delta = p16;
+  } else {
+    const int32_t* p32;
+    if ((rc = upload(h, M.d32.data(), M.d32.size(), &p32))) return rc;
+    D.delta = p32;
+  }
+  const int64_t P = M.padded();
+  for (int c = 0; c < M.comps; ++c)
+    if ((rc = upload_conv<T>(h, M.val.data() + (size_t)c * P, P, 1, 0, 1.0, &D.val[c]))) return rc;
+  return OK;
+}
+
+template <typename T>
 int build_device(pmfem_t h, DevOps<T>& d) {
   using C2 = typename Vec2<T>::type;
   const Setup& s = h->s;
@@ -153,27 +179,10 @@ int build_device(pmfem_t h, DevOps<T>& d) {
     d.fft[a] = s.fft[a];
     d.periodic[a] = s.periodic[a];
   }
-  const size_t ns = L.col_s.size();
   if ((rc = upload(h, L.perm.data(), L.perm.size(), &d.perm))) return rc;
-  if ((rc = upload(h, L.len.data(), L.len.size(), &d.len))) return rc;
-  if ((rc = upload(h, L.sell_off.data(), L.sell_off.size(), &d.sell_off))) return rc;
-  if ((rc = upload(h, L.col_s.data(), ns, &d.col))) return rc;
-  for (int c = 0; c < 3; ++c) {
-    if ((rc = upload_conv<T>(h, L.Wq_s.data() + c * ns, ns, 1, 0, 1.0, &d.wq[c]))) return rc;
-    if ((rc = upload_conv<T>(h, L.Ea_s.data() + c * ns, ns, 1, 0, 1.0, &d.ea[c]))) return rc;
-    if ((rc = upload_conv<T>(h, L.Gr_s.data() + c * ns, ns, 1, 0, 1.0, &d.gr[c]))) return rc;
-  }
-  if ((rc = upload_conv<T>(h, L.Kp_s.data(), ns, 1, 0, 1.0, &d.kp))) return rc;
-  if ((rc = upload(h, L.box.data(), L.box.size(), &d.box))) return rc;
-  if ((rc = upload(h, L.bstart.data(), L.bstart.size(), &d.bstart))) return rc;
-  if ((rc = upload(h, L.csell_off.data(), L.csell_off.size(), &d.csell_off))) return rc;
-  if ((rc = upload_conv<T>(h, L.cval_s.data(), L.cval_s.size(), 1, 0, 1.0, &d.cval))) return rc;
-  if ((rc = upload(h, L.ccol_s.data(), L.ccol_s.size(), &d.ccol))) return rc;
-  if ((rc = upload(h, L.clen.data(), L.clen.size(), &d.clen))) return rc;
-  if ((rc = upload(h, L.psell_off.data(), L.psell_off.size(), &d.psell_off))) return rc;
-  if ((rc = upload_conv<T>(h, L.pw_s.data(), L.pw_s.size(), 1, 0, 1.0, &d.pw))) return rc;
-  if ((rc = upload(h, L.pcol_s.data(), L.pcol_s.size(), &d.pcol))) return rc;
-  if ((rc = upload(h, L.plen.data(), L.plen.size(), &d.plen))) return rc;
+  if ((rc = upload_sell(h, L.adj, d.adj))) return rc;
+  if ((rc = upload_sell(h, L.cor, d.cor))) return rc;
+  if ((rc = upload_sell(h, L.pro, d.pro))) return rc;
   d.nx_exc = (int64_t)L.xnode.size();
   if ((rc = upload(h, L.xnode.data(), L.xnode.size(), &d.xnode))) return rc;
   if ((rc = upload(h, L.xgrid.data(), L.xgrid.size(), &d.xgrid))) return rc;

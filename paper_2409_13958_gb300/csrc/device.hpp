@@ -30,6 +30,21 @@ struct ProfHook {
   }
 };
 
+// A sparse operator in SELL-32: thread t handles row map[t] (t itself when map is null);
+// its element j sits at off[t / 32] + 32 j + t % 32 with column base[t] + delta (delta
+// 16-bit when col16) and values val[c][...]; rows of a chunk are padded to its longest.
+template <typename T>
+struct DevSell {
+  int64_t rows = 0;
+  const int32_t* map = nullptr;
+  const int32_t* len = nullptr;
+  const int32_t* base = nullptr;
+  const int64_t* off = nullptr;
+  const void* delta = nullptr;
+  bool col16 = true;
+  const T* val[10] = {};
+};
+
 // Operator values, grid set-up and work buffers of one precision, all device memory,
 // in the internal (box-sorted) order of the unknowns.
 template <typename T>
@@ -41,28 +56,11 @@ struct DevOps {
   bool periodic[3] = {false, false, false};
   int TY = 1, TZ = 1, pl = 1, pr = 2;
   const int32_t* perm = nullptr;                  // internal -> user unknown
-  // adjacency pattern (shared by charges, near-element, gradient and exchange values) in
-  // SELL-32: element j of row i at sell_off[i/32] + 32 j + i%32
-  const int32_t* len = nullptr;
-  const int64_t* sell_off = nullptr;
-  const int32_t* col = nullptr;
-  const T* wq[3] = {nullptr, nullptr, nullptr};   // Ms W^q
-  const T* ea[3] = {nullptr, nullptr, nullptr};   // Ms E (touching elements)
-  const T* gr[3] = {nullptr, nullptr, nullptr};   // -(W^q)^T / (4 pi V)
-  const T* kp = nullptr;                          // exchange, scaled
-  // point precorrection: values only (SELL-32), sources enumerated from the box structure
-  const int32_t* box = nullptr;                   // Np x 3
-  const int32_t* bstart = nullptr;                // boxes + 1
-  const int64_t* csell_off = nullptr;
-  const int32_t* clen = nullptr;
-  const int32_t* ccol = nullptr;
-  const T* cval = nullptr;
-  // projection gather weights (SELL-32 over grid points) and the exception list
-  const int64_t* psell_off = nullptr;
-  const int32_t* plen = nullptr;
-  const int32_t* pcol = nullptr;
-  const T* pw = nullptr;
-  int64_t nx_exc = 0;
+  // sparse operators in SELL-32 (see DevSell)
+  DevSell<T> adj;   // components: W^q x,y,z (Ms), E x,y,z (Ms), gradient x,y,z, exchange
+  DevSell<T> cor;   // point precorrection
+  DevSell<T> pro;   // projection P^T (rows = grid points)
+  int64_t nx_exc = 0;                             // projection exceptions
   const int32_t* xnode = nullptr;
   const int64_t* xgrid = nullptr;
   const T* xw = nullptr;

@@ -76,13 +76,28 @@ struct Setup {
   bool ready = false;
 };
 
-// Device-side layout: unknowns re-ordered by grid box so that the precorrection sources
-// of a row are a few contiguous node ranges and projection works tile by tile.
-// Box order: tiles of TY rows x TZ planes (y, z); inside a tile z, then y, then x fastest.
+// Device-side layout: unknowns re-ordered by grid box (z-major, then y, then x) so that
+// sparse rows gather from nearby indices, and every sparse operator stored in SELL-32
+// for one-thread-per-row kernels: element j of the row handled by thread t sits at
+// off[t / 32] + 32 j + t % 32.  Columns are stored as deltas to a per-row base, 16-bit
+// when every delta of the operator fits, else 32-bit.
+struct SellMatrix {
+  int64_t rows = 0;
+  std::vector<int32_t> map;          // thread -> row (identity unless rows were length-sorted)
+  std::vector<int32_t> len;          // per thread
+  std::vector<int32_t> base;         // per thread: column = base + delta
+  std::vector<int64_t> off;          // chunks + 1
+  bool col16 = true;
+  std::vector<int16_t> d16;
+  std::vector<int32_t> d32;
+  std::vector<double> val;           // comps x padded size, component-major
+  int comps = 1;
+  int64_t padded() const { return off.empty() ? 0 : off.back(); }
+};
+
 struct Layout {
-  int TY = 1, TZ = 1;
+  int TY = 1, TZ = 1;                // box rows / planes per tile in the box order (1: plain)
   int pl = 1, pr = 2;                // stencil reach below / above a node's box
-  bool tiled = false;                // tile-local projection fits in shared memory
   std::vector<int32_t> perm;         // internal -> user unknown
   std::vector<int32_t> box;          // Np x 3, internal order
   std::vector<int32_t> bstart;       // (boxes + 1): first internal node of each box
@@ -92,26 +107,12 @@ struct Layout {
   std::vector<double> frac;
   std::vector<int64_t> cptr;         // Np + 1: start of each row's precorrection values
   std::vector<double> cval;          // values in (dz, dy, x-segment, node) order
+  std::vector<int32_t> ccol;         // their source nodes
   Csr Ex;                            // near-element entries beyond the pattern, internal
-  // SELL-32 copies for one-thread-per-row kernels: element j of row i sits at
-  // off[i / 32] + 32 j + i % 32 (rows of a chunk padded to the chunk's longest row)
-  std::vector<int64_t> sell_off;     // chunks + 1, adjacency
-  std::vector<int32_t> len;          // Np adjacency row lengths
-  std::vector<int32_t> col_s;        // padded with the row's own index
-  std::vector<double> Wq_s, Ea_s, Gr_s, Kp_s;   // SoA per component: [comp][padded nnz]
-  std::vector<int64_t> csell_off;    // chunks + 1, precorrection values
-  std::vector<int32_t> clen;         // Np row lengths
-  std::vector<int32_t> ccol_s;       // source node of each value (padding: the row itself)
-  std::vector<double> cval_s;
-  // projection as a gather: grid point g (natural grid order) sums w * q over the nodes of
-  // the box rows [g - pr, g + pl]^2 (y, z) and boxes [gx - pr, gx + pl]; weights SELL-32
-  // over grid points; nodes whose stencil does not start at box - pl go to an exception
-  // list added with atomics afterwards
-  std::vector<int64_t> psell_off;    // grid chunks + 1
-  std::vector<int32_t> plen;         // G entries per grid point
-  std::vector<int32_t> pcol_s;       // node of each weight (padding: node 0, weight 0)
-  std::vector<double> pw_s;
-  std::vector<int32_t> xnode;        // exceptions: node, grid index, weight
+  SellMatrix adj;                    // 10 components: W^q (3), E (3), gradient (3), exchange
+  SellMatrix cor;                    // point precorrection, rows length-sorted in windows
+  SellMatrix pro;                    // projection P^T: rows = grid points
+  std::vector<int32_t> xnode;        // projection exceptions: node, grid index, weight
   std::vector<int64_t> xgrid;
   std::vector<double> xw;
   int64_t box_index(int x, int y, int z, const int N[3]) const {

@@ -78,9 +78,10 @@ __global__ void __launch_bounds__(kBlock) k_perm_out(int64_t Np, const int32_t* 
 }
 
 // ---------------------------------------------------------------- charges
-template <typename T>
+// q = W^q M (Eq. 14a) and e = E M (touching-element part of Eq. 14c) on the adjacency.
+template <typename T, typename CT>
 __global__ void __launch_bounds__(kBlock) k_charges(int64_t Np, const int32_t* __restrict__ len,
-                                                   const int64_t* __restrict__ off, const int32_t* __restrict__ col,
+                                                   const int64_t* __restrict__ off, const CT* __restrict__ dcol,
                                                    const T* __restrict__ wx, const T* __restrict__ wy,
                                                    const T* __restrict__ wz, const T* __restrict__ ex,
                                                    const T* __restrict__ ey, const T* __restrict__ ez,
@@ -92,7 +93,7 @@ __global__ void __launch_bounds__(kBlock) k_charges(int64_t Np, const int32_t* _
   T aq = 0, ae = 0;
 #pragma unroll 4
   for (int j = 0; j < n; ++j, o += 32) {
-    const V4<T> mk = m[__ldcs(col + o)];
+    const V4<T> mk = m[i + (int64_t)__ldcs(dcol + o)];
     aq += __ldcs(wx + o) * mk.x + __ldcs(wy + o) * mk.y + __ldcs(wz + o) * mk.z;
     ae += __ldcs(ex + o) * mk.x + __ldcs(ey + o) * mk.y + __ldcs(ez + o) * mk.z;
   }
@@ -104,18 +105,21 @@ __global__ void __launch_bounds__(kBlock) k_charges(int64_t Np, const int32_t* _
 // Q = P^T q as a gather: grid point g (one thread, SELL-32 over grid points) sums w q over
 // the nodes whose stencil covers it (the nodes of the boxes [g - pr, g + pl] per axis,
 // enumerated at set-up).  No atomics: every grid value has one writer.
-template <typename T>
-__global__ void __launch_bounds__(kBlock) k_project(int64_t G, const int32_t* __restrict__ plen,
-                                                   const int64_t* __restrict__ poff, const int32_t* __restrict__ pcol,
-                                                   const T* __restrict__ pw, const T* __restrict__ q,
-                                                   T* __restrict__ grid) {
+template <typename T, typename CT>
+__global__ void __launch_bounds__(kBlock) k_project(int64_t G, const int32_t* __restrict__ len,
+                                                   const int32_t* __restrict__ base, const int64_t* __restrict__ off,
+                                                   const CT* __restrict__ dcol, const T* __restrict__ pw,
+                                                   const T* __restrict__ q, T* __restrict__ grid) {
   const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= G) return;
-  const int n = plen[g];
-  int64_t o = poff[g >> 5] + (g & 31);
+  const int n = len[g];
   T acc = 0;
+  if (n > 0) {
+    const int64_t b = base[g];
+    int64_t o = off[g >> 5] + (g & 31);
 #pragma unroll 4
-  for (int j = 0; j < n; ++j, o += 32) acc += __ldcs(pw + o) * __ldg(q + __ldcs(pcol + o));
+    for (int j = 0; j < n; ++j, o += 32) acc += __ldcs(pw + o) * __ldg(q + b + __ldcs(dcol + o));
+  }
   grid[g] = acc;
 }
 
@@ -130,18 +134,19 @@ __global__ void __launch_bounds__(kBlock) k_project_exc(int64_t n, const int32_t
 }
 
 // ---------------------------------------------------------------- interpolation + precorrection
-// One thread per observer row: the (p+1)^3 stencil gathers from the grid potential, then
-// the row of the point precorrection (sources: the nodes of the boxes within near_boxes).
-template <typename T, int P>
+// One thread per observer row (thread t handles row map[t]; rows are sorted by length in
+// windows so that a warp's rows have similar lengths): the (p+1)^3 stencil gathers from
+// the grid potential, then the row of the point precorrection.
+template <typename T, int P, typename CT>
 __global__ void __launch_bounds__(kBlock) k_interp(
-    int64_t Np, const int32_t* __restrict__ box, const int32_t* __restrict__ base, const T* __restrict__ frac,
-    const T* __restrict__ U, int N0, int N1, int N2, bool p0, bool p1, bool p2,
-    const int32_t* __restrict__ clen, const int64_t* __restrict__ coff, const int32_t* __restrict__ ccol,
-    const T* __restrict__ cval,
+    int64_t Np, const int32_t* __restrict__ map, const int32_t* __restrict__ base, const T* __restrict__ frac,
+    const T* __restrict__ U, int N0, int N1, int N2, bool p0, bool p1, bool p2, const int32_t* __restrict__ clen,
+    const int64_t* __restrict__ coff, const CT* __restrict__ dcol, const T* __restrict__ cval,
     const int32_t* __restrict__ rowptrX, const int32_t* __restrict__ colX, const T* __restrict__ valX,
-    const T* __restrict__ q, const T* __restrict__ e, const V4<T>* __restrict__ m, T* __restrict__ u, int* flag) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= Np) return;
+    const T* __restrict__ q, const T* __restrict__ e, const V4<T>* __restrict__ m, T* __restrict__ u) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= Np) return;
+  const int64_t i = map[t];
   T acc = 0;
   {  // step 3: interpolation of the grid potential
     T w0[P], w1[P], w2[P];
@@ -166,10 +171,10 @@ __global__ void __launch_bounds__(kBlock) k_interp(
     }
   }
   {  // step 4: point precorrection (SELL-32 row)
-    const int n = clen[i];
-    int64_t o = coff[i >> 5] + (i & 31);
+    const int n = clen[t];
+    int64_t o = coff[t >> 5] + (t & 31);
 #pragma unroll 4
-    for (int j = 0; j < n; ++j, o += 32) acc += __ldcs(cval + o) * __ldg(q + __ldcs(ccol + o));
+    for (int j = 0; j < n; ++j, o += 32) acc += __ldcs(cval + o) * __ldg(q + i + __ldcs(dcol + o));
   }
   // near-element entries beyond the adjacency pattern
   for (int32_t p = rowptrX[i]; p < rowptrX[i + 1]; ++p) {
@@ -183,9 +188,9 @@ __global__ void __launch_bounds__(kBlock) k_interp(
 // Both operators annihilate constants (rows of the gradient and of the Laplacian sum to
 // zero), so they act on differences to the row's own value: the same result in exact
 // arithmetic, without the cancellation of large terms in floating point.
-template <typename T, int MODE>
+template <typename T, int MODE, typename CT>
 __global__ void __launch_bounds__(kBlock) k_field(int64_t Np, const int32_t* __restrict__ len,
-                                                 const int64_t* __restrict__ off, const int32_t* __restrict__ col,
+                                                 const int64_t* __restrict__ off, const CT* __restrict__ dcol,
                                                  const T* __restrict__ gx, const T* __restrict__ gy,
                                                  const T* __restrict__ gz, const T* __restrict__ kp,
                                                  const T* __restrict__ u, const V4<T>* __restrict__ m,
@@ -203,7 +208,7 @@ __global__ void __launch_bounds__(kBlock) k_field(int64_t Np, const int32_t* __r
   if (use_ms && use_ex) {
 #pragma unroll 4
     for (int j = 0; j < n; ++j, o += 32) {
-      const int32_t k = __ldcs(col + o);
+      const int64_t k = i + (int64_t)__ldcs(dcol + o);
       const T du = __ldg(u + k) - un;
       const V4<T> mk = m[k];
       const T c = __ldcs(kp + o);
@@ -214,7 +219,7 @@ __global__ void __launch_bounds__(kBlock) k_field(int64_t Np, const int32_t* __r
   } else if (use_ms) {
 #pragma unroll 4
     for (int j = 0; j < n; ++j, o += 32) {
-      const T du = __ldg(u + __ldcs(col + o)) - un;
+      const T du = __ldg(u + i + __ldcs(dcol + o)) - un;
       ax += __ldcs(gx + o) * du;
       ay += __ldcs(gy + o) * du;
       az += __ldcs(gz + o) * du;
@@ -222,7 +227,7 @@ __global__ void __launch_bounds__(kBlock) k_field(int64_t Np, const int32_t* __r
   } else if (use_ex) {
 #pragma unroll 4
     for (int j = 0; j < n; ++j, o += 32) {
-      const V4<T> mk = m[__ldcs(col + o)];
+      const V4<T> mk = m[i + (int64_t)__ldcs(dcol + o)];
       const T c = __ldcs(kp + o);
       ax += c * (mk.x - mn.x);
       ay += c * (mk.y - mn.y);
@@ -281,17 +286,30 @@ void launch_perm_out(const DevOps<T>& d, const V4<T>* m, T* m_user, cudaStream_t
 
 template <typename T>
 void launch_charges(const DevOps<T>& d, const V4<T>* m, cudaStream_t st) {
+  const DevSell<T>& A = d.adj;
   d.prof.begin(KID_CHARGES, st);
-  k_charges<T><<<blocks_for(d.Np), kBlock, 0, st>>>(d.Np, d.len, d.sell_off, d.col, d.wq[0], d.wq[1], d.wq[2],
-                                                    d.ea[0], d.ea[1], d.ea[2], m, d.q, d.e);
+  if (A.col16)
+    k_charges<T, int16_t><<<blocks_for(d.Np), kBlock, 0, st>>>(d.Np, A.len, A.off, (const int16_t*)A.delta, A.val[0],
+                                                               A.val[1], A.val[2], A.val[3], A.val[4], A.val[5], m,
+                                                               d.q, d.e);
+  else
+    k_charges<T, int32_t><<<blocks_for(d.Np), kBlock, 0, st>>>(d.Np, A.len, A.off, (const int32_t*)A.delta, A.val[0],
+                                                               A.val[1], A.val[2], A.val[3], A.val[4], A.val[5], m,
+                                                               d.q, d.e);
   d.prof.end(KID_CHARGES, st);
 }
 
 template <typename T>
 void launch_anterp(const DevOps<T>& d, cudaStream_t st) {
+  const DevSell<T>& Pm = d.pro;
   d.prof.begin(KID_ANTERP, st);
-  const int64_t G = (int64_t)d.dims[0] * d.dims[1] * d.dims[2];
-  k_project<T><<<blocks_for(G), kBlock, 0, st>>>(G, d.plen, d.psell_off, d.pcol, d.pw, d.q, d.grid);
+  const int64_t G = Pm.rows;
+  if (Pm.col16)
+    k_project<T, int16_t><<<blocks_for(G), kBlock, 0, st>>>(G, Pm.len, Pm.base, Pm.off, (const int16_t*)Pm.delta,
+                                                            Pm.val[0], d.q, d.grid);
+  else
+    k_project<T, int32_t><<<blocks_for(G), kBlock, 0, st>>>(G, Pm.len, Pm.base, Pm.off, (const int32_t*)Pm.delta,
+                                                            Pm.val[0], d.q, d.grid);
   if (d.nx_exc > 0)
     k_project_exc<T><<<blocks_for(d.nx_exc), kBlock, 0, st>>>(d.nx_exc, d.xnode, d.xgrid, d.xw, d.q, d.grid);
   d.prof.end(KID_ANTERP, st);
@@ -299,18 +317,27 @@ void launch_anterp(const DevOps<T>& d, cudaStream_t st) {
 
 template <typename T>
 void launch_interp(const DevOps<T>& d, const V4<T>* m, cudaStream_t st) {
+  const DevSell<T>& C = d.cor;
   const unsigned nb = blocks_for(d.Np);
   d.prof.begin(KID_INTERP, st);
-#define PMFEM_INTERP(PP)                                                                                      \
-  k_interp<T, PP><<<nb, kBlock, 0, st>>>(d.Np, d.box, d.base, d.frac, d.grid, d.dims[0], d.dims[1], d.dims[2], \
-                                         d.periodic[0], d.periodic[1], d.periodic[2], d.clen, d.csell_off,       \
-                                         d.ccol, d.cval, d.rowptrX, d.colX, d.valX, d.q, d.e, m, d.u, d.flag)
-  switch (d.p) {
-    case 2: PMFEM_INTERP(3); break;
-    case 3: PMFEM_INTERP(4); break;
-    case 4: PMFEM_INTERP(5); break;
-    default: PMFEM_INTERP(6); break;
+#define PMFEM_INTERP(PP, CT)                                                                                      \
+  k_interp<T, PP, CT><<<nb, kBlock, 0, st>>>(d.Np, C.map, d.base, d.frac, d.grid, d.dims[0], d.dims[1], d.dims[2], \
+                                             d.periodic[0], d.periodic[1], d.periodic[2], C.len, C.off,           \
+                                             (const CT*)C.delta, C.val[0], d.rowptrX, d.colX, d.valX, d.q, d.e, m, \
+                                             d.u)
+#define PMFEM_INTERP_P(CT)              \
+  switch (d.p) {                        \
+    case 2: PMFEM_INTERP(3, CT); break; \
+    case 3: PMFEM_INTERP(4, CT); break; \
+    case 4: PMFEM_INTERP(5, CT); break; \
+    default: PMFEM_INTERP(6, CT); break; \
   }
+  if (C.col16) {
+    PMFEM_INTERP_P(int16_t)
+  } else {
+    PMFEM_INTERP_P(int32_t)
+  }
+#undef PMFEM_INTERP_P
 #undef PMFEM_INTERP
   d.prof.end(KID_INTERP, st);
 }
@@ -318,6 +345,7 @@ void launch_interp(const DevOps<T>& d, const V4<T>* m, cudaStream_t st) {
 template <typename T>
 void launch_field(const DevOps<T>& d, const V4<T>* m, T* H, int comps, double hx, double hy, double hz,
                   const RkArgs& rk, cudaStream_t st) {
+  const DevSell<T>& A = d.adj;
   const unsigned nb = blocks_for(d.Np);
   const int use_ms = (comps & 2) ? 1 : 0, use_ex = (comps & 1) ? 1 : 0;
   const T ax = (comps & 4) ? (T)hx : T(0), ay = (comps & 4) ? (T)hy : T(0), az = (comps & 4) ? (T)hz : T(0);
@@ -325,13 +353,21 @@ void launch_field(const DevOps<T>& d, const V4<T>* m, T* H, int comps, double hx
   V4<T>* mn = (V4<T>*)rk.mnext;
   V4<T>* acc = (V4<T>*)rk.acc;
   d.prof.begin(KID_FIELD, st);
-#define PMFEM_FIELD(MODE)                                                                                          \
-  k_field<T, MODE><<<nb, kBlock, 0, st>>>(d.Np, d.len, d.sell_off, d.col, d.gr[0], d.gr[1], d.gr[2], d.kp, d.u, m, \
-                                          d.perm, H, use_ms, use_ex, ax, ay, az, m0, mn, acc, (T)rk.cdt, (T)rk.bw,  \
-                                          rk.acc_init, (T)rk.dt6, (T)rk.gam, (T)rk.alpha, d.flag)
-  if (rk.mode == 0) PMFEM_FIELD(0);
-  else if (rk.mode == 1) PMFEM_FIELD(1);
-  else PMFEM_FIELD(2);
+#define PMFEM_FIELD(MODE, CT)                                                                                     \
+  k_field<T, MODE, CT><<<nb, kBlock, 0, st>>>(d.Np, A.len, A.off, (const CT*)A.delta, A.val[6], A.val[7], A.val[8], \
+                                              A.val[9], d.u, m, d.perm, H, use_ms, use_ex, ax, ay, az, m0, mn, acc, \
+                                              (T)rk.cdt, (T)rk.bw, rk.acc_init, (T)rk.dt6, (T)rk.gam, (T)rk.alpha,   \
+                                              d.flag)
+#define PMFEM_FIELD_M(CT)                           \
+  if (rk.mode == 0) PMFEM_FIELD(0, CT);             \
+  else if (rk.mode == 1) PMFEM_FIELD(1, CT);        \
+  else PMFEM_FIELD(2, CT);
+  if (A.col16) {
+    PMFEM_FIELD_M(int16_t)
+  } else {
+    PMFEM_FIELD_M(int32_t)
+  }
+#undef PMFEM_FIELD_M
 #undef PMFEM_FIELD
   d.prof.end(KID_FIELD, st);
 }

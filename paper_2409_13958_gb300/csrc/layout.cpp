@@ -1,12 +1,12 @@
 // Device layout of the unknowns (host side).  Unknowns are sorted by the grid box of their
-// folded position, boxes ordered in tiles of TY rows x TZ planes with x fastest, so that
-//   - the precorrection sources of an observer (all nodes in boxes within near_boxes) are
-//     (2 nb + 1)^2 contiguous node ranges, one per neighbouring box row, and the matrix
-//     needs no column indices: only its values are streamed;
-//   - the projection of a tile's nodes lands in a small shared-memory region.
-// Every operator is re-indexed to this order; user-facing arrays keep the unknown order
-// of the C-ABI and are permuted at the boundary.
+// folded position (z-major, then y, x fastest), so that the sources of every sparse row lie
+// at nearby indices: the precorrection sources of an observer (all nodes in boxes within
+// near_boxes) are (2 nb + 1)^2 contiguous node ranges, and the nodes feeding a grid point
+// in the projection are (p + 1)^2 such ranges.  Every operator is re-indexed to this
+// order and stored in SELL-32 with column deltas (16-bit when they fit); user-facing
+// arrays keep the unknown order of the C-ABI and are permuted at the boundary.
 #include <algorithm>
+#include <functional>
 #include <numeric>
 
 #include "internal.hpp"
@@ -50,30 +50,80 @@ bool wrap_axis(int& v, int N, bool per) {
 }
 }  // namespace
 
+// SELL-32 from row callbacks: len(r), base(r) and fill(r, put(col, values[comps])).  With
+// sigma > 1, rows are sorted by decreasing length inside windows of sigma rows so that
+// the 32 rows of a chunk have similar lengths (little padding).
+void build_sell(SellMatrix& M, int64_t rows, int comps, int sigma, const std::function<int64_t(int64_t)>& len,
+                const std::function<int32_t(int64_t)>& base,
+                const std::function<void(int64_t, const std::function<void(int32_t, const double*)>&)>& fill) {
+  M.rows = rows;
+  M.comps = comps;
+  std::vector<int64_t> rl(rows);
+  parallel_for(rows, [&](int64_t b, int64_t e) {
+    for (int64_t r = b; r < e; ++r) rl[r] = len(r);
+  }, 4096);
+  M.map.resize(rows);
+  std::iota(M.map.begin(), M.map.end(), 0);
+  if (sigma > 1)
+    for (int64_t w0 = 0; w0 < rows; w0 += sigma) {
+      const int64_t w1 = std::min(rows, w0 + sigma);
+      std::stable_sort(M.map.begin() + w0, M.map.begin() + w1, [&](int32_t a, int32_t b) { return rl[a] > rl[b]; });
+    }
+  const int64_t nch = (rows + 31) / 32;
+  M.len.resize(rows);
+  M.base.resize(rows);
+  M.off.assign(nch + 1, 0);
+  for (int64_t t = 0; t < rows; ++t) M.len[t] = (int32_t)rl[M.map[t]];
+  for (int64_t c = 0; c < nch; ++c) {
+    int64_t w = 0;
+    for (int64_t t = 32 * c; t < std::min(rows, 32 * c + 32); ++t) w = std::max<int64_t>(w, M.len[t]);
+    M.off[c + 1] = M.off[c] + 32 * w;
+  }
+  const int64_t P = M.off[nch];
+  std::vector<int32_t> delta(P, 0);
+  M.val.assign((size_t)comps * P, 0.0);
+  int64_t maxd = 0;
+  std::vector<int64_t> maxd_t(nch, 0);
+  parallel_for(nch, [&](int64_t cb, int64_t ce) {
+    for (int64_t c = cb; c < ce; ++c) {
+      int64_t md = 0;
+      for (int64_t t = 32 * c; t < std::min(rows, 32 * c + 32); ++t) {
+        const int64_t r = M.map[t];
+        const int32_t bse = base(r);
+        M.base[t] = bse;
+        int64_t o = M.off[c] + (t - 32 * c);
+        fill(r, [&](int32_t col, const double* v) {
+          const int64_t d = (int64_t)col - bse;
+          md = std::max<int64_t>(md, d < 0 ? -d : d);
+          delta[o] = (int32_t)d;
+          for (int k = 0; k < comps; ++k) M.val[(size_t)k * P + o] = v[k];
+          o += 32;
+        });
+      }
+      maxd_t[c] = md;
+    }
+  }, 64);
+  for (int64_t c = 0; c < nch; ++c) maxd = std::max(maxd, maxd_t[c]);
+  M.col16 = maxd <= 32767;
+  if (M.col16) {
+    M.d16.assign(delta.begin(), delta.end());
+    M.d32.clear();
+  } else {
+    M.d32.swap(delta);
+    M.d16.clear();
+  }
+}
+
 int build_layout(const Setup& s, Layout& L, size_t smem_budget, size_t elem_bytes, Error& err) {
   const int64_t Np = s.Np;
   const int N[3] = {s.dims[0], s.dims[1], s.dims[2]};
   const int p = s.p, nb = s.near_boxes;
   L.pl = (p % 2 == 1) ? (p - 1) / 2 : p / 2;
   L.pr = (p % 2 == 1) ? (p + 1) / 2 : p / 2 + 1;
-  // largest tile whose projection region fits the shared-memory budget
-  L.tiled = false;
+  (void)smem_budget;
+  (void)elem_bytes;
   L.TY = 1;
   L.TZ = 1;
-  const int reach = L.pl + L.pr;
-  for (int ty : {8, 4, 2, 1}) {
-    for (int tz : {4, 2, 1}) {
-      if (ty > N[1] || tz > N[2]) continue;
-      size_t bytes = (size_t)(N[0] + reach) * (ty + reach) * (tz + reach) * elem_bytes;
-      if (bytes <= smem_budget) {
-        L.TY = ty;
-        L.TZ = tz;
-        L.tiled = true;
-        break;
-      }
-    }
-    if (L.tiled) break;
-  }
   // permutation: by box index, then by unknown index
   std::vector<int64_t> key(Np);
   for (int64_t u = 0; u < Np; ++u) key[u] = L.box_index(s.box[3 * u], s.box[3 * u + 1], s.box[3 * u + 2], N);
@@ -172,6 +222,7 @@ int build_layout(const Setup& s, Layout& L, size_t smem_budget, size_t elem_byte
     L.cptr[i + 1] = L.cptr[i] + len;
   }
   L.cval.assign(L.cptr[Np], 0.0);
+  L.ccol.assign(L.cptr[Np], 0);
   std::vector<char> bad(Np, 0);
   parallel_for(Np, [&](int64_t b, int64_t e) {
     std::vector<char> used;
@@ -183,6 +234,7 @@ int build_layout(const Setup& s, Layout& L, size_t smem_budget, size_t elem_byte
       int64_t o = L.cptr[i], consumed = 0;
       for_segments(i, [&](int64_t k0, int64_t k1) {
         for (int64_t k = k0; k < k1; ++k, ++o) {
+          L.ccol[o] = (int32_t)k;
           const int32_t ku = L.perm[k];
           const int32_t* it = std::lower_bound(cb, cb + rl, ku);
           const int64_t pos = it - cb;
@@ -201,65 +253,23 @@ int build_layout(const Setup& s, Layout& L, size_t smem_budget, size_t elem_byte
       err = {EINVAL_, "precorrection layout does not cover row " + std::to_string(i)};
       return EINVAL_;
     }
-  // SELL-32 copies
-  const int64_t nch = (Np + 31) / 32;
-  L.len.resize(Np);
-  for (int64_t i = 0; i < Np; ++i) L.len[i] = L.rowptr[i + 1] - L.rowptr[i];
-  L.sell_off.assign(nch + 1, 0);
-  L.csell_off.assign(nch + 1, 0);
-  for (int64_t c = 0; c < nch; ++c) {
-    int64_t w = 0, wc = 0;
-    for (int64_t i = 32 * c; i < std::min<int64_t>(Np, 32 * c + 32); ++i) {
-      w = std::max<int64_t>(w, L.len[i]);
-      wc = std::max<int64_t>(wc, L.cptr[i + 1] - L.cptr[i]);
-    }
-    L.sell_off[c + 1] = L.sell_off[c] + 32 * w;
-    L.csell_off[c + 1] = L.csell_off[c] + 32 * wc;
-  }
-  const int64_t ns = L.sell_off[nch], ncs = L.csell_off[nch];
-  L.col_s.assign(ns, 0);
-  L.Wq_s.assign(3 * ns, 0.0);
-  L.Ea_s.assign(3 * ns, 0.0);
-  L.Gr_s.assign(3 * ns, 0.0);
-  L.Kp_s.assign(ns, 0.0);
-  L.cval_s.assign(ncs, 0.0);
-  L.ccol_s.assign(ncs, 0);
-  L.clen.resize(Np);
-  for (int64_t i = 0; i < Np; ++i) L.clen[i] = (int32_t)(L.cptr[i + 1] - L.cptr[i]);
-  parallel_for(nch, [&](int64_t b, int64_t e) {
-    for (int64_t c = b; c < e; ++c) {
-      const int64_t w = (L.sell_off[c + 1] - L.sell_off[c]) / 32;
-      for (int64_t i = 32 * c; i < std::min<int64_t>(Np, 32 * c + 32); ++i) {
-        const int64_t lane = i - 32 * c;
-        for (int64_t j = 0; j < w; ++j) {
-          const int64_t o = L.sell_off[c] + 32 * j + lane;
-          if (j < L.len[i]) {
-            const int64_t q = L.rowptr[i] + j;
-            L.col_s[o] = L.col[q];
-            L.Kp_s[o] = L.Kp[q];
-            for (int d = 0; d < 3; ++d) {
-              L.Wq_s[d * ns + o] = L.Wq[3 * q + d];
-              L.Ea_s[d * ns + o] = L.Ea[3 * q + d];
-              L.Gr_s[d * ns + o] = L.Gr[3 * q + d];
-            }
-          } else {
-            L.col_s[o] = (int32_t)i;
-          }
-        }
-        const int64_t cw = (L.csell_off[c + 1] - L.csell_off[c]) / 32;
-        int64_t j = 0;
-        for_segments(i, [&](int64_t k0, int64_t k1) {
-          for (int64_t k = k0; k < k1; ++k, ++j) {
-            L.cval_s[L.csell_off[c] + 32 * j + lane] = L.cval[L.cptr[i] + j];
-            L.ccol_s[L.csell_off[c] + 32 * j + lane] = (int32_t)k;
-          }
-        });
-        for (; j < cw; ++j) L.ccol_s[L.csell_off[c] + 32 * j + lane] = (int32_t)i;
-      }
-    }
-  }, 256);
+  // SELL-32 operators
+  build_sell(L.adj, Np, 10, 1, [&](int64_t i) { return (int64_t)(L.rowptr[i + 1] - L.rowptr[i]); },
+             [&](int64_t i) { return (int32_t)i; },
+             [&](int64_t i, const std::function<void(int32_t, const double*)>& put) {
+               for (int64_t q = L.rowptr[i]; q < L.rowptr[i + 1]; ++q) {
+                 const double v[10] = {L.Wq[3 * q], L.Wq[3 * q + 1], L.Wq[3 * q + 2], L.Ea[3 * q], L.Ea[3 * q + 1],
+                                       L.Ea[3 * q + 2], L.Gr[3 * q], L.Gr[3 * q + 1], L.Gr[3 * q + 2], L.Kp[q]};
+                 put(L.col[q], v);
+               }
+             });
+  build_sell(L.cor, Np, 1, 256, [&](int64_t i) { return L.cptr[i + 1] - L.cptr[i]; },
+             [&](int64_t i) { return (int32_t)i; },
+             [&](int64_t i, const std::function<void(int32_t, const double*)>& put) {
+               for (int64_t o = L.cptr[i]; o < L.cptr[i + 1]; ++o) put(L.ccol[o], &L.cval[o]);
+             });
 
-  // projection gather weights
+  // projection P^T: grid point g gathers from the nodes whose stencil covers it
   auto lagr = [&](double sv, int i) {
     double v = 1.0;
     for (int j = 0; j <= p; ++j)
@@ -293,49 +303,40 @@ int build_layout(const Setup& s, Layout& L, size_t smem_budget, size_t elem_byte
       }
     }
   };
+  auto gcoord = [&](int64_t g, int gc[3]) {
+    gc[0] = (int)(g % N[0]);
+    gc[1] = (int)((g / N[0]) % N[1]);
+    gc[2] = (int)(g / ((int64_t)N[0] * N[1]));
+  };
   const int64_t G = (int64_t)N[0] * N[1] * N[2];
-  const int64_t gch = (G + 31) / 32;
-  std::vector<int32_t> glen(G);
-  parallel_for(G, [&](int64_t b, int64_t e) {
-    for (int64_t g = b; g < e; ++g) {
-      int64_t n = 0;
-      for_pull((int)(g % N[0]), (int)((g / N[0]) % N[1]), (int)(g / ((int64_t)N[0] * N[1])),
-               [&](int64_t k0, int64_t k1) { n += k1 - k0; });
-      glen[g] = (int32_t)n;
-    }
-  }, 4096);
-  L.psell_off.assign(gch + 1, 0);
-  for (int64_t c = 0; c < gch; ++c) {
-    int64_t w = 0;
-    for (int64_t g = 32 * c; g < std::min<int64_t>(G, 32 * c + 32); ++g) w = std::max<int64_t>(w, glen[g]);
-    L.psell_off[c + 1] = L.psell_off[c] + 32 * w;
-  }
-  L.pw_s.assign(L.psell_off[gch], 0.0);
-  L.pcol_s.assign(L.psell_off[gch], 0);
-  L.plen = glen;
-  parallel_for(G, [&](int64_t b, int64_t e) {
-    for (int64_t g = b; g < e; ++g) {
-      const int gc[3] = {(int)(g % N[0]), (int)((g / N[0]) % N[1]), (int)(g / ((int64_t)N[0] * N[1]))};
-      int64_t o = L.psell_off[g / 32] + (g % 32);
-      for_pull(gc[0], gc[1], gc[2], [&](int64_t k0, int64_t k1) {
-        for (int64_t k = k0; k < k1; ++k, o += 32) {
-          L.pcol_s[o] = (int32_t)k;
-          if (!regular[k]) continue;
-          double w = 1.0;
-          for (int a = 0; a < 3; ++a) {
-            int i = gc[a] - L.base[3 * k + a];
-            if (s.periodic[a]) i = ((i % N[a]) + N[a]) % N[a];
-            if (i < 0 || i > p) {
-              w = 0.0;
-              break;
-            }
-            w *= lagr(L.frac[3 * k + a], i);
-          }
-          L.pw_s[o] = w;
-        }
-      });
-    }
-  }, 4096);
+  build_sell(L.pro, G, 1, 1,
+             [&](int64_t g) {
+               int gc[3];
+               gcoord(g, gc);
+               int64_t n = 0;
+               for_pull(gc[0], gc[1], gc[2], [&](int64_t k0, int64_t k1) { n += k1 - k0; });
+               return n;
+             },
+             [&](int64_t g) {
+               int gc[3];
+               gcoord(g, gc);
+               return L.bstart[L.box_index(gc[0], gc[1], gc[2], N)];
+             },
+             [&](int64_t g, const std::function<void(int32_t, const double*)>& put) {
+               int gc[3];
+               gcoord(g, gc);
+               for_pull(gc[0], gc[1], gc[2], [&](int64_t k0, int64_t k1) {
+                 for (int64_t k = k0; k < k1; ++k) {
+                   double w = regular[k] ? 1.0 : 0.0;
+                   for (int a = 0; a < 3 && w != 0.0; ++a) {
+                     int i = gc[a] - L.base[3 * k + a];
+                     if (s.periodic[a]) i = ((i % N[a]) + N[a]) % N[a];
+                     w = (i < 0 || i > p) ? 0.0 : w * lagr(L.frac[3 * k + a], i);
+                   }
+                   put((int32_t)k, &w);
+                 }
+               });
+             });
   L.xnode.clear();
   L.xgrid.clear();
   L.xw.clear();
