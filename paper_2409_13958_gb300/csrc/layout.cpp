@@ -263,7 +263,9 @@ int build_layout(const Setup& s, Layout& L, size_t smem_budget, size_t elem_byte
                  put(L.col[q], v);
                }
              });
-  build_sell(L.cor, Np, 1, 256, [&](int64_t i) { return L.cptr[i + 1] - L.cptr[i]; },
+  // rows keep the box order (no length sort): a warp's 32 rows are neighbours and share
+  // their gathers in L1
+  build_sell(L.cor, Np, 1, 1, [&](int64_t i) { return L.cptr[i + 1] - L.cptr[i]; },
              [&](int64_t i) { return (int32_t)i; },
              [&](int64_t i, const std::function<void(int32_t, const double*)>& put) {
                for (int64_t o = L.cptr[i]; o < L.cptr[i + 1]; ++o) put(L.ccol[o], &L.cval[o]);
