@@ -134,9 +134,9 @@ __global__ void __launch_bounds__(kBlock) k_project_exc(int64_t n, const int32_t
 }
 
 // ---------------------------------------------------------------- interpolation + precorrection
-// One thread per observer row (thread t handles row map[t]; rows are sorted by length in
-// windows so that a warp's rows have similar lengths): the (p+1)^3 stencil gathers from
-// the grid potential, then the row of the point precorrection.
+// One thread per observer row (thread t handles row map[t], or row t when the operator
+// keeps the box order): the (p+1)^3 stencil gathers from the grid potential, then the row
+// of the point precorrection.
 template <typename T, int P, typename CT>
 __global__ void __launch_bounds__(kBlock) k_interp(
     int64_t Np, const int32_t* __restrict__ map, const int32_t* __restrict__ base, const T* __restrict__ frac,
@@ -146,7 +146,7 @@ __global__ void __launch_bounds__(kBlock) k_interp(
     const T* __restrict__ q, const T* __restrict__ e, const V4<T>* __restrict__ m, T* __restrict__ u) {
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= Np) return;
-  const int64_t i = map[t];
+  const int64_t i = map ? (int64_t)map[t] : t;   // a null map is the identity
   T acc = 0;
   {  // step 3: interpolation of the grid potential
     T w0[P], w1[P], w2[P];
