@@ -107,6 +107,16 @@ int pmfem_set_aim(pmfem_t h, int Nx, int Ny, int Nz, int order_p, int near_boxes
  */
 int pmfem_set_periodicity(pmfem_t h, double L1, double L2, double L3);
 
+/*
+ * Device layout tuning (no paper counterpart; it changes speed, not results beyond
+ * rounding).  Unknowns are stored sorted by grid box in tiles of tile_y box rows x tile_z
+ * box planes (x fastest); precorrection rows may be sorted by length inside windows of
+ * sort_window rows; column indices are stored as 16-bit deltas when every delta fits
+ * (col_bits 0 or 16) or as 32-bit deltas (col_bits 32).  0 selects the defaults (8, 4, 1024,
+ * 16-bit when possible).  Takes effect at the next device upload; may come before or after pmfem_set_periodicity.
+ */
+int pmfem_set_layout(pmfem_t h, int tile_y, int tile_z, int sort_window, int col_bits);
+
 int pmfem_set_precision(pmfem_t h, int mode);                       /* PMFEM_FP64 | FP32 | BF16SPLIT */
 int pmfem_set_applied_field(pmfem_t h, double Hx, double Hy, double Hz);   /* A/m, uniform       */
 

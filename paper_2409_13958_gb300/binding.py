@@ -27,6 +27,7 @@ SIGNATURES = {
     "pmfem_create_mesh": (_c.c_int, [_c.POINTER(_vp), _vp, _i64, _vp, _i64, _dbl, _dbl, _dbl]),
     "pmfem_set_aim": (_c.c_int, [_vp, _c.c_int, _c.c_int, _c.c_int, _c.c_int, _c.c_int, _dbl]),
     "pmfem_set_periodicity": (_c.c_int, [_vp, _dbl, _dbl, _dbl]),
+    "pmfem_set_layout": (_c.c_int, [_vp, _c.c_int, _c.c_int, _c.c_int, _c.c_int]),
     "pmfem_set_precision": (_c.c_int, [_vp, _c.c_int]),
     "pmfem_set_applied_field": (_c.c_int, [_vp, _dbl, _dbl, _dbl]),
     "pmfem_num_unknowns": (_c.c_int, [_vp, _pi64]),
@@ -127,6 +128,9 @@ class Pmfem:
 
     def set_periodicity(self, L1=0.0, L2=0.0, L3=0.0):
         self._ck(self._lib.pmfem_set_periodicity(self.h, L1, L2, L3))
+
+    def set_layout(self, tile_y=0, tile_z=0, sort_window=0, col_bits=0):
+        self._ck(self._lib.pmfem_set_layout(self.h, tile_y, tile_z, sort_window, col_bits))
 
     def set_precision(self, mode: int):
         self._ck(self._lib.pmfem_set_precision(self.h, mode))

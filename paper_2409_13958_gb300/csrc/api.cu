@@ -358,6 +358,19 @@ int pmfem_set_aim(pmfem_t h, int Nx, int Ny, int Nz, int order_p, int near_boxes
   return OK;
 }
 
+int pmfem_set_layout(pmfem_t h, int tile_y, int tile_z, int sort_window, int col_bits) {
+  if (!h) return EINVAL_;
+  if (tile_y < 0 || tile_y > 64 || tile_z < 0 || tile_z > 64 || sort_window < 0 || sort_window > 65536)
+    return fail(h, EINVAL_, "tile sizes must be in [0, 64] and sort_window in [0, 65536]");
+  if (col_bits != 0 && col_bits != 16 && col_bits != 32) return fail(h, EINVAL_, "col_bits must be 0, 16 or 32");
+  h->s.tile_y = tile_y;
+  h->s.tile_z = tile_z;
+  h->s.sort_window = sort_window;
+  h->s.col_bits = col_bits;
+  free_device(h);
+  return OK;
+}
+
 int pmfem_set_periodicity(pmfem_t h, double L1, double L2, double L3) {
   if (!h) return EINVAL_;
   double L[3] = {L1, L2, L3};

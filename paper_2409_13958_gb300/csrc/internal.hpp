@@ -43,6 +43,8 @@ struct Setup {
   int p = 3;
   int near_boxes = 3;
   double near_elem_factor = 0.0;
+  // ---- device layout tuning (0 = default)
+  int tile_y = 0, tile_z = 0, sort_window = 0, col_bits = 0;
   // ---- periodicity
   double L[3] = {0, 0, 0};
   bool periodic[3] = {false, false, false};

@@ -49,6 +49,29 @@ __device__ __forceinline__ int wrap(int i, int N, bool per) {
 
 
 
+// sum_j val[o_j] * x[b + delta[o_j]] over one SELL row, o_j = o + 32 j: the value and
+// column loads of a batch of B elements are issued together, then their B gathers, so
+// each thread keeps 2B independent loads in flight instead of one dependent pair
+template <int B, typename T, typename CT>
+__device__ __forceinline__ T sell_dot(const T* __restrict__ val, const CT* __restrict__ dcol,
+                                      const T* __restrict__ x, int64_t b, int64_t o, int n) {
+  T acc = 0;
+  int j = 0;
+  for (; j + B <= n; j += B, o += 32 * B) {
+    T v[B];
+    int64_t c[B];
+#pragma unroll
+    for (int k = 0; k < B; ++k) {
+      v[k] = __ldcs(val + o + 32 * k);
+      c[k] = b + (int64_t)__ldcs(dcol + o + 32 * k);
+    }
+#pragma unroll
+    for (int k = 0; k < B; ++k) acc += v[k] * __ldg(x + c[k]);
+  }
+  for (; j < n; ++j, o += 32) acc += __ldcs(val + o) * __ldg(x + b + __ldcs(dcol + o));
+  return acc;
+}
+
 // ---------------------------------------------------------------- boundary permutations
 template <typename T>
 __global__ void __launch_bounds__(kBlock) k_perm_in(int64_t Np, const int32_t* __restrict__ perm,
@@ -106,20 +129,17 @@ __global__ void __launch_bounds__(kBlock) k_charges(int64_t Np, const int32_t* _
 // the nodes whose stencil covers it (the nodes of the boxes [g - pr, g + pl] per axis,
 // enumerated at set-up).  No atomics: every grid value has one writer.
 template <typename T, typename CT>
-__global__ void __launch_bounds__(kBlock) k_project(int64_t G, const int32_t* __restrict__ len,
-                                                   const int32_t* __restrict__ base, const int64_t* __restrict__ off,
-                                                   const CT* __restrict__ dcol, const T* __restrict__ pw,
-                                                   const T* __restrict__ q, T* __restrict__ grid) {
-  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (g >= G) return;
-  const int n = len[g];
+__global__ void __launch_bounds__(kBlock) k_project(int64_t G, const int32_t* __restrict__ map,
+                                                   const int32_t* __restrict__ len, const int32_t* __restrict__ base,
+                                                   const int64_t* __restrict__ off, const CT* __restrict__ dcol,
+                                                   const T* __restrict__ pw, const T* __restrict__ q,
+                                                   T* __restrict__ grid) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= G) return;
+  const int64_t g = map ? (int64_t)map[t] : t;   // grid point of this thread (null map: identity)
+  const int n = len[t];
   T acc = 0;
-  if (n > 0) {
-    const int64_t b = base[g];
-    int64_t o = off[g >> 5] + (g & 31);
-#pragma unroll 4
-    for (int j = 0; j < n; ++j, o += 32) acc += __ldcs(pw + o) * __ldg(q + b + __ldcs(dcol + o));
-  }
+  if (n > 0) acc = sell_dot<8>(pw, dcol, q, (int64_t)base[t], off[t >> 5] + (t & 31), n);
   grid[g] = acc;
 }
 
@@ -171,10 +191,7 @@ __global__ void __launch_bounds__(kBlock) k_interp(
     }
   }
   {  // step 4: point precorrection (SELL-32 row)
-    const int n = clen[t];
-    int64_t o = coff[t >> 5] + (t & 31);
-#pragma unroll 4
-    for (int j = 0; j < n; ++j, o += 32) acc += __ldcs(cval + o) * __ldg(q + i + __ldcs(dcol + o));
+    acc += sell_dot<8>(cval, dcol, q, i, coff[t >> 5] + (t & 31), clen[t]);
   }
   // near-element entries beyond the adjacency pattern
   for (int32_t p = rowptrX[i]; p < rowptrX[i + 1]; ++p) {
@@ -305,11 +322,11 @@ void launch_anterp(const DevOps<T>& d, cudaStream_t st) {
   d.prof.begin(KID_ANTERP, st);
   const int64_t G = Pm.rows;
   if (Pm.col16)
-    k_project<T, int16_t><<<blocks_for(G), kBlock, 0, st>>>(G, Pm.len, Pm.base, Pm.off, (const int16_t*)Pm.delta,
-                                                            Pm.val[0], d.q, d.grid);
+    k_project<T, int16_t><<<blocks_for(G), kBlock, 0, st>>>(G, Pm.map, Pm.len, Pm.base, Pm.off,
+                                                            (const int16_t*)Pm.delta, Pm.val[0], d.q, d.grid);
   else
-    k_project<T, int32_t><<<blocks_for(G), kBlock, 0, st>>>(G, Pm.len, Pm.base, Pm.off, (const int32_t*)Pm.delta,
-                                                            Pm.val[0], d.q, d.grid);
+    k_project<T, int32_t><<<blocks_for(G), kBlock, 0, st>>>(G, Pm.map, Pm.len, Pm.base, Pm.off,
+                                                            (const int32_t*)Pm.delta, Pm.val[0], d.q, d.grid);
   if (d.nx_exc > 0)
     k_project_exc<T><<<blocks_for(d.nx_exc), kBlock, 0, st>>>(d.nx_exc, d.xnode, d.xgrid, d.xw, d.q, d.grid);
   d.prof.end(KID_ANTERP, st);

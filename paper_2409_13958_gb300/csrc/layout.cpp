@@ -53,7 +53,8 @@ bool wrap_axis(int& v, int N, bool per) {
 // SELL-32 from row callbacks: len(r), base(r) and fill(r, put(col, values[comps])).  With
 // sigma > 1, rows are sorted by decreasing length inside windows of sigma rows so that
 // the 32 rows of a chunk have similar lengths (little padding).
-void build_sell(SellMatrix& M, int64_t rows, int comps, int sigma, const std::function<int64_t(int64_t)>& len,
+void build_sell(SellMatrix& M, int64_t rows, int comps, int sigma, int col_bits,
+                const std::function<int64_t(int64_t)>& len,
                 const std::function<int32_t(int64_t)>& base,
                 const std::function<void(int64_t, const std::function<void(int32_t, const double*)>&)>& fill) {
   M.rows = rows;
@@ -104,7 +105,7 @@ void build_sell(SellMatrix& M, int64_t rows, int comps, int sigma, const std::fu
     }
   }, 64);
   for (int64_t c = 0; c < nch; ++c) maxd = std::max(maxd, maxd_t[c]);
-  M.col16 = maxd <= 32767;
+  M.col16 = col_bits == 16 ? maxd <= 32767 : (col_bits == 32 ? false : maxd <= 32767);
   if (M.col16) {
     M.d16.assign(delta.begin(), delta.end());
     M.d32.clear();
@@ -122,8 +123,13 @@ int build_layout(const Setup& s, Layout& L, size_t smem_budget, size_t elem_byte
   L.pr = (p % 2 == 1) ? (p + 1) / 2 : p / 2 + 1;
   (void)smem_budget;
   (void)elem_bytes;
-  L.TY = 1;
-  L.TZ = 1;
+  // box order: tiles of TY rows x TZ planes (defaults favour gather locality)
+  L.TY = s.tile_y > 0 ? s.tile_y : 8;
+  L.TZ = s.tile_z > 0 ? s.tile_z : 4;
+  while (L.TY > 1 && N[1] % L.TY) L.TY /= 2;
+  while (L.TZ > 1 && N[2] % L.TZ) L.TZ /= 2;
+  L.TY = std::min(L.TY, N[1]);
+  L.TZ = std::min(L.TZ, N[2]);
   // permutation: by box index, then by unknown index
   std::vector<int64_t> key(Np);
   for (int64_t u = 0; u < Np; ++u) key[u] = L.box_index(s.box[3 * u], s.box[3 * u + 1], s.box[3 * u + 2], N);
@@ -254,7 +260,7 @@ int build_layout(const Setup& s, Layout& L, size_t smem_budget, size_t elem_byte
       return EINVAL_;
     }
   // SELL-32 operators
-  build_sell(L.adj, Np, 10, 1, [&](int64_t i) { return (int64_t)(L.rowptr[i + 1] - L.rowptr[i]); },
+  build_sell(L.adj, Np, 10, 1, s.col_bits, [&](int64_t i) { return (int64_t)(L.rowptr[i + 1] - L.rowptr[i]); },
              [&](int64_t i) { return (int32_t)i; },
              [&](int64_t i, const std::function<void(int32_t, const double*)>& put) {
                for (int64_t q = L.rowptr[i]; q < L.rowptr[i + 1]; ++q) {
@@ -263,9 +269,9 @@ int build_layout(const Setup& s, Layout& L, size_t smem_budget, size_t elem_byte
                  put(L.col[q], v);
                }
              });
-  // rows keep the box order (no length sort): a warp's 32 rows are neighbours and share
-  // their gathers in L1
-  build_sell(L.cor, Np, 1, 1, [&](int64_t i) { return L.cptr[i + 1] - L.cptr[i]; },
+  // rows sorted by length in windows of 1024 (about a dozen box rows): a warp's rows stay
+  // near one another (shared gathers) and have similar lengths (little idle lanes)
+  build_sell(L.cor, Np, 1, s.sort_window > 0 ? s.sort_window : 1024, s.col_bits, [&](int64_t i) { return L.cptr[i + 1] - L.cptr[i]; },
              [&](int64_t i) { return (int32_t)i; },
              [&](int64_t i, const std::function<void(int32_t, const double*)>& put) {
                for (int64_t o = L.cptr[i]; o < L.cptr[i + 1]; ++o) put(L.ccol[o], &L.cval[o]);
@@ -311,7 +317,7 @@ int build_layout(const Setup& s, Layout& L, size_t smem_budget, size_t elem_byte
     gc[2] = (int)(g / ((int64_t)N[0] * N[1]));
   };
   const int64_t G = (int64_t)N[0] * N[1] * N[2];
-  build_sell(L.pro, G, 1, 1,
+  build_sell(L.pro, G, 1, s.sort_window > 0 ? s.sort_window : 1024, s.col_bits,
              [&](int64_t g) {
                int gc[3];
                gcoord(g, gc);
