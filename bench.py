@@ -165,17 +165,21 @@ def stable_dt(K_rowabs_max: float) -> float:
 
 
 def alg_bytes(name: str, s: int, sz: dict) -> float:
-    """Algorithmic bytes of one launch: every operand read once, every result written once."""
-    Np, nnz, nC, nX = sz["Np"], sz["nnz"], sz["nnzC"], sz["nnzX"]
+    """Algorithmic bytes of one launch: every stored operand read once (sparse operators as
+    stored: values plus 16- or 32-bit column deltas), every result written once."""
+    Np = sz["Np"]
     N0, N1, N2 = sz["dims"]
     F0, F1, F2 = sz["fft"]
     Hx, H1, H2 = F0 // 2 + 1, F1 // 2 + 1, F2 // 2 + 1
     G = N0 * N1 * N2
-    idx = 4 * (Np + 1) + 4 * nnz
-    if name == "charges":
-        return idx + 6 * s * nnz + 3 * s * Np + 2 * s * Np
-    if name == "projection":
-        return 12 * Np + 3 * s * Np + s * Np + 2 * s * G
+    dev = sz["dev"]
+    cb = {k: dev[k]["col_bits"] // 8 for k in ("adjacency", "precorrection", "projection")}
+    na, nc, npro = (dev[k]["entries"] for k in ("adjacency", "precorrection", "projection"))
+    v4 = 4 * s                                  # internal magnetisation 4-vector
+    if name == "charges":                      # len, W^q and E values, m once, q and e written
+        return 4 * Np + na * (cb["adjacency"] + 6 * s) + v4 * Np + 2 * s * Np
+    if name == "projection":                   # len + base per grid point, weights, q once, grid written
+        return 8 * G + npro * (cb["projection"] + s) + s * Np + s * G
     if name == "fft_x_fwd":
         return s * G + 2 * s * Hx * N1 * N2
     if name == "fft_y_fwd":
@@ -186,14 +190,12 @@ def alg_bytes(name: str, s: int, sz: dict) -> float:
         return 2 * s * Hx * F1 * N2 + 2 * s * Hx * N1 * N2
     if name == "fft_x_inv":
         return 2 * s * Hx * N1 * N2 + s * G
-    if name == "interp_precorr":
-        # stencil (base + fractions), grid U once, C (rowptr, col, value), q and e once, u written,
-        # plus the near-element entries beyond the adjacency pattern (and m) when present
-        return (12 + 3 * s) * Np + s * G + 4 * (Np + 1) + (4 + s) * nC + 3 * s * Np \
-            + ((4 * (Np + 1) + (4 + 3 * s) * nX + 3 * s * Np) if nX else 0)
-    if name == "gradient_exchange":
-        # RK stage epilogue averaged over the four stages: m_s, m0 read; m_next / m0 written; acc
-        return idx + 4 * s * nnz + s * Np + 3 * s * Np + 3 * s * Np + 3 * s * Np + 4.5 * s * Np
+    if name == "interp_precorr":               # stencil data, grid once, precorrection row, q and e once, u written
+        return (12 + 3 * s + 4) * Np + s * G + nc * (cb["precorrection"] + s) + 3 * s * Np
+    if name == "gradient_exchange":            # gradient + exchange values, u and m once, RK4 stage state
+        return 4 * Np + na * (cb["adjacency"] + 4 * s) + s * Np + v4 * Np + 3.5 * v4 * Np
+    if name == "permute":
+        return 4 * Np + 3 * s * Np + v4 * Np
     if name == "grid_clear":
         return s * G
     raise KeyError(name)
@@ -326,6 +328,8 @@ def run_native(args):
             rowabs = np.add.reduceat(np.abs(vals[:, 0]), rp[:-1]) if col.size else np.zeros(1)
     dims, fft, origin, delta = h.grid_info()
     sizes["dims"], sizes["fft"] = [int(x) for x in dims], [int(x) for x in fft]
+    h.set_precision(PMFEM_FP32)
+    sizes["dev"] = h.device_info()
     dt = stable_dt(float(rowabs.max()))
 
     stream = torch.cuda.Stream()          # explicit stream: every launch and event goes on it
@@ -447,7 +451,7 @@ def run_native(args):
                    "tets": int(mesh.n_tets), "grid": [int(x) for x in dims], "fft": [int(x) for x in fft],
                    "p": P_ORDER, "near_boxes": NEAR_BOXES, "near_elem_factor": NEAR_ELEM, "precision": "fp32",
                    "step": "one RK4 LLG step = 4 field evaluations", "dt_s": dt,
-                   "nnz_adjacency": sizes["nnz"], "nnz_precorrection": sizes["nnzC"],
+                   "nnz_adjacency": sizes["nnz"], "nnz_precorrection": sizes["nnzC"], "device_layout": sizes["dev"],
                    "l2": "inputs larger than L2 (operator data streamed every evaluation)",
                    "parallelism": f"replicas x{world}", "setup_s": round(t_setup, 1), "mesh_s": round(t_mesh, 1)},
         "clocks": ck,

@@ -182,6 +182,14 @@ int pmfem_destroy(pmfem_t h);
 int pmfem_operator_info(pmfem_t h, int which, int64_t* rows, int64_t* nnz, int* comps);
 int pmfem_operator_export(pmfem_t h, int which, int32_t* rowptr, int32_t* col, double* vals);
 
+/*
+ * Device layout facts (uploads the device data for the current precision if needed):
+ * out[0..2] adjacency entries, padded SELL slots, column bits; out[3..5] the same for the
+ * point precorrection; out[6..8] for the projection; out[9] projection exception entries;
+ * out[10..11] box-order tile rows and planes.
+ */
+int pmfem_device_info(pmfem_t h, int64_t* out, int n);
+
 /* Grid of Eq. 16 as set up: dims[3], fft[3], origin[3], delta[3] (host). */
 int pmfem_grid_info(pmfem_t h, int32_t* dims, int32_t* fft, double* origin, double* delta);
 /* PGF spectrum (Eq. 15 on the grid, transformed), reduced by symmetry:

@@ -43,6 +43,7 @@ SIGNATURES = {
     "pmfem_destroy": (_c.c_int, [_vp]),
     "pmfem_operator_info": (_c.c_int, [_vp, _c.c_int, _pi64, _pi64, _c.POINTER(_c.c_int)]),
     "pmfem_operator_export": (_c.c_int, [_vp, _c.c_int, _vp, _vp, _vp]),
+    "pmfem_device_info": (_c.c_int, [_vp, _vp, _c.c_int]),
     "pmfem_grid_info": (_c.c_int, [_vp, _vp, _vp, _vp, _vp]),
     "pmfem_export_spectrum": (_c.c_int, [_vp, _vp]),
     "pmfem_folded_positions": (_c.c_int, [_vp, _vp]),
@@ -195,6 +196,16 @@ class Pmfem:
         vals = np.empty((nnz.value, comps.value), dtype=np.float64)
         self._ck(self._lib.pmfem_operator_export(self.h, which, rp.ctypes.data, col.ctypes.data, vals.ctypes.data))
         return rp, col, vals
+
+    def device_info(self) -> dict:
+        out = np.zeros(12, dtype=np.int64)
+        self._ck(self._lib.pmfem_device_info(self.h, out.ctypes.data, 12))
+        names = ("adjacency", "precorrection", "projection")
+        d = {n: {"entries": int(out[3 * k]), "padded": int(out[3 * k + 1]), "col_bits": int(out[3 * k + 2])}
+             for k, n in enumerate(names)}
+        d["projection_exceptions"] = int(out[9])
+        d["tile"] = (int(out[10]), int(out[11]))
+        return d
 
     def grid_info(self):
         dims = np.zeros(3, np.int32)

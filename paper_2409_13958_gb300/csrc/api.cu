@@ -41,6 +41,7 @@ struct pmfem_state {
   cudaEvent_t open_ev[KID_COUNT] = {};
   int64_t prof_count[KID_COUNT] = {};
   double prof_ms[KID_COUNT] = {};
+  int64_t dev_info[12] = {};   // layout facts of the current device upload
 };
 
 namespace {
@@ -183,6 +184,17 @@ int build_device(pmfem_t h, DevOps<T>& d) {
   if ((rc = upload_sell(h, L.adj, d.adj))) return rc;
   if ((rc = upload_sell(h, L.cor, d.cor))) return rc;
   if ((rc = upload_sell(h, L.pro, d.pro))) return rc;
+  const SellMatrix* ms[3] = {&L.adj, &L.cor, &L.pro};
+  for (int k = 0; k < 3; ++k) {
+    int64_t nnz = 0;
+    for (int32_t v : ms[k]->len) nnz += v;
+    h->dev_info[3 * k] = nnz;
+    h->dev_info[3 * k + 1] = ms[k]->padded();
+    h->dev_info[3 * k + 2] = ms[k]->col16 ? 16 : 32;
+  }
+  h->dev_info[9] = (int64_t)L.xnode.size();
+  h->dev_info[10] = L.TY;
+  h->dev_info[11] = L.TZ;
   d.nx_exc = (int64_t)L.xnode.size();
   if ((rc = upload(h, L.xnode.data(), L.xnode.size(), &d.xnode))) return rc;
   if ((rc = upload(h, L.xgrid.data(), L.xgrid.size(), &d.xgrid))) return rc;
@@ -571,6 +583,14 @@ int pmfem_operator_export(pmfem_t h, int which, int32_t* rowptr, int32_t* col, d
   std::memcpy(rowptr, rp.data(), sizeof(int32_t) * rp.size());
   std::memcpy(col, cl.data(), sizeof(int32_t) * cl.size());
   std::memcpy(vals, v.data(), sizeof(double) * v.size());
+  return OK;
+}
+
+int pmfem_device_info(pmfem_t h, int64_t* out, int n) {
+  if (!h || !out || n <= 0) return EINVAL_;
+  int rc = ensure_device(h);
+  if (rc) return rc;
+  for (int i = 0; i < n; ++i) out[i] = i < 12 ? h->dev_info[i] : 0;
   return OK;
 }
 
