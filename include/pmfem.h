@@ -138,6 +138,25 @@ int pmfem_field(pmfem_t h, const void* m, void* H, int components, void* stream)
  * out and synchronises the stream before returning. */
 int pmfem_field_host(pmfem_t h, const void* m_host, void* H_host, int components, void* stream);
 
+/*
+ * pmfem_field without any allocation (the paper has no counterpart; this is a service for
+ * callers that must not allocate device memory when they ask for a field: real-time loops
+ * that forbid allocator calls, or hosts whose device memory belongs to a pooling
+ * allocator).  Same arguments and same result as
+ * pmfem_field; all scratch of the evaluation lives in one fixed 64 MiB device array
+ * compiled into the library, which every GPU that loads the library keeps until the
+ * process exits.  The call allocates nothing itself:
+ *   - the handle's operators must already be on the device at the current precision (one
+ *     earlier pmfem_field or pmfem_set_m call); otherwise ESTATE;
+ *   - a mesh and grid whose scratch exceeds 64 MiB give EINVAL (use pmfem_field);
+ *   - the first call on a device looks up the array's address (cudaGetSymbolAddress) and
+ *     should therefore come before any stream capture;
+ *   - every call on a device shares the one array: calls that overlap on the GPU (other
+ *     streams, other handles) race and must be serialised by the caller.  Nothing in the
+ *     array needs to start at zero; it keeps whatever the last call left.
+ */
+int pmfem_field_noalloc(pmfem_t h, const void* m, void* H, int components, void* stream);
+
 /* Internal magnetisation state (checkpoint / resume), device N' x 3 T; set_m copies in,
  * get_m copies out.  set_m normalises nothing: pass unit vectors. */
 int pmfem_set_m(pmfem_t h, const void* m, void* stream);

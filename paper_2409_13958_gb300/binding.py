@@ -34,6 +34,7 @@ SIGNATURES = {
     "pmfem_lca_map": (_c.c_int, [_vp, _vp]),
     "pmfem_field": (_c.c_int, [_vp, _vp, _vp, _c.c_int, _vp]),
     "pmfem_field_host": (_c.c_int, [_vp, _vp, _vp, _c.c_int, _vp]),
+    "pmfem_field_noalloc": (_c.c_int, [_vp, _vp, _vp, _c.c_int, _vp]),
     "pmfem_set_m": (_c.c_int, [_vp, _vp, _vp]),
     "pmfem_get_m": (_c.c_int, [_vp, _vp, _vp]),
     "pmfem_llg_step": (_c.c_int, [_vp, _dbl, _c.c_int, _vp]),
@@ -155,6 +156,9 @@ class Pmfem:
 
     def field_host(self, m_host, H_host, components: int = PMFEM_ALL, stream=None):
         self._ck(self._lib.pmfem_field_host(self.h, _addr(m_host), _addr(H_host), components, _stream(stream)))
+
+    def field_noalloc(self, m, H, components: int = PMFEM_ALL, stream=None):
+        self._ck(self._lib.pmfem_field_noalloc(self.h, _addr(m), _addr(H), components, _stream(stream)))
 
     def set_m(self, m, stream=None):
         self._ck(self._lib.pmfem_set_m(self.h, _addr(m), _stream(stream)))

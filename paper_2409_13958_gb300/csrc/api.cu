@@ -1,6 +1,7 @@
 // C-ABI of libpmfem (declared in include/pmfem.h).
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -621,3 +622,102 @@ int pmfem_folded_positions(pmfem_t h, double* out) {
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------------------------------------
+// Field evaluation without any allocation.
+//
+// Some callers cannot allocate device memory at the moment they need a field: real-time
+// loops that forbid allocator calls, or hosts whose memory is owned by a pooling allocator
+// that the library must not bypass.
+// pmfem_field_noalloc serves them: it computes exactly what pmfem_field computes, but every
+// scratch buffer of the evaluation (the permuted magnetisation, charges, potentials, the
+// grid and the FFT spectrum buffer) is carved out of one file-scope device array of fixed
+// size, and the call makes no allocating CUDA or library call.  The array exists on every
+// GPU that loads this library, for the lifetime of the process.
+// ------------------------------------------------------------------------------------
+namespace {
+
+constexpr size_t kNoAllocBytes = 64u << 20;   // 64 MiB of shared scratch per device
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+constexpr int kMaxDevices = 128;
+void* g_noalloc_ptr[kMaxDevices] = {};
+std::mutex g_noalloc_mutex;
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// bytes of scratch one evaluation of this handle needs at precision T
+template <typename T>
+size_t noalloc_need(const Setup& s) {
+  using C2 = typename Vec2<T>::type;
+  const size_t np = (size_t)s.Np;
+  const size_t G = (size_t)s.dims[0] * s.dims[1] * s.dims[2];
+  const size_t ncb = (size_t)(s.fft[0] / 2 + 1) * s.fft[1] * s.fft[2];
+  return align256(np * sizeof(V4<T>)) + 3 * align256(np * sizeof(T)) + align256(G * sizeof(T)) +
+         align256(ncb * sizeof(C2));
+}
+
+template <typename T>
+void noalloc_eval(pmfem_t h, const DevOps<T>& d, unsigned char* base, const void* m, void* H, int comps,
+                  cudaStream_t st) {
+  using C2 = typename Vec2<T>::type;
+  DevOps<T> x = d;          // same operators, scratch redirected into the static array
+  x.prof = ProfHook();      // no event creation on this path
+  const size_t np = (size_t)d.Np;
+  const size_t G = (size_t)d.dims[0] * d.dims[1] * d.dims[2];
+  size_t off = 0;
+  V4<T>* mf = (V4<T>*)(base + off);
+  off += align256(np * sizeof(V4<T>));
+  x.q = (T*)(base + off);
+  off += align256(np * sizeof(T));
+  x.e = (T*)(base + off);
+  off += align256(np * sizeof(T));
+  x.u = (T*)(base + off);
+  off += align256(np * sizeof(T));
+  x.grid = (T*)(base + off);
+  off += align256(G * sizeof(T));
+  x.cbuf = (C2*)(base + off);
+  // every scratch element is written by the evaluation before it is read, so nothing has
+  // to start at zero
+  launch_perm_in(x, (const T*)m, mf, st);
+  RkArgs none;
+  enqueue_eval(h, x, (const V4<T>*)mf, (T*)H, comps, none, st);
+}
+
+}  // namespace
+
+extern "C" int pmfem_field_noalloc(pmfem_t h, const void* m, void* H, int components, void* stream) {
+  if (!h) return EINVAL_;
+  if (!m || !H || m == H) return fail(h, EINVAL_, "m and H must be distinct device pointers");
+  if (components <= 0 || components > PMFEM_ALL) return fail(h, EINVAL_, "components must be a non-empty PMFEM_EX|MS|AP mask");
+  if (!h->s.ready) return fail(h, ESTATE_, "call pmfem_set_periodicity first");
+  const size_t need = h->prec == PMFEM_FP64 ? noalloc_need<double>(h->s) : noalloc_need<float>(h->s);
+  if (need > kNoAllocBytes)
+    return fail(h, EINVAL_, "pmfem_field_noalloc: this mesh and grid need " + std::to_string(need) +
+                                " bytes of scratch, more than its fixed " + std::to_string(kNoAllocBytes) +
+                                " bytes; use pmfem_field");
+  if (!h->dev_ready || h->dev_prec != h->prec)
+    return fail(h, ESTATE_, "pmfem_field_noalloc needs the operators on the device: make one pmfem_field (or "
+                            "pmfem_set_m) call at this precision first");
+  int dev = 0;
+  PMFEM_CK(h, cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDevices) return fail(h, EINVAL_, "device index out of range");
+  void* base = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(g_noalloc_mutex);
+    if (!g_noalloc_ptr[dev]) {
+      // once per device, with that device current: the array's device address
+      void* p = nullptr;
+      cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+      if (e != cudaSuccess || !p)
+        return fail(h, ECUDA_, std::string("cudaGetSymbolAddress of the no-alloc scratch failed: ") +
+                                   cudaGetErrorString(e));
+      g_noalloc_ptr[dev] = p;
+    }
+    base = g_noalloc_ptr[dev];
+  }
+  cudaStream_t st = stream ? (cudaStream_t)stream : h->stream;
+  if (h->dev_prec == PMFEM_FP64) noalloc_eval(h, h->d64, (unsigned char*)base, m, H, components, st);
+  else noalloc_eval(h, h->d32, (unsigned char*)base, m, H, components, st);
+  return check_launch(h);
+}
