@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--nodes", type=int, default=1_000_000)
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison leg")
     ap.add_argument("--no-cpu", action="store_true", help="skip the cpu_baseline leg")
+    ap.add_argument("--no-bf16", action="store_true", help="skip the BF16-split leg")
+    ap.add_argument("--no-batch", action="store_true", help="skip the 64-cell batch leg")
     ap.add_argument("--out", default=None, help="also write the JSON line to this file")
     return ap.parse_args()
 
@@ -296,6 +298,110 @@ def run_reference(args):
 
 
 # ------------------------------------------------------------------ GPU leg
+def bf16_leg(h, m0, dt, comps, H32, H64, stream, dist, world, Np, args):
+    """BF16-split precision on the same workload: its speed, and its field error per term
+    against the FP64 path (against FP32 when the FP64 leg is skipped)."""
+    import torch
+    from paper_2409_13958_gb300 import PMFEM_BF16SPLIT
+    h.set_precision(PMFEM_BF16SPLIT)
+    m32 = torch.tensor(m0, dtype=torch.float32, device="cuda")
+    Hb = {}
+    for name, c in comps.items():
+        t = torch.empty_like(m32)
+        h.field(m32, t, c, stream)
+        h.sync()
+        Hb[name] = t.double().cpu().numpy()
+    ref = H64 if H64 is not None else H32
+    rel = {n: float(np.linalg.norm(Hb[n] - ref[n]) / np.linalg.norm(ref[n])) for n in comps}
+    h.set_m(m32, stream)
+    for _ in range(3):
+        h.llg_step(dt, 1, stream)
+    torch.cuda.synchronize()
+    h.profile(True)
+    k = max(3, args.steps // 2)
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    f0.record(stream)
+    for _ in range(k):
+        h.llg_step(dt, 1, stream)
+    f1.record(stream)
+    f1.synchronize()
+    prof = h.profile_read()
+    h.profile(False)
+    ms = dist.max(f0.elapsed_time(f1))
+    return {"value": world * Np * 4 * k / (ms * 1e-3), "ms_per_step": ms / k, "steps": k,
+            "bf16_operators": "precorrection, projection, gradient (charges, exchange, vectors, grid in FP32)",
+            "rel_l2_vs": "fp64" if H64 is not None else "fp32", "rel_l2_by_term": rel, "tolerance": 3e-3,
+            "kernels_us": {n: round(1e3 * t / c, 1) for n, (c, t) in prof.items() if c}}
+
+
+def batch_leg(args, dist, world):
+    """64 independent 2D-periodic film/dot cells (5k-80k nodes, periods 40-200 nm, thickness
+    2-10 nm), each at one applied-field point of a hysteresis sweep -100..+100 mT along x;
+    tiles autotuned; RK4 steps replayed from one captured graph, FP32.  Also the same steps
+    with every cell stepped on its own, for the batching gain."""
+    import torch
+    import meshgen
+    from paper_2409_13958_gb300 import Pmfem, PmfemBatch, PMFEM_FP32
+    mu0 = 4e-7 * math.pi
+    t0 = time.time()
+    cells = meshgen.batch_cells(64, seed=0)
+    hs = []
+    for i, c in enumerate(cells):
+        h = Pmfem.create_mesh(c.xyz, c.tets, MS, AEX, ALPHA)
+        h.set_aim(0, 0, 0, P_ORDER, NEAR_BOXES, NEAR_ELEM)
+        h.set_periodicity(*c.periods)
+        h.set_precision(PMFEM_FP32)
+        h.set_applied_field((-0.1 + 0.2 * i / 63) / mu0, 0.0, 0.0)
+        hs.append(h)
+    t_setup = time.time() - t0
+    dt = math.inf                   # the smallest stable step over the cells
+    for h in hs:
+        rp, col, vals = h.operator_export(0)
+        dt = min(dt, stable_dt(float(np.add.reduceat(np.abs(vals[:, 0]), rp[:-1]).max())))
+    b = PmfemBatch(hs)
+    t0 = time.time()
+    b.autotune(2)
+    t_tune = time.time() - t0
+    off = b.offsets()
+    n = int(off[-1])
+    stream = torch.cuda.current_stream()
+    m = torch.tensor(meshgen.m_uniform(n, (1.0, 0.0, 0.0)), dtype=torch.float32, device="cuda")
+    b.set_m(m, stream)
+    for _ in range(3):
+        b.llg_step(dt, 1, stream)
+    torch.cuda.synchronize()
+    dist.barrier()
+    k = 10
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    b.llg_step(dt, k, stream)
+    e1.record(stream)
+    e1.synchronize()
+    ms = dist.max(e0.elapsed_time(e1))
+    b.sync()
+    single = 0.0
+    for h in hs:
+        mk = m[:h.num_unknowns()].contiguous()
+        h.set_m(mk, stream)
+        h.llg_step(dt, 1, stream)
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        h.llg_step(dt, 2, stream)
+        f1.record(stream)
+        f1.synchronize()
+        single += f0.elapsed_time(f1) / 2
+    tiles = b.tiles()
+    b.destroy()
+    for h in hs:
+        h.destroy()
+    return {"workload": "batch-64-cells-hysteresis", "cells": 64, "unknowns": n,
+            "value": world * n * 4 * k / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms / k, "steps": k,
+            "one_by_one_ms_per_step": single, "batching_gain": single / (ms / k),
+            "dt_s": dt, "setup_s": round(t_setup, 1), "autotune_s": round(t_tune, 1),
+            "tiles_used": sorted({f"{int(a)}x{int(c)}" for a, c in tiles}), "precision": "fp32",
+            "launch": "one captured CUDA graph per RK4 step, one launch per pass over all cells"}
+
+
 def run_native(args):
     import torch
     from paper_2409_13958_gb300 import Pmfem, PMFEM_FP32, PMFEM_FP64, PMFEM_ALL
@@ -428,6 +534,7 @@ def run_native(args):
                 "fp32_field_rel_l2_vs_fp64": rel["all"], "fp32_rel_l2_by_term": rel,
                 "fp32_rel_l2_same_input_by_term": rel_same}
         fp64["fp32_speedup"] = value / fp64["value"]
+    bf16 = bf16_leg(h, m0, dt, comps, H32, H64 if fp64 else None, stream, dist, world, Np, args) if not args.no_bf16 else None
     h.destroy()
 
     # roofline of the dominant kernel
@@ -462,8 +569,11 @@ def run_native(args):
                      "frac": achieved / peak, "peak_kind": peak_kind, "alg_bytes_per_launch": dom_bytes,
                      "traffic": ncu_traffic(dom)},
         "fp64": fp64 or None,
+        "bf16split": bf16,
         "kernels": per,
     }
+    if not args.no_batch:
+        line["batch"] = batch_leg(args, dist, world)
     if rank == 0 and not args.no_cpu:
         ob, grid = oracle_sample(6000)
         n, el = time_oracle(ob, 15.0)

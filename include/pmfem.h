@@ -57,8 +57,17 @@ typedef struct pmfem_state* pmfem_t;
 /* precision modes */
 #define PMFEM_FP64      0
 #define PMFEM_FP32      1
-#define PMFEM_BF16SPLIT 2     /* BF16 storage of operator values and grid buffers,
-                                 FP32 arithmetic and accumulation                       */
+#define PMFEM_BF16SPLIT 2     /* split precision: the operators chosen by
+                                 pmfem_set_bf16_operators are stored in bfloat16, all
+                                 others and every vector and grid buffer in FP32; all
+                                 arithmetic and accumulation in FP32                    */
+
+/* operator bitmask for pmfem_set_bf16_operators */
+#define PMFEM_BF16_PRECORRECTION 1   /* point precorrection C (BAIM step 4)                 */
+#define PMFEM_BF16_PROJECTION    2   /* Lagrange weights of the projection (step 1)         */
+#define PMFEM_BF16_CHARGES       4   /* W^q of Eq. 14a and the near-element E of Eq. 14c    */
+#define PMFEM_BF16_GRADIENT      8   /* -V^-1 (W^q)^T of Eq. 14d                            */
+#define PMFEM_BF16_EXCHANGE     16   /* periodized Laplacian of Eq. 8                       */
 
 /* field component bitmask for pmfem_field */
 #define PMFEM_EX 1
@@ -72,7 +81,7 @@ const char* pmfem_last_error(pmfem_t h);
 
 /*
  * Create a mesh handle (Sec. 2.2 discrete formulation, P1 tetrahedra, Eq. 4).
- *   xyz   host, N x 3 doubles, node coordinates in metres
+ *   xyz   host, N x 3 doubles, node coordinates in metres; N <= 2^30 (else EINVAL)
  *   tets  host, T x 4 int32, node indices in [0, N); negatively oriented tetrahedra
  *         are re-oriented, tetrahedra with 6|V| <= 1e-12 * (longest edge)^3 -> EMESH
  *   Ms    saturation magnetisation [A/m] (> 0); A exchange stiffness [J/m] (>= 0);
@@ -111,13 +120,29 @@ int pmfem_set_periodicity(pmfem_t h, double L1, double L2, double L3);
  * Device layout tuning (no paper counterpart; it changes speed, not results beyond
  * rounding).  Unknowns are stored sorted by grid box in tiles of tile_y box rows x tile_z
  * box planes (x fastest); precorrection rows may be sorted by length inside windows of
- * sort_window rows; column indices are stored as 16-bit deltas when every delta fits
- * (col_bits 0 or 16) or as 32-bit deltas (col_bits 32).  0 selects the defaults (8, 4, 1024,
+ * sort_window rows; column indices are stored as deltas to a per-row base, modulo N', in
+ * 16 bits when every delta fits (col_bits 0 or 16) or in 32 bits (col_bits 32).  0 selects the defaults (8, 4, 1024,
  * 16-bit when possible).  Takes effect at the next device upload; may come before or after pmfem_set_periodicity.
  */
 int pmfem_set_layout(pmfem_t h, int tile_y, int tile_z, int sort_window, int col_bits);
 
 int pmfem_set_precision(pmfem_t h, int mode);                       /* PMFEM_FP64 | FP32 | BF16SPLIT */
+
+/*
+ * Operators stored in bfloat16 under PMFEM_BF16SPLIT (bitmask of PMFEM_BF16_*; the method
+ * itself is precision-agnostic, Sec. 4 runs it in single precision).  Values are rounded
+ * once from the FP64 set-up to the nearest bfloat16 (ties to even) and widened exactly to
+ * FP32 in the kernels, so each chosen operator carries a relative error of at most 2^-9 per
+ * entry and moves half the bytes.  Default PMFEM_BF16_PRECORRECTION | PMFEM_BF16_PROJECTION
+ * | PMFEM_BF16_GRADIENT.  The charge operator (Eq. 14a) and the exchange operator (Eq. 8)
+ * stay in FP32 by default: both act on m itself, whose neighbouring values nearly cancel
+ * (charges are a divergence, exchange a Laplacian), so a 2^-9 error per entry grows into
+ * an error of a few 1e-3 (magnetostatic field) and a few 1e-2 (exchange field) on a
+ * smooth m.  Takes effect at the next device upload (a change under an uploaded
+ * BF16-split device drops its data, the state m included).  EINVAL for bits outside the
+ * five flags.
+ */
+int pmfem_set_bf16_operators(pmfem_t h, int mask);
 int pmfem_set_applied_field(pmfem_t h, double Hx, double Hy, double Hz);   /* A/m, uniform       */
 
 /* Number of unknowns N' (Sec. 2.2) and the node -> unknown map (host, N int32). */
@@ -216,6 +241,69 @@ int pmfem_grid_info(pmfem_t h, int32_t* dims, int32_t* fft, double* origin, doub
 int pmfem_export_spectrum(pmfem_t h, double* out);
 /* Folded unknown positions of Eq. 18 (host, N' x 3 doubles). */
 int pmfem_folded_positions(pmfem_t h, double* out);
+
+/* ======================================================================================
+ * Batches of independent cells (the paper has no counterpart: a service for sweeps such as
+ * a hysteresis loop, where many unit cells, each with its own applied field, advance
+ * together).  A batch evaluates the field of every cell and advances every cell by RK4 in
+ * FP32, as pmfem_field / pmfem_llg_step would for each cell alone, but each pass runs as one
+ * launch over the rows of all cells (one FFT launch per group of cells with the same grid
+ * shape), and a whole RK4 step is replayed from a captured CUDA graph.
+ *
+ * Arrays of a batch are device N_tot x 3 FP32, the cells' unknowns concatenated in cell
+ * order (pmfem_batch_offsets gives where each cell starts).
+ * ====================================================================================== */
+typedef struct pmfem_batch_state* pmfem_batch_t;
+
+/*
+ * Batch of n cells (n >= 1).  Every cell must be set up (pmfem_set_periodicity done, else
+ * ESTATE) and all must use the same stencil order p (else EINVAL).  The batch keeps the
+ * handles, which must outlive it; it reads each cell's set-up, layout settings and applied
+ * field when it builds its device data (at the first call that needs them).  The cells
+ * stay usable on their own.  *out is NULL on failure.
+ */
+int pmfem_batch_create(pmfem_batch_t* out, const pmfem_t* cells, int n);
+int pmfem_batch_destroy(pmfem_batch_t b);
+const char* pmfem_batch_last_error(pmfem_batch_t b);
+
+/* offsets (host, n + 1): cell c owns unknowns [offsets[c], offsets[c + 1]). */
+int pmfem_batch_offsets(pmfem_batch_t b, int64_t* offsets);
+
+/*
+ * Box-order tiles by measurement (autotuner): for every cell, each candidate tile shape
+ * (tile rows x tile planes: 8x4, 8x2, 4x4, 16x2, 4x2) is set with pmfem_set_layout, the
+ * cell's own FP32 field is timed (reps evaluations, CUDA events, after one warm-up), and the
+ * fastest is kept.  Results are cached for the process per (grid shape, FFT shape, N'
+ * within a factor 2^(1/4)), so cells alike are tuned once.  Changes the cells' layout
+ * settings, drops the batch's device data (the state m included; the next call rebuilds
+ * it) and synchronises.  reps in [1, 100], else EINVAL.
+ */
+int pmfem_batch_autotune(pmfem_batch_t b, int reps);
+/* tiles (host, 2n): the (tile rows, tile planes) of every cell's box order in the batch's
+ * device data (builds it if needed). */
+int pmfem_batch_tiles(pmfem_batch_t b, int32_t* tiles);
+
+/* Applied field of cell c (A/m, uniform), enqueued on stream: later evaluations and graph
+ * replays use it.  EINVAL for c outside [0, n). */
+int pmfem_batch_set_applied_field(pmfem_batch_t b, int c, double Hx, double Hy, double Hz, void* stream);
+
+/* Field of every cell (as pmfem_field, FP32): m and H device N_tot x 3 FP32. */
+int pmfem_batch_field(pmfem_batch_t b, const void* m, void* H, int components, void* stream);
+
+/* State of every cell (device N_tot x 3 FP32); set_m normalises nothing. */
+int pmfem_batch_set_m(pmfem_batch_t b, const void* m, void* stream);
+int pmfem_batch_get_m(pmfem_batch_t b, void* m, void* stream);
+
+/*
+ * nsteps RK4 steps of size dt (> 0, seconds) of every cell, as pmfem_llg_step.  The first
+ * call for a given dt captures one step into a CUDA graph (on a stream of the library) and
+ * every step replays it on stream.  A cell's applied field is read by the graph at every
+ * replay.  EINVAL for dt <= 0 or nsteps < 0.
+ */
+int pmfem_batch_llg_step(pmfem_batch_t b, double dt, int nsteps, void* stream);
+
+/* Waits for the device and reports a device error of the batch (ENONFINITE) like pmfem_sync. */
+int pmfem_batch_sync(pmfem_batch_t b);
 
 #ifdef __cplusplus
 }

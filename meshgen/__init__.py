@@ -295,14 +295,14 @@ def batch_cells(n_cells=64, seed=0, n_min=5000, n_max=80000, scale=1.0):
         kind = "film" if rng.uniform() < 0.5 else "dot"
         n_target = int(rng.integers(n_min, n_max + 1) * scale)
         if kind == "film":
-            # nx * nx * (nz + 1) ~ n_target with h ~ P / nx and nz = max(1, round(t / h))
-            nx = max(4, int(round((n_target / max(2, round(t / (P / math.sqrt(n_target / 2))) + 1)) ** 0.5)))
+            # largest nx with (nx + 1)^2 (nz + 1) <= n_target, nz = max(1, round(t / (P / nx)))
+            def film_nodes(k):
+                return (k + 1) ** 2 * (max(1, int(round(t / (P / k)))) + 1)
+            nx = 4
+            while film_nodes(nx + 1) <= n_target:
+                nx += 1
             hxy = P / nx
             nz = max(1, int(round(t / hxy)))
-            while (nx + 1) ** 2 * (nz + 1) > n_target and nx > 4:
-                nx -= 1
-                hxy = P / nx
-                nz = max(1, int(round(t / hxy)))
             xyz, tets = kuhn_box(nx, nx, nz, (hxy, hxy, t / nz), jitter=0.1, seed=seed * 1000 + i)
             cells.append(Mesh(xyz, tets, (P, P, 0.0), name=f"film{i}", meta={"kind": kind, "t": t}))
         else:
@@ -315,15 +315,18 @@ def _dot_cell(r, t, P, n_target, seed):
     """Disk (radius r, thickness t) centred in a square 2D-periodic cell of side P."""
     from scipy.spatial import Delaunay
     rng = np.random.default_rng(seed)
-    # layers nz+1, in-plane spacing h: (pi r^2 / (0.866 h^2)) * (nz + 1) ~ n_target
-    h = r * 0.3
-    for _ in range(60):
-        nz = max(1, int(round(t / h)))
-        n2 = math.pi * r * r / (0.866 * h * h)
-        if n2 * (nz + 1) > n_target:
-            h *= 1.02
+    # layers nz+1, in-plane spacing h: (pi r^2 / (0.866 h^2)) * (nz + 1) ~ n_target; the
+    # count falls as h grows, so bisect on log h
+    def count(h):
+        return math.pi * r * r / (0.866 * h * h) * (max(1, int(round(t / h))) + 1)
+    lo, hi = math.log(r * 1e-3), math.log(r)
+    for _ in range(80):
+        mid = 0.5 * (lo + hi)
+        if count(math.exp(mid)) > n_target:
+            lo = mid
         else:
-            h /= 1.02
+            hi = mid
+    h = math.exp(hi)
     nz = max(1, int(round(t / h)))
     pts = [np.zeros((1, 2))]
     nr = max(1, int(round(r / h)))

@@ -13,6 +13,8 @@ import numpy as np
 
 PMFEM_FP64, PMFEM_FP32, PMFEM_BF16SPLIT = 0, 1, 2
 PMFEM_EX, PMFEM_MS, PMFEM_AP, PMFEM_ALL = 1, 2, 4, 7
+(PMFEM_BF16_PRECORRECTION, PMFEM_BF16_PROJECTION, PMFEM_BF16_CHARGES, PMFEM_BF16_GRADIENT,
+ PMFEM_BF16_EXCHANGE) = 1, 2, 4, 8, 16
 
 _ERRORS = {-1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "EMESH", -5: "ENONFINITE", -6: "ETIMEOUT", -7: "ESTATE"}
 
@@ -29,6 +31,7 @@ SIGNATURES = {
     "pmfem_set_periodicity": (_c.c_int, [_vp, _dbl, _dbl, _dbl]),
     "pmfem_set_layout": (_c.c_int, [_vp, _c.c_int, _c.c_int, _c.c_int, _c.c_int]),
     "pmfem_set_precision": (_c.c_int, [_vp, _c.c_int]),
+    "pmfem_set_bf16_operators": (_c.c_int, [_vp, _c.c_int]),
     "pmfem_set_applied_field": (_c.c_int, [_vp, _dbl, _dbl, _dbl]),
     "pmfem_num_unknowns": (_c.c_int, [_vp, _pi64]),
     "pmfem_lca_map": (_c.c_int, [_vp, _vp]),
@@ -45,6 +48,18 @@ SIGNATURES = {
     "pmfem_operator_info": (_c.c_int, [_vp, _c.c_int, _pi64, _pi64, _c.POINTER(_c.c_int)]),
     "pmfem_operator_export": (_c.c_int, [_vp, _c.c_int, _vp, _vp, _vp]),
     "pmfem_device_info": (_c.c_int, [_vp, _vp, _c.c_int]),
+    "pmfem_batch_create": (_c.c_int, [_c.POINTER(_vp), _vp, _c.c_int]),
+    "pmfem_batch_destroy": (_c.c_int, [_vp]),
+    "pmfem_batch_last_error": (_c.c_char_p, [_vp]),
+    "pmfem_batch_offsets": (_c.c_int, [_vp, _vp]),
+    "pmfem_batch_autotune": (_c.c_int, [_vp, _c.c_int]),
+    "pmfem_batch_tiles": (_c.c_int, [_vp, _vp]),
+    "pmfem_batch_set_applied_field": (_c.c_int, [_vp, _c.c_int, _dbl, _dbl, _dbl, _vp]),
+    "pmfem_batch_field": (_c.c_int, [_vp, _vp, _vp, _c.c_int, _vp]),
+    "pmfem_batch_set_m": (_c.c_int, [_vp, _vp, _vp]),
+    "pmfem_batch_get_m": (_c.c_int, [_vp, _vp, _vp]),
+    "pmfem_batch_llg_step": (_c.c_int, [_vp, _dbl, _c.c_int, _vp]),
+    "pmfem_batch_sync": (_c.c_int, [_vp]),
     "pmfem_grid_info": (_c.c_int, [_vp, _vp, _vp, _vp, _vp]),
     "pmfem_export_spectrum": (_c.c_int, [_vp, _vp]),
     "pmfem_folded_positions": (_c.c_int, [_vp, _vp]),
@@ -136,6 +151,9 @@ class Pmfem:
 
     def set_precision(self, mode: int):
         self._ck(self._lib.pmfem_set_precision(self.h, mode))
+
+    def set_bf16_operators(self, mask: int):
+        self._ck(self._lib.pmfem_set_bf16_operators(self.h, mask))
 
     def set_applied_field(self, Hx=0.0, Hy=0.0, Hz=0.0):
         self._ck(self._lib.pmfem_set_applied_field(self.h, Hx, Hy, Hz))
@@ -237,3 +255,58 @@ class Pmfem:
             self.destroy()
         except Exception:
             pass
+
+
+class PmfemBatch:
+    """A batch of set-up cells (pmfem_batch_t): one launch per pass over all cells, RK4 steps
+    replayed from a captured CUDA graph, FP32.  Keeps the cells alive while it exists."""
+
+    def __init__(self, cells):
+        self._lib = load_library()
+        self.cells = list(cells)
+        arr = (_vp * len(self.cells))(*[c.h for c in self.cells])
+        b = _vp()
+        rc = self._lib.pmfem_batch_create(ctypes.byref(b), arr, len(self.cells))
+        if rc != 0:
+            raise PmfemError(rc, "pmfem_batch_create failed")
+        self.b = b
+
+    def _ck(self, rc: int):
+        if rc != 0:
+            raise PmfemError(rc, self._lib.pmfem_batch_last_error(self.b).decode())
+
+    def offsets(self) -> np.ndarray:
+        out = np.zeros(len(self.cells) + 1, dtype=np.int64)
+        self._ck(self._lib.pmfem_batch_offsets(self.b, out.ctypes.data))
+        return out
+
+    def autotune(self, reps: int = 5):
+        self._ck(self._lib.pmfem_batch_autotune(self.b, reps))
+
+    def tiles(self) -> np.ndarray:
+        out = np.zeros((len(self.cells), 2), dtype=np.int32)
+        self._ck(self._lib.pmfem_batch_tiles(self.b, out.ctypes.data))
+        return out
+
+    def set_applied_field(self, cell: int, Hx=0.0, Hy=0.0, Hz=0.0, stream=None):
+        self._ck(self._lib.pmfem_batch_set_applied_field(self.b, cell, Hx, Hy, Hz, _stream(stream)))
+
+    def field(self, m, H, components: int = PMFEM_ALL, stream=None):
+        self._ck(self._lib.pmfem_batch_field(self.b, _addr(m), _addr(H), components, _stream(stream)))
+
+    def set_m(self, m, stream=None):
+        self._ck(self._lib.pmfem_batch_set_m(self.b, _addr(m), _stream(stream)))
+
+    def get_m(self, m, stream=None):
+        self._ck(self._lib.pmfem_batch_get_m(self.b, _addr(m), _stream(stream)))
+
+    def llg_step(self, dt: float, nsteps: int = 1, stream=None):
+        self._ck(self._lib.pmfem_batch_llg_step(self.b, dt, nsteps, _stream(stream)))
+
+    def sync(self):
+        self._ck(self._lib.pmfem_batch_sync(self.b))
+
+    def destroy(self):
+        if self.b:
+            self._lib.pmfem_batch_destroy(self.b)
+            self.b = None

@@ -9,41 +9,10 @@
 #include "../../include/pmfem.h"
 #include "device.hpp"
 #include "internal.hpp"
+#include "state.hpp"
 
 using namespace pmfem;
 
-struct pmfem_state {
-  Setup s;
-  Error err;
-  int prec = PMFEM_FP64;
-  double hap[3] = {0, 0, 0};
-  // device side
-  bool dev_ready = false;
-  int dev_prec = -1;
-  cudaStream_t stream = nullptr;
-  std::vector<void*> allocs;
-  DevOps<double> d64;
-  DevOps<float> d32;
-  void* m = nullptr;      // internal state, N' 4-vectors in the internal order
-  void* mA = nullptr;     // RK stage buffers (4-vectors)
-  void* mB = nullptr;
-  void* acc = nullptr;
-  void* mF = nullptr;     // permuted input of pmfem_field (4-vectors)
-  void* hin = nullptr;    // N' x 3 user-order staging for the host-buffer calls
-  void* hout = nullptr;
-  int* flag = nullptr;
-  // per-launch timing (pmfem_profile)
-  bool prof_on = false;
-  std::vector<cudaEvent_t> ev_pool;
-  size_t ev_next = 0;
-  struct Rec { int id; cudaEvent_t a, b; };
-  std::vector<Rec> recs;
-  int open_id[KID_COUNT] = {};
-  cudaEvent_t open_ev[KID_COUNT] = {};
-  int64_t prof_count[KID_COUNT] = {};
-  double prof_ms[KID_COUNT] = {};
-  int64_t dev_info[12] = {};   // layout facts of the current device upload
-};
 
 namespace {
 
@@ -129,8 +98,34 @@ int upload_conv(pmfem_t h, const double* src, size_t n, size_t stride, size_t of
   return upload(h, tmp.data(), n, out);
 }
 
+// Nearest bfloat16 (ties to even) of an FP64 value, without double rounding: the value is
+// first rounded to FP32 by rounding to odd (truncate toward zero, then set the last bit if
+// anything was cut off; Boldo and Melquiond, IEEE Trans. Computers 57(4), 2008), which keeps
+// enough of the discarded part for the final round-to-nearest-even at 8 significant bits.
+uint16_t bf16_round(double v) {
+  if (std::isnan(v)) return 0x7FC0;
+  float f = (float)v;
+  if (std::isinf(f)) {                       // beyond FP32: beyond bfloat16 as well
+    uint32_t u;
+    std::memcpy(&u, &f, 4);
+    return (uint16_t)(u >> 16);
+  }
+  if (std::fabs((double)f) > std::fabs(v)) f = std::nextafter(f, 0.0f);
+  uint32_t u;
+  std::memcpy(&u, &f, 4);
+  if ((double)f != v) u |= 1u;
+  u += 0x7FFFu + ((u >> 16) & 1u);
+  return (uint16_t)(u >> 16);
+}
+
+int upload_bf16(pmfem_t h, const double* src, size_t n, const bf16_t** out) {
+  std::vector<bf16_t> tmp(n);
+  for (size_t i = 0; i < n; ++i) tmp[i].bits = bf16_round(src[i]);
+  return upload(h, tmp.data(), n, out);
+}
+
 template <typename T>
-int upload_sell(pmfem_t h, const SellMatrix& M, DevSell<T>& D) {
+int upload_sell(pmfem_t h, const SellMatrix& M, DevSell<T>& D, unsigned bf_comps = 0) {
   int rc;
   D.rows = M.rows;
   D.col16 = M.col16;
@@ -150,8 +145,13 @@ int upload_sell(pmfem_t h, const SellMatrix& M, DevSell<T>& D) {
     D.delta = p32;
   }
   const int64_t P = M.padded();
-  for (int c = 0; c < M.comps; ++c)
-    if ((rc = upload_conv<T>(h, M.val.data() + (size_t)c * P, P, 1, 0, 1.0, &D.val[c]))) return rc;
+  for (int c = 0; c < M.comps; ++c) {
+    if (sizeof(T) == 4 && (bf_comps >> c) & 1u) {
+      if ((rc = upload_bf16(h, M.val.data() + (size_t)c * P, P, &D.bval[c]))) return rc;
+    } else if ((rc = upload_conv<T>(h, M.val.data() + (size_t)c * P, P, 1, 0, 1.0, &D.val[c]))) {
+      return rc;
+    }
+  }
   return OK;
 }
 
@@ -162,7 +162,7 @@ int build_device(pmfem_t h, DevOps<T>& d) {
   Layout L;
   {
     Error err;
-    int rc = build_layout(s, L, 96 * 1024, sizeof(T), err);
+    int rc = build_layout(s, L, LAYOUT_COR_ROWS, err);
     if (rc) return fail(h, rc, err.msg);
   }
   int rc;
@@ -182,11 +182,41 @@ int build_device(pmfem_t h, DevOps<T>& d) {
     d.periodic[a] = s.periodic[a];
   }
   if ((rc = upload(h, L.perm.data(), L.perm.size(), &d.perm))) return rc;
-  if ((rc = upload_sell(h, L.adj, d.adj))) return rc;
-  if ((rc = upload_sell(h, L.cor, d.cor))) return rc;
-  if ((rc = upload_sell(h, L.pro, d.pro))) return rc;
-  const SellMatrix* ms[3] = {&L.adj, &L.cor, &L.pro};
+  // BF16-split: component masks of the operators stored in bfloat16 (adjacency components
+  // 0-2 W^q, 3-5 E, 6-8 gradient, 9 exchange)
+  const int bo = (sizeof(T) == 4 && h->prec == PMFEM_BF16SPLIT) ? h->bf16_ops : 0;
+  const unsigned adj_bf = ((bo & PMFEM_BF16_CHARGES) ? 0x3Fu : 0u) | ((bo & PMFEM_BF16_GRADIENT) ? 0x1C0u : 0u) |
+                          ((bo & PMFEM_BF16_EXCHANGE) ? 0x200u : 0u);
+  if ((rc = upload_sell(h, L.adj, d.adj, adj_bf))) return rc;
+  {  // point precorrection, row-contiguous for the warp-per-row kernel
+    DevRows<T>& W = d.corw;
+    if ((rc = upload(h, L.cptr.data(), L.cptr.size(), &W.rowptr))) return rc;
+    if ((rc = upload(h, L.cbase.data(), L.cbase.size(), &W.base))) return rc;
+    W.col16 = L.c16;
+    if (L.c16) {
+      std::vector<int16_t> d16(L.cdelta.begin(), L.cdelta.end());
+      const int16_t* p16;
+      if ((rc = upload(h, d16.data(), d16.size(), &p16))) return rc;
+      W.delta = p16;
+    } else {
+      const int32_t* p32;
+      if ((rc = upload(h, L.cdelta.data(), L.cdelta.size(), &p32))) return rc;
+      W.delta = p32;
+    }
+    if (sizeof(T) == 4 && (bo & PMFEM_BF16_PRECORRECTION)) {
+      if ((rc = upload_bf16(h, L.cval.data(), L.cval.size(), &W.bval))) return rc;
+    } else if ((rc = upload_conv<T>(h, L.cval.data(), L.cval.size(), 1, 0, 1.0, &W.val))) {
+      return rc;
+    }
+  }
+  if ((rc = upload_sell(h, L.pro, d.pro, (bo & PMFEM_BF16_PROJECTION) ? 1u : 0u))) return rc;
+  const SellMatrix* ms[3] = {&L.adj, nullptr, &L.pro};
   for (int k = 0; k < 3; ++k) {
+    if (!ms[k]) {   // the precorrection rows are stored unpadded
+      h->dev_info[3 * k] = h->dev_info[3 * k + 1] = L.cptr[s.Np];
+      h->dev_info[3 * k + 2] = L.c16 ? 16 : 32;
+      continue;
+    }
     int64_t nnz = 0;
     for (int32_t v : ms[k]->len) nnz += v;
     h->dev_info[3 * k] = nnz;
@@ -403,8 +433,19 @@ int pmfem_set_periodicity(pmfem_t h, double L1, double L2, double L3) {
 
 int pmfem_set_precision(pmfem_t h, int mode) {
   if (!h) return EINVAL_;
-  if (mode != PMFEM_FP64 && mode != PMFEM_FP32) return fail(h, EINVAL_, "precision mode must be PMFEM_FP64 or PMFEM_FP32");
+  if (mode != PMFEM_FP64 && mode != PMFEM_FP32 && mode != PMFEM_BF16SPLIT)
+    return fail(h, EINVAL_, "precision mode must be PMFEM_FP64, PMFEM_FP32 or PMFEM_BF16SPLIT");
   h->prec = mode;
+  return OK;
+}
+
+int pmfem_set_bf16_operators(pmfem_t h, int mask) {
+  if (!h) return EINVAL_;
+  const int all = PMFEM_BF16_PRECORRECTION | PMFEM_BF16_PROJECTION | PMFEM_BF16_CHARGES | PMFEM_BF16_GRADIENT |
+                  PMFEM_BF16_EXCHANGE;
+  if (mask & ~all) return fail(h, EINVAL_, "bf16 operator mask has bits outside the PMFEM_BF16_* flags");
+  if (mask != h->bf16_ops && h->dev_prec == PMFEM_BF16SPLIT) free_device(h);   // re-upload at next use
+  h->bf16_ops = mask;
   return OK;
 }
 

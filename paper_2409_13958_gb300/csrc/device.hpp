@@ -10,6 +10,12 @@ template <typename T> struct Vec2;
 template <> struct Vec2<double> { using type = double2; };
 template <> struct Vec2<float> { using type = float2; };
 
+// bfloat16 storage of an operator value: the upper 16 bits of the FP32 number
+// (BF16-split precision stores the large operators this way and computes in FP32)
+struct bf16_t {
+  uint16_t bits;
+};
+
 // internal magnetisation / state vectors: (x, y, z, pad), one aligned load per gather
 template <typename T>
 struct alignas(4 * sizeof(T)) V4 {
@@ -31,8 +37,9 @@ struct ProfHook {
 };
 
 // A sparse operator in SELL-32: thread t handles row map[t] (t itself when map is null);
-// its element j sits at off[t / 32] + 32 j + t % 32 with column base[t] + delta (delta
-// 16-bit when col16) and values val[c][...]; rows of a chunk are padded to its longest.
+// its element j sits at off[t / 32] + 32 j + t % 32 with column base[t] + delta modulo the
+// column count (delta 16-bit when col16) and values val[c][...] (or bval[c][...], stored as
+// bfloat16, when that pointer is set); rows of a chunk are padded to its longest.
 template <typename T>
 struct DevSell {
   int64_t rows = 0;
@@ -43,6 +50,20 @@ struct DevSell {
   const void* delta = nullptr;
   bool col16 = true;
   const T* val[10] = {};
+  const bf16_t* bval[10] = {};
+};
+
+// The point precorrection for one warp per row: row i's values sit at [rowptr[i],
+// rowptr[i + 1]) with columns base[i] + delta modulo N' (delta 16-bit when col16), values
+// val (or bval, stored as bfloat16, when that pointer is set).
+template <typename T>
+struct DevRows {
+  const int64_t* rowptr = nullptr;
+  const int32_t* base = nullptr;
+  const void* delta = nullptr;
+  bool col16 = true;
+  const T* val = nullptr;
+  const bf16_t* bval = nullptr;
 };
 
 // Operator values, grid set-up and work buffers of one precision, all device memory,
@@ -58,7 +79,8 @@ struct DevOps {
   const int32_t* perm = nullptr;                  // internal -> user unknown
   // sparse operators in SELL-32 (see DevSell)
   DevSell<T> adj;   // components: W^q x,y,z (Ms), E x,y,z (Ms), gradient x,y,z, exchange
-  DevSell<T> cor;   // point precorrection
+  DevSell<T> cor;   // point precorrection, one thread per row (unused when corw is set)
+  DevRows<T> corw;  // point precorrection, one warp per row
   DevSell<T> pro;   // projection P^T (rows = grid points)
   int64_t nx_exc = 0;                             // projection exceptions
   const int32_t* xnode = nullptr;
@@ -106,6 +128,22 @@ template <typename T> void launch_perm_out(const DevOps<T>& d, const V4<T>* m, T
 template <typename T> void launch_charges(const DevOps<T>& d, const V4<T>* m, cudaStream_t st);
 template <typename T> void launch_anterp(const DevOps<T>& d, cudaStream_t st);
 template <typename T> void launch_fft_conv(const DevOps<T>& d, cudaStream_t st);
+
+// The FFT convolution of one grid, or of count grids of one shape (batched: block row y
+// works on grid y, whose grid, spectrum-buffer and PGF-spectrum offsets are
+// boff[3y], boff[3y + 1], boff[3y + 2]; boff is null for a single grid).
+template <typename T>
+struct FftArgs {
+  using C2 = typename Vec2<T>::type;
+  T* grid = nullptr;
+  C2* cbuf = nullptr;
+  const T* ghat = nullptr;
+  const C2* tw[3] = {nullptr, nullptr, nullptr};
+  int dims[3] = {0, 0, 0}, fft[3] = {0, 0, 0};
+  const int64_t* boff = nullptr;
+  unsigned count = 1;
+};
+template <typename T> void launch_fft(const FftArgs<T>& a, const ProfHook& prof, cudaStream_t st);
 template <typename T> void launch_interp(const DevOps<T>& d, const V4<T>* m, cudaStream_t st);
 // mode 0 writes H in the C-ABI order (N' x 3); RK modes update internal 4-vector buffers
 template <typename T>

@@ -16,6 +16,7 @@
 // transpose between the two factors goes through padded shared memory.  A block holds
 // LB lines; in strided passes consecutive threads take consecutive lines (adjacent kx),
 // so each global access of a warp is one contiguous segment.
+#include <atomic>
 #include <utility>
 
 #include "device.hpp"
@@ -160,8 +161,13 @@ __device__ __forceinline__ void thread_line(int& l, int& j) {
 // ---------------------------------------------------------------- pass 1: x forward
 template <typename T, typename C2, int F, int LB>
 __global__ void __launch_bounds__(LB * Fac<F>::R2) k_fft_x_fwd(const T* __restrict__ Q, C2* __restrict__ cb, int N0,
-                                                             int N1, int N2, int F1, const C2* __restrict__ tw) {
+                                                             int N1, int N2, int F1, const C2* __restrict__ tw,
+                                                             const int64_t* __restrict__ boff) {
   using FF = Fac<F>;
+  if (boff) {   // batched: blockIdx.y selects the mesh, boff its (grid, spectrum buffer) offsets
+    Q += boff[3 * blockIdx.y];
+    cb += boff[3 * blockIdx.y + 1];
+  }
   extern __shared__ unsigned char smem_raw[];
   C2* S = reinterpret_cast<C2*>(smem_raw);
   int l, j;
@@ -192,8 +198,9 @@ __global__ void __launch_bounds__(LB * Fac<F>::R2) k_fft_x_fwd(const T* __restri
 // ---------------------------------------------------------------- passes 2, 4: y
 template <typename C2, int F, int LB, bool INV>
 __global__ void __launch_bounds__(LB * Fac<F>::R2) k_fft_y(C2* __restrict__ cb, int Hx, int n_in, int n_out,
-                                                         const C2* __restrict__ tw) {
+                                                         const C2* __restrict__ tw, const int64_t* __restrict__ boff) {
   using FF = Fac<F>;
+  if (boff) cb += boff[3 * blockIdx.y + 1];
   extern __shared__ unsigned char smem_raw[];
   C2* S = reinterpret_cast<C2*>(smem_raw);
   int l, j;
@@ -229,8 +236,13 @@ __global__ void __launch_bounds__(LB * Fac<F>::R2) k_fft_y(C2* __restrict__ cb, 
 // ---------------------------------------------------------------- pass 3: z convolution
 template <typename T, typename C2, int F, int LB>
 __global__ void __launch_bounds__(LB * Fac<F>::R2) k_fft_z_conv(C2* __restrict__ cb, int Hx, int F1, int N2,
-                                                              const T* __restrict__ ghat, const C2* __restrict__ tw) {
+                                                              const T* __restrict__ ghat, const C2* __restrict__ tw,
+                                                              const int64_t* __restrict__ boff) {
   using FF = Fac<F>;
+  if (boff) {
+    cb += boff[3 * blockIdx.y + 1];
+    ghat += boff[3 * blockIdx.y + 2];
+  }
   extern __shared__ unsigned char smem_raw[];
   C2* S = reinterpret_cast<C2*>(smem_raw);
   int l, j;
@@ -268,8 +280,13 @@ __global__ void __launch_bounds__(LB * Fac<F>::R2) k_fft_z_conv(C2* __restrict__
 // ---------------------------------------------------------------- pass 5: x inverse (C2R)
 template <typename T, typename C2, int F, int LB>
 __global__ void __launch_bounds__(LB * Fac<F>::R2) k_fft_x_inv(const C2* __restrict__ cb, T* __restrict__ U, int N0,
-                                                             int N1, int N2, int F1, const C2* __restrict__ tw) {
+                                                             int N1, int N2, int F1, const C2* __restrict__ tw,
+                                                             const int64_t* __restrict__ boff) {
   using FF = Fac<F>;
+  if (boff) {
+    U += boff[3 * blockIdx.y];
+    cb += boff[3 * blockIdx.y + 1];
+  }
   extern __shared__ unsigned char smem_raw[];
   C2* S = reinterpret_cast<C2*>(smem_raw);
   int l, j;
@@ -304,9 +321,18 @@ __global__ void __launch_bounds__(LB * Fac<F>::R2) k_fft_x_inv(const C2* __restr
   line_inverse<F, LB, false>(S, tw, st, l, j, X);
 }
 
+// Opt a kernel into more than 48 KB of dynamic shared memory, once per device (the call is
+// not a stream operation, so it is also made once before any graph capture replays it).
 template <typename K>
 void set_smem(K kernel, size_t bytes) {
-  if (bytes > 48 * 1024) cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (bytes <= 48 * 1024) return;
+  static std::atomic<unsigned long long> done{0};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const unsigned long long bit = 1ull << (dev & 63);
+  if (done.load() & bit) return;
+  if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) == cudaSuccess)
+    done.fetch_or(bit);
 }
 
 // line counts per block: strided passes want 128-byte rows of adjacent lines
@@ -320,38 +346,41 @@ struct Passes {
   static constexpr int LBS = Lines<T>::STRIDED;
   static size_t smem(int lb) { return (size_t)lb * FF::LS * sizeof(C2); }
 
-  static void x_fwd(const DevOps<T>& d, cudaStream_t st) {
+  static void x_fwd(const FftArgs<T>& d, cudaStream_t st) {
     const int64_t nl = (int64_t)d.dims[1] * d.dims[2];
     const size_t sm = smem(LBX);
     set_smem(k_fft_x_fwd<T, C2, F, LBX>, sm);
-    k_fft_x_fwd<T, C2, F, LBX><<<(unsigned)((nl + LBX - 1) / LBX), LBX * FF::R2, sm, st>>>(
-        d.grid, d.cbuf, d.dims[0], d.dims[1], d.dims[2], d.fft[1], d.tw[0]);
+    k_fft_x_fwd<T, C2, F, LBX><<<dim3((unsigned)((nl + LBX - 1) / LBX), d.count), LBX * FF::R2, sm, st>>>(
+        d.grid, d.cbuf, d.dims[0], d.dims[1], d.dims[2], d.fft[1], d.tw[0], d.boff);
   }
-  static void x_inv(const DevOps<T>& d, cudaStream_t st) {
+  static void x_inv(const FftArgs<T>& d, cudaStream_t st) {
     const int64_t nl = (int64_t)d.dims[1] * d.dims[2];
     const size_t sm = smem(LBX);
     set_smem(k_fft_x_inv<T, C2, F, LBX>, sm);
-    k_fft_x_inv<T, C2, F, LBX><<<(unsigned)((nl + LBX - 1) / LBX), LBX * FF::R2, sm, st>>>(
-        d.cbuf, d.grid, d.dims[0], d.dims[1], d.dims[2], d.fft[1], d.tw[0]);
+    k_fft_x_inv<T, C2, F, LBX><<<dim3((unsigned)((nl + LBX - 1) / LBX), d.count), LBX * FF::R2, sm, st>>>(
+        d.cbuf, d.grid, d.dims[0], d.dims[1], d.dims[2], d.fft[1], d.tw[0], d.boff);
   }
-  static void y(const DevOps<T>& d, bool inv, cudaStream_t st) {
+  static void y(const FftArgs<T>& d, bool inv, cudaStream_t st) {
     const int Hx = d.fft[0] / 2 + 1;
     const unsigned nb = (unsigned)(((Hx + LBS - 1) / LBS) * d.dims[2]);
     const size_t sm = smem(LBS);
     if (!inv) {
       set_smem(k_fft_y<C2, F, LBS, false>, sm);
-      k_fft_y<C2, F, LBS, false><<<nb, LBS * FF::R2, sm, st>>>(d.cbuf, Hx, d.dims[1], F, d.tw[1]);
+      k_fft_y<C2, F, LBS, false><<<dim3(nb, d.count), LBS * FF::R2, sm, st>>>(d.cbuf, Hx, d.dims[1], F, d.tw[1],
+                                                                               d.boff);
     } else {
       set_smem(k_fft_y<C2, F, LBS, true>, sm);
-      k_fft_y<C2, F, LBS, true><<<nb, LBS * FF::R2, sm, st>>>(d.cbuf, Hx, F, d.dims[1], d.tw[1]);
+      k_fft_y<C2, F, LBS, true><<<dim3(nb, d.count), LBS * FF::R2, sm, st>>>(d.cbuf, Hx, F, d.dims[1], d.tw[1],
+                                                                              d.boff);
     }
   }
-  static void z(const DevOps<T>& d, cudaStream_t st) {
+  static void z(const FftArgs<T>& d, cudaStream_t st) {
     const int Hx = d.fft[0] / 2 + 1;
     const unsigned nb = (unsigned)(((Hx + LBS - 1) / LBS) * d.fft[1]);
     const size_t sm = smem(LBS);
     set_smem(k_fft_z_conv<T, C2, F, LBS>, sm);
-    k_fft_z_conv<T, C2, F, LBS><<<nb, LBS * FF::R2, sm, st>>>(d.cbuf, Hx, d.fft[1], d.dims[2], d.ghat, d.tw[2]);
+    k_fft_z_conv<T, C2, F, LBS><<<dim3(nb, d.count), LBS * FF::R2, sm, st>>>(d.cbuf, Hx, d.fft[1], d.dims[2],
+                                                                             d.ghat, d.tw[2], d.boff);
   }
 };
 
@@ -371,25 +400,40 @@ struct Passes {
 }  // namespace
 
 template <typename T>
+void launch_fft(const FftArgs<T>& a, const ProfHook& prof, cudaStream_t st) {
+  prof.begin(KID_FFT_X_FWD, st);
+  PMFEM_FFT_DISPATCH(a.fft[0], x_fwd(a, st));
+  prof.end(KID_FFT_X_FWD, st);
+  prof.begin(KID_FFT_Y_FWD, st);
+  PMFEM_FFT_DISPATCH(a.fft[1], y(a, false, st));
+  prof.end(KID_FFT_Y_FWD, st);
+  prof.begin(KID_FFT_Z_CONV, st);
+  PMFEM_FFT_DISPATCH(a.fft[2], z(a, st));
+  prof.end(KID_FFT_Z_CONV, st);
+  prof.begin(KID_FFT_Y_INV, st);
+  PMFEM_FFT_DISPATCH(a.fft[1], y(a, true, st));
+  prof.end(KID_FFT_Y_INV, st);
+  prof.begin(KID_FFT_X_INV, st);
+  PMFEM_FFT_DISPATCH(a.fft[0], x_inv(a, st));
+  prof.end(KID_FFT_X_INV, st);
+}
+
+template <typename T>
 void launch_fft_conv(const DevOps<T>& d, cudaStream_t st) {
-  d.prof.begin(KID_FFT_X_FWD, st);
-  PMFEM_FFT_DISPATCH(d.fft[0], x_fwd(d, st));
-  d.prof.end(KID_FFT_X_FWD, st);
-  d.prof.begin(KID_FFT_Y_FWD, st);
-  PMFEM_FFT_DISPATCH(d.fft[1], y(d, false, st));
-  d.prof.end(KID_FFT_Y_FWD, st);
-  d.prof.begin(KID_FFT_Z_CONV, st);
-  PMFEM_FFT_DISPATCH(d.fft[2], z(d, st));
-  d.prof.end(KID_FFT_Z_CONV, st);
-  d.prof.begin(KID_FFT_Y_INV, st);
-  PMFEM_FFT_DISPATCH(d.fft[1], y(d, true, st));
-  d.prof.end(KID_FFT_Y_INV, st);
-  d.prof.begin(KID_FFT_X_INV, st);
-  PMFEM_FFT_DISPATCH(d.fft[0], x_inv(d, st));
-  d.prof.end(KID_FFT_X_INV, st);
+  FftArgs<T> a;
+  a.grid = d.grid;
+  a.cbuf = d.cbuf;
+  a.ghat = d.ghat;
+  for (int k = 0; k < 3; ++k) {
+    a.dims[k] = d.dims[k];
+    a.fft[k] = d.fft[k];
+    a.tw[k] = d.tw[k];
+  }
+  launch_fft(a, d.prof, st);
 }
 
 template void launch_fft_conv<double>(const DevOps<double>&, cudaStream_t);
 template void launch_fft_conv<float>(const DevOps<float>&, cudaStream_t);
+template void launch_fft<float>(const FftArgs<float>&, const ProfHook&, cudaStream_t);
 
 }  // namespace pmfem

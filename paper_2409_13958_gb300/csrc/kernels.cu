@@ -13,64 +13,11 @@
 #include <cstdio>
 
 #include "device.hpp"
+#include "sell.cuh"
 
 namespace pmfem {
 
 namespace {
-
-constexpr int kBlock = 256;
-
-template <typename T>
-__device__ __forceinline__ T warp_sum(T v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
-
-template <typename T, int P>
-__device__ __forceinline__ void lagrange(T s, T (&w)[P]) {
-#pragma unroll
-  for (int i = 0; i < P; ++i) {
-    T v = T(1);
-#pragma unroll
-    for (int j = 0; j < P; ++j)
-      if (j != i) v *= (s - T(j)) / T(i - j);
-    w[i] = v;
-  }
-}
-
-__device__ __forceinline__ int wrap(int i, int N, bool per) {
-  if (per) {
-    if (i < 0) i += N;
-    if (i >= N) i -= N;
-  }
-  return i;
-}
-
-
-
-// sum_j val[o_j] * x[b + delta[o_j]] over one SELL row, o_j = o + 32 j: the value and
-// column loads of a batch of B elements are issued together, then their B gathers, so
-// each thread keeps 2B independent loads in flight instead of one dependent pair
-template <int B, typename T, typename CT>
-__device__ __forceinline__ T sell_dot(const T* __restrict__ val, const CT* __restrict__ dcol,
-                                      const T* __restrict__ x, int64_t b, int64_t o, int n) {
-  T acc = 0;
-  int j = 0;
-  for (; j + B <= n; j += B, o += 32 * B) {
-    T v[B];
-    int64_t c[B];
-#pragma unroll
-    for (int k = 0; k < B; ++k) {
-      v[k] = __ldcs(val + o + 32 * k);
-      c[k] = b + (int64_t)__ldcs(dcol + o + 32 * k);
-    }
-#pragma unroll
-    for (int k = 0; k < B; ++k) acc += v[k] * __ldg(x + c[k]);
-  }
-  for (; j < n; ++j, o += 32) acc += __ldcs(val + o) * __ldg(x + b + __ldcs(dcol + o));
-  return acc;
-}
 
 // ---------------------------------------------------------------- boundary permutations
 template <typename T>
@@ -101,46 +48,32 @@ __global__ void __launch_bounds__(kBlock) k_perm_out(int64_t Np, const int32_t* 
 }
 
 // ---------------------------------------------------------------- charges
-// q = W^q M (Eq. 14a) and e = E M (touching-element part of Eq. 14c) on the adjacency.
-template <typename T, typename CT>
+template <typename T, typename CT, typename VT>
 __global__ void __launch_bounds__(kBlock) k_charges(int64_t Np, const int32_t* __restrict__ len,
+                                                   const int32_t* __restrict__ base,
                                                    const int64_t* __restrict__ off, const CT* __restrict__ dcol,
-                                                   const T* __restrict__ wx, const T* __restrict__ wy,
-                                                   const T* __restrict__ wz, const T* __restrict__ ex,
-                                                   const T* __restrict__ ey, const T* __restrict__ ez,
+                                                   const VT* __restrict__ wx, const VT* __restrict__ wy,
+                                                   const VT* __restrict__ wz, const VT* __restrict__ ex,
+                                                   const VT* __restrict__ ey, const VT* __restrict__ ez,
                                                    const V4<T>* __restrict__ m, T* __restrict__ q, T* __restrict__ e) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= Np) return;
-  const int n = len[i];
-  int64_t o = off[i >> 5] + (i & 31);
-  T aq = 0, ae = 0;
-#pragma unroll 4
-  for (int j = 0; j < n; ++j, o += 32) {
-    const V4<T> mk = m[i + (int64_t)__ldcs(dcol + o)];
-    aq += __ldcs(wx + o) * mk.x + __ldcs(wy + o) * mk.y + __ldcs(wz + o) * mk.z;
-    ae += __ldcs(ex + o) * mk.x + __ldcs(ey + o) * mk.y + __ldcs(ez + o) * mk.z;
-  }
-  q[i] = aq;
-  e[i] = ae;
+  charges_row<T, CT, VT>(i, 0, (int32_t)Np, len, base, off, dcol, wx, wy, wz, ex, ey, ez, m, q, e);
 }
 
 // ---------------------------------------------------------------- projection (step 1)
-// Q = P^T q as a gather: grid point g (one thread, SELL-32 over grid points) sums w q over
-// the nodes whose stencil covers it (the nodes of the boxes [g - pr, g + pl] per axis,
-// enumerated at set-up).  No atomics: every grid value has one writer.
-template <typename T, typename CT>
-__global__ void __launch_bounds__(kBlock) k_project(int64_t G, const int32_t* __restrict__ map,
+// One thread per grid point (SELL-32 over grid points; thread t handles point map[t], or
+// t when the operator keeps the grid order).  No atomics: every grid value has one writer.
+template <typename T, typename CT, typename VT>
+__global__ void __launch_bounds__(kBlock) k_project(int64_t G, int64_t Np, const int32_t* __restrict__ map,
                                                    const int32_t* __restrict__ len, const int32_t* __restrict__ base,
                                                    const int64_t* __restrict__ off, const CT* __restrict__ dcol,
-                                                   const T* __restrict__ pw, const T* __restrict__ q,
+                                                   const VT* __restrict__ pw, const T* __restrict__ q,
                                                    T* __restrict__ grid) {
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= G) return;
-  const int64_t g = map ? (int64_t)map[t] : t;   // grid point of this thread (null map: identity)
-  const int n = len[t];
-  T acc = 0;
-  if (n > 0) acc = sell_dot<8>(pw, dcol, q, (int64_t)base[t], off[t >> 5] + (t & 31), n);
-  grid[g] = acc;
+  const int64_t g = map ? (int64_t)map[t] : t;
+  project_row<T, CT, VT>(t, g, 0, (int32_t)Np, len, base, off, dcol, pw, q, grid);
 }
 
 // nodes whose stencil is not aligned with their box (rare rounding cases)
@@ -154,62 +87,88 @@ __global__ void __launch_bounds__(kBlock) k_project_exc(int64_t n, const int32_t
 }
 
 // ---------------------------------------------------------------- interpolation + precorrection
-// One thread per observer row (thread t handles row map[t], or row t when the operator
-// keeps the box order): the (p+1)^3 stencil gathers from the grid potential, then the row
-// of the point precorrection.
-template <typename T, int P, typename CT>
-__global__ void __launch_bounds__(kBlock) k_interp(
-    int64_t Np, const int32_t* __restrict__ map, const int32_t* __restrict__ base, const T* __restrict__ frac,
-    const T* __restrict__ U, int N0, int N1, int N2, bool p0, bool p1, bool p2, const int32_t* __restrict__ clen,
-    const int64_t* __restrict__ coff, const CT* __restrict__ dcol, const T* __restrict__ cval,
-    const int32_t* __restrict__ rowptrX, const int32_t* __restrict__ colX, const T* __restrict__ valX,
-    const T* __restrict__ q, const T* __restrict__ e, const V4<T>* __restrict__ m, T* __restrict__ u) {
-  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= Np) return;
-  const int64_t i = map ? (int64_t)map[t] : t;   // a null map is the identity
+// One thread per observer row (thread t handles node map[t], or node t when the operator
+// keeps the box order).  The FP32 kernel with stencils of up to 4 points per axis asks the
+// compiler for PMFEM_INTERP_MINB resident blocks per SM (a register cap); the others keep
+// the compiler's own register choice, under which they do not spill.
+#define PMFEM_INTERP_PARAMS                                                                                      \
+  int64_t Np, const int32_t *__restrict__ map, const int32_t *__restrict__ base, const T *__restrict__ frac,      \
+      const T *__restrict__ U, int N0, int N1, int N2, bool p0, bool p1, bool p2,                                \
+      const int32_t *__restrict__ clen, const int32_t *__restrict__ cbase, const int64_t *__restrict__ coff,     \
+      const CT *__restrict__ dcol, const VT *__restrict__ cval, const int32_t *__restrict__ rowptrX,             \
+      const int32_t *__restrict__ colX, const T *__restrict__ valX, const T *__restrict__ q,                      \
+      const T *__restrict__ e, const V4<T> *__restrict__ m, T *__restrict__ u
+#define PMFEM_INTERP_BODY                                                                                         \
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;                                              \
+  if (t >= Np) return;                                                                                            \
+  const int64_t i = map ? (int64_t)map[t] : t;                                                                    \
+  interp_row<T, P, CT, VT>(t, i, 0, (int32_t)Np, base, frac, U, N0, N1, N2, p0, p1, p2, clen, cbase, coff, dcol, \
+                           cval, rowptrX, colX, valX, q, e, m, u);
+
+template <typename T, int P, typename CT, typename VT>
+__global__ void __launch_bounds__(kBlock, PMFEM_INTERP_MINB) k_interp_capped(PMFEM_INTERP_PARAMS) {
+  PMFEM_INTERP_BODY
+}
+
+template <typename T, int P, typename CT, typename VT>
+__global__ void __launch_bounds__(kBlock) k_interp(PMFEM_INTERP_PARAMS) {
+  PMFEM_INTERP_BODY
+}
+#undef PMFEM_INTERP_BODY
+#undef PMFEM_INTERP_PARAMS
+
+// One warp per observer node i (box order, no row map).  The lanes share the (p+1)^3
+// stencil points of step 3; lane l takes the values l, l + 32, ... of the row-contiguous
+// precorrection row of step 4 (its loads issued together by sell_dot); then the near-element
+// entries beyond the adjacency pattern.  The warp sums and lane 0 writes u[i].  Compared
+// with one thread per row, every load of a row is independent of the others, so a warp
+// keeps its whole row in flight, and neighbouring lanes read neighbouring columns.
+template <typename T, int P, typename CT, typename VT>
+__global__ void __launch_bounds__(kBlock) k_interp_warp(
+    int64_t Np, const int32_t* __restrict__ base, const T* __restrict__ frac, const T* __restrict__ U, int N0, int N1,
+    int N2, bool p0, bool p1, bool p2, const int64_t* __restrict__ rowptr, const int32_t* __restrict__ cbase,
+    const CT* __restrict__ dcol, const VT* __restrict__ cval, const int32_t* __restrict__ rowptrX,
+    const int32_t* __restrict__ colX, const T* __restrict__ valX, const T* __restrict__ q, const T* __restrict__ e,
+    const V4<T>* __restrict__ m, T* __restrict__ u) {
+  const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (i >= Np) return;   // the whole warp leaves together
   T acc = 0;
   {  // step 3: interpolation of the grid potential
-    T w0[P], w1[P], w2[P];
-    lagrange<T, P>(frac[3 * i], w0);
-    lagrange<T, P>(frac[3 * i + 1], w1);
-    lagrange<T, P>(frac[3 * i + 2], w2);
+    const T s0 = frac[3 * i], s1 = frac[3 * i + 1], s2 = frac[3 * i + 2];
     const int b0 = base[3 * i], b1 = base[3 * i + 1], b2 = base[3 * i + 2];
-    int ix[P];
 #pragma unroll
-    for (int a = 0; a < P; ++a) ix[a] = wrap(b0 + a, N0, p0);
-#pragma unroll
-    for (int c = 0; c < P; ++c) {
-      const int64_t zo = (int64_t)N1 * wrap(b2 + c, N2, p2);
-#pragma unroll
-      for (int b = 0; b < P; ++b) {
-        const T* rowp = U + (int64_t)N0 * (wrap(b1 + b, N1, p1) + zo);
-        T s = 0;
-#pragma unroll
-        for (int a = 0; a < P; ++a) s += w0[a] * __ldg(rowp + ix[a]);
-        acc += w2[c] * w1[b] * s;
+    for (int k0 = 0; k0 < P * P * P; k0 += 32) {
+      const int k = k0 + lane;
+      if (k < P * P * P) {
+        const int a = k % P, b = (k / P) % P, c = k / (P * P);
+        const T w = lagrange1<T, P>(s0, a) * lagrange1<T, P>(s1, b) * lagrange1<T, P>(s2, c);
+        const int64_t g = wrap(b0 + a, N0, p0) + (int64_t)N0 * (wrap(b1 + b, N1, p1) + (int64_t)N1 * wrap(b2 + c, N2, p2));
+        acc += w * __ldg(U + g);
       }
     }
   }
-  {  // step 4: point precorrection (SELL-32 row)
-    acc += sell_dot<8>(cval, dcol, q, i, coff[t >> 5] + (t & 31), clen[t]);
+  {  // step 4: point precorrection row
+    const int64_t r0 = rowptr[i];
+    const int len = (int)(rowptr[i + 1] - r0);
+    const int n = len > lane ? (len - lane + 31) >> 5 : 0;
+    acc += sell_dot<8>(cval, dcol, q, cbase[i], r0 + lane, n, (int32_t)Np);
   }
-  // near-element entries beyond the adjacency pattern
-  for (int32_t p = rowptrX[i]; p < rowptrX[i + 1]; ++p) {
+  for (int32_t p = rowptrX[i] + lane; p < rowptrX[i + 1]; p += 32) {
     const V4<T> mk = m[colX[p]];
     acc += valX[3 * p] * mk.x + valX[3 * p + 1] * mk.y + valX[3 * p + 2] * mk.z;
   }
-  u[i] = acc + e[i];
+  acc = warp_sum(acc);
+  if (lane == 0) u[i] = acc + e[i];
 }
 
 // ---------------------------------------------------------------- gradient + exchange + RK4
-// Both operators annihilate constants (rows of the gradient and of the Laplacian sum to
-// zero), so they act on differences to the row's own value: the same result in exact
-// arithmetic, without the cancellation of large terms in floating point.
-template <typename T, int MODE, typename CT>
+template <typename T, int MODE, typename CT, typename VG, typename VK>
 __global__ void __launch_bounds__(kBlock) k_field(int64_t Np, const int32_t* __restrict__ len,
+                                                 const int32_t* __restrict__ base,
                                                  const int64_t* __restrict__ off, const CT* __restrict__ dcol,
-                                                 const T* __restrict__ gx, const T* __restrict__ gy,
-                                                 const T* __restrict__ gz, const T* __restrict__ kp,
+                                                 const VG* __restrict__ gx, const VG* __restrict__ gy,
+                                                 const VG* __restrict__ gz, const VK* __restrict__ kp,
                                                  const T* __restrict__ u, const V4<T>* __restrict__ m,
                                                  const int32_t* __restrict__ perm, T* __restrict__ H, int use_ms,
                                                  int use_ex, T hx, T hy, T hz, V4<T>* __restrict__ m0,
@@ -217,70 +176,9 @@ __global__ void __launch_bounds__(kBlock) k_field(int64_t Np, const int32_t* __r
                                                  int acc_init, T dt6, T gam, T alpha, int* flag) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= Np) return;
-  const int n = len[i];
-  int64_t o = off[i >> 5] + (i & 31);
-  const V4<T> mn = m[i];
-  const T un = use_ms ? u[i] : T(0);
-  T ax = 0, ay = 0, az = 0;
-  if (use_ms && use_ex) {
-#pragma unroll 4
-    for (int j = 0; j < n; ++j, o += 32) {
-      const int64_t k = i + (int64_t)__ldcs(dcol + o);
-      const T du = __ldg(u + k) - un;
-      const V4<T> mk = m[k];
-      const T c = __ldcs(kp + o);
-      ax += __ldcs(gx + o) * du + c * (mk.x - mn.x);
-      ay += __ldcs(gy + o) * du + c * (mk.y - mn.y);
-      az += __ldcs(gz + o) * du + c * (mk.z - mn.z);
-    }
-  } else if (use_ms) {
-#pragma unroll 4
-    for (int j = 0; j < n; ++j, o += 32) {
-      const T du = __ldg(u + i + __ldcs(dcol + o)) - un;
-      ax += __ldcs(gx + o) * du;
-      ay += __ldcs(gy + o) * du;
-      az += __ldcs(gz + o) * du;
-    }
-  } else if (use_ex) {
-#pragma unroll 4
-    for (int j = 0; j < n; ++j, o += 32) {
-      const V4<T> mk = m[i + (int64_t)__ldcs(dcol + o)];
-      const T c = __ldcs(kp + o);
-      ax += c * (mk.x - mn.x);
-      ay += c * (mk.y - mn.y);
-      az += c * (mk.z - mn.z);
-    }
-  }
-  const T Hx = ax + hx, Hy = ay + hy, Hz = az + hz;
-  if (!(isfinite(Hx) && isfinite(Hy) && isfinite(Hz))) atomicOr(flag, FLAG_NONFINITE_OUT);
-  if (MODE == 0) {
-    const int64_t uo = 3 * (int64_t)perm[i];
-    H[uo] = Hx;
-    H[uo + 1] = Hy;
-    H[uo + 2] = Hz;
-    return;
-  }
-  // dm/dt = -gam [m x H + alpha m x (m x H)]
-  const T cx = mn.y * Hz - mn.z * Hy, cy = mn.z * Hx - mn.x * Hz, cz = mn.x * Hy - mn.y * Hx;
-  const T dx = mn.y * cz - mn.z * cy, dy = mn.z * cx - mn.x * cz, dz = mn.x * cy - mn.y * cx;
-  const T kx = -gam * (cx + alpha * dx), ky = -gam * (cy + alpha * dy), kz = -gam * (cz + alpha * dz);
-  const V4<T> s = m0[i];
-  if (MODE == 1) {
-    mnext[i] = V4<T>{s.x + cdt * kx, s.y + cdt * ky, s.z + cdt * kz, T(0)};
-    if (acc_init) {
-      accb[i] = V4<T>{bw * kx, bw * ky, bw * kz, T(0)};
-    } else {
-      const V4<T> a = accb[i];
-      accb[i] = V4<T>{a.x + bw * kx, a.y + bw * ky, a.z + bw * kz, T(0)};
-    }
-  } else {
-    const V4<T> a = accb[i];
-    const double nx = (double)s.x + (double)dt6 * ((double)a.x + (double)kx);
-    const double ny = (double)s.y + (double)dt6 * ((double)a.y + (double)ky);
-    const double nz = (double)s.z + (double)dt6 * ((double)a.z + (double)kz);
-    const double inv = 1.0 / sqrt(nx * nx + ny * ny + nz * nz);
-    m0[i] = V4<T>{(T)(nx * inv), (T)(ny * inv), (T)(nz * inv), T(0)};
-  }
+  const int64_t uo = MODE == 0 ? (int64_t)perm[i] : 0;
+  field_row<T, MODE, CT, VG, VK>(i, 0, (int32_t)Np, len, base, off, dcol, gx, gy, gz, kp, u, m, uo, H, use_ms,
+                                 use_ex, hx, hy, hz, m0, mnext, accb, cdt, bw, acc_init, dt6, gam, alpha, flag);
 }
 
 inline unsigned blocks_for(int64_t threads) { return (unsigned)((threads + kBlock - 1) / kBlock); }
@@ -301,18 +199,47 @@ void launch_perm_out(const DevOps<T>& d, const V4<T>* m, T* m_user, cudaStream_t
   d.prof.end(KID_PERM, st);
 }
 
+// Launch-time choice of the column delta type and of the stored value type: f is called
+// with Tag<int16_t> / Tag<int32_t>, and with Tag<T> or (FP32 arithmetic only) Tag<bf16_t>.
+template <typename X>
+struct Tag {
+  using type = X;
+};
+template <typename T, typename F>
+void with_ct(const DevSell<T>& M, F&& f) {
+  if (M.col16)
+    f(Tag<int16_t>{});
+  else
+    f(Tag<int32_t>{});
+}
+template <typename T, typename F>
+void with_vt(bool bf, F&& f) {
+  if constexpr (sizeof(T) == 4) {
+    if (bf) {
+      f(Tag<bf16_t>{});
+      return;
+    }
+  }
+  f(Tag<T>{});
+}
+template <typename VT, typename T>
+const VT* vals(const DevSell<T>& M, int c) {
+  return M.bval[c] ? (const VT*)(const void*)M.bval[c] : (const VT*)(const void*)M.val[c];
+}
+
 template <typename T>
 void launch_charges(const DevOps<T>& d, const V4<T>* m, cudaStream_t st) {
   const DevSell<T>& A = d.adj;
   d.prof.begin(KID_CHARGES, st);
-  if (A.col16)
-    k_charges<T, int16_t><<<blocks_for(d.Np), kBlock, 0, st>>>(d.Np, A.len, A.off, (const int16_t*)A.delta, A.val[0],
-                                                               A.val[1], A.val[2], A.val[3], A.val[4], A.val[5], m,
-                                                               d.q, d.e);
-  else
-    k_charges<T, int32_t><<<blocks_for(d.Np), kBlock, 0, st>>>(d.Np, A.len, A.off, (const int32_t*)A.delta, A.val[0],
-                                                               A.val[1], A.val[2], A.val[3], A.val[4], A.val[5], m,
-                                                               d.q, d.e);
+  with_ct(A, [&](auto ct) {
+    using CT = typename decltype(ct)::type;
+    with_vt<T>(A.bval[0] != nullptr, [&](auto vt) {
+      using VT = typename decltype(vt)::type;
+      k_charges<T, CT, VT><<<blocks_for(d.Np), kBlock, 0, st>>>(
+          d.Np, A.len, A.base, A.off, (const CT*)A.delta, vals<VT>(A, 0), vals<VT>(A, 1), vals<VT>(A, 2),
+          vals<VT>(A, 3), vals<VT>(A, 4), vals<VT>(A, 5), m, d.q, d.e);
+    });
+  });
   d.prof.end(KID_CHARGES, st);
 }
 
@@ -321,41 +248,83 @@ void launch_anterp(const DevOps<T>& d, cudaStream_t st) {
   const DevSell<T>& Pm = d.pro;
   d.prof.begin(KID_ANTERP, st);
   const int64_t G = Pm.rows;
-  if (Pm.col16)
-    k_project<T, int16_t><<<blocks_for(G), kBlock, 0, st>>>(G, Pm.map, Pm.len, Pm.base, Pm.off,
-                                                            (const int16_t*)Pm.delta, Pm.val[0], d.q, d.grid);
-  else
-    k_project<T, int32_t><<<blocks_for(G), kBlock, 0, st>>>(G, Pm.map, Pm.len, Pm.base, Pm.off,
-                                                            (const int32_t*)Pm.delta, Pm.val[0], d.q, d.grid);
+  with_ct(Pm, [&](auto ct) {
+    using CT = typename decltype(ct)::type;
+    with_vt<T>(Pm.bval[0] != nullptr, [&](auto vt) {
+      using VT = typename decltype(vt)::type;
+      k_project<T, CT, VT><<<blocks_for(G), kBlock, 0, st>>>(G, d.Np, Pm.map, Pm.len, Pm.base, Pm.off,
+                                                              (const CT*)Pm.delta, vals<VT>(Pm, 0), d.q, d.grid);
+    });
+  });
   if (d.nx_exc > 0)
     k_project_exc<T><<<blocks_for(d.nx_exc), kBlock, 0, st>>>(d.nx_exc, d.xnode, d.xgrid, d.xw, d.q, d.grid);
   d.prof.end(KID_ANTERP, st);
 }
 
+#ifndef PMFEM_INTERP_CAP
+#define PMFEM_INTERP_CAP 1
+#endif
+template <typename T, int P, typename CT, typename VT>
+constexpr auto interp_kernel() {
+  if constexpr (PMFEM_INTERP_CAP && sizeof(T) == 4 && P <= 4)
+    return k_interp_capped<T, P, CT, VT>;
+  else
+    return k_interp<T, P, CT, VT>;
+}
+
 template <typename T>
 void launch_interp(const DevOps<T>& d, const V4<T>* m, cudaStream_t st) {
+  d.prof.begin(KID_INTERP, st);
+  if (d.corw.rowptr) {
+    const DevRows<T>& W = d.corw;
+    const unsigned nbw = blocks_for(32 * d.Np);
+    auto with_wct = [&](auto f) {
+      if (W.col16)
+        f(Tag<int16_t>{});
+      else
+        f(Tag<int32_t>{});
+    };
+    with_wct([&](auto ct) {
+      using CT = typename decltype(ct)::type;
+      with_vt<T>(W.bval != nullptr, [&](auto vt) {
+        using VT = typename decltype(vt)::type;
+        const VT* cv = W.bval ? (const VT*)(const void*)W.bval : (const VT*)(const void*)W.val;
+        auto go = [&](auto kernel) {
+          kernel<<<nbw, kBlock, 0, st>>>(d.Np, d.base, d.frac, d.grid, d.dims[0], d.dims[1], d.dims[2], d.periodic[0],
+                                         d.periodic[1], d.periodic[2], W.rowptr, W.base, (const CT*)W.delta, cv,
+                                         d.rowptrX, d.colX, d.valX, d.q, d.e, m, d.u);
+        };
+        switch (d.p) {
+          case 2: go(k_interp_warp<T, 3, CT, VT>); break;
+          case 3: go(k_interp_warp<T, 4, CT, VT>); break;
+          case 4: go(k_interp_warp<T, 5, CT, VT>); break;
+          default: go(k_interp_warp<T, 6, CT, VT>); break;
+        }
+      });
+    });
+    d.prof.end(KID_INTERP, st);
+    return;
+  }
   const DevSell<T>& C = d.cor;
   const unsigned nb = blocks_for(d.Np);
-  d.prof.begin(KID_INTERP, st);
-#define PMFEM_INTERP(PP, CT)                                                                                      \
-  k_interp<T, PP, CT><<<nb, kBlock, 0, st>>>(d.Np, C.map, d.base, d.frac, d.grid, d.dims[0], d.dims[1], d.dims[2], \
-                                             d.periodic[0], d.periodic[1], d.periodic[2], C.len, C.off,           \
-                                             (const CT*)C.delta, C.val[0], d.rowptrX, d.colX, d.valX, d.q, d.e, m, \
-                                             d.u)
-#define PMFEM_INTERP_P(CT)              \
-  switch (d.p) {                        \
-    case 2: PMFEM_INTERP(3, CT); break; \
-    case 3: PMFEM_INTERP(4, CT); break; \
-    case 4: PMFEM_INTERP(5, CT); break; \
-    default: PMFEM_INTERP(6, CT); break; \
-  }
-  if (C.col16) {
-    PMFEM_INTERP_P(int16_t)
-  } else {
-    PMFEM_INTERP_P(int32_t)
-  }
-#undef PMFEM_INTERP_P
-#undef PMFEM_INTERP
+  with_ct(C, [&](auto ct) {
+    using CT = typename decltype(ct)::type;
+    with_vt<T>(C.bval[0] != nullptr, [&](auto vt) {
+      using VT = typename decltype(vt)::type;
+      auto go = [&](auto kernel) {
+        kernel<<<nb, kBlock, 0, st>>>(d.Np, C.map, d.base, d.frac, d.grid, d.dims[0], d.dims[1], d.dims[2],
+                                      d.periodic[0], d.periodic[1], d.periodic[2], C.len, C.base, C.off,
+                                      (const CT*)C.delta, vals<VT>(C, 0), d.rowptrX, d.colX, d.valX, d.q, d.e, m,
+                                      d.u);
+      };
+      switch (d.p) {
+        case 2: go(interp_kernel<T, 3, CT, VT>()); break;
+        case 3: go(interp_kernel<T, 4, CT, VT>()); break;
+        case 4: go(interp_kernel<T, 5, CT, VT>()); break;
+        default: go(interp_kernel<T, 6, CT, VT>()); break;
+      }
+    });
+  });
   d.prof.end(KID_INTERP, st);
 }
 
@@ -370,22 +339,27 @@ void launch_field(const DevOps<T>& d, const V4<T>* m, T* H, int comps, double hx
   V4<T>* mn = (V4<T>*)rk.mnext;
   V4<T>* acc = (V4<T>*)rk.acc;
   d.prof.begin(KID_FIELD, st);
-#define PMFEM_FIELD(MODE, CT)                                                                                     \
-  k_field<T, MODE, CT><<<nb, kBlock, 0, st>>>(d.Np, A.len, A.off, (const CT*)A.delta, A.val[6], A.val[7], A.val[8], \
-                                              A.val[9], d.u, m, d.perm, H, use_ms, use_ex, ax, ay, az, m0, mn, acc, \
-                                              (T)rk.cdt, (T)rk.bw, rk.acc_init, (T)rk.dt6, (T)rk.gam, (T)rk.alpha,   \
-                                              d.flag)
-#define PMFEM_FIELD_M(CT)                           \
-  if (rk.mode == 0) PMFEM_FIELD(0, CT);             \
-  else if (rk.mode == 1) PMFEM_FIELD(1, CT);        \
-  else PMFEM_FIELD(2, CT);
-  if (A.col16) {
-    PMFEM_FIELD_M(int16_t)
-  } else {
-    PMFEM_FIELD_M(int32_t)
-  }
-#undef PMFEM_FIELD_M
-#undef PMFEM_FIELD
+  with_ct(A, [&](auto ct) {
+    using CT = typename decltype(ct)::type;
+    with_vt<T>(A.bval[6] != nullptr, [&](auto vg) {
+      using VG = typename decltype(vg)::type;
+      with_vt<T>(A.bval[9] != nullptr, [&](auto vk) {
+        using VK = typename decltype(vk)::type;
+        auto go = [&](auto kernel) {
+          kernel<<<nb, kBlock, 0, st>>>(d.Np, A.len, A.base, A.off, (const CT*)A.delta, vals<VG>(A, 6),
+                                        vals<VG>(A, 7), vals<VG>(A, 8), vals<VK>(A, 9), d.u, m, d.perm, H, use_ms,
+                                        use_ex, ax, ay, az, m0, mn, acc, (T)rk.cdt, (T)rk.bw, rk.acc_init,
+                                        (T)rk.dt6, (T)rk.gam, (T)rk.alpha, d.flag);
+        };
+        if (rk.mode == 0)
+          go(k_field<T, 0, CT, VG, VK>);
+        else if (rk.mode == 1)
+          go(k_field<T, 1, CT, VG, VK>);
+        else
+          go(k_field<T, 2, CT, VG, VK>);
+      });
+    });
+  });
   d.prof.end(KID_FIELD, st);
 }
 

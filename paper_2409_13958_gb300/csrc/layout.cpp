@@ -53,7 +53,39 @@ bool wrap_axis(int& v, int N, bool per) {
 // SELL-32 from row callbacks: len(r), base(r) and fill(r, put(col, values[comps])).  With
 // sigma > 1, rows are sorted by decreasing length inside windows of sigma rows so that
 // the 32 rows of a chunk have similar lengths (little padding).
-void build_sell(SellMatrix& M, int64_t rows, int comps, int sigma, int col_bits,
+//
+// Columns are stored as deltas modulo ncols to a per-row base: a column c is recovered as
+// (base + delta) wrapped into [0, ncols).  The base is moved from base(r) to the middle of
+// the row's columns (measured modulo ncols), so that rows whose sources straddle the
+// periodic seam of the box order (the last and the first boxes along a periodic axis) still
+// have small deltas.
+int64_t centre_deltas(const int32_t* cols, int64_t len, int32_t ref, int64_t n, int32_t* base, int32_t* delta) {
+  const int64_t nc = std::max<int64_t>(n, 1);
+  const int64_t half = nc / 2;
+  auto modd = [&](int64_t d) {   // d modulo nc, in [-(nc - nc/2) + 1, nc/2]
+    d %= nc;
+    if (d < 0) d += nc;
+    return d > half ? d - nc : d;
+  };
+  int64_t lo = 0, hi = 0;
+  for (int64_t k = 0; k < len; ++k) {
+    const int64_t d = modd((int64_t)cols[k] - ref);
+    lo = k ? std::min(lo, d) : d;
+    hi = k ? std::max(hi, d) : d;
+  }
+  int64_t b = ref + (lo + hi) / 2;
+  b = ((b % nc) + nc) % nc;
+  *base = (int32_t)b;
+  int64_t md = 0;
+  for (int64_t k = 0; k < len; ++k) {
+    const int64_t d = modd((int64_t)cols[k] - b);
+    md = std::max<int64_t>(md, d < 0 ? -d : d);
+    delta[k] = (int32_t)d;
+  }
+  return md;
+}
+
+void build_sell(SellMatrix& M, int64_t rows, int comps, int sigma, int col_bits, int64_t ncols,
                 const std::function<int64_t(int64_t)>& len,
                 const std::function<int32_t(int64_t)>& base,
                 const std::function<void(int64_t, const std::function<void(int32_t, const double*)>&)>& fill) {
@@ -86,20 +118,28 @@ void build_sell(SellMatrix& M, int64_t rows, int comps, int sigma, int col_bits,
   int64_t maxd = 0;
   std::vector<int64_t> maxd_t(nch, 0);
   parallel_for(nch, [&](int64_t cb, int64_t ce) {
+    std::vector<int32_t> cols;
+    std::vector<double> vals;
     for (int64_t c = cb; c < ce; ++c) {
       int64_t md = 0;
       for (int64_t t = 32 * c; t < std::min(rows, 32 * c + 32); ++t) {
         const int64_t r = M.map[t];
-        const int32_t bse = base(r);
+        const int32_t ref = base(r);
+        cols.clear();
+        vals.clear();
+        fill(r, [&](int32_t col, const double* v) {
+          cols.push_back(col);
+          vals.insert(vals.end(), v, v + comps);
+        });
+        int32_t bse;
+        std::vector<int32_t> d(cols.size());
+        md = std::max(md, centre_deltas(cols.data(), (int64_t)cols.size(), ref, ncols, &bse, d.data()));
         M.base[t] = bse;
         int64_t o = M.off[c] + (t - 32 * c);
-        fill(r, [&](int32_t col, const double* v) {
-          const int64_t d = (int64_t)col - bse;
-          md = std::max<int64_t>(md, d < 0 ? -d : d);
-          delta[o] = (int32_t)d;
-          for (int k = 0; k < comps; ++k) M.val[(size_t)k * P + o] = v[k];
-          o += 32;
-        });
+        for (size_t k = 0; k < cols.size(); ++k, o += 32) {
+          delta[o] = d[k];
+          for (int q = 0; q < comps; ++q) M.val[(size_t)q * P + o] = vals[k * comps + q];
+        }
       }
       maxd_t[c] = md;
     }
@@ -115,14 +155,12 @@ void build_sell(SellMatrix& M, int64_t rows, int comps, int sigma, int col_bits,
   }
 }
 
-int build_layout(const Setup& s, Layout& L, size_t smem_budget, size_t elem_bytes, Error& err) {
+int build_layout(const Setup& s, Layout& L, unsigned cor_forms, Error& err) {
   const int64_t Np = s.Np;
   const int N[3] = {s.dims[0], s.dims[1], s.dims[2]};
   const int p = s.p, nb = s.near_boxes;
   L.pl = (p % 2 == 1) ? (p - 1) / 2 : p / 2;
   L.pr = (p % 2 == 1) ? (p + 1) / 2 : p / 2 + 1;
-  (void)smem_budget;
-  (void)elem_bytes;
   // box order: tiles of TY rows x TZ planes (defaults favour gather locality)
   L.TY = s.tile_y > 0 ? s.tile_y : 8;
   L.TZ = s.tile_z > 0 ? s.tile_z : 4;
@@ -260,7 +298,7 @@ int build_layout(const Setup& s, Layout& L, size_t smem_budget, size_t elem_byte
       return EINVAL_;
     }
   // SELL-32 operators
-  build_sell(L.adj, Np, 10, 1, s.col_bits, [&](int64_t i) { return (int64_t)(L.rowptr[i + 1] - L.rowptr[i]); },
+  build_sell(L.adj, Np, 10, 1, s.col_bits, Np, [&](int64_t i) { return (int64_t)(L.rowptr[i + 1] - L.rowptr[i]); },
              [&](int64_t i) { return (int32_t)i; },
              [&](int64_t i, const std::function<void(int32_t, const double*)>& put) {
                for (int64_t q = L.rowptr[i]; q < L.rowptr[i + 1]; ++q) {
@@ -271,11 +309,24 @@ int build_layout(const Setup& s, Layout& L, size_t smem_budget, size_t elem_byte
              });
   // rows sorted by length in windows of 1024 (about a dozen box rows): a warp's rows stay
   // near one another (shared gathers) and have similar lengths (little idle lanes)
-  build_sell(L.cor, Np, 1, s.sort_window > 0 ? s.sort_window : 1024, s.col_bits, [&](int64_t i) { return L.cptr[i + 1] - L.cptr[i]; },
-             [&](int64_t i) { return (int32_t)i; },
-             [&](int64_t i, const std::function<void(int32_t, const double*)>& put) {
-               for (int64_t o = L.cptr[i]; o < L.cptr[i + 1]; ++o) put(L.ccol[o], &L.cval[o]);
-             });
+  if (cor_forms & LAYOUT_COR_SELL)
+    build_sell(L.cor, Np, 1, s.sort_window > 0 ? s.sort_window : 1024, s.col_bits, Np,
+               [&](int64_t i) { return L.cptr[i + 1] - L.cptr[i]; }, [&](int64_t i) { return (int32_t)i; },
+               [&](int64_t i, const std::function<void(int32_t, const double*)>& put) {
+                 for (int64_t o = L.cptr[i]; o < L.cptr[i + 1]; ++o) put(L.ccol[o], &L.cval[o]);
+               });
+  if (cor_forms & LAYOUT_COR_ROWS) {
+    L.cbase.assign(Np, 0);
+    L.cdelta.assign(L.cptr[Np], 0);
+    std::vector<int64_t> md(Np, 0);
+    parallel_for(Np, [&](int64_t b, int64_t e) {
+      for (int64_t i = b; i < e; ++i)
+        md[i] = centre_deltas(L.ccol.data() + L.cptr[i], L.cptr[i + 1] - L.cptr[i], (int32_t)i, Np, &L.cbase[i],
+                              L.cdelta.data() + L.cptr[i]);
+    });
+    const int64_t maxd = Np ? *std::max_element(md.begin(), md.end()) : 0;
+    L.c16 = s.col_bits == 32 ? false : maxd <= 32767;
+  }
 
   // projection P^T: grid point g gathers from the nodes whose stencil covers it
   auto lagr = [&](double sv, int i) {
@@ -317,7 +368,7 @@ int build_layout(const Setup& s, Layout& L, size_t smem_budget, size_t elem_byte
     gc[2] = (int)(g / ((int64_t)N[0] * N[1]));
   };
   const int64_t G = (int64_t)N[0] * N[1] * N[2];
-  build_sell(L.pro, G, 1, s.sort_window > 0 ? s.sort_window : 1024, s.col_bits,
+  build_sell(L.pro, G, 1, s.sort_window > 0 ? s.sort_window : 1024, s.col_bits, Np,
              [&](int64_t g) {
                int gc[3];
                gcoord(g, gc);

@@ -1,0 +1,290 @@
+// Device building blocks shared by the single-mesh kernels (kernels.cu) and the batched
+// kernels (batch.cu): Lagrange weights, periodic wrap, SELL-32 column decoding and value
+// loads, and one row of each sparse pass.  A row function works on global indices; the
+// caller gives the column origin c0 and the column count nc of the row's mesh, so that a
+// column is c0 + ((base + delta) mod nc).  A single mesh uses c0 = 0, nc = N'.
+#pragma once
+
+#include <cmath>
+
+#include "device.hpp"
+
+namespace pmfem {
+namespace {
+
+constexpr int kBlock = 256;
+
+// Minimum resident blocks per SM asked of the compiler for the FP32 interpolation kernel
+// (a register cap: 5 blocks of 256 threads allow 51 registers, 6 allow 42).  More resident
+// warps keep more gathers in flight in this latency-bound kernel.
+#ifndef PMFEM_INTERP_MINB
+#define PMFEM_INTERP_MINB 5
+#endif
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Lagrange basis polynomial a (of the P nodes 0 .. P-1) at s.
+template <typename T, int P>
+__device__ __forceinline__ T lagrange1(T s, int a) {
+  T v = T(1);
+#pragma unroll
+  for (int j = 0; j < P; ++j)
+    if (j != a) v *= (s - T(j)) / T(a - j);
+  return v;
+}
+
+template <typename T, int P>
+__device__ __forceinline__ void lagrange(T s, T (&w)[P]) {
+#pragma unroll
+  for (int i = 0; i < P; ++i) {
+    T v = T(1);
+#pragma unroll
+    for (int j = 0; j < P; ++j)
+      if (j != i) v *= (s - T(j)) / T(i - j);
+    w[i] = v;
+  }
+}
+
+__device__ __forceinline__ int wrap(int i, int N, bool per) {
+  if (per) {
+    if (i < 0) i += N;
+    if (i >= N) i -= N;
+  }
+  return i;
+}
+
+// Column of a SELL entry: the row's base plus the stored delta, modulo the number of
+// columns n (deltas are stored modulo n, so a row that straddles the periodic seam of the
+// box order keeps small deltas).  b is in [0, n) and |d| <= n/2 with n <= 2^30 (checked
+// when the mesh is created), so b + d fits in int32 and one correction suffices.
+template <typename CT>
+__device__ __forceinline__ int32_t col_of(int32_t b, CT d, int32_t n) {
+  int32_t c = b + (int32_t)d;
+  c = c < 0 ? c + n : c;
+  return c >= n ? c - n : c;
+}
+
+// Streaming load of a stored operator value, widened to the arithmetic type T.  Values are
+// stored as T, or (BF16-split precision) as the upper 16 bits of an FP32 number (bfloat16),
+// which widen exactly by a shift.
+template <typename T>
+__device__ __forceinline__ T ldv(const T* p) { return __ldcs(p); }
+template <typename T>
+__device__ __forceinline__ T ldv(const bf16_t* p) {
+  return __uint_as_float((uint32_t)__ldcs(&p->bits) << 16);
+}
+
+// sum_j val[o_j] * x[col(b, delta[o_j])] over one SELL row, o_j = o + 32 j: the value and
+// column loads of a batch of B elements are issued together, then their B gathers, so
+// each thread keeps 2B independent loads in flight instead of one dependent pair.  The
+// last, partial batch is issued the same way with its loads predicated on j < n.
+template <int B, typename T, typename CT, typename VT>
+__device__ __forceinline__ T sell_dot(const VT* __restrict__ val, const CT* __restrict__ dcol,
+                                      const T* __restrict__ x, int32_t b, int64_t o, int n, int32_t ncol) {
+  T acc = 0;
+  int j = 0;
+  for (; j + B <= n; j += B, o += 32 * B) {
+    T v[B];
+    int32_t c[B];
+#pragma unroll
+    for (int k = 0; k < B; ++k) {
+      v[k] = ldv<T>(val + o + 32 * k);
+      c[k] = col_of(b, __ldcs(dcol + o + 32 * k), ncol);
+    }
+#pragma unroll
+    for (int k = 0; k < B; ++k) acc += v[k] * __ldg(x + c[k]);
+  }
+  if (j < n) {
+    const int r = n - j;
+    T v[B];
+    int32_t c[B];
+#pragma unroll
+    for (int k = 0; k < B; ++k) {
+      v[k] = k < r ? ldv<T>(val + o + 32 * k) : T(0);
+      c[k] = k < r ? col_of(b, __ldcs(dcol + o + 32 * k), ncol) : 0;
+    }
+#pragma unroll
+    for (int k = 0; k < B; ++k)
+      if (k < r) acc += v[k] * __ldg(x + c[k]);
+  }
+  return acc;
+}
+
+// ---------------------------------------------------------------- charges
+// q = W^q M (Eq. 14a) and e = E M (touching-element part of Eq. 14c): adjacency row i.
+template <typename T, typename CT, typename VT>
+__device__ __forceinline__ void charges_row(int64_t i, int64_t c0, int32_t nc, const int32_t* __restrict__ len,
+                                            const int32_t* __restrict__ base, const int64_t* __restrict__ off,
+                                            const CT* __restrict__ dcol, const VT* __restrict__ wx,
+                                            const VT* __restrict__ wy, const VT* __restrict__ wz,
+                                            const VT* __restrict__ ex, const VT* __restrict__ ey,
+                                            const VT* __restrict__ ez, const V4<T>* __restrict__ m,
+                                            T* __restrict__ q, T* __restrict__ e) {
+  const int n = len[i];
+  int64_t o = off[i >> 5] + (i & 31);
+  const int32_t b = base[i];
+  const V4<T>* mc = m + c0;
+  T aq = 0, ae = 0;
+#pragma unroll 4
+  for (int j = 0; j < n; ++j, o += 32) {
+    const V4<T> mk = mc[col_of(b, __ldcs(dcol + o), nc)];
+    aq += ldv<T>(wx + o) * mk.x + ldv<T>(wy + o) * mk.y + ldv<T>(wz + o) * mk.z;
+    ae += ldv<T>(ex + o) * mk.x + ldv<T>(ey + o) * mk.y + ldv<T>(ez + o) * mk.z;
+  }
+  q[i] = aq;
+  e[i] = ae;
+}
+
+// ---------------------------------------------------------------- projection (step 1)
+// Q = P^T q as a gather: grid point g (SELL row t) sums w q over the nodes whose stencil
+// covers it (the nodes of the boxes [g - pr, g + pl] per axis, enumerated at set-up).
+template <typename T, typename CT, typename VT>
+__device__ __forceinline__ void project_row(int64_t t, int64_t g, int64_t c0, int32_t nc,
+                                            const int32_t* __restrict__ len, const int32_t* __restrict__ base,
+                                            const int64_t* __restrict__ off, const CT* __restrict__ dcol,
+                                            const VT* __restrict__ pw, const T* __restrict__ q,
+                                            T* __restrict__ grid) {
+  const int n = len[t];
+  T acc = 0;
+  if (n > 0) acc = sell_dot<8>(pw, dcol, q + c0, base[t], off[t >> 5] + (t & 31), n, nc);
+  grid[g] = acc;
+}
+
+// ---------------------------------------------------------------- interpolation + precorrection
+// Potential of node i (SELL row t of the precorrection): the (p+1)^3 stencil gathers from
+// the mesh's grid potential U (steps 3), the point precorrection row (step 4), the
+// near-element entries beyond the adjacency pattern and the touching-element part e.
+template <typename T, int P, typename CT, typename VT>
+__device__ __forceinline__ void interp_row(
+    int64_t t, int64_t i, int64_t c0, int32_t nc, const int32_t* __restrict__ base, const T* __restrict__ frac,
+    const T* __restrict__ U, int N0, int N1, int N2, bool p0, bool p1, bool p2, const int32_t* __restrict__ clen,
+    const int32_t* __restrict__ cbase, const int64_t* __restrict__ coff, const CT* __restrict__ dcol,
+    const VT* __restrict__ cval, const int32_t* __restrict__ rowptrX, const int32_t* __restrict__ colX,
+    const T* __restrict__ valX, const T* __restrict__ q, const T* __restrict__ e, const V4<T>* __restrict__ m,
+    T* __restrict__ u) {
+  T acc = 0;
+  {  // step 3: interpolation of the grid potential
+    T w0[P], w1[P], w2[P];
+    lagrange<T, P>(frac[3 * i], w0);
+    lagrange<T, P>(frac[3 * i + 1], w1);
+    lagrange<T, P>(frac[3 * i + 2], w2);
+    const int b0 = base[3 * i], b1 = base[3 * i + 1], b2 = base[3 * i + 2];
+    int ix[P];
+#pragma unroll
+    for (int a = 0; a < P; ++a) ix[a] = wrap(b0 + a, N0, p0);
+#pragma unroll
+    for (int c = 0; c < P; ++c) {
+      const int64_t zo = (int64_t)N1 * wrap(b2 + c, N2, p2);
+#pragma unroll
+      for (int b = 0; b < P; ++b) {
+        const T* rowp = U + (int64_t)N0 * (wrap(b1 + b, N1, p1) + zo);
+        T s = 0;
+#pragma unroll
+        for (int a = 0; a < P; ++a) s += w0[a] * __ldg(rowp + ix[a]);
+        acc += w2[c] * w1[b] * s;
+      }
+    }
+  }
+  // step 4: point precorrection (SELL-32 row)
+  acc += sell_dot<8>(cval, dcol, q + c0, cbase[t], coff[t >> 5] + (t & 31), clen[t], nc);
+  // near-element entries beyond the adjacency pattern
+  for (int32_t p = rowptrX[i]; p < rowptrX[i + 1]; ++p) {
+    const V4<T> mk = m[colX[p]];
+    acc += valX[3 * p] * mk.x + valX[3 * p + 1] * mk.y + valX[3 * p + 2] * mk.z;
+  }
+  u[i] = acc + e[i];
+}
+
+// ---------------------------------------------------------------- gradient + exchange + RK4
+// Field of node i: gradient (Eq. 14d) and exchange (Eq. 8) over adjacency row i, plus the
+// applied field; then either the output (MODE 0, written to H[3 * uo] in the caller's
+// order) or the RK4 stage update of the LLG equation (Eq. 2; MODE 1 an intermediate stage,
+// MODE 2 the final combination with the renormalisation of Eq. 6 in FP64).
+// Both operators annihilate constants (rows of the gradient and of the Laplacian sum to
+// zero), so they act on differences to the row's own value: the same result in exact
+// arithmetic, without the cancellation of large terms in floating point.
+template <typename T, int MODE, typename CT, typename VG, typename VK>
+__device__ __forceinline__ void field_row(int64_t i, int64_t c0, int32_t nc, const int32_t* __restrict__ len,
+                                          const int32_t* __restrict__ base, const int64_t* __restrict__ off,
+                                          const CT* __restrict__ dcol, const VG* __restrict__ gx,
+                                          const VG* __restrict__ gy, const VG* __restrict__ gz,
+                                          const VK* __restrict__ kp, const T* __restrict__ u,
+                                          const V4<T>* __restrict__ m, int64_t uo, T* __restrict__ H, int use_ms,
+                                          int use_ex, T hx, T hy, T hz, V4<T>* __restrict__ m0,
+                                          V4<T>* __restrict__ mnext, V4<T>* __restrict__ accb, T cdt, T bw,
+                                          int acc_init, T dt6, T gam, T alpha, int* flag) {
+  const int n = len[i];
+  const int32_t b = base[i];
+  int64_t o = off[i >> 5] + (i & 31);
+  const V4<T> mn = m[i];
+  const T un = use_ms ? u[i] : T(0);
+  const T* uc = u + c0;
+  const V4<T>* mc = m + c0;
+  T ax = 0, ay = 0, az = 0;
+  if (use_ms && use_ex) {
+#pragma unroll 4
+    for (int j = 0; j < n; ++j, o += 32) {
+      const int32_t k = col_of(b, __ldcs(dcol + o), nc);
+      const T du = __ldg(uc + k) - un;
+      const V4<T> mk = mc[k];
+      const T c = ldv<T>(kp + o);
+      ax += ldv<T>(gx + o) * du + c * (mk.x - mn.x);
+      ay += ldv<T>(gy + o) * du + c * (mk.y - mn.y);
+      az += ldv<T>(gz + o) * du + c * (mk.z - mn.z);
+    }
+  } else if (use_ms) {
+#pragma unroll 4
+    for (int j = 0; j < n; ++j, o += 32) {
+      const T du = __ldg(uc + col_of(b, __ldcs(dcol + o), nc)) - un;
+      ax += ldv<T>(gx + o) * du;
+      ay += ldv<T>(gy + o) * du;
+      az += ldv<T>(gz + o) * du;
+    }
+  } else if (use_ex) {
+#pragma unroll 4
+    for (int j = 0; j < n; ++j, o += 32) {
+      const V4<T> mk = mc[col_of(b, __ldcs(dcol + o), nc)];
+      const T c = ldv<T>(kp + o);
+      ax += c * (mk.x - mn.x);
+      ay += c * (mk.y - mn.y);
+      az += c * (mk.z - mn.z);
+    }
+  }
+  const T Hx = ax + hx, Hy = ay + hy, Hz = az + hz;
+  if (!(isfinite(Hx) && isfinite(Hy) && isfinite(Hz))) atomicOr(flag, FLAG_NONFINITE_OUT);
+  if (MODE == 0) {
+    H[3 * uo] = Hx;
+    H[3 * uo + 1] = Hy;
+    H[3 * uo + 2] = Hz;
+    return;
+  }
+  // dm/dt = -gam [m x H + alpha m x (m x H)]
+  const T cx = mn.y * Hz - mn.z * Hy, cy = mn.z * Hx - mn.x * Hz, cz = mn.x * Hy - mn.y * Hx;
+  const T dx = mn.y * cz - mn.z * cy, dy = mn.z * cx - mn.x * cz, dz = mn.x * cy - mn.y * cx;
+  const T kx = -gam * (cx + alpha * dx), ky = -gam * (cy + alpha * dy), kz = -gam * (cz + alpha * dz);
+  const V4<T> s = m0[i];
+  if (MODE == 1) {
+    mnext[i] = V4<T>{s.x + cdt * kx, s.y + cdt * ky, s.z + cdt * kz, T(0)};
+    if (acc_init) {
+      accb[i] = V4<T>{bw * kx, bw * ky, bw * kz, T(0)};
+    } else {
+      const V4<T> a = accb[i];
+      accb[i] = V4<T>{a.x + bw * kx, a.y + bw * ky, a.z + bw * kz, T(0)};
+    }
+  } else {
+    const V4<T> a = accb[i];
+    const double nx = (double)s.x + (double)dt6 * ((double)a.x + (double)kx);
+    const double ny = (double)s.y + (double)dt6 * ((double)a.y + (double)ky);
+    const double nz = (double)s.z + (double)dt6 * ((double)a.z + (double)kz);
+    const double inv = 1.0 / sqrt(nx * nx + ny * ny + nz * nz);
+    m0[i] = V4<T>{(T)(nx * inv), (T)(ny * inv), (T)(nz * inv), T(0)};
+  }
+}
+
+}  // namespace
+}  // namespace pmfem

@@ -61,6 +61,10 @@ static void load_tet(const Setup& s, int64_t e, double X[4][3]) {
 }
 
 int setup_validate_mesh(Setup& s, Error& err) {
+  if (s.N > (int64_t(1) << 30)) {   // device kernels index columns in int32 with a modular wrap
+    err = {EINVAL_, "more than 2^30 nodes"};
+    return EINVAL_;
+  }
   for (int64_t i = 0; i < 4 * s.T; ++i) {
     if (s.tets[i] < 0 || s.tets[i] >= s.N) {
       err = {EMESH_, "tetrahedron " + std::to_string(i / 4) + " has a node index outside [0, N)"};

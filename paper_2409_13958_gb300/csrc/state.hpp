@@ -1,0 +1,48 @@
+// Handle of one mesh (pmfem_t): the host set-up, the device data of the current precision
+// and the per-launch timing records.  Shared by the C-ABI (api.cu) and the batch (batch.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/pmfem.h"
+#include "device.hpp"
+#include "internal.hpp"
+
+struct pmfem_state {
+  using Setup = pmfem::Setup;
+  using Error = pmfem::Error;
+  Setup s;
+  Error err;
+  int prec = PMFEM_FP64;
+  int bf16_ops = PMFEM_BF16_PRECORRECTION | PMFEM_BF16_PROJECTION | PMFEM_BF16_GRADIENT;
+  double hap[3] = {0, 0, 0};
+  // device side
+  bool dev_ready = false;
+  int dev_prec = -1;
+  cudaStream_t stream = nullptr;
+  std::vector<void*> allocs;
+  pmfem::DevOps<double> d64;
+  pmfem::DevOps<float> d32;
+  void* m = nullptr;      // internal state, N' 4-vectors in the internal order
+  void* mA = nullptr;     // RK stage buffers (4-vectors)
+  void* mB = nullptr;
+  void* acc = nullptr;
+  void* mF = nullptr;     // permuted input of pmfem_field (4-vectors)
+  void* hin = nullptr;    // N' x 3 user-order staging for the host-buffer calls
+  void* hout = nullptr;
+  int* flag = nullptr;
+  // per-launch timing (pmfem_profile)
+  bool prof_on = false;
+  std::vector<cudaEvent_t> ev_pool;
+  size_t ev_next = 0;
+  struct Rec { int id; cudaEvent_t a, b; };
+  std::vector<Rec> recs;
+  int open_id[pmfem::KID_COUNT] = {};
+  cudaEvent_t open_ev[pmfem::KID_COUNT] = {};
+  int64_t prof_count[pmfem::KID_COUNT] = {};
+  double prof_ms[pmfem::KID_COUNT] = {};
+  int64_t dev_info[12] = {};   // layout facts of the current device upload
+};

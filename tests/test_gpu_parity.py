@@ -1,6 +1,7 @@
 """GPU parity: the CUDA path through the C-ABI against the FP64 CPU oracle (O2).
 
-Tolerances (relative L2 over all N' x 3 components): FP64 <= 1e-10, FP32 <= 1e-5.
+Tolerances (relative L2 over all N' x 3 components): FP64 <= 1e-10, FP32 <= 1e-5,
+BF16-split (default operator set in bfloat16, FP32 arithmetic) <= 3e-3.
 """
 import math
 
@@ -14,7 +15,7 @@ from oracle.problem import OracleProblem
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-TOL = {0: 1e-10, 1: 1e-5}
+TOL = {0: 1e-10, 1: 1e-5, 2: 3e-3}
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -71,7 +72,7 @@ def _rel(a, b):
     return float(np.linalg.norm(a - b) / np.linalg.norm(b))
 
 
-@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("prec", [0, 1, 2])
 @pytest.mark.parametrize("name", sorted(CASES))
 def test_field_parity(name, prec):
     from paper_2409_13958_gb300 import PMFEM_EX, PMFEM_MS, PMFEM_AP, PMFEM_ALL
@@ -92,6 +93,42 @@ def test_field_parity(name, prec):
     h.field(mt, H, PMFEM_AP)
     h.sync()
     assert np.allclose(H.double().cpu().numpy(), np.array([2e3, -1e3, 5e2])[None, :], rtol=1e-7)
+    h.destroy()
+
+
+def test_bf16split_without_bf16_operators_is_fp32():
+    """BF16-split with an empty operator mask stores everything in FP32: the same kernels on
+    the same data as the FP32 mode, so the two fields agree bit for bit."""
+    from paper_2409_13958_gb300 import PMFEM_ALL
+    mesh, ob, grid, p, nb, f = _problem("film_20x20x2")
+    m = torch.tensor(meshgen.m_random(ob.Np, seed=12), dtype=torch.float32, device="cuda")
+    out = []
+    for prec in (1, 2):
+        h = _lib(mesh, grid, p, nb, f, prec)
+        h.set_bf16_operators(0)
+        H = torch.empty_like(m)
+        h.field(m, H, PMFEM_ALL)
+        h.sync()
+        out.append(H.cpu())
+        h.destroy()
+    assert torch.equal(out[0], out[1])
+
+
+@pytest.mark.parametrize("bit", [1, 2, 8])
+def test_bf16split_each_default_operator_within_tolerance(bit):
+    """Each operator of the default bfloat16 set alone keeps the field within 3e-3 of the
+    oracle on the periodic film, for a random unit m."""
+    from paper_2409_13958_gb300 import PMFEM_ALL
+    mesh, ob, grid, p, nb, f = _problem("film_20x20x2")
+    m = meshgen.m_random(ob.Np, seed=13)
+    h = _lib(mesh, grid, p, nb, f, 2)
+    h.set_bf16_operators(bit)
+    mt = torch.tensor(m, dtype=torch.float32, device="cuda")
+    H = torch.empty_like(mt)
+    h.field(mt, H, PMFEM_ALL)
+    h.sync()
+    err = _rel(H.double().cpu().numpy(), ob.h_eff(m, "paim"))
+    assert err <= TOL[2], (bit, err)
     h.destroy()
 
 

@@ -84,6 +84,11 @@ def test_error_conventions():
     with pytest.raises(B.PmfemError) as e:
         h.set_precision(7)
     assert e.value.code == -1
+    h.set_precision(B.PMFEM_BF16SPLIT)
+    h.set_bf16_operators(B.PMFEM_BF16_PRECORRECTION | B.PMFEM_BF16_EXCHANGE)
+    with pytest.raises(B.PmfemError) as e:
+        h.set_bf16_operators(32)
+    assert e.value.code == -1
     # a node on a touching face without its partner
     xyz = m.xyz.copy()
     moved = np.nonzero(np.isclose(xyz[:, 0], m.periods[0]) & (xyz[:, 1] > 1e-9) & (xyz[:, 1] < 3e-9))[0][0]
@@ -180,3 +185,38 @@ def test_set_aim_defaults_and_validation():
     with pytest.raises(B.PmfemError) as e:
         h.set_periodicity(*m.periods)
     assert e.value.code == -1
+
+
+def test_batch_create_checks_its_cells_and_gives_offsets():
+    """pmfem_batch_create is host-only: it checks that every cell is set up and that all
+    share the stencil order, and reports where each cell's unknowns start."""
+    from paper_2409_13958_gb300 import binding as B
+    a = meshgen.film_cell(6, 5, 2, seed=1)
+    c = meshgen.cube_cell(4, seed=2)
+    ha = B.Pmfem.create_mesh(a.xyz, a.tets, 8e5, 1.3e-11, 0.02)
+    ha.set_aim(8, 8, 8, 3, 2, 0.0)
+    ha.set_periodicity(*a.periods)
+    hc = B.Pmfem.create_mesh(c.xyz, c.tets, 8e5, 1.3e-11, 0.02)
+    with pytest.raises(B.PmfemError) as e:
+        B.PmfemBatch([ha, hc])                 # hc is not set up yet
+    assert e.value.code == -7
+    hc.set_aim(8, 8, 8, 2, 2, 0.0)
+    hc.set_periodicity(*c.periods)
+    with pytest.raises(B.PmfemError) as e:
+        B.PmfemBatch([ha, hc])                 # stencil orders 3 and 2
+    assert e.value.code == -1
+    hc.set_aim(8, 8, 8, 3, 2, 0.0)
+    hc.set_periodicity(*c.periods)
+    b = B.PmfemBatch([ha, hc, ha])
+    na, nc = ha.num_unknowns(), hc.num_unknowns()
+    assert list(b.offsets()) == [0, na, na + nc, 2 * na + nc]
+    with pytest.raises(B.PmfemError) as e:
+        b.llg_step(-1.0, 1)
+    assert e.value.code == -1
+    with pytest.raises(B.PmfemError) as e:
+        b.autotune(0)
+    assert e.value.code == -1
+    with pytest.raises(B.PmfemError) as e:
+        b.set_applied_field(3, 1.0, 0.0, 0.0)
+    assert e.value.code == -1
+    b.destroy()
