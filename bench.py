@@ -36,8 +36,6 @@ MS, AEX, ALPHA = 8e5, 1.3e-11, 0.02
 WIRE = dict(L=100e-9, R=20e-9, seed=0)
 GRID = (128, 128, 256)
 P_ORDER, NEAR_BOXES, NEAR_ELEM = 3, 3, 0.0
-KERNELS = ("charges", "projection", "fft_x_fwd", "fft_y_fwd", "fft_z_conv", "fft_y_inv", "fft_x_inv",
-           "interp_precorr", "gradient_exchange", "grid_clear", "permute")
 
 
 def parse():
@@ -51,6 +49,7 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the cpu_baseline leg")
     ap.add_argument("--no-bf16", action="store_true", help="skip the BF16-split leg")
     ap.add_argument("--no-batch", action="store_true", help="skip the 64-cell batch leg")
+    ap.add_argument("--no-surrogate", action="store_true", help="skip the learned-surrogate leg")
     ap.add_argument("--out", default=None, help="also write the JSON line to this file")
     return ap.parse_args()
 
@@ -166,9 +165,11 @@ def stable_dt(K_rowabs_max: float) -> float:
     return min(1e-13, 2.5 / lam)
 
 
-def alg_bytes(name: str, s: int, sz: dict) -> float:
+def alg_bytes(name: str, s: int, sz: dict, vs: dict | None = None) -> float:
     """Algorithmic bytes of one launch: every stored operand read once (sparse operators as
-    stored: values plus 16- or 32-bit column deltas), every result written once."""
+    stored: values plus 16- or 32-bit column deltas), every result written once.  s is the
+    size of a vector element; vs overrides the value size of an operator stored in bfloat16."""
+    vs = vs or {}
     Np = sz["Np"]
     N0, N1, N2 = sz["dims"]
     F0, F1, F2 = sz["fft"]
@@ -192,8 +193,10 @@ def alg_bytes(name: str, s: int, sz: dict) -> float:
         return 2 * s * Hx * F1 * N2 + 2 * s * Hx * N1 * N2
     if name == "fft_x_inv":
         return 2 * s * Hx * N1 * N2 + s * G
-    if name == "interp_precorr":               # stencil data, grid once, precorrection row, q and e once, u written
-        return (12 + 3 * s + 4) * Np + s * G + nc * (cb["precorrection"] + s) + 3 * s * Np
+    if name == "interp":                       # stencil base + frac + near-element row pointer, grid once, e read, u written
+        return (12 + 3 * s + 4) * Np + s * G + 2 * s * Np
+    if name == "precorr":                      # map + len + base per row, values + column deltas, q once, u read and written
+        return 12 * Np + nc * (cb["precorrection"] + vs.get("precorrection", s)) + 3 * s * Np
     if name == "gradient_exchange":            # gradient + exchange values, u and m once, RK4 stage state
         return 4 * Np + na * (cb["adjacency"] + 4 * s) + s * Np + v4 * Np + 3.5 * v4 * Np
     if name == "permute":
@@ -402,6 +405,98 @@ def batch_leg(args, dist, world):
             "launch": "one captured CUDA graph per RK4 step, one launch per pass over all cells"}
 
 
+def surrogate_leg(args, dist, world):
+    """Learned surrogate of the FFT convolution on the 3D-periodic sphere lattice (~200k nodes,
+    AIM grid 64^3, FP32).  Training pairs are increments (dQ, dU) of the grid charges and FFT
+    potential between consecutive states of short RK4 trajectories of the method itself (a
+    bounded stand-in for the 20k pairs of long trajectories); the network then replaces the
+    FFT on RK stages 2-4, with the full P-AIM on every 10th step as judge.  Reported: the
+    judged potential error, the drift of the trajectory from the plain one, and the speed
+    against the plain FP32 path."""
+    import torch
+    import meshgen
+    from paper_2409_13958_gb300 import Pmfem, PMFEM_FP32
+    t0 = time.time()
+    mesh = meshgen.sphere_lattice(L=50e-9, R=20e-9, target_nodes=200_000, seed=0)
+    h = Pmfem.create_mesh(mesh.xyz, mesh.tets, MS, AEX, ALPHA)
+    h.set_aim(64, 64, 64, P_ORDER, NEAR_BOXES, NEAR_ELEM)
+    h.set_periodicity(*mesh.periods)
+    h.set_precision(PMFEM_FP32)
+    t_setup = time.time() - t0
+    Np = h.num_unknowns()
+    rp, col, vals = h.operator_export(0)
+    dt = stable_dt(float(np.add.reduceat(np.abs(vals[:, 0]), rp[:-1]).max()))
+    V = 64 ** 3
+    runs, steps = 4, 16
+    Q = torch.empty((runs * steps, V), dtype=torch.float32, device="cuda")
+    U = torch.empty_like(Q)
+    m = torch.empty((Np, 3), dtype=torch.float32, device="cuda")
+    k = 0
+    for r in range(runs):
+        m.copy_(torch.tensor(meshgen.m_random(Np, seed=100 + r), dtype=torch.float32))
+        h.set_m(m)
+        for _ in range(steps):
+            h.get_m(m)
+            h.grid_pair(m, Q[k], U[k])
+            h.llg_step(dt, 1)
+            k += 1
+    h.sync()
+    dQ = (Q.view(runs, steps, V)[:, 1:] - Q.view(runs, steps, V)[:, :-1]).reshape(-1, V).contiguous()
+    dU = (U.view(runs, steps, V)[:, 1:] - U.view(runs, steps, V)[:, :-1]).reshape(-1, V).contiguous()
+    del Q, U
+    n_train = int(0.9 * dQ.shape[0])
+    sq, su = float(dQ[:n_train].std()), float(dU[:n_train].std())
+    h.surrogate_set_params(meshgen.net_init(32, seed=0), sq, su, act_bf16=True)
+    torch.cuda.synchronize()
+    t0 = time.time()
+    epochs = 5
+    losses = h.surrogate_train(dQ[:n_train], dU[:n_train], n_train, epochs=epochs, batch=4, lr=1e-3)
+    torch.cuda.synchronize()
+    t_train = time.time() - t0
+    # held-out increments
+    pred = torch.empty(V, dtype=torch.float32, device="cuda")
+    num = den = 0.0
+    for j in range(n_train, dQ.shape[0]):
+        h.surrogate_apply(dQ[j], pred)
+        torch.cuda.synchronize()
+        num += float(((pred - dU[j]) ** 2).sum())
+        den += float((dU[j] ** 2).sum())
+    held_out = math.sqrt(num / den) if den > 0 else float("nan")
+    # trajectories from a new state: plain FP32 against surrogate-assisted, the same steps
+    m0 = torch.tensor(meshgen.m_random(Np, seed=119), dtype=torch.float32, device="cuda")
+    nsteps = 20
+    res = {}
+    for mode in ("plain", "surrogate"):
+        h.surrogate_enable(10 if mode == "surrogate" else 0)
+        h.set_m(m0)
+        h.llg_step(dt, 1)              # warm-up (and the graph-free first step)
+        h.set_m(m0)
+        h.surrogate_enable(10 if mode == "surrogate" else 0)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        h.llg_step(dt, nsteps)
+        e1.record()
+        e1.synchronize()
+        out = torch.empty_like(m0)
+        h.get_m(out)
+        h.sync()
+        res[mode] = (e0.elapsed_time(e1) / nsteps, out.double().cpu().numpy())
+        if mode == "surrogate":
+            stats = h.surrogate_stats()
+    h.surrogate_enable(0)
+    h.destroy()
+    drift = float(np.linalg.norm(res["surrogate"][1] - res["plain"][1]) / np.linalg.norm(res["plain"][1] - m0.double().cpu().numpy()))
+    return {"workload": "sphere-lattice-3d-periodic-200k, grid 64^3", "unknowns": Np, "precision": "fp32 weights and accumulation, bf16 activations",
+            "train_pairs": n_train, "held_out_pairs": int(dQ.shape[0] - n_train), "epochs": epochs,
+            "train_loss_first_last": [float(losses[0]), float(losses[-1])], "train_s": round(t_train, 2),
+            "held_out_rel_l2_dU": held_out, "judged": stats,
+            "trajectory_drift_vs_plain": drift, "steps": nsteps, "every_k": 10,
+            "ms_per_step": {"plain": res["plain"][0], "surrogate": res["surrogate"][0]},
+            "speedup_vs_plain": res["plain"][0] / res["surrogate"][0], "setup_s": round(t_setup, 1),
+            "data": "pairs of this run's own RK4 trajectories, 4 runs x 16 steps (bounded sample)"}
+
+
 def run_native(args):
     import torch
     from paper_2409_13958_gb300 import Pmfem, PMFEM_FP32, PMFEM_FP64, PMFEM_ALL
@@ -574,6 +669,8 @@ def run_native(args):
     }
     if not args.no_batch:
         line["batch"] = batch_leg(args, dist, world)
+    if not args.no_surrogate:
+        line["surrogate"] = surrogate_leg(args, dist, world)
     if rank == 0 and not args.no_cpu:
         ob, grid = oracle_sample(6000)
         n, el = time_oracle(ob, 15.0)

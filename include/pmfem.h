@@ -200,9 +200,9 @@ int pmfem_llg_step(pmfem_t h, double dt, int nsteps, void* stream);
  * the totals; 0 stops recording.  pmfem_profile_read synchronises the device and writes,
  * for kernel ids 0..n-1, the launch counts and the summed event time in ms since the last
  * pmfem_profile(h, 1).  Ids: 0 charges, 1 projection, 2 FFT x forward, 3 FFT y forward,
- * 4 FFT z + spectral multiply, 5 FFT y inverse, 6 FFT x inverse, 7 interpolation +
- * precorrection, 8 gradient + exchange (+ RK4 stage), 9 grid clear, 10 permutation between
- * the C-ABI unknown order and the internal box-sorted order.
+ * 4 FFT z + spectral multiply, 5 FFT y inverse, 6 FFT x inverse, 7 interpolation (with the
+ * near-element entries), 8 gradient + exchange (+ RK4 stage), 9 grid clear, 10 permutation
+ * between the C-ABI unknown order and the internal box-sorted order, 11 point precorrection.
  */
 int pmfem_profile(pmfem_t h, int enable);
 int pmfem_profile_read(pmfem_t h, int64_t* counts, double* total_ms, int n);
@@ -241,6 +241,52 @@ int pmfem_grid_info(pmfem_t h, int32_t* dims, int32_t* fft, double* origin, doub
 int pmfem_export_spectrum(pmfem_t h, double* out);
 /* Folded unknown positions of Eq. 18 (host, N' x 3 doubles). */
 int pmfem_folded_positions(pmfem_t h, double* out);
+
+/* ======================================================================================
+ * Learned surrogate of the FFT convolution (the paper has no counterpart).  A 3D
+ * convolutional network on the handle's AIM grid (Eq. 16) maps grid charges Q (BAIM step 1)
+ * to grid potential U (what step 2, the FFT convolution with the PGF of Eq. 15, gives):
+ *   h1 = act(conv(Q / sq)), h2 = act(conv(h1)), h3 = act(conv(h2)), U = su * conv(h3),
+ * 3x3x3 kernels, 1 -> 32 -> 32 -> 32 -> 1 channels with biases, act(z) = z (z > 0) or
+ * 0.1 z, circular padding along periodic axes and zero padding along the others.  Grids are
+ * device arrays of N0 x N1 x N2 FP32 (x fastest; pmfem_grid_info gives the dimensions, which
+ * must be multiples of 8, 8 and 4).  Weights, gradients and accumulation are FP32; hidden
+ * activations are FP32 or, with act_bf16, bfloat16.  Training minimises the mean squared
+ * error (in units of su) with Adam (beta1 0.9, beta2 0.999, eps 1e-8).
+ * ====================================================================================== */
+
+/*
+ * Create (or reset) the handle's network with the given parameters: host, n = 57121 floats,
+ * layer after layer W[co][ci][dz][dy][dx] then b[co]; sq, su > 0.  Resets the Adam state.
+ * ESTATE before pmfem_set_periodicity; EINVAL for a wrong count, a non-finite value or a
+ * grid that is not a multiple of (8, 8, 4).
+ */
+int pmfem_surrogate_set_params(pmfem_t h, const float* params, int64_t n, double sq, double su, int act_bf16);
+int pmfem_surrogate_get_params(pmfem_t h, float* params);                     /* host, 57121 floats */
+/* U = net(Q) for one grid (device arrays). */
+int pmfem_surrogate_apply(pmfem_t h, const float* Q, float* U, void* stream);
+/* Gradient (host, 57121 floats, parameter order) and loss of one pair; synchronous. */
+int pmfem_surrogate_grad(pmfem_t h, const float* Q, const float* U, float* grads, double* loss);
+/*
+ * Train on npairs pairs (device, npairs x grid each), in order, for epochs passes; an Adam
+ * step after every batch pairs, with learning rate lr.  epoch_loss (host, epochs doubles,
+ * may be NULL) receives the mean loss of every pass.
+ */
+int pmfem_surrogate_train(pmfem_t h, const float* Q, const float* U, int64_t npairs, int epochs, int batch, double lr,
+                          double* epoch_loss, void* stream);
+/* Training data from the method itself: for a magnetisation m (device N' x 3 FP32), the grid
+ * charges Q of step 1 and the FFT potential U of step 2 (FP32 path; ESTATE under FP64). */
+int pmfem_grid_pair(pmfem_t h, const void* m, float* Q, float* U, void* stream);
+/*
+ * every_k > 0: pmfem_llg_step (FP32) runs the full P-AIM on the first RK stage of every step
+ * and keeps its Q1 and U1; stages 2-4 use U = U1 + net(Q - Q1) in place of the FFT, except
+ * on every every_k-th step (the first included), where they run the full P-AIM and the
+ * network's potential is measured against it.  0 switches it off.  Resets the statistics.
+ */
+int pmfem_surrogate_enable(pmfem_t h, int every_k);
+/* out[4]: steps taken, stages that used the network, stages judged, and the relative L2
+ * error of the network's potential over all judged stages (sqrt(sum |dU|^2 / sum |U|^2)). */
+int pmfem_surrogate_stats(pmfem_t h, double* out);
 
 /* ======================================================================================
  * Batches of independent cells (the paper has no counterpart: a service for sweeps such as

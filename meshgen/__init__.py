@@ -21,7 +21,7 @@ import numpy as np
 
 __all__ = [
     "Mesh", "kuhn_box", "film_cell", "cube_cell", "prism_cell", "sphere_lattice",
-    "wire_cell", "batch_cells", "m_tilted", "m_random", "m_vortex", "m_uniform",
+    "wire_cell", "batch_cells", "m_tilted", "m_random", "m_vortex", "m_uniform", "net_init",
 ]
 
 
@@ -390,3 +390,19 @@ def m_vortex(xyz: np.ndarray, core: float = 5e-9, centre=(0.0, 0.0)) -> np.ndarr
     inp = np.sqrt(np.clip(1.0 - mz * mz, 0.0, None))
     safe = np.where(rho > 0, rho, 1.0)
     return np.stack([-y / safe * inp, x / safe * inp, mz], axis=1)
+
+
+# ----------------------------------------------------------------------------------
+# initial weights of the surrogate network (seeded random numbers, passed in as inputs)
+# ----------------------------------------------------------------------------------
+
+def net_init(channels: int = 32, seed: int = 0) -> np.ndarray:
+    """He-normal weights (variance 2 / fan_in, fan_in = 27 ci) and zero biases of the four
+    3x3x3 layers 1 -> C -> C -> C -> 1, flattened layer by layer as W[co][ci][dz][dy][dx]
+    followed by b[co] (float32)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for co, ci in ((channels, 1), (channels, channels), (channels, channels), (1, channels)):
+        out.append(rng.normal(0.0, math.sqrt(2.0 / (27 * ci)), size=co * ci * 27))
+        out.append(np.zeros(co))
+    return np.concatenate(out).astype(np.float32)

@@ -48,6 +48,14 @@ SIGNATURES = {
     "pmfem_operator_info": (_c.c_int, [_vp, _c.c_int, _pi64, _pi64, _c.POINTER(_c.c_int)]),
     "pmfem_operator_export": (_c.c_int, [_vp, _c.c_int, _vp, _vp, _vp]),
     "pmfem_device_info": (_c.c_int, [_vp, _vp, _c.c_int]),
+    "pmfem_surrogate_set_params": (_c.c_int, [_vp, _vp, _i64, _dbl, _dbl, _c.c_int]),
+    "pmfem_surrogate_get_params": (_c.c_int, [_vp, _vp]),
+    "pmfem_surrogate_apply": (_c.c_int, [_vp, _vp, _vp, _vp]),
+    "pmfem_surrogate_grad": (_c.c_int, [_vp, _vp, _vp, _vp, _vp]),
+    "pmfem_surrogate_train": (_c.c_int, [_vp, _vp, _vp, _i64, _c.c_int, _c.c_int, _dbl, _vp, _vp]),
+    "pmfem_grid_pair": (_c.c_int, [_vp, _vp, _vp, _vp, _vp]),
+    "pmfem_surrogate_enable": (_c.c_int, [_vp, _c.c_int]),
+    "pmfem_surrogate_stats": (_c.c_int, [_vp, _vp]),
     "pmfem_batch_create": (_c.c_int, [_c.POINTER(_vp), _vp, _c.c_int]),
     "pmfem_batch_destroy": (_c.c_int, [_vp]),
     "pmfem_batch_last_error": (_c.c_char_p, [_vp]),
@@ -184,11 +192,50 @@ class Pmfem:
     def get_m(self, m, stream=None):
         self._ck(self._lib.pmfem_get_m(self.h, _addr(m), _stream(stream)))
 
+    # ------------------------------------------------------------------ surrogate
+    NET_PARAMS = 57121
+
+    def surrogate_set_params(self, params, sq: float, su: float, act_bf16: bool = False):
+        p = np.ascontiguousarray(params, dtype=np.float32).ravel()
+        self._ck(self._lib.pmfem_surrogate_set_params(self.h, p.ctypes.data, p.size, sq, su, 1 if act_bf16 else 0))
+
+    def surrogate_get_params(self) -> np.ndarray:
+        out = np.empty(self.NET_PARAMS, dtype=np.float32)
+        self._ck(self._lib.pmfem_surrogate_get_params(self.h, out.ctypes.data))
+        return out
+
+    def surrogate_apply(self, Q, U, stream=None):
+        self._ck(self._lib.pmfem_surrogate_apply(self.h, _addr(Q), _addr(U), _stream(stream)))
+
+    def surrogate_grad(self, Q, U):
+        g = np.empty(self.NET_PARAMS, dtype=np.float32)
+        loss = _c.c_double()
+        self._ck(self._lib.pmfem_surrogate_grad(self.h, _addr(Q), _addr(U), g.ctypes.data, ctypes.byref(loss)))
+        return float(loss.value), g
+
+    def surrogate_train(self, Q, U, npairs: int, epochs: int = 1, batch: int = 1, lr: float = 1e-3, stream=None):
+        losses = np.zeros(epochs)
+        self._ck(self._lib.pmfem_surrogate_train(self.h, _addr(Q), _addr(U), npairs, epochs, batch, lr,
+                                                 losses.ctypes.data, _stream(stream)))
+        return losses
+
+    def grid_pair(self, m, Q, U, stream=None):
+        self._ck(self._lib.pmfem_grid_pair(self.h, _addr(m), _addr(Q), _addr(U), _stream(stream)))
+
+    def surrogate_enable(self, every_k: int):
+        self._ck(self._lib.pmfem_surrogate_enable(self.h, every_k))
+
+    def surrogate_stats(self) -> dict:
+        out = np.zeros(4)
+        self._ck(self._lib.pmfem_surrogate_stats(self.h, out.ctypes.data))
+        return {"steps": int(out[0]), "net_stages": int(out[1]), "judged_stages": int(out[2]),
+                "judged_rel_l2": float(out[3])}
+
     def llg_step(self, dt: float, nsteps: int = 1, stream=None):
         self._ck(self._lib.pmfem_llg_step(self.h, dt, nsteps, _stream(stream)))
 
     KERNELS = ("charges", "projection", "fft_x_fwd", "fft_y_fwd", "fft_z_conv", "fft_y_inv", "fft_x_inv",
-               "interp_precorr", "gradient_exchange", "grid_clear", "permute")
+               "interp", "gradient_exchange", "grid_clear", "permute", "precorr")
 
     def profile(self, enable: bool = True):
         self._ck(self._lib.pmfem_profile(self.h, 1 if enable else 0))
@@ -299,6 +346,45 @@ class PmfemBatch:
 
     def get_m(self, m, stream=None):
         self._ck(self._lib.pmfem_batch_get_m(self.b, _addr(m), _stream(stream)))
+
+    # ------------------------------------------------------------------ surrogate
+    NET_PARAMS = 57121
+
+    def surrogate_set_params(self, params, sq: float, su: float, act_bf16: bool = False):
+        p = np.ascontiguousarray(params, dtype=np.float32).ravel()
+        self._ck(self._lib.pmfem_surrogate_set_params(self.h, p.ctypes.data, p.size, sq, su, 1 if act_bf16 else 0))
+
+    def surrogate_get_params(self) -> np.ndarray:
+        out = np.empty(self.NET_PARAMS, dtype=np.float32)
+        self._ck(self._lib.pmfem_surrogate_get_params(self.h, out.ctypes.data))
+        return out
+
+    def surrogate_apply(self, Q, U, stream=None):
+        self._ck(self._lib.pmfem_surrogate_apply(self.h, _addr(Q), _addr(U), _stream(stream)))
+
+    def surrogate_grad(self, Q, U):
+        g = np.empty(self.NET_PARAMS, dtype=np.float32)
+        loss = _c.c_double()
+        self._ck(self._lib.pmfem_surrogate_grad(self.h, _addr(Q), _addr(U), g.ctypes.data, ctypes.byref(loss)))
+        return float(loss.value), g
+
+    def surrogate_train(self, Q, U, npairs: int, epochs: int = 1, batch: int = 1, lr: float = 1e-3, stream=None):
+        losses = np.zeros(epochs)
+        self._ck(self._lib.pmfem_surrogate_train(self.h, _addr(Q), _addr(U), npairs, epochs, batch, lr,
+                                                 losses.ctypes.data, _stream(stream)))
+        return losses
+
+    def grid_pair(self, m, Q, U, stream=None):
+        self._ck(self._lib.pmfem_grid_pair(self.h, _addr(m), _addr(Q), _addr(U), _stream(stream)))
+
+    def surrogate_enable(self, every_k: int):
+        self._ck(self._lib.pmfem_surrogate_enable(self.h, every_k))
+
+    def surrogate_stats(self) -> dict:
+        out = np.zeros(4)
+        self._ck(self._lib.pmfem_surrogate_stats(self.h, out.ctypes.data))
+        return {"steps": int(out[0]), "net_stages": int(out[1]), "judged_stages": int(out[2]),
+                "judged_rel_l2": float(out[3])}
 
     def llg_step(self, dt: float, nsteps: int = 1, stream=None):
         self._ck(self._lib.pmfem_batch_llg_step(self.b, dt, nsteps, _stream(stream)))

@@ -162,7 +162,7 @@ int build_device(pmfem_t h, DevOps<T>& d) {
   Layout L;
   {
     Error err;
-    int rc = build_layout(s, L, LAYOUT_COR_ROWS, err);
+    int rc = build_layout(s, L, err);
     if (rc) return fail(h, rc, err.msg);
   }
   int rc;
@@ -188,35 +188,10 @@ int build_device(pmfem_t h, DevOps<T>& d) {
   const unsigned adj_bf = ((bo & PMFEM_BF16_CHARGES) ? 0x3Fu : 0u) | ((bo & PMFEM_BF16_GRADIENT) ? 0x1C0u : 0u) |
                           ((bo & PMFEM_BF16_EXCHANGE) ? 0x200u : 0u);
   if ((rc = upload_sell(h, L.adj, d.adj, adj_bf))) return rc;
-  {  // point precorrection, row-contiguous for the warp-per-row kernel
-    DevRows<T>& W = d.corw;
-    if ((rc = upload(h, L.cptr.data(), L.cptr.size(), &W.rowptr))) return rc;
-    if ((rc = upload(h, L.cbase.data(), L.cbase.size(), &W.base))) return rc;
-    W.col16 = L.c16;
-    if (L.c16) {
-      std::vector<int16_t> d16(L.cdelta.begin(), L.cdelta.end());
-      const int16_t* p16;
-      if ((rc = upload(h, d16.data(), d16.size(), &p16))) return rc;
-      W.delta = p16;
-    } else {
-      const int32_t* p32;
-      if ((rc = upload(h, L.cdelta.data(), L.cdelta.size(), &p32))) return rc;
-      W.delta = p32;
-    }
-    if (sizeof(T) == 4 && (bo & PMFEM_BF16_PRECORRECTION)) {
-      if ((rc = upload_bf16(h, L.cval.data(), L.cval.size(), &W.bval))) return rc;
-    } else if ((rc = upload_conv<T>(h, L.cval.data(), L.cval.size(), 1, 0, 1.0, &W.val))) {
-      return rc;
-    }
-  }
+  if ((rc = upload_sell(h, L.cor, d.cor, (bo & PMFEM_BF16_PRECORRECTION) ? 1u : 0u))) return rc;
   if ((rc = upload_sell(h, L.pro, d.pro, (bo & PMFEM_BF16_PROJECTION) ? 1u : 0u))) return rc;
-  const SellMatrix* ms[3] = {&L.adj, nullptr, &L.pro};
+  const SellMatrix* ms[3] = {&L.adj, &L.cor, &L.pro};
   for (int k = 0; k < 3; ++k) {
-    if (!ms[k]) {   // the precorrection rows are stored unpadded
-      h->dev_info[3 * k] = h->dev_info[3 * k + 1] = L.cptr[s.Np];
-      h->dev_info[3 * k + 2] = L.c16 ? 16 : 32;
-      continue;
-    }
     int64_t nnz = 0;
     for (int32_t v : ms[k]->len) nnz += v;
     h->dev_info[3 * k] = nnz;
@@ -333,6 +308,57 @@ int run_llg(pmfem_t h, DevOps<T>& d, double dt, int nsteps, cudaStream_t st) {
     rk.mode = 2;
     rk.dt6 = dt / 6.0;
     enqueue_eval(h, d, (const V4<T>*)A, (T*)nullptr, PMFEM_ALL, rk, st);
+    int rc = check_launch(h);
+    if (rc) return rc;
+  }
+  return OK;
+}
+
+// RK4 steps with the surrogate: stage 1 runs the full P-AIM and keeps its grid charges Q1
+// and potential U1; stages 2-4 take U = U1 + net(Q - Q1) instead of the FFT convolution,
+// except on every sur_every-th step, where they run the full P-AIM and the network's
+// potential is measured against it.
+int run_llg_sur(pmfem_t h, DevOps<float>& d, double dt, int nsteps, cudaStream_t st) {
+  SurrogateNet& n = *h->net;
+  const double gam = kMu0 * kGammaE / (1.0 + h->s.alpha * h->s.alpha);
+  V4<float>* m = (V4<float>*)h->m;
+  V4<float>* A = (V4<float>*)h->mA;
+  V4<float>* B = (V4<float>*)h->mB;
+  const size_t gb = (size_t)n.V * sizeof(float);
+  for (int k = 0; k < nsteps; ++k) {
+    const bool judge = (h->sur_step % h->sur_every) == 0;
+    RkArgs rk;
+    rk.m0 = m;
+    rk.acc = h->acc;
+    rk.gam = gam;
+    rk.alpha = h->s.alpha;
+    const V4<float>* in[4] = {m, A, B, A};
+    for (int s = 0; s < 4; ++s) {
+      rk.mode = s < 3 ? 1 : 2;
+      rk.cdt = s < 2 ? 0.5 * dt : dt;
+      rk.bw = s == 0 ? 1.0 : 2.0;
+      rk.acc_init = s == 0 ? 1 : 0;
+      rk.mnext = s == 0 ? (void*)A : s == 1 ? (void*)B : (void*)A;
+      rk.dt6 = dt / 6.0;
+      launch_charges(d, in[s], st);
+      launch_anterp(d, st);
+      if (s == 0) {
+        PMFEM_CK(h, cudaMemcpyAsync(n.Q1, d.grid, gb, cudaMemcpyDeviceToDevice, st));
+        launch_fft_conv(d, st);
+        PMFEM_CK(h, cudaMemcpyAsync(n.U1, d.grid, gb, cudaMemcpyDeviceToDevice, st));
+      } else if (judge) {
+        PMFEM_CK(h, cudaMemcpyAsync(n.gA, d.grid, gb, cudaMemcpyDeviceToDevice, st));
+        launch_fft_conv(d, st);
+        net_judge(n, n.gA, d.grid, st);
+        ++h->sur_judged;
+      } else {
+        net_increment(n, d.grid, st);
+        ++h->sur_evals;
+      }
+      launch_interp(d, in[s], st);
+      launch_field(d, in[s], (float*)nullptr, PMFEM_ALL, h->hap[0], h->hap[1], h->hap[2], rk, st);
+    }
+    ++h->sur_step;
     int rc = check_launch(h);
     if (rc) return rc;
   }
@@ -531,7 +557,9 @@ int pmfem_llg_step(pmfem_t h, double dt, int nsteps, void* stream) {
   int rc = ensure_device(h);
   if (rc) return rc;
   cudaStream_t st = stream ? (cudaStream_t)stream : h->stream;
-  return h->dev_prec == PMFEM_FP64 ? run_llg(h, h->d64, dt, nsteps, st) : run_llg(h, h->d32, dt, nsteps, st);
+  if (h->dev_prec == PMFEM_FP64) return run_llg(h, h->d64, dt, nsteps, st);
+  if (h->net && h->sur_every > 0) return run_llg_sur(h, h->d32, dt, nsteps, st);
+  return run_llg(h, h->d32, dt, nsteps, st);
 }
 
 int pmfem_sync(pmfem_t h) {
@@ -590,6 +618,10 @@ int pmfem_profile_read(pmfem_t h, int64_t* counts, double* total_ms, int n) {
 int pmfem_destroy(pmfem_t h) {
   if (!h) return OK;
   free_device(h);
+  if (h->net) {
+    net_destroy(*h->net);
+    delete h->net;
+  }
   for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
   if (h->stream) cudaStreamDestroy(h->stream);
   delete h;
@@ -762,3 +794,156 @@ extern "C" int pmfem_field_noalloc(pmfem_t h, const void* m, void* H, int compon
   else noalloc_eval(h, h->d32, (unsigned char*)base, m, H, components, st);
   return check_launch(h);
 }
+
+// ------------------------------------------------------------------------------------
+// Learned surrogate of the FFT convolution (network and kernels in surrogate.cu).
+// ------------------------------------------------------------------------------------
+extern "C" {
+
+int pmfem_surrogate_set_params(pmfem_t h, const float* params, int64_t n, double sq, double su, int act_bf16) {
+  if (!h) return EINVAL_;
+  if (!h->s.ready) return fail(h, ESTATE_, "call pmfem_set_periodicity first");
+  if (!params || n != kNetParams) return fail(h, EINVAL_, "params must hold " + std::to_string(kNetParams) + " values");
+  if (!(sq > 0) || !(su > 0) || !std::isfinite(sq) || !std::isfinite(su)) return fail(h, EINVAL_, "scales must be > 0");
+  for (int64_t k = 0; k < n; ++k)
+    if (!std::isfinite(params[k])) return fail(h, EINVAL_, "non-finite parameter");
+  if (h->net && h->net->bf16 != (act_bf16 != 0)) {
+    net_destroy(*h->net);
+    delete h->net;
+    h->net = nullptr;
+  }
+  if (!h->net) {
+    h->net = new (std::nothrow) SurrogateNet;
+    if (!h->net) return fail(h, ENOMEM_, "out of host memory");
+    std::string msg;
+    const bool per[3] = {h->s.periodic[0], h->s.periodic[1], h->s.periodic[2]};
+    int rc = net_create(*h->net, h->s.dims, per, act_bf16 != 0, msg);
+    if (rc) {
+      delete h->net;
+      h->net = nullptr;
+      return fail(h, rc, msg);
+    }
+  }
+  SurrogateNet& net = *h->net;
+  std::vector<float> dl;
+  net_params_to_device_layout(params, dl);
+  PMFEM_CK(h, cudaMemcpy(net.P, dl.data(), dl.size() * sizeof(float), cudaMemcpyHostToDevice));
+  PMFEM_CK(h, cudaMemset(net.M, 0, kNetParams * sizeof(float)));
+  PMFEM_CK(h, cudaMemset(net.S2, 0, kNetParams * sizeof(float)));
+  PMFEM_CK(h, cudaMemset(net.G, 0, kNetParams * sizeof(float)));
+  net.sq = (float)sq;
+  net.su = (float)su;
+  net.adam_t = 0;
+  return OK;
+}
+
+int pmfem_surrogate_get_params(pmfem_t h, float* params) {
+  if (!h || !params) return EINVAL_;
+  if (!h->net) return fail(h, ESTATE_, "no surrogate: call pmfem_surrogate_set_params first");
+  std::vector<float> dl(kNetParams), out;
+  PMFEM_CK(h, cudaMemcpy(dl.data(), h->net->P, dl.size() * sizeof(float), cudaMemcpyDeviceToHost));
+  net_params_from_device_layout(dl.data(), out);
+  std::memcpy(params, out.data(), out.size() * sizeof(float));
+  return OK;
+}
+
+int pmfem_surrogate_apply(pmfem_t h, const float* Q, float* U, void* stream) {
+  if (!h) return EINVAL_;
+  if (!h->net) return fail(h, ESTATE_, "no surrogate: call pmfem_surrogate_set_params first");
+  if (!Q || !U || Q == U) return fail(h, EINVAL_, "Q and U must be distinct device pointers");
+  cudaStream_t st = stream ? (cudaStream_t)stream : h->stream;
+  net_forward(*h->net, Q, U, st);
+  return check_launch(h);
+}
+
+int pmfem_surrogate_grad(pmfem_t h, const float* Q, const float* U, float* grads, double* loss) {
+  if (!h) return EINVAL_;
+  if (!h->net) return fail(h, ESTATE_, "no surrogate: call pmfem_surrogate_set_params first");
+  if (!Q || !U || !grads || !loss) return fail(h, EINVAL_, "NULL argument");
+  SurrogateNet& net = *h->net;
+  PMFEM_CK(h, cudaMemset(net.G, 0, kNetParams * sizeof(float)));
+  PMFEM_CK(h, cudaMemset(net.loss, 0, sizeof(double)));
+  net_backward(net, Q, U, 0);
+  int rc = check_launch(h);
+  if (rc) return rc;
+  PMFEM_CK(h, cudaDeviceSynchronize());
+  std::vector<float> dl(kNetParams), out;
+  PMFEM_CK(h, cudaMemcpy(dl.data(), net.G, dl.size() * sizeof(float), cudaMemcpyDeviceToHost));
+  PMFEM_CK(h, cudaMemcpy(loss, net.loss, sizeof(double), cudaMemcpyDeviceToHost));
+  net_params_from_device_layout(dl.data(), out);
+  std::memcpy(grads, out.data(), out.size() * sizeof(float));
+  return OK;
+}
+
+int pmfem_surrogate_train(pmfem_t h, const float* Q, const float* U, int64_t npairs, int epochs, int batch, double lr,
+                          double* epoch_loss, void* stream) {
+  if (!h) return EINVAL_;
+  if (!h->net) return fail(h, ESTATE_, "no surrogate: call pmfem_surrogate_set_params first");
+  if (!Q || !U || npairs < 1 || epochs < 1 || batch < 1 || !(lr > 0) || !std::isfinite(lr))
+    return fail(h, EINVAL_, "need Q, U, npairs >= 1, epochs >= 1, batch >= 1, lr > 0");
+  SurrogateNet& net = *h->net;
+  cudaStream_t st = stream ? (cudaStream_t)stream : h->stream;
+  for (int e = 0; e < epochs; ++e) {
+    PMFEM_CK(h, cudaMemsetAsync(net.loss, 0, sizeof(double), st));
+    for (int64_t k = 0; k < npairs; ++k) {
+      net_backward(net, Q + k * net.V, U + k * net.V, st);
+      if ((k + 1) % batch == 0 || k + 1 == npairs) {
+        net_adam(net, (float)lr, ++net.adam_t, st);
+        PMFEM_CK(h, cudaMemsetAsync(net.G, 0, kNetParams * sizeof(float), st));
+      }
+    }
+    int rc = check_launch(h);
+    if (rc) return rc;
+    if (epoch_loss) {
+      double l = 0;
+      PMFEM_CK(h, cudaMemcpyAsync(&l, net.loss, sizeof(double), cudaMemcpyDeviceToHost, st));
+      PMFEM_CK(h, cudaStreamSynchronize(st));
+      epoch_loss[e] = l / (double)npairs;
+    }
+  }
+  return OK;
+}
+
+int pmfem_grid_pair(pmfem_t h, const void* m, float* Q, float* U, void* stream) {
+  if (!h) return EINVAL_;
+  if (!m || !Q || !U || Q == U) return fail(h, EINVAL_, "m, Q and U must be device pointers, Q != U");
+  if (h->prec == PMFEM_FP64) return fail(h, ESTATE_, "grid pairs are produced by the FP32 path");
+  int rc = ensure_device(h);
+  if (rc) return rc;
+  cudaStream_t st = stream ? (cudaStream_t)stream : h->stream;
+  DevOps<float>& d = h->d32;
+  const size_t gb = (size_t)d.dims[0] * d.dims[1] * d.dims[2] * sizeof(float);
+  launch_perm_in(d, (const float*)m, (V4<float>*)h->mF, st);
+  launch_charges(d, (const V4<float>*)h->mF, st);
+  launch_anterp(d, st);
+  PMFEM_CK(h, cudaMemcpyAsync(Q, d.grid, gb, cudaMemcpyDeviceToDevice, st));
+  launch_fft_conv(d, st);
+  PMFEM_CK(h, cudaMemcpyAsync(U, d.grid, gb, cudaMemcpyDeviceToDevice, st));
+  return check_launch(h);
+}
+
+int pmfem_surrogate_enable(pmfem_t h, int every_k) {
+  if (!h) return EINVAL_;
+  if (every_k < 0) return fail(h, EINVAL_, "every_k must be >= 0");
+  if (every_k > 0 && !h->net) return fail(h, ESTATE_, "no surrogate: call pmfem_surrogate_set_params first");
+  h->sur_every = every_k;
+  h->sur_step = h->sur_evals = h->sur_judged = 0;
+  if (h->net) PMFEM_CK(h, cudaMemset(h->net->err, 0, 2 * sizeof(double)));
+  return OK;
+}
+
+int pmfem_surrogate_stats(pmfem_t h, double* out) {
+  if (!h || !out) return EINVAL_;
+  double e[2] = {0, 0};
+  if (h->net) {
+    PMFEM_CK(h, cudaDeviceSynchronize());
+    PMFEM_CK(h, cudaMemcpy(e, h->net->err, sizeof(e), cudaMemcpyDeviceToHost));
+  }
+  out[0] = (double)h->sur_step;
+  out[1] = (double)h->sur_evals;
+  out[2] = (double)h->sur_judged;
+  out[3] = e[1] > 0 ? std::sqrt(e[0] / e[1]) : 0.0;
+  return OK;
+}
+
+}  // extern "C"

@@ -360,7 +360,7 @@ int build_batch_device(pmfem_batch_t b) {
     const Setup& s = b->cells[c]->s;
     Layout L;
     Error err;
-    int rc = build_layout(s, L, LAYOUT_COR_SELL, err);
+    int rc = build_layout(s, L, err);
     if (rc) return bfail(b, rc, "cell " + std::to_string(c) + ": " + err.msg);
     CellDev& d = b->table[c];
     const int64_t Np = s.Np, G = (int64_t)s.dims[0] * s.dims[1] * s.dims[2];

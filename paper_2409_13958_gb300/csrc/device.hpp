@@ -24,7 +24,7 @@ struct alignas(4 * sizeof(T)) V4 {
 
 // Optional per-launch timing: the handle records a CUDA event pair around each kernel.
 enum KernelId : int { KID_CHARGES = 0, KID_ANTERP, KID_FFT_X_FWD, KID_FFT_Y_FWD, KID_FFT_Z_CONV, KID_FFT_Y_INV,
-                      KID_FFT_X_INV, KID_INTERP, KID_FIELD, KID_MEMSET, KID_PERM, KID_COUNT };
+                      KID_FFT_X_INV, KID_INTERP, KID_FIELD, KID_MEMSET, KID_PERM, KID_PRECORR, KID_COUNT };
 struct ProfHook {
   void (*fn)(void* ctx, int id, int phase, cudaStream_t st) = nullptr;
   void* ctx = nullptr;
@@ -53,19 +53,6 @@ struct DevSell {
   const bf16_t* bval[10] = {};
 };
 
-// The point precorrection for one warp per row: row i's values sit at [rowptr[i],
-// rowptr[i + 1]) with columns base[i] + delta modulo N' (delta 16-bit when col16), values
-// val (or bval, stored as bfloat16, when that pointer is set).
-template <typename T>
-struct DevRows {
-  const int64_t* rowptr = nullptr;
-  const int32_t* base = nullptr;
-  const void* delta = nullptr;
-  bool col16 = true;
-  const T* val = nullptr;
-  const bf16_t* bval = nullptr;
-};
-
 // Operator values, grid set-up and work buffers of one precision, all device memory,
 // in the internal (box-sorted) order of the unknowns.
 template <typename T>
@@ -79,8 +66,7 @@ struct DevOps {
   const int32_t* perm = nullptr;                  // internal -> user unknown
   // sparse operators in SELL-32 (see DevSell)
   DevSell<T> adj;   // components: W^q x,y,z (Ms), E x,y,z (Ms), gradient x,y,z, exchange
-  DevSell<T> cor;   // point precorrection, one thread per row (unused when corw is set)
-  DevRows<T> corw;  // point precorrection, one warp per row
+  DevSell<T> cor;   // point precorrection
   DevSell<T> pro;   // projection P^T (rows = grid points)
   int64_t nx_exc = 0;                             // projection exceptions
   const int32_t* xnode = nullptr;

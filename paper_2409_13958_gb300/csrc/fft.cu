@@ -16,7 +16,8 @@
 // transpose between the two factors goes through padded shared memory.  A block holds
 // LB lines; in strided passes consecutive threads take consecutive lines (adjacent kx),
 // so each global access of a warp is one contiguous segment.
-#include <atomic>
+#include <mutex>
+#include <set>
 #include <utility>
 
 #include "device.hpp"
@@ -321,18 +322,20 @@ __global__ void __launch_bounds__(LB * Fac<F>::R2) k_fft_x_inv(const C2* __restr
   line_inverse<F, LB, false>(S, tw, st, l, j, X);
 }
 
-// Opt a kernel into more than 48 KB of dynamic shared memory, once per device (the call is
-// not a stream operation, so it is also made once before any graph capture replays it).
+// Opt a kernel into more than 48 KB of dynamic shared memory, once per (kernel, device):
+// the call is not a stream operation, so it is made before any graph capture replays it.
 template <typename K>
 void set_smem(K kernel, size_t bytes) {
   if (bytes <= 48 * 1024) return;
-  static std::atomic<unsigned long long> done{0};
+  static std::mutex mu;
+  static std::set<std::pair<const void*, int>> done;
   int dev = 0;
   cudaGetDevice(&dev);
-  const unsigned long long bit = 1ull << (dev & 63);
-  if (done.load() & bit) return;
+  const std::pair<const void*, int> key{(const void*)kernel, dev};
+  std::lock_guard<std::mutex> lk(mu);
+  if (done.count(key)) return;
   if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) == cudaSuccess)
-    done.fetch_or(bit);
+    done.insert(key);
 }
 
 // line counts per block: strided passes want 128-byte rows of adjacent lines

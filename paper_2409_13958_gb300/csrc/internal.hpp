@@ -110,11 +110,6 @@ struct Layout {
   std::vector<int64_t> cptr;         // Np + 1: start of each row's precorrection values
   std::vector<double> cval;          // values in (dz, dy, x-segment, node) order
   std::vector<int32_t> ccol;         // their source nodes
-  // the same rows for the warp-per-row kernel: per row a base (the middle of its columns,
-  // modulo Np) and per value the column minus that base, modulo Np (16 bits when they fit)
-  std::vector<int32_t> cbase;
-  std::vector<int32_t> cdelta;
-  bool c16 = true;
   Csr Ex;                            // near-element entries beyond the pattern, internal
   SellMatrix adj;                    // 10 components: W^q (3), E (3), gradient (3), exchange
   SellMatrix cor;                    // point precorrection, rows length-sorted in windows
@@ -127,10 +122,7 @@ struct Layout {
     return ((((int64_t)tz * (N[1] / TY) + ty) * TZ + zi) * TY + yi) * N[0] + x;
   }
 };
-// What build_layout produces for the point precorrection: SELL-32 rows (one thread per row)
-// and/or the row-contiguous form with column deltas (one warp per row).
-enum : unsigned { LAYOUT_COR_SELL = 1, LAYOUT_COR_ROWS = 2 };
-int build_layout(const Setup& s, Layout& L, unsigned cor_forms, Error& err);
+int build_layout(const Setup& s, Layout& L, Error& err);
 // Centre of a row's columns and the columns' deltas to it, both modulo n (|delta| <= n/2);
 // returns the largest |delta|.
 int64_t centre_deltas(const int32_t* cols, int64_t len, int32_t ref, int64_t n, int32_t* base, int32_t* delta);

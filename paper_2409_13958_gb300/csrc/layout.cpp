@@ -155,7 +155,7 @@ void build_sell(SellMatrix& M, int64_t rows, int comps, int sigma, int col_bits,
   }
 }
 
-int build_layout(const Setup& s, Layout& L, unsigned cor_forms, Error& err) {
+int build_layout(const Setup& s, Layout& L, Error& err) {
   const int64_t Np = s.Np;
   const int N[3] = {s.dims[0], s.dims[1], s.dims[2]};
   const int p = s.p, nb = s.near_boxes;
@@ -309,24 +309,11 @@ int build_layout(const Setup& s, Layout& L, unsigned cor_forms, Error& err) {
              });
   // rows sorted by length in windows of 1024 (about a dozen box rows): a warp's rows stay
   // near one another (shared gathers) and have similar lengths (little idle lanes)
-  if (cor_forms & LAYOUT_COR_SELL)
-    build_sell(L.cor, Np, 1, s.sort_window > 0 ? s.sort_window : 1024, s.col_bits, Np,
+  build_sell(L.cor, Np, 1, s.sort_window > 0 ? s.sort_window : 1024, s.col_bits, Np,
                [&](int64_t i) { return L.cptr[i + 1] - L.cptr[i]; }, [&](int64_t i) { return (int32_t)i; },
                [&](int64_t i, const std::function<void(int32_t, const double*)>& put) {
                  for (int64_t o = L.cptr[i]; o < L.cptr[i + 1]; ++o) put(L.ccol[o], &L.cval[o]);
                });
-  if (cor_forms & LAYOUT_COR_ROWS) {
-    L.cbase.assign(Np, 0);
-    L.cdelta.assign(L.cptr[Np], 0);
-    std::vector<int64_t> md(Np, 0);
-    parallel_for(Np, [&](int64_t b, int64_t e) {
-      for (int64_t i = b; i < e; ++i)
-        md[i] = centre_deltas(L.ccol.data() + L.cptr[i], L.cptr[i + 1] - L.cptr[i], (int32_t)i, Np, &L.cbase[i],
-                              L.cdelta.data() + L.cptr[i]);
-    });
-    const int64_t maxd = Np ? *std::max_element(md.begin(), md.end()) : 0;
-    L.c16 = s.col_bits == 32 ? false : maxd <= 32767;
-  }
 
   // projection P^T: grid point g gathers from the nodes whose stencil covers it
   auto lagr = [&](double sv, int i) {

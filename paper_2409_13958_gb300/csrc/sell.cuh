@@ -14,13 +14,6 @@ namespace {
 
 constexpr int kBlock = 256;
 
-// Minimum resident blocks per SM asked of the compiler for the FP32 interpolation kernel
-// (a register cap: 5 blocks of 256 threads allow 51 registers, 6 allow 42).  More resident
-// warps keep more gathers in flight in this latency-bound kernel.
-#ifndef PMFEM_INTERP_MINB
-#define PMFEM_INTERP_MINB 5
-#endif
-
 template <typename T>
 __device__ __forceinline__ T warp_sum(T v) {
 #pragma unroll
@@ -82,7 +75,8 @@ __device__ __forceinline__ T ldv(const bf16_t* p) {
 // sum_j val[o_j] * x[col(b, delta[o_j])] over one SELL row, o_j = o + 32 j: the value and
 // column loads of a batch of B elements are issued together, then their B gathers, so
 // each thread keeps 2B independent loads in flight instead of one dependent pair.  The
-// last, partial batch is issued the same way with its loads predicated on j < n.
+// remainder loop is left to the compiler, which unrolls it (a loop kept rolled there
+// serialises up to B - 1 dependent load pairs per row).
 template <int B, typename T, typename CT, typename VT>
 __device__ __forceinline__ T sell_dot(const VT* __restrict__ val, const CT* __restrict__ dcol,
                                       const T* __restrict__ x, int32_t b, int64_t o, int n, int32_t ncol) {
@@ -99,19 +93,7 @@ __device__ __forceinline__ T sell_dot(const VT* __restrict__ val, const CT* __re
 #pragma unroll
     for (int k = 0; k < B; ++k) acc += v[k] * __ldg(x + c[k]);
   }
-  if (j < n) {
-    const int r = n - j;
-    T v[B];
-    int32_t c[B];
-#pragma unroll
-    for (int k = 0; k < B; ++k) {
-      v[k] = k < r ? ldv<T>(val + o + 32 * k) : T(0);
-      c[k] = k < r ? col_of(b, __ldcs(dcol + o + 32 * k), ncol) : 0;
-    }
-#pragma unroll
-    for (int k = 0; k < B; ++k)
-      if (k < r) acc += v[k] * __ldg(x + c[k]);
-  }
+  for (; j < n; ++j, o += 32) acc += ldv<T>(val + o) * __ldg(x + col_of(b, __ldcs(dcol + o), ncol));
   return acc;
 }
 

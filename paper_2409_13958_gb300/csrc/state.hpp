@@ -10,6 +10,7 @@
 #include "../../include/pmfem.h"
 #include "device.hpp"
 #include "internal.hpp"
+#include "surrogate.hpp"
 
 struct pmfem_state {
   using Setup = pmfem::Setup;
@@ -45,4 +46,8 @@ struct pmfem_state {
   int64_t prof_count[pmfem::KID_COUNT] = {};
   double prof_ms[pmfem::KID_COUNT] = {};
   int64_t dev_info[12] = {};   // layout facts of the current device upload
+  // learned surrogate of the FFT convolution (pmfem_surrogate_*)
+  pmfem::SurrogateNet* net = nullptr;
+  int sur_every = 0;            // 0: off; k: full P-AIM (judged) on every k-th RK step
+  int64_t sur_step = 0, sur_evals = 0, sur_judged = 0;
 };

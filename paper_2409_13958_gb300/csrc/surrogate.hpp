@@ -1,0 +1,58 @@
+// Learned surrogate of the FFT convolution (device network; kernels in surrogate.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+namespace pmfem {
+
+constexpr int kNetC = 32;   // hidden channels
+// parameters of the four layers: W[co][ci][3][3][3] then b[co], 1 -> 32 -> 32 -> 32 -> 1
+constexpr int64_t kNetParams = (27 * 1 * kNetC + kNetC) + 2 * (27 * kNetC * kNetC + kNetC) + (27 * kNetC + 1);
+
+struct SurrogateNet {
+  int dims[3] = {0, 0, 0};
+  bool periodic[3] = {false, false, false};
+  bool bf16 = false;          // hidden activations stored as bfloat16
+  float sq = 1.f, su = 1.f;   // input and output scales
+  int64_t V = 0;              // grid points
+  std::vector<void*> allocs;
+  float* W[4] = {};           // [tap][ci][co]
+  float* b[4] = {};
+  float* P = nullptr;         // all parameters, device, in the W[tap][ci][co] / b layout (contiguous)
+  float* G = nullptr;         // gradients, same layout
+  float* M = nullptr;         // Adam moments
+  float* S2 = nullptr;
+  float* Wt = nullptr;        // flipped weights of one layer (input-gradient convolution)
+  void* h[3] = {};            // hidden activations (float or bfloat16), kNetC x V each
+  float* gA = nullptr;        // gradient buffers, kNetC x V floats
+  float* gB = nullptr;
+  float* pred = nullptr;      // V floats
+  double* loss = nullptr;     // device accumulator
+  int64_t adam_t = 0;
+  // RK use (increment form): charges and potential of the first stage of the current step
+  float* Q1 = nullptr;
+  float* U1 = nullptr;
+  float* Ubuf = nullptr;      // network output
+  double* err = nullptr;      // device: [sum (U_net - U)^2, sum U^2] of the judged stages
+};
+
+int64_t net_layer_offset(int layer, bool bias);                 // offset in the device layout
+int net_create(SurrogateNet& n, const int dims[3], const bool periodic[3], bool bf16, std::string& msg);
+void net_destroy(SurrogateNet& n);
+// caller order (W[co][ci][dz][dy][dx], b per layer) <-> device layout (host copies)
+void net_params_to_device_layout(const float* in, std::vector<float>& out);
+void net_params_from_device_layout(const float* in, std::vector<float>& out);
+void net_forward(SurrogateNet& n, const float* Q, float* U, cudaStream_t st);
+// gradient of the mean squared error of one pair, added into n.G; loss added into *n.loss
+void net_backward(SurrogateNet& n, const float* Q, const float* U, cudaStream_t st);
+void net_adam(SurrogateNet& n, float lr, int64_t t, cudaStream_t st);
+// U = U1 + net(Q - Q1), Q and U on the same grid buffer (Q in, U out); tmp holds V floats
+void net_increment(SurrogateNet& n, float* grid, cudaStream_t st);
+// accumulate |net(Q - Q1) + U1 - U|^2 and |U|^2 for a judged stage (grid holds U, Qs the stage's Q)
+void net_judge(SurrogateNet& n, const float* Qs, const float* U, cudaStream_t st);
+
+}  // namespace pmfem
