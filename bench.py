@@ -193,10 +193,10 @@ def alg_bytes(name: str, s: int, sz: dict, vs: dict | None = None) -> float:
         return 2 * s * Hx * F1 * N2 + 2 * s * Hx * N1 * N2
     if name == "fft_x_inv":
         return 2 * s * Hx * N1 * N2 + s * G
-    if name == "interp":                       # stencil base + frac + near-element row pointer, grid once, e read, u written
-        return (12 + 3 * s + 4) * Np + s * G + 2 * s * Np
-    if name == "precorr":                      # map + len + base per row, values + column deltas, q once, u read and written
-        return 12 * Np + nc * (cb["precorrection"] + vs.get("precorrection", s)) + 3 * s * Np
+    if name == "interp_precorr":               # stencil base + frac + near-element row pointer, grid once,
+        # row map + len + base, values + column deltas, q once, e read, u written
+        return ((12 + 3 * s + 4) * Np + s * G + 12 * Np + nc * (cb["precorrection"] + vs.get("precorrection", s))
+                + 3 * s * Np)
     if name == "gradient_exchange":            # gradient + exchange values, u and m once, RK4 stage state
         return 4 * Np + na * (cb["adjacency"] + 4 * s) + s * Np + v4 * Np + 3.5 * v4 * Np
     if name == "permute":
@@ -427,6 +427,7 @@ def surrogate_leg(args, dist, world):
     rp, col, vals = h.operator_export(0)
     dt = stable_dt(float(np.add.reduceat(np.abs(vals[:, 0]), rp[:-1]).max()))
     V = 64 ** 3
+    st = torch.cuda.current_stream()   # every launch on one stream, ordered with the torch copies
     runs, steps = 4, 16
     Q = torch.empty((runs * steps, V), dtype=torch.float32, device="cuda")
     U = torch.empty_like(Q)
@@ -434,13 +435,13 @@ def surrogate_leg(args, dist, world):
     k = 0
     for r in range(runs):
         m.copy_(torch.tensor(meshgen.m_random(Np, seed=100 + r), dtype=torch.float32))
-        h.set_m(m)
+        h.set_m(m, st)
         for _ in range(steps):
-            h.get_m(m)
-            h.grid_pair(m, Q[k], U[k])
-            h.llg_step(dt, 1)
+            h.get_m(m, st)
+            h.grid_pair(m, Q[k], U[k], st)
+            h.llg_step(dt, 1, st)
             k += 1
-    h.sync()
+    torch.cuda.synchronize()
     dQ = (Q.view(runs, steps, V)[:, 1:] - Q.view(runs, steps, V)[:, :-1]).reshape(-1, V).contiguous()
     dU = (U.view(runs, steps, V)[:, 1:] - U.view(runs, steps, V)[:, :-1]).reshape(-1, V).contiguous()
     del Q, U
@@ -450,14 +451,14 @@ def surrogate_leg(args, dist, world):
     torch.cuda.synchronize()
     t0 = time.time()
     epochs = 5
-    losses = h.surrogate_train(dQ[:n_train], dU[:n_train], n_train, epochs=epochs, batch=4, lr=1e-3)
+    losses = h.surrogate_train(dQ[:n_train], dU[:n_train], n_train, epochs=epochs, batch=4, lr=1e-3, stream=st)
     torch.cuda.synchronize()
     t_train = time.time() - t0
     # held-out increments
     pred = torch.empty(V, dtype=torch.float32, device="cuda")
     num = den = 0.0
     for j in range(n_train, dQ.shape[0]):
-        h.surrogate_apply(dQ[j], pred)
+        h.surrogate_apply(dQ[j], pred, st)
         torch.cuda.synchronize()
         num += float(((pred - dU[j]) ** 2).sum())
         den += float((dU[j] ** 2).sum())
@@ -468,18 +469,18 @@ def surrogate_leg(args, dist, world):
     res = {}
     for mode in ("plain", "surrogate"):
         h.surrogate_enable(10 if mode == "surrogate" else 0)
-        h.set_m(m0)
-        h.llg_step(dt, 1)              # warm-up (and the graph-free first step)
-        h.set_m(m0)
+        h.set_m(m0, st)
+        h.llg_step(dt, 1, st)          # warm-up
+        h.set_m(m0, st)
         h.surrogate_enable(10 if mode == "surrogate" else 0)
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        h.llg_step(dt, nsteps)
-        e1.record()
+        e0.record(st)
+        h.llg_step(dt, nsteps, st)
+        e1.record(st)
         e1.synchronize()
         out = torch.empty_like(m0)
-        h.get_m(out)
+        h.get_m(out, st)
         h.sync()
         res[mode] = (e0.elapsed_time(e1) / nsteps, out.double().cpu().numpy())
         if mode == "surrogate":

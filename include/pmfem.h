@@ -200,9 +200,9 @@ int pmfem_llg_step(pmfem_t h, double dt, int nsteps, void* stream);
  * the totals; 0 stops recording.  pmfem_profile_read synchronises the device and writes,
  * for kernel ids 0..n-1, the launch counts and the summed event time in ms since the last
  * pmfem_profile(h, 1).  Ids: 0 charges, 1 projection, 2 FFT x forward, 3 FFT y forward,
- * 4 FFT z + spectral multiply, 5 FFT y inverse, 6 FFT x inverse, 7 interpolation (with the
- * near-element entries), 8 gradient + exchange (+ RK4 stage), 9 grid clear, 10 permutation
- * between the C-ABI unknown order and the internal box-sorted order, 11 point precorrection.
+ * 4 FFT z + spectral multiply, 5 FFT y inverse, 6 FFT x inverse, 7 interpolation +
+ * precorrection, 8 gradient + exchange (+ RK4 stage), 9 grid clear, 10 permutation between
+ * the C-ABI unknown order and the internal box-sorted order.
  */
 int pmfem_profile(pmfem_t h, int enable);
 int pmfem_profile_read(pmfem_t h, int64_t* counts, double* total_ms, int n);
@@ -251,7 +251,9 @@ int pmfem_folded_positions(pmfem_t h, double* out);
  * 0.1 z, circular padding along periodic axes and zero padding along the others.  Grids are
  * device arrays of N0 x N1 x N2 FP32 (x fastest; pmfem_grid_info gives the dimensions, which
  * must be multiples of 8, 8 and 4).  Weights, gradients and accumulation are FP32; hidden
- * activations are FP32 or, with act_bf16, bfloat16.  Training minimises the mean squared
+ * activations are FP32 or, with act_bf16, bfloat16.  With bfloat16 activations on a grid
+ * whose x and y dimensions are multiples of 8 and 16, the two 32 -> 32 layers run on the
+ * tensor cores (tcgen05, BF16 operands, FP32 accumulation).  Training minimises the mean squared
  * error (in units of su) with Adam (beta1 0.9, beta2 0.999, eps 1e-8).
  * ====================================================================================== */
 
@@ -285,7 +287,8 @@ int pmfem_grid_pair(pmfem_t h, const void* m, float* Q, float* U, void* stream);
  */
 int pmfem_surrogate_enable(pmfem_t h, int every_k);
 /* out[4]: steps taken, stages that used the network, stages judged, and the relative L2
- * error of the network's potential over all judged stages (sqrt(sum |dU|^2 / sum |U|^2)). */
+ * error of the network's potential over all judged stages (sqrt(sum |dU|^2 / sum |U|^2)).
+ * Synchronises; ETIMEOUT if a tensor-core convolution gave up waiting for its MMAs. */
 int pmfem_surrogate_stats(pmfem_t h, double* out);
 
 /* ======================================================================================

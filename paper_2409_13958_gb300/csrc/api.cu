@@ -201,6 +201,7 @@ int build_device(pmfem_t h, DevOps<T>& d) {
   h->dev_info[9] = (int64_t)L.xnode.size();
   h->dev_info[10] = L.TY;
   h->dev_info[11] = L.TZ;
+
   d.nx_exc = (int64_t)L.xnode.size();
   if ((rc = upload(h, L.xnode.data(), L.xnode.size(), &d.xnode))) return rc;
   if ((rc = upload(h, L.xgrid.data(), L.xgrid.size(), &d.xgrid))) return rc;
@@ -798,6 +799,20 @@ extern "C" int pmfem_field_noalloc(pmfem_t h, const void* m, void* H, int compon
 // ------------------------------------------------------------------------------------
 // Learned surrogate of the FFT convolution (network and kernels in surrogate.cu).
 // ------------------------------------------------------------------------------------
+namespace {
+// A tensor-core convolution that gave up waiting on its MMAs leaves a flag (ETIMEOUT).
+int surrogate_check(pmfem_t h) {
+  if (!h->net || !h->net->tc_err) return OK;
+  int f = 0;
+  PMFEM_CK(h, cudaMemcpy(&f, h->net->tc_err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (f) {
+    PMFEM_CK(h, cudaMemset(h->net->tc_err, 0, sizeof(int)));
+    return fail(h, ETIMEOUT_, "a tensor-core convolution of the surrogate timed out waiting for its MMAs");
+  }
+  return OK;
+}
+}  // namespace
+
 extern "C" {
 
 int pmfem_surrogate_set_params(pmfem_t h, const float* params, int64_t n, double sq, double su, int act_bf16) {
@@ -872,7 +887,7 @@ int pmfem_surrogate_grad(pmfem_t h, const float* Q, const float* U, float* grads
   PMFEM_CK(h, cudaMemcpy(loss, net.loss, sizeof(double), cudaMemcpyDeviceToHost));
   net_params_from_device_layout(dl.data(), out);
   std::memcpy(grads, out.data(), out.size() * sizeof(float));
-  return OK;
+  return surrogate_check(h);
 }
 
 int pmfem_surrogate_train(pmfem_t h, const float* Q, const float* U, int64_t npairs, int epochs, int batch, double lr,
@@ -943,7 +958,7 @@ int pmfem_surrogate_stats(pmfem_t h, double* out) {
   out[1] = (double)h->sur_evals;
   out[2] = (double)h->sur_judged;
   out[3] = e[1] > 0 ? std::sqrt(e[0] / e[1]) : 0.0;
-  return OK;
+  return surrogate_check(h);
 }
 
 }  // extern "C"

@@ -85,6 +85,8 @@ struct Setup {
 // when every delta of the operator fits, else 32-bit.
 struct SellMatrix {
   int64_t rows = 0;
+  int vw = 1;                        // values per lane and step: element j of a row sits at
+                                     // off[c] + ((j / vw) * 32 + lane) * vw + j % vw
   std::vector<int32_t> map;          // thread -> row (identity unless rows were length-sorted)
   std::vector<int32_t> len;          // per thread
   std::vector<int32_t> base;         // per thread: column = base + delta

@@ -87,60 +87,41 @@ __global__ void __launch_bounds__(kBlock) k_project_exc(int64_t n, const int32_t
 }
 
 // ---------------------------------------------------------------- interpolation + precorrection
-// The same two steps as two kernels, so that the precorrection SpMV, the dominant pass,
-// runs with few registers and many resident warps.  k_interp_stencil: one thread per node
-// (box order) writes u = interpolated grid potential + near-element entries + e.
-template <typename T, int P>
-__global__ void __launch_bounds__(kBlock) k_interp_stencil(
-    int64_t Np, const int32_t* __restrict__ base, const T* __restrict__ frac, const T* __restrict__ U, int N0, int N1,
-    int N2, bool p0, bool p1, bool p2, const int32_t* __restrict__ rowptrX, const int32_t* __restrict__ colX,
-    const T* __restrict__ valX, const T* __restrict__ e, const V4<T>* __restrict__ m, T* __restrict__ u) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= Np) return;
-  T w0[P], w1[P], w2[P];
-  lagrange<T, P>(frac[3 * i], w0);
-  lagrange<T, P>(frac[3 * i + 1], w1);
-  lagrange<T, P>(frac[3 * i + 2], w2);
-  const int b0 = base[3 * i], b1 = base[3 * i + 1], b2 = base[3 * i + 2];
-  int ix[P];
-#pragma unroll
-  for (int a = 0; a < P; ++a) ix[a] = wrap(b0 + a, N0, p0);
-  T acc = 0;
-#pragma unroll
-  for (int c = 0; c < P; ++c) {
-    const int64_t zo = (int64_t)N1 * wrap(b2 + c, N2, p2);
-#pragma unroll
-    for (int b = 0; b < P; ++b) {
-      const T* rowp = U + (int64_t)N0 * (wrap(b1 + b, N1, p1) + zo);
-      T s = 0;
-#pragma unroll
-      for (int a = 0; a < P; ++a) s += w0[a] * __ldg(rowp + ix[a]);
-      acc += w2[c] * w1[b] * s;
-    }
-  }
-  for (int32_t p = rowptrX[i]; p < rowptrX[i + 1]; ++p) {
-    const V4<T> mk = m[colX[p]];
-    acc += valX[3 * p] * mk.x + valX[3 * p + 1] * mk.y + valX[3 * p + 2] * mk.z;
-  }
-  u[i] = acc + e[i];
-}
-
-// k_precorr: one thread per precorrection row (SELL-32, thread t handles node map[t]),
-// u[i] += sum_k C_ik q_k (step 4).  PMFEM_PRECORR_B values per thread are loaded together.
-#ifndef PMFEM_PRECORR_B
-#define PMFEM_PRECORR_B 8
+// Fused form: one thread per precorrection row t (node map[t]) does both steps, so u is
+// written once and the node data are read once.  The FP32 kernel with stencils of up to 4
+// points per axis asks for PMFEM_INTERP_MINB resident blocks per SM (a register cap).
+#ifndef PMFEM_INTERP_MINB
+#define PMFEM_INTERP_MINB 5
 #endif
-template <typename T, typename CT, typename VT>
-__global__ void __launch_bounds__(kBlock) k_precorr(int64_t Np, const int32_t* __restrict__ map,
-                                                   const int32_t* __restrict__ len, const int32_t* __restrict__ cbase,
-                                                   const int64_t* __restrict__ off, const CT* __restrict__ dcol,
-                                                   const VT* __restrict__ cval, const T* __restrict__ q,
-                                                   T* __restrict__ u) {
-  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= Np) return;
-  const int64_t i = map ? (int64_t)map[t] : t;
-  const T acc = sell_dot<PMFEM_PRECORR_B>(cval, dcol, q, cbase[t], off[t >> 5] + (t & 31), len[t], (int32_t)Np);
-  u[i] += acc;
+#define PMFEM_INTERP_PARAMS                                                                                      \
+  int64_t Np, const int32_t *__restrict__ map, const int32_t *__restrict__ base, const T *__restrict__ frac,      \
+      const T *__restrict__ U, int N0, int N1, int N2, bool p0, bool p1, bool p2,                                \
+      const int32_t *__restrict__ clen, const int32_t *__restrict__ cbase, const int64_t *__restrict__ coff,     \
+      const CT *__restrict__ dcol, const VT *__restrict__ cval, const int32_t *__restrict__ rowptrX,             \
+      const int32_t *__restrict__ colX, const T *__restrict__ valX, const T *__restrict__ q,                      \
+      const T *__restrict__ e, const V4<T> *__restrict__ m, T *__restrict__ u
+#define PMFEM_INTERP_BODY                                                                                         \
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;                                              \
+  if (t >= Np) return;                                                                                            \
+  const int64_t i = map ? (int64_t)map[t] : t;                                                                    \
+  interp_row<T, P, CT, VT>(t, i, 0, (int32_t)Np, base, frac, U, N0, N1, N2, p0, p1, p2, clen, cbase, coff, dcol, \
+                           cval, rowptrX, colX, valX, q, e, m, u);
+template <typename T, int P, typename CT, typename VT>
+__global__ void __launch_bounds__(kBlock, PMFEM_INTERP_MINB) k_interp_capped(PMFEM_INTERP_PARAMS) {
+  PMFEM_INTERP_BODY
+}
+template <typename T, int P, typename CT, typename VT>
+__global__ void __launch_bounds__(kBlock) k_interp(PMFEM_INTERP_PARAMS) {
+  PMFEM_INTERP_BODY
+}
+#undef PMFEM_INTERP_BODY
+#undef PMFEM_INTERP_PARAMS
+template <typename T, int P, typename CT, typename VT>
+constexpr auto interp_kernel() {
+  if constexpr (sizeof(T) == 4 && P <= 4)
+    return k_interp_capped<T, P, CT, VT>;
+  else
+    return k_interp<T, P, CT, VT>;
 }
 
 // ---------------------------------------------------------------- gradient + exchange + RK4
@@ -245,29 +226,27 @@ void launch_anterp(const DevOps<T>& d, cudaStream_t st) {
 template <typename T>
 void launch_interp(const DevOps<T>& d, const V4<T>* m, cudaStream_t st) {
   const unsigned nb = blocks_for(d.Np);
-  d.prof.begin(KID_INTERP, st);
-  auto stencil = [&](auto kernel) {
-    kernel<<<nb, kBlock, 0, st>>>(d.Np, d.base, d.frac, d.grid, d.dims[0], d.dims[1], d.dims[2], d.periodic[0],
-                                  d.periodic[1], d.periodic[2], d.rowptrX, d.colX, d.valX, d.e, m, d.u);
-  };
-  switch (d.p) {
-    case 2: stencil(k_interp_stencil<T, 3>); break;
-    case 3: stencil(k_interp_stencil<T, 4>); break;
-    case 4: stencil(k_interp_stencil<T, 5>); break;
-    default: stencil(k_interp_stencil<T, 6>); break;
-  }
-  d.prof.end(KID_INTERP, st);
-  d.prof.begin(KID_PRECORR, st);
   const DevSell<T>& C = d.cor;
+  d.prof.begin(KID_INTERP, st);
   with_ct(C, [&](auto ct) {
     using CT = typename decltype(ct)::type;
     with_vt<T>(C.bval[0] != nullptr, [&](auto vt) {
       using VT = typename decltype(vt)::type;
-      k_precorr<T, CT, VT><<<nb, kBlock, 0, st>>>(d.Np, C.map, C.len, C.base, C.off, (const CT*)C.delta,
-                                                  vals<VT>(C, 0), d.q, d.u);
+      auto go = [&](auto kernel) {
+        kernel<<<nb, kBlock, 0, st>>>(d.Np, C.map, d.base, d.frac, d.grid, d.dims[0], d.dims[1], d.dims[2],
+                                      d.periodic[0], d.periodic[1], d.periodic[2], C.len, C.base, C.off,
+                                      (const CT*)C.delta, vals<VT>(C, 0), d.rowptrX, d.colX, d.valX, d.q, d.e, m,
+                                      d.u);
+      };
+      switch (d.p) {
+        case 2: go(interp_kernel<T, 3, CT, VT>()); break;
+        case 3: go(interp_kernel<T, 4, CT, VT>()); break;
+        case 4: go(interp_kernel<T, 5, CT, VT>()); break;
+        default: go(interp_kernel<T, 6, CT, VT>()); break;
+      }
     });
   });
-  d.prof.end(KID_PRECORR, st);
+  d.prof.end(KID_INTERP, st);
 }
 
 template <typename T>

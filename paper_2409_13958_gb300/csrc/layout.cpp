@@ -85,12 +85,13 @@ int64_t centre_deltas(const int32_t* cols, int64_t len, int32_t ref, int64_t n, 
   return md;
 }
 
-void build_sell(SellMatrix& M, int64_t rows, int comps, int sigma, int col_bits, int64_t ncols,
+void build_sell(SellMatrix& M, int64_t rows, int comps, int sigma, int col_bits, int64_t ncols, int vw,
                 const std::function<int64_t(int64_t)>& len,
                 const std::function<int32_t(int64_t)>& base,
                 const std::function<void(int64_t, const std::function<void(int32_t, const double*)>&)>& fill) {
   M.rows = rows;
   M.comps = comps;
+  M.vw = vw;
   std::vector<int64_t> rl(rows);
   parallel_for(rows, [&](int64_t b, int64_t e) {
     for (int64_t r = b; r < e; ++r) rl[r] = len(r);
@@ -110,6 +111,7 @@ void build_sell(SellMatrix& M, int64_t rows, int comps, int sigma, int col_bits,
   for (int64_t c = 0; c < nch; ++c) {
     int64_t w = 0;
     for (int64_t t = 32 * c; t < std::min(rows, 32 * c + 32); ++t) w = std::max<int64_t>(w, M.len[t]);
+    w = (w + vw - 1) / vw * vw;   // whole vectors per lane
     M.off[c + 1] = M.off[c] + 32 * w;
   }
   const int64_t P = M.off[nch];
@@ -135,8 +137,9 @@ void build_sell(SellMatrix& M, int64_t rows, int comps, int sigma, int col_bits,
         std::vector<int32_t> d(cols.size());
         md = std::max(md, centre_deltas(cols.data(), (int64_t)cols.size(), ref, ncols, &bse, d.data()));
         M.base[t] = bse;
-        int64_t o = M.off[c] + (t - 32 * c);
-        for (size_t k = 0; k < cols.size(); ++k, o += 32) {
+        const int64_t lane = t - 32 * c;
+        for (size_t k = 0; k < cols.size(); ++k) {
+          const int64_t o = M.off[c] + ((int64_t)(k / vw) * 32 + lane) * vw + (int64_t)(k % vw);
           delta[o] = d[k];
           for (int q = 0; q < comps; ++q) M.val[(size_t)q * P + o] = vals[k * comps + q];
         }
@@ -298,7 +301,7 @@ int build_layout(const Setup& s, Layout& L, Error& err) {
       return EINVAL_;
     }
   // SELL-32 operators
-  build_sell(L.adj, Np, 10, 1, s.col_bits, Np, [&](int64_t i) { return (int64_t)(L.rowptr[i + 1] - L.rowptr[i]); },
+  build_sell(L.adj, Np, 10, 1, s.col_bits, Np, 1, [&](int64_t i) { return (int64_t)(L.rowptr[i + 1] - L.rowptr[i]); },
              [&](int64_t i) { return (int32_t)i; },
              [&](int64_t i, const std::function<void(int32_t, const double*)>& put) {
                for (int64_t q = L.rowptr[i]; q < L.rowptr[i + 1]; ++q) {
@@ -309,7 +312,7 @@ int build_layout(const Setup& s, Layout& L, Error& err) {
              });
   // rows sorted by length in windows of 1024 (about a dozen box rows): a warp's rows stay
   // near one another (shared gathers) and have similar lengths (little idle lanes)
-  build_sell(L.cor, Np, 1, s.sort_window > 0 ? s.sort_window : 1024, s.col_bits, Np,
+  build_sell(L.cor, Np, 1, s.sort_window > 0 ? s.sort_window : 1024, s.col_bits, Np, 4,
                [&](int64_t i) { return L.cptr[i + 1] - L.cptr[i]; }, [&](int64_t i) { return (int32_t)i; },
                [&](int64_t i, const std::function<void(int32_t, const double*)>& put) {
                  for (int64_t o = L.cptr[i]; o < L.cptr[i + 1]; ++o) put(L.ccol[o], &L.cval[o]);
@@ -355,7 +358,7 @@ int build_layout(const Setup& s, Layout& L, Error& err) {
     gc[2] = (int)(g / ((int64_t)N[0] * N[1]));
   };
   const int64_t G = (int64_t)N[0] * N[1] * N[2];
-  build_sell(L.pro, G, 1, s.sort_window > 0 ? s.sort_window : 1024, s.col_bits, Np,
+  build_sell(L.pro, G, 1, s.sort_window > 0 ? s.sort_window : 1024, s.col_bits, Np, 1,
              [&](int64_t g) {
                int gc[3];
                gcoord(g, gc);

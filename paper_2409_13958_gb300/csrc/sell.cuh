@@ -97,6 +97,65 @@ __device__ __forceinline__ T sell_dot(const VT* __restrict__ val, const CT* __re
   return acc;
 }
 
+// Four consecutive stored values of one lane (16 B of FP32, 32 B of FP64, 8 B of bfloat16),
+// widened to T, and four consecutive column deltas (8 B of int16 or 16 B of int32).
+__device__ __forceinline__ void ldv4(const float* p, float (&v)[4]) {
+  const float4 a = __ldcs(reinterpret_cast<const float4*>(p));
+  v[0] = a.x, v[1] = a.y, v[2] = a.z, v[3] = a.w;
+}
+__device__ __forceinline__ void ldv4(const double* p, double (&v)[4]) {
+  const double2 a = __ldcs(reinterpret_cast<const double2*>(p));
+  const double2 b = __ldcs(reinterpret_cast<const double2*>(p + 2));
+  v[0] = a.x, v[1] = a.y, v[2] = b.x, v[3] = b.y;
+}
+__device__ __forceinline__ void ldv4(const bf16_t* p, float (&v)[4]) {
+  const uint2 a = __ldcs(reinterpret_cast<const uint2*>(p));
+  v[0] = __uint_as_float(a.x << 16), v[1] = __uint_as_float(a.x & 0xffff0000u);
+  v[2] = __uint_as_float(a.y << 16), v[3] = __uint_as_float(a.y & 0xffff0000u);
+}
+__device__ __forceinline__ void ldc4(const int16_t* p, int32_t (&c)[4]) {
+  const short4 a = __ldcs(reinterpret_cast<const short4*>(p));
+  c[0] = a.x, c[1] = a.y, c[2] = a.z, c[3] = a.w;
+}
+__device__ __forceinline__ void ldc4(const int32_t* p, int32_t (&c)[4]) {
+  const int4 a = __ldcs(reinterpret_cast<const int4*>(p));
+  c[0] = a.x, c[1] = a.y, c[2] = a.z, c[3] = a.w;
+}
+
+// sell_dot for a SELL-32 operator stored four values per lane and step (vector width 4):
+// the lane's group g of elements 4g .. 4g+3 sits at o0 + 128 g, where o0 = off[c] + 4 lane.
+// Rows are padded to whole groups with value 0 and delta 0 (a valid column), so every group
+// is read whole; G groups (4G values, 4G deltas, then 4G gathers) are kept in flight.
+template <int G, typename T, typename CT, typename VT>
+__device__ __forceinline__ T sell_dot4(const VT* __restrict__ val, const CT* __restrict__ dcol,
+                                       const T* __restrict__ x, int32_t b, int64_t o0, int n, int32_t ncol) {
+  T acc = 0;
+  const int ng = (n + 3) >> 2;
+  int g = 0;
+  for (; g + G <= ng; g += G, o0 += 128 * G) {
+    T v[G][4];
+    int32_t c[G][4];
+#pragma unroll
+    for (int k = 0; k < G; ++k) {
+      ldv4(val + o0 + 128 * k, v[k]);
+      ldc4(dcol + o0 + 128 * k, c[k]);
+    }
+#pragma unroll
+    for (int k = 0; k < G; ++k)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) acc += v[k][e] * __ldg(x + col_of(b, c[k][e], ncol));
+  }
+  for (; g < ng; ++g, o0 += 128) {
+    T v[4];
+    int32_t c[4];
+    ldv4(val + o0, v);
+    ldc4(dcol + o0, c);
+#pragma unroll
+    for (int e = 0; e < 4; ++e) acc += v[e] * __ldg(x + col_of(b, c[e], ncol));
+  }
+  return acc;
+}
+
 // ---------------------------------------------------------------- charges
 // q = W^q M (Eq. 14a) and e = E M (touching-element part of Eq. 14c): adjacency row i.
 template <typename T, typename CT, typename VT>
@@ -138,9 +197,49 @@ __device__ __forceinline__ void project_row(int64_t t, int64_t g, int64_t c0, in
 }
 
 // ---------------------------------------------------------------- interpolation + precorrection
-// Potential of node i (SELL row t of the precorrection): the (p+1)^3 stencil gathers from
-// the mesh's grid potential U (steps 3), the point precorrection row (step 4), the
-// near-element entries beyond the adjacency pattern and the touching-element part e.
+// Step 3 for node i: the (p+1)^3 Lagrange stencil over the grid potential U.
+template <typename T, int P>
+__device__ __forceinline__ T stencil_row(int64_t i, const int32_t* __restrict__ base, const T* __restrict__ frac,
+                                         const T* __restrict__ U, int N0, int N1, int N2, bool p0, bool p1, bool p2) {
+  T w0[P], w1[P], w2[P];
+  lagrange<T, P>(frac[3 * i], w0);
+  lagrange<T, P>(frac[3 * i + 1], w1);
+  lagrange<T, P>(frac[3 * i + 2], w2);
+  const int b0 = base[3 * i], b1 = base[3 * i + 1], b2 = base[3 * i + 2];
+  int ix[P];
+#pragma unroll
+  for (int a = 0; a < P; ++a) ix[a] = wrap(b0 + a, N0, p0);
+  T acc = 0;
+#pragma unroll
+  for (int c = 0; c < P; ++c) {
+    const int64_t zo = (int64_t)N1 * wrap(b2 + c, N2, p2);
+#pragma unroll
+    for (int b = 0; b < P; ++b) {
+      const T* rowp = U + (int64_t)N0 * (wrap(b1 + b, N1, p1) + zo);
+      T s = 0;
+#pragma unroll
+      for (int a = 0; a < P; ++a) s += w0[a] * __ldg(rowp + ix[a]);
+      acc += w2[c] * w1[b] * s;
+    }
+  }
+  return acc;
+}
+
+// Near-element entries of node i beyond the adjacency pattern (CSR, 3-vector values on M).
+template <typename T>
+__device__ __forceinline__ T extras_row(int64_t i, const int32_t* __restrict__ rowptrX, const int32_t* __restrict__ colX,
+                                        const T* __restrict__ valX, const V4<T>* __restrict__ m) {
+  T acc = 0;
+  for (int32_t p = rowptrX[i]; p < rowptrX[i + 1]; ++p) {
+    const V4<T> mk = m[colX[p]];
+    acc += valX[3 * p] * mk.x + valX[3 * p + 1] * mk.y + valX[3 * p + 2] * mk.z;
+  }
+  return acc;
+}
+
+// Potential of node i (SELL row t of the precorrection, stored with vector width 4): the
+// stencil (step 3), the point precorrection row (step 4), the near-element entries beyond the
+// adjacency pattern and the touching-element part e.
 template <typename T, int P, typename CT, typename VT>
 __device__ __forceinline__ void interp_row(
     int64_t t, int64_t i, int64_t c0, int32_t nc, const int32_t* __restrict__ base, const T* __restrict__ frac,
@@ -149,36 +248,9 @@ __device__ __forceinline__ void interp_row(
     const VT* __restrict__ cval, const int32_t* __restrict__ rowptrX, const int32_t* __restrict__ colX,
     const T* __restrict__ valX, const T* __restrict__ q, const T* __restrict__ e, const V4<T>* __restrict__ m,
     T* __restrict__ u) {
-  T acc = 0;
-  {  // step 3: interpolation of the grid potential
-    T w0[P], w1[P], w2[P];
-    lagrange<T, P>(frac[3 * i], w0);
-    lagrange<T, P>(frac[3 * i + 1], w1);
-    lagrange<T, P>(frac[3 * i + 2], w2);
-    const int b0 = base[3 * i], b1 = base[3 * i + 1], b2 = base[3 * i + 2];
-    int ix[P];
-#pragma unroll
-    for (int a = 0; a < P; ++a) ix[a] = wrap(b0 + a, N0, p0);
-#pragma unroll
-    for (int c = 0; c < P; ++c) {
-      const int64_t zo = (int64_t)N1 * wrap(b2 + c, N2, p2);
-#pragma unroll
-      for (int b = 0; b < P; ++b) {
-        const T* rowp = U + (int64_t)N0 * (wrap(b1 + b, N1, p1) + zo);
-        T s = 0;
-#pragma unroll
-        for (int a = 0; a < P; ++a) s += w0[a] * __ldg(rowp + ix[a]);
-        acc += w2[c] * w1[b] * s;
-      }
-    }
-  }
-  // step 4: point precorrection (SELL-32 row)
-  acc += sell_dot<8>(cval, dcol, q + c0, cbase[t], coff[t >> 5] + (t & 31), clen[t], nc);
-  // near-element entries beyond the adjacency pattern
-  for (int32_t p = rowptrX[i]; p < rowptrX[i + 1]; ++p) {
-    const V4<T> mk = m[colX[p]];
-    acc += valX[3 * p] * mk.x + valX[3 * p + 1] * mk.y + valX[3 * p + 2] * mk.z;
-  }
+  T acc = stencil_row<T, P>(i, base, frac, U, N0, N1, N2, p0, p1, p2);
+  acc += sell_dot4<2>(cval, dcol, q + c0, cbase[t], coff[t >> 5] + 4 * (t & 31), clen[t], nc);
+  acc += extras_row<T>(i, rowptrX, colX, valX, m);
   u[i] = acc + e[i];
 }
 

@@ -51,7 +51,7 @@ __device__ __forceinline__ int wrapc(int i, int n, bool per, bool& inside) {
 }
 
 // Halo tile of CK input channels starting at c0 into s[CK][HALO], scaled by scale; padding per axis.
-template <int CK, typename AIN>
+template <int CK, typename AIN, bool CL = false>
 __device__ __forceinline__ void load_halo(float* s, const AIN* __restrict__ in, int c0, int Cin, int X, int Y, int Z,
                                           int x0, int y0, int z0, bool px, bool py, bool pz, float scale) {
   const int64_t plane = (int64_t)X * Y * Z;
@@ -61,14 +61,15 @@ __device__ __forceinline__ void load_halo(float* s, const AIN* __restrict__ in, 
     bool ix, iy, iz;
     const int gx = wrapc(x0 + hx - 1, X, px, ix), gy = wrapc(y0 + hy - 1, Y, py, iy), gz = wrapc(z0 + hz - 1, Z, pz, iz);
     float v = 0.f;
-    if (c0 + c < Cin && ix && iy && iz) v = scale * ld_act(in + (int64_t)(c0 + c) * plane + gx + (int64_t)X * (gy + (int64_t)Y * gz));
+    const int64_t vox = gx + (int64_t)X * (gy + (int64_t)Y * gz);
+    if (c0 + c < Cin && ix && iy && iz) v = scale * ld_act(in + (CL ? vox * Cin + c0 + c : (int64_t)(c0 + c) * plane + vox));
     s[k] = v;
   }
 }
 
 // y[co] = act?(b[co] + sum_ci sum_tap W[tap][ci][co] x[ci](v + tap - 1)) * oscale for a tile.
 // Cin arbitrary (chunks of CK), COUT <= 32 output channels, one voxel per thread.
-template <int CK, int COUT, bool ACT, typename AIN, typename AOUT>
+template <int CK, int COUT, bool ACT, typename AIN, typename AOUT, bool CL_IN = false, bool CL_OUT = false>
 __global__ void __launch_bounds__(TILE) k_conv_fwd(const AIN* __restrict__ in, int Cin, const float* __restrict__ W,
                                                    const float* __restrict__ b, AOUT* __restrict__ out, int X, int Y,
                                                    int Z, bool px, bool py, bool pz, float in_scale, float out_scale) {
@@ -83,7 +84,7 @@ __global__ void __launch_bounds__(TILE) k_conv_fwd(const AIN* __restrict__ in, i
   for (int o = 0; o < COUT; ++o) acc[o] = b ? b[o] : 0.f;
   for (int c0 = 0; c0 < Cin; c0 += CK) {
     __syncthreads();
-    load_halo<CK>(s_in, in, c0, Cin, X, Y, Z, x0, y0, z0, px, py, pz, in_scale);
+    load_halo<CK, AIN, CL_IN>(s_in, in, c0, Cin, X, Y, Z, x0, y0, z0, px, py, pz, in_scale);
     for (int k = threadIdx.x; k < 27 * CK * COUT; k += blockDim.x) {
       const int tap = k / (CK * COUT), r = k - tap * CK * COUT, ci = r / COUT;
       s_w[k] = (c0 + ci < Cin) ? W[((int64_t)tap * Cin + c0 + ci) * COUT + (r - ci * COUT)] : 0.f;
@@ -108,15 +109,17 @@ __global__ void __launch_bounds__(TILE) k_conv_fwd(const AIN* __restrict__ in, i
   for (int o = 0; o < COUT; ++o) {
     float z = acc[o];
     if (ACT) z = z > 0.f ? z : kSlope * z;
-    st_act(out + (int64_t)o * plane + vox, z * out_scale);
+    st_act(out + (CL_OUT ? vox * COUT + o : (int64_t)o * plane + vox), z * out_scale);
   }
 }
 
 // g[c](v) *= act'(h[c](v)), read from the activation h (act keeps the sign of its argument).
-template <typename A>
-__global__ void k_act_bwd(float* __restrict__ g, const A* __restrict__ h, int64_t n) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n && !(ld_act(h + i) > 0.f)) g[i] *= kSlope;
+template <typename A, bool CL = false>
+__global__ void k_act_bwd(float* __restrict__ g, const A* __restrict__ h, int64_t n, int64_t V, int C) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;   // g is planar: i = c V + v
+  if (i >= n) return;
+  const int64_t hi = CL ? (i % V) * C + i / V : i;
+  if (!(ld_act(h + hi) > 0.f)) g[i] *= kSlope;
 }
 
 // Weights of the input-gradient convolution: the adjoint of y = W * x is x' = W' * y with
@@ -130,7 +133,7 @@ __global__ void k_flip(const float* __restrict__ W, float* __restrict__ Wt, int 
 
 // dW[tap][ci][co] += sum_v g[co](v) x[ci](v + tap - 1) and db[co] += sum_v g[co](v), over
 // the tiles of this block (grid-stride), one (ci, co) pair per thread with 27 accumulators.
-template <int CI, int CO, typename AIN>
+template <int CI, int CO, typename AIN, bool CL_IN = false>
 __global__ void __launch_bounds__(1024) k_conv_wgrad(const AIN* __restrict__ x, const float* __restrict__ g, int X,
                                                     int Y, int Z, bool px, bool py, bool pz, float in_scale,
                                                     float* __restrict__ dW, float* __restrict__ db) {
@@ -148,7 +151,7 @@ __global__ void __launch_bounds__(1024) k_conv_wgrad(const AIN* __restrict__ x, 
   for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const int x0 = (tile % ntx) * TX, y0 = ((tile / ntx) % nty) * TY, z0 = (tile / (ntx * nty)) * TZ;
     __syncthreads();
-    load_halo<CI>(s_x, x, 0, CI, X, Y, Z, x0, y0, z0, px, py, pz, in_scale);
+    load_halo<CI, AIN, CL_IN>(s_x, x, 0, CI, X, Y, Z, x0, y0, z0, px, py, pz, in_scale);
     for (int k = threadIdx.x; k < CO * TILE; k += blockDim.x) {
       const int c = k / TILE, v = k - c * TILE;
       const int lx = v % TX, ly = (v / TX) % TY, lz = v / (TX * TY);
@@ -243,12 +246,12 @@ void opt_in_smem(K kernel, size_t bytes) {
 
 unsigned ntiles(const SurrogateNet& n) { return (unsigned)((n.dims[0] / TX) * (n.dims[1] / TY) * (n.dims[2] / TZ)); }
 
-template <int CI, int CO, typename A>
+template <int CI, int CO, typename A, bool CL = false>
 void wgrad(const SurrogateNet& n, const A* x, const float* g, float in_scale, int layer, cudaStream_t st) {
   const size_t sm = (size_t)(CI * HALO + CO * TILE) * sizeof(float);
-  opt_in_smem(k_conv_wgrad<CI, CO, A>, sm);
+  opt_in_smem(k_conv_wgrad<CI, CO, A, CL>, sm);
   const unsigned nb = std::min(ntiles(n), 2u * 152u);
-  k_conv_wgrad<CI, CO, A><<<nb, 1024, sm, st>>>(x, g, n.dims[0], n.dims[1], n.dims[2], n.periodic[0], n.periodic[1],
+  k_conv_wgrad<CI, CO, A, CL><<<nb, 1024, sm, st>>>(x, g, n.dims[0], n.dims[1], n.dims[2], n.periodic[0], n.periodic[1],
                                                n.periodic[2], in_scale, n.G + net_layer_offset(layer, false),
                                                n.G + net_layer_offset(layer, true));
 }
@@ -261,14 +264,29 @@ void forward_t(SurrogateNet& n, const float* Q, float* U, cudaStream_t st) {
   A* h0 = (A*)n.h[0];
   A* h1 = (A*)n.h[1];
   A* h2 = (A*)n.h[2];
+  if constexpr (sizeof(A) == 2) {
+    if (n.tc) {   // channels-last activations, layers 1 and 2 on the tensor cores
+      conv32_tc_pack(n.W[1], n.Wp[0], st);
+      conv32_tc_pack(n.W[2], n.Wp[1], st);
+      k_conv_fwd<1, kNetC, true, float, A, false, true><<<nt, TILE, 0, st>>>(Q, 1, n.W[0], n.b[0], h0, X, Y, Z, px, py,
+                                                                              pz, 1.f / n.sq, 1.f);
+      conv32_tc(h0, n.Wp[0], n.b[1], h1, n.dims, n.periodic, true, n.tc_err, st);
+      conv32_tc(h1, n.Wp[1], n.b[2], h2, n.dims, n.periodic, true, n.tc_err, st);
+      k_conv_fwd<8, 1, false, A, float, true, false><<<nt, TILE, 0, st>>>(h2, kNetC, n.W[3], n.b[3], U, X, Y, Z, px,
+                                                                           py, pz, 1.f, n.su);
+      return;
+    }
+  }
   k_conv_fwd<1, kNetC, true, float, A><<<nt, TILE, 0, st>>>(Q, 1, n.W[0], n.b[0], h0, X, Y, Z, px, py, pz, 1.f / n.sq, 1.f);
   k_conv_fwd<8, kNetC, true, A, A><<<nt, TILE, 0, st>>>(h0, kNetC, n.W[1], n.b[1], h1, X, Y, Z, px, py, pz, 1.f, 1.f);
   k_conv_fwd<8, kNetC, true, A, A><<<nt, TILE, 0, st>>>(h1, kNetC, n.W[2], n.b[2], h2, X, Y, Z, px, py, pz, 1.f, 1.f);
   k_conv_fwd<8, 1, false, A, float><<<nt, TILE, 0, st>>>(h2, kNetC, n.W[3], n.b[3], U, X, Y, Z, px, py, pz, 1.f, n.su);
 }
 
-template <typename A>
-void backward_t(SurrogateNet& n, const float* Q, const float* Ut, cudaStream_t st) {
+// Backward pass: the input gradients run as convolutions with mirrored weights (planar FP32
+// gradient buffers, CUDA cores); CL says whether the stored activations are channels-last.
+template <typename A, bool CL>
+void backward_layers(SurrogateNet& n, const float* Q, cudaStream_t st) {
   const unsigned nt = ntiles(n);
   const int X = n.dims[0], Y = n.dims[1], Z = n.dims[2];
   const bool px = n.periodic[0], py = n.periodic[1], pz = n.periodic[2];
@@ -276,25 +294,33 @@ void backward_t(SurrogateNet& n, const float* Q, const float* Ut, cudaStream_t s
   const A* h0 = (const A*)n.h[0];
   const A* h1 = (const A*)n.h[1];
   const A* h2 = (const A*)n.h[2];
-  forward_t<A>(n, Q, n.pred, st);
-  k_out_grad<<<nb256(V), 256, 0, st>>>(n.pred, Ut, n.gA, V, 1.f / n.su, n.loss);
   // layer 3: 32 -> 1
-  wgrad<kNetC, 1, A>(n, h2, n.gA, 1.f, 3, st);
+  wgrad<kNetC, 1, A, CL>(n, h2, n.gA, 1.f, 3, st);
   k_flip<<<nb256(27 * kNetC), 256, 0, st>>>(n.W[3], n.Wt, kNetC, 1);
   k_conv_fwd<1, kNetC, false, float, float><<<nt, TILE, 0, st>>>(n.gA, 1, n.Wt, nullptr, n.gB, X, Y, Z, px, py, pz, 1.f, 1.f);
-  k_act_bwd<A><<<nb256(VC), 256, 0, st>>>(n.gB, h2, VC);
+  k_act_bwd<A, CL><<<nb256(VC), 256, 0, st>>>(n.gB, h2, VC, V, kNetC);
   // layer 2: 32 -> 32
-  wgrad<kNetC, kNetC, A>(n, h1, n.gB, 1.f, 2, st);
+  wgrad<kNetC, kNetC, A, CL>(n, h1, n.gB, 1.f, 2, st);
   k_flip<<<nb256(27 * kNetC * kNetC), 256, 0, st>>>(n.W[2], n.Wt, kNetC, kNetC);
   k_conv_fwd<8, kNetC, false, float, float><<<nt, TILE, 0, st>>>(n.gB, kNetC, n.Wt, nullptr, n.gA, X, Y, Z, px, py, pz, 1.f, 1.f);
-  k_act_bwd<A><<<nb256(VC), 256, 0, st>>>(n.gA, h1, VC);
+  k_act_bwd<A, CL><<<nb256(VC), 256, 0, st>>>(n.gA, h1, VC, V, kNetC);
   // layer 1: 32 -> 32
-  wgrad<kNetC, kNetC, A>(n, h0, n.gA, 1.f, 1, st);
+  wgrad<kNetC, kNetC, A, CL>(n, h0, n.gA, 1.f, 1, st);
   k_flip<<<nb256(27 * kNetC * kNetC), 256, 0, st>>>(n.W[1], n.Wt, kNetC, kNetC);
   k_conv_fwd<8, kNetC, false, float, float><<<nt, TILE, 0, st>>>(n.gA, kNetC, n.Wt, nullptr, n.gB, X, Y, Z, px, py, pz, 1.f, 1.f);
-  k_act_bwd<A><<<nb256(VC), 256, 0, st>>>(n.gB, h0, VC);
+  k_act_bwd<A, CL><<<nb256(VC), 256, 0, st>>>(n.gB, h0, VC, V, kNetC);
   // layer 0: 1 -> 32, input Q / sq
-  wgrad<1, kNetC, float>(n, Q, n.gB, 1.f / n.sq, 0, st);
+  wgrad<1, kNetC, float, false>(n, Q, n.gB, 1.f / n.sq, 0, st);
+}
+
+template <typename A>
+void backward_t(SurrogateNet& n, const float* Q, const float* Ut, cudaStream_t st) {
+  forward_t<A>(n, Q, n.pred, st);
+  k_out_grad<<<nb256(n.V), 256, 0, st>>>(n.pred, Ut, n.gA, n.V, 1.f / n.su, n.loss);
+  if (sizeof(A) == 2 && n.tc)
+    backward_layers<A, true>(n, Q, st);
+  else
+    backward_layers<A, false>(n, Q, st);
 }
 
 }  // namespace
@@ -358,6 +384,10 @@ int net_create(SurrogateNet& n, const int dims[3], const bool periodic[3], bool 
        ((n.U1 = (float*)p), true) && alloc(&p, n.V * 4) && ((n.Ubuf = (float*)p), true) &&
        alloc(&p, 2 * sizeof(double)) && ((n.loss = (double*)p), true) && alloc(&p, 2 * sizeof(double)) &&
        ((n.err = (double*)p), true);
+  n.tc = bf16 && conv32_tc_fits(dims);
+  if (ok && n.tc)
+    ok = alloc(&n.Wp[0], 27 * kNetC * kNetC * 2) && alloc(&n.Wp[1], 27 * kNetC * kNetC * 2) &&
+         alloc(&p, sizeof(int)) && ((n.tc_err = (int*)p), true);
   if (!ok) {
     net_destroy(n);
     msg = "device allocation for the surrogate failed";

@@ -38,7 +38,17 @@ struct SurrogateNet {
   float* U1 = nullptr;
   float* Ubuf = nullptr;      // network output
   double* err = nullptr;      // device: [sum (U_net - U)^2, sum U^2] of the judged stages
+  // tensor-core path (bfloat16 activations on a grid whose x and y are multiples of 8 and 16):
+  // hidden activations channels-last [V][32], the two 32 -> 32 layers on tcgen05
+  bool tc = false;
+  void* Wp[2] = {};           // packed bfloat16 weights of layers 1 and 2
+  int* tc_err = nullptr;      // device: set when a tensor-core wait gave up
 };
+
+bool conv32_tc_fits(const int dims[3]);
+void conv32_tc_pack(const float* W, void* Wp, cudaStream_t st);
+void conv32_tc(const void* in, const void* Wp, const float* bias, void* out, const int dims[3], const bool per[3],
+               bool act, int* err, cudaStream_t st);
 
 int64_t net_layer_offset(int layer, bool bias);                 // offset in the device layout
 int net_create(SurrogateNet& n, const int dims[3], const bool periodic[3], bool bf16, std::string& msg);

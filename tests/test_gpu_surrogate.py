@@ -35,6 +35,10 @@ def _handle(kind):
     from paper_2409_13958_gb300 import Pmfem, PMFEM_FP32
     if kind == "cube":          # 3D periodic, grid 8 x 8 x 8 (circular padding on every axis)
         mesh, grid = meshgen.cube_cell(4, jitter=0.2, seed=61), (8, 8, 8)
+    elif kind == "cube16":      # 3D periodic, grid 16^3: the tensor-core path with bfloat16 activations
+        mesh, grid = meshgen.cube_cell(6, jitter=0.2, seed=63), (16, 16, 16)
+    elif kind == "film16":      # 2D periodic film, grid 16 x 16 x 8 (tensor-core path, zero padding along z)
+        mesh, grid = meshgen.film_cell(10, 10, 2, seed=64), (16, 16, 8)
     else:                       # 2D periodic film, grid 16 x 8 x 8 with zero padding along z
         mesh, grid = meshgen.film_cell(10, 6, 2, seed=62), (16, 8, 8)
     h = Pmfem.create_mesh(mesh.xyz, mesh.tets, 8e5, 1.3e-11, 0.02)
@@ -49,7 +53,8 @@ def _rel(a, b):
     return float(np.linalg.norm(np.ravel(a) - np.ravel(b)) / np.linalg.norm(np.ravel(b)))
 
 
-@pytest.mark.parametrize("kind,bf16,tol", [("cube", False, 1e-5), ("film", False, 1e-5), ("film", True, 2e-2)])
+@pytest.mark.parametrize("kind,bf16,tol", [("cube", False, 1e-5), ("film", False, 1e-5), ("film", True, 2e-2),
+                                          ("cube16", True, 2e-2), ("film16", True, 2e-2), ("film16", False, 1e-5)])
 def test_forward_matches_oracle(kind, bf16, tol):
     h, mesh, dims, per = _handle(kind)
     params = S.init_params(C=32, seed=5)
@@ -69,23 +74,23 @@ def test_forward_matches_oracle(kind, bf16, tol):
     h.destroy()
 
 
-@pytest.mark.parametrize("kind", ["cube", "film"])
-def test_gradients_match_oracle(kind):
+@pytest.mark.parametrize("kind,bf16,tol", [("cube", False, 1e-4), ("film", False, 1e-4), ("film16", True, 5e-2)])
+def test_gradients_match_oracle(kind, bf16, tol):
     h, mesh, dims, per = _handle(kind)
     params = S.init_params(C=32, seed=6)
     for k in range(1, 8, 2):
         params[k] = np.random.default_rng(20 + k).normal(0, 0.05, params[k].shape)
     sq, su = 1.5, 0.4
-    h.surrogate_set_params(_flat(params), sq, su)
+    h.surrogate_set_params(_flat(params), sq, su, act_bf16=bf16)
     rng = np.random.default_rng(7)
     Q = rng.standard_normal(dims[::-1])
     U = rng.standard_normal(dims[::-1])
     loss, g = h.surrogate_grad(torch.tensor(Q, dtype=torch.float32, device="cuda"),
                                torch.tensor(U, dtype=torch.float32, device="cuda"))
     ref_loss, ref_g = S.loss_and_grad(params, Q, U, sq, su, per)
-    assert abs(loss - ref_loss) <= 1e-5 * ref_loss
+    assert abs(loss - ref_loss) <= 0.1 * tol * ref_loss
     for k, (a, b) in enumerate(zip(_unflat(g, params), ref_g)):
-        assert _rel(a, b) <= 1e-4, k
+        assert _rel(a, b) <= tol, k
     h.destroy()
 
 
@@ -158,4 +163,44 @@ def test_rk4_with_surrogate_is_judged_and_stays_normalised():
     nrm = np.linalg.norm(out.double().cpu().numpy(), axis=1)
     assert np.abs(nrm - 1).max() < 1e-6
     h.surrogate_enable(0)
+    h.destroy()
+
+
+def test_trained_network_beats_the_frozen_potential():
+    """What the trained network gains: on RK stages 2-4 the step either freezes the potential
+    of stage 1 (a network that outputs zero) or adds the trained network's increment.  The
+    full P-AIM judges both on the same steps; the trained network must be closer to it."""
+    h, mesh, dims, per = _handle("film")
+    Np = h.num_unknowns()
+    V = dims[0] * dims[1] * dims[2]
+    # training increments from the method's own trajectory
+    dt = 2e-14
+    steps = 24
+    Q = torch.empty((steps, V), dtype=torch.float32, device="cuda")
+    U = torch.empty_like(Q)
+    m = torch.tensor(meshgen.m_tilted(Np, polar_deg=30.0, seed=80), dtype=torch.float32, device="cuda")
+    h.set_m(m)
+    for k in range(steps):
+        h.get_m(m)
+        h.grid_pair(m, Q[k], U[k])
+        h.llg_step(dt, 1)
+    h.sync()
+    dQ = (Q[1:] - Q[:-1]).contiguous()
+    dU = (U[1:] - U[:-1]).contiguous()
+    sq, su = float(dQ.std()), float(dU.std())
+
+    def judged_error(params):
+        h.surrogate_set_params(params, sq, su)
+        h.set_m(torch.tensor(meshgen.m_tilted(Np, polar_deg=30.0, seed=81), dtype=torch.float32, device="cuda"))
+        h.surrogate_enable(1)            # judge every step: the error of every network stage is measured
+        h.llg_step(dt, 6)
+        st = h.surrogate_stats()
+        h.surrogate_enable(0)
+        return st["judged_rel_l2"]
+
+    frozen = judged_error(np.zeros(h.NET_PARAMS, dtype=np.float32))
+    h.surrogate_set_params(_flat(S.init_params(C=32, seed=14)), sq, su)
+    h.surrogate_train(dQ, dU, dQ.shape[0], epochs=60, batch=1, lr=2e-3)
+    trained = judged_error(h.surrogate_get_params())
+    assert trained < frozen, (trained, frozen)
     h.destroy()
