@@ -301,7 +301,7 @@ int build_layout(const Setup& s, Layout& L, Error& err) {
       return EINVAL_;
     }
   // SELL-32 operators
-  build_sell(L.adj, Np, 10, 1, s.col_bits, Np, 1, [&](int64_t i) { return (int64_t)(L.rowptr[i + 1] - L.rowptr[i]); },
+  build_sell(L.adj, Np, 10, 1, s.col_bits, Np, 4, [&](int64_t i) { return (int64_t)(L.rowptr[i + 1] - L.rowptr[i]); },
              [&](int64_t i) { return (int32_t)i; },
              [&](int64_t i, const std::function<void(int32_t, const double*)>& put) {
                for (int64_t q = L.rowptr[i]; q < L.rowptr[i + 1]; ++q) {
@@ -358,7 +358,7 @@ int build_layout(const Setup& s, Layout& L, Error& err) {
     gc[2] = (int)(g / ((int64_t)N[0] * N[1]));
   };
   const int64_t G = (int64_t)N[0] * N[1] * N[2];
-  build_sell(L.pro, G, 1, s.sort_window > 0 ? s.sort_window : 1024, s.col_bits, Np, 1,
+  build_sell(L.pro, G, 1, s.sort_window > 0 ? s.sort_window : 1024, s.col_bits, Np, 4,
              [&](int64_t g) {
                int gc[3];
                gcoord(g, gc);

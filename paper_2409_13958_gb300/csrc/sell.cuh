@@ -157,7 +157,8 @@ __device__ __forceinline__ T sell_dot4(const VT* __restrict__ val, const CT* __r
 }
 
 // ---------------------------------------------------------------- charges
-// q = W^q M (Eq. 14a) and e = E M (touching-element part of Eq. 14c): adjacency row i.
+// q = W^q M (Eq. 14a) and e = E M (touching-element part of Eq. 14c): adjacency row i, stored
+// with vector width 4 (group g of the row at off[c] + 4 lane + 128 g; padded with zeros).
 template <typename T, typename CT, typename VT>
 __device__ __forceinline__ void charges_row(int64_t i, int64_t c0, int32_t nc, const int32_t* __restrict__ len,
                                             const int32_t* __restrict__ base, const int64_t* __restrict__ off,
@@ -166,16 +167,27 @@ __device__ __forceinline__ void charges_row(int64_t i, int64_t c0, int32_t nc, c
                                             const VT* __restrict__ ex, const VT* __restrict__ ey,
                                             const VT* __restrict__ ez, const V4<T>* __restrict__ m,
                                             T* __restrict__ q, T* __restrict__ e) {
-  const int n = len[i];
-  int64_t o = off[i >> 5] + (i & 31);
+  const int ng = (len[i] + 3) >> 2;
+  int64_t o = off[i >> 5] + 4 * (i & 31);
   const int32_t b = base[i];
   const V4<T>* mc = m + c0;
   T aq = 0, ae = 0;
-#pragma unroll 4
-  for (int j = 0; j < n; ++j, o += 32) {
-    const V4<T> mk = mc[col_of(b, __ldcs(dcol + o), nc)];
-    aq += ldv<T>(wx + o) * mk.x + ldv<T>(wy + o) * mk.y + ldv<T>(wz + o) * mk.z;
-    ae += ldv<T>(ex + o) * mk.x + ldv<T>(ey + o) * mk.y + ldv<T>(ez + o) * mk.z;
+  for (int g = 0; g < ng; ++g, o += 128) {
+    int32_t c[4];
+    T a0[4], a1[4], a2[4], e0[4], e1[4], e2[4];
+    ldc4(dcol + o, c);
+    ldv4(wx + o, a0);
+    ldv4(wy + o, a1);
+    ldv4(wz + o, a2);
+    ldv4(ex + o, e0);
+    ldv4(ey + o, e1);
+    ldv4(ez + o, e2);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const V4<T> mk = mc[col_of(b, c[k], nc)];
+      aq += a0[k] * mk.x + a1[k] * mk.y + a2[k] * mk.z;
+      ae += e0[k] * mk.x + e1[k] * mk.y + e2[k] * mk.z;
+    }
   }
   q[i] = aq;
   e[i] = ae;
@@ -192,7 +204,7 @@ __device__ __forceinline__ void project_row(int64_t t, int64_t g, int64_t c0, in
                                             T* __restrict__ grid) {
   const int n = len[t];
   T acc = 0;
-  if (n > 0) acc = sell_dot<8>(pw, dcol, q + c0, base[t], off[t >> 5] + (t & 31), n, nc);
+  if (n > 0) acc = sell_dot4<2>(pw, dcol, q + c0, base[t], off[t >> 5] + 4 * (t & 31), n, nc);
   grid[g] = acc;
 }
 
@@ -255,7 +267,8 @@ __device__ __forceinline__ void interp_row(
 }
 
 // ---------------------------------------------------------------- gradient + exchange + RK4
-// Field of node i: gradient (Eq. 14d) and exchange (Eq. 8) over adjacency row i, plus the
+// Field of node i: gradient (Eq. 14d) and exchange (Eq. 8) over adjacency row i (vector
+// width 4, as in charges_row), plus the
 // applied field; then either the output (MODE 0, written to H[3 * uo] in the caller's
 // order) or the RK4 stage update of the LLG equation (Eq. 2; MODE 1 an intermediate stage,
 // MODE 2 the final combination with the renormalisation of Eq. 6 in FP64).
@@ -272,41 +285,62 @@ __device__ __forceinline__ void field_row(int64_t i, int64_t c0, int32_t nc, con
                                           int use_ex, T hx, T hy, T hz, V4<T>* __restrict__ m0,
                                           V4<T>* __restrict__ mnext, V4<T>* __restrict__ accb, T cdt, T bw,
                                           int acc_init, T dt6, T gam, T alpha, int* flag) {
-  const int n = len[i];
+  const int ng = (len[i] + 3) >> 2;
   const int32_t b = base[i];
-  int64_t o = off[i >> 5] + (i & 31);
+  int64_t o = off[i >> 5] + 4 * (i & 31);
   const V4<T> mn = m[i];
   const T un = use_ms ? u[i] : T(0);
   const T* uc = u + c0;
   const V4<T>* mc = m + c0;
   T ax = 0, ay = 0, az = 0;
   if (use_ms && use_ex) {
-#pragma unroll 4
-    for (int j = 0; j < n; ++j, o += 32) {
-      const int32_t k = col_of(b, __ldcs(dcol + o), nc);
-      const T du = __ldg(uc + k) - un;
-      const V4<T> mk = mc[k];
-      const T c = ldv<T>(kp + o);
-      ax += ldv<T>(gx + o) * du + c * (mk.x - mn.x);
-      ay += ldv<T>(gy + o) * du + c * (mk.y - mn.y);
-      az += ldv<T>(gz + o) * du + c * (mk.z - mn.z);
+    for (int g = 0; g < ng; ++g, o += 128) {
+      int32_t c[4];
+      T g0[4], g1[4], g2[4], kk[4];
+      ldc4(dcol + o, c);
+      ldv4(gx + o, g0);
+      ldv4(gy + o, g1);
+      ldv4(gz + o, g2);
+      ldv4(kp + o, kk);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const int32_t col = col_of(b, c[k], nc);
+        const T du = __ldg(uc + col) - un;
+        const V4<T> mk = mc[col];
+        ax += g0[k] * du + kk[k] * (mk.x - mn.x);
+        ay += g1[k] * du + kk[k] * (mk.y - mn.y);
+        az += g2[k] * du + kk[k] * (mk.z - mn.z);
+      }
     }
   } else if (use_ms) {
-#pragma unroll 4
-    for (int j = 0; j < n; ++j, o += 32) {
-      const T du = __ldg(uc + col_of(b, __ldcs(dcol + o), nc)) - un;
-      ax += ldv<T>(gx + o) * du;
-      ay += ldv<T>(gy + o) * du;
-      az += ldv<T>(gz + o) * du;
+    for (int g = 0; g < ng; ++g, o += 128) {
+      int32_t c[4];
+      T g0[4], g1[4], g2[4];
+      ldc4(dcol + o, c);
+      ldv4(gx + o, g0);
+      ldv4(gy + o, g1);
+      ldv4(gz + o, g2);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const T du = __ldg(uc + col_of(b, c[k], nc)) - un;
+        ax += g0[k] * du;
+        ay += g1[k] * du;
+        az += g2[k] * du;
+      }
     }
   } else if (use_ex) {
-#pragma unroll 4
-    for (int j = 0; j < n; ++j, o += 32) {
-      const V4<T> mk = mc[col_of(b, __ldcs(dcol + o), nc)];
-      const T c = ldv<T>(kp + o);
-      ax += c * (mk.x - mn.x);
-      ay += c * (mk.y - mn.y);
-      az += c * (mk.z - mn.z);
+    for (int g = 0; g < ng; ++g, o += 128) {
+      int32_t c[4];
+      T kk[4];
+      ldc4(dcol + o, c);
+      ldv4(kp + o, kk);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const V4<T> mk = mc[col_of(b, c[k], nc)];
+        ax += kk[k] * (mk.x - mn.x);
+        ay += kk[k] * (mk.y - mn.y);
+        az += kk[k] * (mk.z - mn.z);
+      }
     }
   }
   const T Hx = ax + hx, Hy = ay + hy, Hz = az + hz;
