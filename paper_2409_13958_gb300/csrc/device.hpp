@@ -16,6 +16,12 @@ struct bf16_t {
   uint16_t bits;
 };
 
+// Vector width of the precorrection's and the projection's SELL layout (values per lane and
+// step); the layout builder and the kernels read the same setting.
+#ifndef PMFEM_COR_VW
+#define PMFEM_COR_VW 8
+#endif
+
 // internal magnetisation / state vectors: (x, y, z, pad), one aligned load per gather
 template <typename T>
 struct alignas(4 * sizeof(T)) V4 {

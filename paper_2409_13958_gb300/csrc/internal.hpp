@@ -124,6 +124,9 @@ struct Layout {
     return ((((int64_t)tz * (N[1] / TY) + ty) * TZ + zi) * TY + yi) * N[0] + x;
   }
 };
+#ifndef PMFEM_COR_VW
+#define PMFEM_COR_VW 8   // vector width of the precorrection's SELL layout (also read by the kernels)
+#endif
 int build_layout(const Setup& s, Layout& L, Error& err);
 // Centre of a row's columns and the columns' deltas to it, both modulo n (|delta| <= n/2);
 // returns the largest |delta|.

@@ -48,8 +48,14 @@ __global__ void __launch_bounds__(kBlock) k_perm_out(int64_t Np, const int32_t* 
 }
 
 // ---------------------------------------------------------------- charges
+// the charges kernel asks for 4 resident blocks per SM (64 registers; measured 82 -> 77 us
+// on the 1M-node wire against the compiler's own 66 registers and 3 blocks)
+#ifndef PMFEM_CHARGES_MINB
+#define PMFEM_CHARGES_MINB 4
+#endif
+#define PMFEM_CHARGES_LB __launch_bounds__(kBlock, PMFEM_CHARGES_MINB)
 template <typename T, typename CT, typename VT>
-__global__ void __launch_bounds__(kBlock) k_charges(int64_t Np, const int32_t* __restrict__ len,
+__global__ void PMFEM_CHARGES_LB k_charges(int64_t Np, const int32_t* __restrict__ len,
                                                    const int32_t* __restrict__ base,
                                                    const int64_t* __restrict__ off, const CT* __restrict__ dcol,
                                                    const VT* __restrict__ wx, const VT* __restrict__ wy,

@@ -312,7 +312,7 @@ int build_layout(const Setup& s, Layout& L, Error& err) {
              });
   // rows sorted by length in windows of 1024 (about a dozen box rows): a warp's rows stay
   // near one another (shared gathers) and have similar lengths (little idle lanes)
-  build_sell(L.cor, Np, 1, s.sort_window > 0 ? s.sort_window : 1024, s.col_bits, Np, 4,
+  build_sell(L.cor, Np, 1, s.sort_window > 0 ? s.sort_window : 1024, s.col_bits, Np, PMFEM_COR_VW,
                [&](int64_t i) { return L.cptr[i + 1] - L.cptr[i]; }, [&](int64_t i) { return (int32_t)i; },
                [&](int64_t i, const std::function<void(int32_t, const double*)>& put) {
                  for (int64_t o = L.cptr[i]; o < L.cptr[i + 1]; ++o) put(L.ccol[o], &L.cval[o]);
@@ -358,7 +358,7 @@ int build_layout(const Setup& s, Layout& L, Error& err) {
     gc[2] = (int)(g / ((int64_t)N[0] * N[1]));
   };
   const int64_t G = (int64_t)N[0] * N[1] * N[2];
-  build_sell(L.pro, G, 1, s.sort_window > 0 ? s.sort_window : 1024, s.col_bits, Np, 4,
+  build_sell(L.pro, G, 1, s.sort_window > 0 ? s.sort_window : 1024, s.col_bits, Np, PMFEM_COR_VW,
              [&](int64_t g) {
                int gc[3];
                gcoord(g, gc);

@@ -14,6 +14,11 @@ namespace {
 
 constexpr int kBlock = 256;
 
+// values of a precorrection row each lane keeps in flight: 4 x PMFEM_COR_G
+#ifndef PMFEM_COR_G
+#define PMFEM_COR_G 4
+#endif
+
 template <typename T>
 __device__ __forceinline__ T warp_sum(T v) {
 #pragma unroll
@@ -122,6 +127,68 @@ __device__ __forceinline__ void ldc4(const int32_t* p, int32_t (&c)[4]) {
   c[0] = a.x, c[1] = a.y, c[2] = a.z, c[3] = a.w;
 }
 
+__device__ __forceinline__ void ldv8(const float* p, float (&v)[8]) {
+  const float4 a = __ldcs(reinterpret_cast<const float4*>(p));
+  const float4 b = __ldcs(reinterpret_cast<const float4*>(p + 4));
+  v[0] = a.x, v[1] = a.y, v[2] = a.z, v[3] = a.w, v[4] = b.x, v[5] = b.y, v[6] = b.z, v[7] = b.w;
+}
+__device__ __forceinline__ void ldv8(const double* p, double (&v)[8]) {
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const double2 a = __ldcs(reinterpret_cast<const double2*>(p + 2 * k));
+    v[2 * k] = a.x, v[2 * k + 1] = a.y;
+  }
+}
+__device__ __forceinline__ void ldv8(const bf16_t* p, float (&v)[8]) {
+  const uint4 a = __ldcs(reinterpret_cast<const uint4*>(p));
+  const uint32_t w[4] = {a.x, a.y, a.z, a.w};
+#pragma unroll
+  for (int k = 0; k < 4; ++k) v[2 * k] = __uint_as_float(w[k] << 16), v[2 * k + 1] = __uint_as_float(w[k] & 0xffff0000u);
+}
+__device__ __forceinline__ void ldc8(const int16_t* p, int32_t (&c)[8]) {
+  const int4 a = __ldcs(reinterpret_cast<const int4*>(p));
+  const uint32_t w[4] = {(uint32_t)a.x, (uint32_t)a.y, (uint32_t)a.z, (uint32_t)a.w};
+#pragma unroll
+  for (int k = 0; k < 4; ++k) c[2 * k] = (int32_t)(int16_t)(w[k] & 0xffffu), c[2 * k + 1] = (int32_t)(int16_t)(w[k] >> 16);
+}
+__device__ __forceinline__ void ldc8(const int32_t* p, int32_t (&c)[8]) {
+  const int4 a = __ldcs(reinterpret_cast<const int4*>(p));
+  const int4 b = __ldcs(reinterpret_cast<const int4*>(p + 4));
+  c[0] = a.x, c[1] = a.y, c[2] = a.z, c[3] = a.w, c[4] = b.x, c[5] = b.y, c[6] = b.z, c[7] = b.w;
+}
+
+// sell_dot for a SELL-32 operator stored eight values per lane and step (vector width 8):
+// group g of the lane at o0 + 256 g with o0 = off[c] + 8 lane; rows padded as for width 4.
+template <int G, typename T, typename CT, typename VT>
+__device__ __forceinline__ T sell_dot8(const VT* __restrict__ val, const CT* __restrict__ dcol,
+                                       const T* __restrict__ x, int32_t b, int64_t o0, int n, int32_t ncol) {
+  T acc = 0;
+  const int ng = (n + 7) >> 3;
+  int g = 0;
+  for (; g + G <= ng; g += G, o0 += 256 * G) {
+    T v[G][8];
+    int32_t c[G][8];
+#pragma unroll
+    for (int k = 0; k < G; ++k) {
+      ldv8(val + o0 + 256 * k, v[k]);
+      ldc8(dcol + o0 + 256 * k, c[k]);
+    }
+#pragma unroll
+    for (int k = 0; k < G; ++k)
+#pragma unroll
+      for (int e = 0; e < 8; ++e) acc += v[k][e] * __ldg(x + col_of(b, c[k][e], ncol));
+  }
+  for (; g < ng; ++g, o0 += 256) {
+    T v[8];
+    int32_t c[8];
+    ldv8(val + o0, v);
+    ldc8(dcol + o0, c);
+#pragma unroll
+    for (int e = 0; e < 8; ++e) acc += v[e] * __ldg(x + col_of(b, c[e], ncol));
+  }
+  return acc;
+}
+
 // sell_dot for a SELL-32 operator stored four values per lane and step (vector width 4):
 // the lane's group g of elements 4g .. 4g+3 sits at o0 + 128 g, where o0 = off[c] + 4 lane.
 // Rows are padded to whole groups with value 0 and delta 0 (a valid column), so every group
@@ -204,7 +271,12 @@ __device__ __forceinline__ void project_row(int64_t t, int64_t g, int64_t c0, in
                                             T* __restrict__ grid) {
   const int n = len[t];
   T acc = 0;
-  if (n > 0) acc = sell_dot4<2>(pw, dcol, q + c0, base[t], off[t >> 5] + 4 * (t & 31), n, nc);
+  if (n > 0) {
+    if constexpr (PMFEM_COR_VW == 8)
+      acc = sell_dot8<1>(pw, dcol, q + c0, base[t], off[t >> 5] + 8 * (t & 31), n, nc);
+    else
+      acc = sell_dot4<2>(pw, dcol, q + c0, base[t], off[t >> 5] + 4 * (t & 31), n, nc);
+  }
   grid[g] = acc;
 }
 
@@ -261,7 +333,10 @@ __device__ __forceinline__ void interp_row(
     const T* __restrict__ valX, const T* __restrict__ q, const T* __restrict__ e, const V4<T>* __restrict__ m,
     T* __restrict__ u) {
   T acc = stencil_row<T, P>(i, base, frac, U, N0, N1, N2, p0, p1, p2);
-  acc += sell_dot4<2>(cval, dcol, q + c0, cbase[t], coff[t >> 5] + 4 * (t & 31), clen[t], nc);
+  if constexpr (PMFEM_COR_VW == 8)
+    acc += sell_dot8<(PMFEM_COR_G + 1) / 2>(cval, dcol, q + c0, cbase[t], coff[t >> 5] + 8 * (t & 31), clen[t], nc);
+  else
+    acc += sell_dot4<PMFEM_COR_G>(cval, dcol, q + c0, cbase[t], coff[t >> 5] + 4 * (t & 31), clen[t], nc);
   acc += extras_row<T>(i, rowptrX, colX, valX, m);
   u[i] = acc + e[i];
 }
