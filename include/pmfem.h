@@ -190,7 +190,9 @@ int pmfem_get_m(pmfem_t h, void* m, void* stream);
 /*
  * nsteps classical RK4 steps of size dt [s] of Eq. 2 on the internal state, each with
  * four field evaluations and m <- m/|m| at the end of the step (norm taken in FP64).
- * dt <= 0 or nsteps < 0 -> EINVAL.
+ * The first call for a dt captures one step as a CUDA graph (on a private stream, after
+ * synchronising stream) and every step replays it; per-launch timing (pmfem_profile) and
+ * the surrogate run the launches directly.  dt <= 0 or nsteps < 0 -> EINVAL.
  */
 int pmfem_llg_step(pmfem_t h, double dt, int nsteps, void* stream);
 

@@ -58,6 +58,8 @@ void apply_prof(pmfem_t h) {
 }
 
 void free_device(pmfem_t h) {
+  if (h->graph) cudaGraphExecDestroy(h->graph);
+  h->graph = nullptr;
   for (void* p : h->allocs) cudaFree(p);
   h->allocs.clear();
   h->d64 = DevOps<double>();
@@ -482,6 +484,8 @@ int pmfem_set_applied_field(pmfem_t h, double Hx, double Hy, double Hz) {
   h->hap[0] = Hx;
   h->hap[1] = Hy;
   h->hap[2] = Hz;
+  if (h->graph) cudaGraphExecDestroy(h->graph);   // the captured step holds the old field
+  h->graph = nullptr;
   return OK;
 }
 
@@ -558,9 +562,38 @@ int pmfem_llg_step(pmfem_t h, double dt, int nsteps, void* stream) {
   int rc = ensure_device(h);
   if (rc) return rc;
   cudaStream_t st = stream ? (cudaStream_t)stream : h->stream;
-  if (h->dev_prec == PMFEM_FP64) return run_llg(h, h->d64, dt, nsteps, st);
-  if (h->net && h->sur_every > 0) return run_llg_sur(h, h->d32, dt, nsteps, st);
-  return run_llg(h, h->d32, dt, nsteps, st);
+  if (h->net && h->sur_every > 0 && h->dev_prec != PMFEM_FP64) return run_llg_sur(h, h->d32, dt, nsteps, st);
+  if (h->prof_on || nsteps == 0)   // per-launch timing needs the launches themselves
+    return h->dev_prec == PMFEM_FP64 ? run_llg(h, h->d64, dt, nsteps, st) : run_llg(h, h->d32, dt, nsteps, st);
+  if (!h->graph || h->graph_dt != dt) {
+    // capture one step on a private stream, after the caller's work (the capture reads the
+    // state buffers by address only); the FFT kernels opt into large shared memory first
+    if (h->graph) cudaGraphExecDestroy(h->graph);
+    h->graph = nullptr;
+    PMFEM_CK(h, cudaStreamSynchronize(st));
+    if (h->dev_prec == PMFEM_FP64) launch_fft_conv(h->d64, h->stream);
+    else launch_fft_conv(h->d32, h->stream);
+    PMFEM_CK(h, cudaStreamSynchronize(h->stream));
+    cudaStream_t cs;
+    PMFEM_CK(h, cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      if (h->dev_prec == PMFEM_FP64) run_llg(h, h->d64, dt, 1, cs);
+      else run_llg(h, h->d32, dt, 1, cs);
+      e = cudaStreamEndCapture(cs, &g);
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&h->graph, g, 0);
+    if (g) cudaGraphDestroy(g);
+    cudaStreamDestroy(cs);
+    if (e != cudaSuccess) {
+      h->graph = nullptr;
+      return fail(h, ECUDA_, std::string("RK4 step capture failed: ") + cudaGetErrorString(e));
+    }
+    h->graph_dt = dt;
+  }
+  for (int k = 0; k < nsteps; ++k) PMFEM_CK(h, cudaGraphLaunch(h->graph, st));
+  return OK;
 }
 
 int pmfem_sync(pmfem_t h) {

@@ -46,6 +46,9 @@ struct pmfem_state {
   int64_t prof_count[pmfem::KID_COUNT] = {};
   double prof_ms[pmfem::KID_COUNT] = {};
   int64_t dev_info[12] = {};   // layout facts of the current device upload
+  // one RK4 step captured as a CUDA graph (pmfem_llg_step without timing or surrogate)
+  cudaGraphExec_t graph = nullptr;
+  double graph_dt = 0.0;
   // learned surrogate of the FFT convolution (pmfem_surrogate_*)
   pmfem::SurrogateNet* net = nullptr;
   int sur_every = 0;            // 0: off; k: full P-AIM (judged) on every k-th RK step

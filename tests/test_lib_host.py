@@ -47,6 +47,10 @@ def _mk(mesh, periods=None, grid=(0, 0, 0), p=3, nb=3, f=0.0, Ms=8e5, A=1.3e-11)
 
 def test_error_conventions():
     m = meshgen.film_cell(4, 4, 2)
+    for xyz, tets in ((np.zeros((0, 3)), np.zeros((0, 4), np.int32)), (m.xyz, np.zeros((0, 4), np.int32))):
+        with pytest.raises(B.PmfemError) as e:      # empty mesh or no tetrahedra
+            B.Pmfem.create_mesh(xyz, tets, 8e5, 1e-11, 0.02)
+        assert e.value.code == -1
     bad = m.tets.copy()
     bad[0, 0] = m.n_nodes + 5
     with pytest.raises(B.PmfemError) as e:
