@@ -567,12 +567,18 @@ int pmfem_llg_step(pmfem_t h, double dt, int nsteps, void* stream) {
     return h->dev_prec == PMFEM_FP64 ? run_llg(h, h->d64, dt, nsteps, st) : run_llg(h, h->d32, dt, nsteps, st);
   if (!h->graph || h->graph_dt != dt) {
     // capture one step on a private stream, after the caller's work (the capture reads the
-    // state buffers by address only); the FFT kernels opt into large shared memory first
+    // state buffers by address only); the FFT and interpolation kernels opt into large shared
+    // memory first (their scratch outputs are rewritten by the step itself)
     if (h->graph) cudaGraphExecDestroy(h->graph);
     h->graph = nullptr;
     PMFEM_CK(h, cudaStreamSynchronize(st));
-    if (h->dev_prec == PMFEM_FP64) launch_fft_conv(h->d64, h->stream);
-    else launch_fft_conv(h->d32, h->stream);
+    if (h->dev_prec == PMFEM_FP64) {
+      launch_fft_conv(h->d64, h->stream);
+      launch_interp(h->d64, (const V4<double>*)h->m, h->stream);
+    } else {
+      launch_fft_conv(h->d32, h->stream);
+      launch_interp(h->d32, (const V4<float>*)h->m, h->stream);
+    }
     PMFEM_CK(h, cudaStreamSynchronize(h->stream));
     cudaStream_t cs;
     PMFEM_CK(h, cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));

@@ -2,9 +2,29 @@
 #pragma once
 
 #include <cuda_runtime.h>
+
 #include <cstdint>
+#include <mutex>
+#include <set>
+#include <utility>
 
 namespace pmfem {
+
+// Opt a kernel into more than 48 KB of dynamic shared memory, once per (kernel, device):
+// the call is not a stream operation, so it is made before any graph capture replays it.
+template <typename K>
+inline void set_smem(K kernel, size_t bytes) {
+  if (bytes <= 48 * 1024) return;
+  static std::mutex mu;
+  static std::set<std::pair<const void*, int>> done;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const std::pair<const void*, int> key{(const void*)kernel, dev};
+  std::lock_guard<std::mutex> lk(mu);
+  if (done.count(key)) return;
+  if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) == cudaSuccess)
+    done.insert(key);
+}
 
 template <typename T> struct Vec2;
 template <> struct Vec2<double> { using type = double2; };

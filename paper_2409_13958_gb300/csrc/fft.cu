@@ -358,31 +358,31 @@ __global__ void __launch_bounds__(LB * Fac<F>::R2) k_fft_x_inv(const C2* __restr
   line_inverse<F, LB, false>(S, tw, st, l, j, X);
 }
 
-// Opt a kernel into more than 48 KB of dynamic shared memory, once per (kernel, device):
-// the call is not a stream operation, so it is made before any graph capture replays it.
-template <typename K>
-void set_smem(K kernel, size_t bytes) {
-  if (bytes <= 48 * 1024) return;
-  static std::mutex mu;
-  static std::set<std::pair<const void*, int>> done;
-  int dev = 0;
-  cudaGetDevice(&dev);
-  const std::pair<const void*, int> key{(const void*)kernel, dev};
-  std::lock_guard<std::mutex> lk(mu);
-  if (done.count(key)) return;
-  if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) == cudaSuccess)
-    done.insert(key);
-}
-
-// line counts per block: strided passes want 128-byte rows of adjacent lines
-template <typename T> struct Lines { static constexpr int STRIDED = sizeof(T) == 4 ? 16 : 8; };
+// Line counts per block (measured on the 256^3 transform of the 1M-node wire): the y passes
+// read 128-byte rows of 16 adjacent FP32 lines; the z pass, whose block also multiplies by the
+// spectrum and transforms back, runs faster with 8 lines (more blocks in flight); the
+// contiguous x passes take 128 threads per block.  FP64 halves the strided line counts.
+#ifndef PMFEM_FFT_LBS
+#define PMFEM_FFT_LBS 16
+#endif
+#ifndef PMFEM_FFT_LBZ
+#define PMFEM_FFT_LBZ 8
+#endif
+#ifndef PMFEM_FFT_TPB
+#define PMFEM_FFT_TPB 128
+#endif
+template <typename T> struct Lines {
+  static constexpr int STRIDED = sizeof(T) == 4 ? PMFEM_FFT_LBS : PMFEM_FFT_LBS / 2;
+  static constexpr int Z = sizeof(T) == 4 ? PMFEM_FFT_LBZ : (PMFEM_FFT_LBZ / 2 > 0 ? PMFEM_FFT_LBZ / 2 : 1);
+};
 
 template <typename T, int F>
 struct Passes {
   using C2 = typename Vec2<T>::type;
   using FF = Fac<F>;
-  static constexpr int LBX = (256 / FF::R2) > 0 ? (256 / FF::R2) : 1;   // contiguous passes
+  static constexpr int LBX = (PMFEM_FFT_TPB / FF::R2) > 0 ? (PMFEM_FFT_TPB / FF::R2) : 1;   // contiguous passes
   static constexpr int LBS = Lines<T>::STRIDED;
+  static constexpr int LBZ = Lines<T>::Z;
   static size_t smem(int lb) { return (size_t)lb * FF::LS * sizeof(C2); }
 
   static void x_fwd(const FftArgs<T>& d, cudaStream_t st) {
@@ -415,10 +415,10 @@ struct Passes {
   }
   static void z(const FftArgs<T>& d, cudaStream_t st) {
     const int Hx = d.fft[0] / 2 + 1;
-    const unsigned nb = strided_blocks<true>(Hx, LBS, d.fft[1]);
-    const size_t sm = smem(LBS);
-    set_smem(k_fft_z_conv<T, C2, F, LBS>, sm);
-    k_fft_z_conv<T, C2, F, LBS><<<dim3(nb, d.count), LBS * FF::R2, sm, st>>>(d.cbuf, Hx, d.fft[1], d.dims[2],
+    const unsigned nb = strided_blocks<true>(Hx, LBZ, d.fft[1]);
+    const size_t sm = smem(LBZ);
+    set_smem(k_fft_z_conv<T, C2, F, LBZ>, sm);
+    k_fft_z_conv<T, C2, F, LBZ><<<dim3(nb, d.count), LBZ * FF::R2, sm, st>>>(d.cbuf, Hx, d.fft[1], d.dims[2],
                                                                              d.ghat, d.tw[2], d.boff);
   }
 };

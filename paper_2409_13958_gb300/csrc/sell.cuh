@@ -189,6 +189,107 @@ __device__ __forceinline__ T sell_dot8(const VT* __restrict__ val, const CT* __r
   return acc;
 }
 
+// Pipelined form of sell_dot8: each lane streams its own groups into shared memory with
+// 16-byte cp.async copies, S - 1 groups ahead of the one it multiplies, so the DRAM latency
+// of the value and delta streams overlaps the gathers of x instead of holding registers.
+// buf is the warp's buffer of S stages; a stage holds, for each of the 32 lanes, the lane's
+// 8 values and 8 deltas as 16-byte pieces, piece k of lane l at (32 k + l) x 16 bytes (eight
+// consecutive lanes read 128 contiguous bytes: no bank conflicts).  A lane reads only the
+// pieces it copied itself, so no barrier is needed; cp.async.wait_group orders them.
+template <typename VT, typename CT>
+struct PipeStage {
+  static constexpr int PV = 8 * (int)sizeof(VT) / 16;   // 16-byte pieces of values
+  static constexpr int PC = 8 * (int)sizeof(CT) / 16;   // 16-byte pieces of deltas
+  static constexpr int BYTES = 32 * 16 * (PV + PC);      // one stage of one warp
+};
+
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+__device__ __forceinline__ uint4 lds16(uint32_t a) {
+  uint4 v;
+  asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];\n" : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "r"(a));
+  return v;
+}
+__device__ __forceinline__ void unpack8(const uint4 (&w)[2], float (&v)[8]) {
+  const uint32_t a[8] = {w[0].x, w[0].y, w[0].z, w[0].w, w[1].x, w[1].y, w[1].z, w[1].w};
+#pragma unroll
+  for (int k = 0; k < 8; ++k) v[k] = __uint_as_float(a[k]);
+}
+__device__ __forceinline__ void unpack8(const uint4 (&w)[4], double (&v)[8]) {
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    v[2 * k] = __hiloint2double((int)w[k].y, (int)w[k].x);
+    v[2 * k + 1] = __hiloint2double((int)w[k].w, (int)w[k].z);
+  }
+}
+__device__ __forceinline__ void unpack8(const uint4 (&w)[1], float (&v)[8]) {   // bfloat16
+  const uint32_t a[4] = {w[0].x, w[0].y, w[0].z, w[0].w};
+#pragma unroll
+  for (int k = 0; k < 4; ++k) v[2 * k] = __uint_as_float(a[k] << 16), v[2 * k + 1] = __uint_as_float(a[k] & 0xffff0000u);
+}
+__device__ __forceinline__ void unpackc8(const uint4 (&w)[1], int32_t (&c)[8]) {   // int16 deltas
+  const uint32_t a[4] = {w[0].x, w[0].y, w[0].z, w[0].w};
+#pragma unroll
+  for (int k = 0; k < 4; ++k) c[2 * k] = (int32_t)(int16_t)(a[k] & 0xffffu), c[2 * k + 1] = (int32_t)(int16_t)(a[k] >> 16);
+}
+__device__ __forceinline__ void unpackc8(const uint4 (&w)[2], int32_t (&c)[8]) {   // int32 deltas
+  const uint32_t a[8] = {w[0].x, w[0].y, w[0].z, w[0].w, w[1].x, w[1].y, w[1].z, w[1].w};
+#pragma unroll
+  for (int k = 0; k < 8; ++k) c[k] = (int32_t)a[k];
+}
+
+template <int S, typename T, typename CT, typename VT>
+__device__ __forceinline__ T sell_dot8_pipe(const VT* __restrict__ val, const CT* __restrict__ dcol,
+                                            const T* __restrict__ x, int32_t b, int64_t o0, int n, int32_t ncol,
+                                            unsigned char* buf) {
+  using PS = PipeStage<VT, CT>;
+  const int lane = threadIdx.x & 31;
+  const uint32_t s0 = (uint32_t)__cvta_generic_to_shared(buf) + 16u * (uint32_t)lane;
+  const int ng = (n + 7) >> 3;
+  auto issue = [&](int g, int slot) {
+    const uint32_t s = s0 + (uint32_t)(slot * PS::BYTES);
+    const char* pv = reinterpret_cast<const char*>(val + o0 + 256 * (int64_t)g);
+    const char* pc = reinterpret_cast<const char*>(dcol + o0 + 256 * (int64_t)g);
+#pragma unroll
+    for (int k = 0; k < PS::PV; ++k) cp_async16(s + 512u * k, pv + 16 * k);
+#pragma unroll
+    for (int k = 0; k < PS::PC; ++k) cp_async16(s + 512u * (PS::PV + k), pc + 16 * k);
+  };
+#pragma unroll
+  for (int g = 0; g < S - 1; ++g) {
+    if (g < ng) issue(g, g);
+    cp_async_commit();
+  }
+  T acc = 0;
+  int slot = 0;                       // slot of group g; group g + S - 1 goes to the slot of g - 1
+  for (int g = 0; g < ng; ++g) {
+    const int fill = slot == 0 ? S - 1 : slot - 1;
+    if (g + S - 1 < ng) issue(g + S - 1, fill);
+    cp_async_commit();
+    cp_async_wait<S - 1>();
+    const uint32_t s = s0 + (uint32_t)(slot * PS::BYTES);
+    uint4 wv[PS::PV], wc[PS::PC];
+#pragma unroll
+    for (int k = 0; k < PS::PV; ++k) wv[k] = lds16(s + 512u * k);
+#pragma unroll
+    for (int k = 0; k < PS::PC; ++k) wc[k] = lds16(s + 512u * (PS::PV + k));
+    T v[8];
+    int32_t c[8];
+    unpack8(wv, v);
+    unpackc8(wc, c);
+#pragma unroll
+    for (int e = 0; e < 8; ++e) acc += v[e] * __ldg(x + col_of(b, c[e], ncol));
+    slot = slot == S - 1 ? 0 : slot + 1;
+  }
+  return acc;
+}
+
 // sell_dot for a SELL-32 operator stored four values per lane and step (vector width 4):
 // the lane's group g of elements 4g .. 4g+3 sits at o0 + 128 g, where o0 = off[c] + 4 lane.
 // Rows are padded to whole groups with value 0 and delta 0 (a valid column), so every group
@@ -324,16 +425,20 @@ __device__ __forceinline__ T extras_row(int64_t i, const int32_t* __restrict__ r
 // Potential of node i (SELL row t of the precorrection, stored with vector width 4): the
 // stencil (step 3), the point precorrection row (step 4), the near-element entries beyond the
 // adjacency pattern and the touching-element part e.
-template <typename T, int P, typename CT, typename VT>
+// PIPE > 0 streams the precorrection row through the warp's PIPE-stage shared-memory buffer
+// buf (sell_dot8_pipe; vector width 8 only); PIPE = 0 loads it into registers.
+template <typename T, int P, typename CT, typename VT, int PIPE = 0>
 __device__ __forceinline__ void interp_row(
     int64_t t, int64_t i, int64_t c0, int32_t nc, const int32_t* __restrict__ base, const T* __restrict__ frac,
     const T* __restrict__ U, int N0, int N1, int N2, bool p0, bool p1, bool p2, const int32_t* __restrict__ clen,
     const int32_t* __restrict__ cbase, const int64_t* __restrict__ coff, const CT* __restrict__ dcol,
     const VT* __restrict__ cval, const int32_t* __restrict__ rowptrX, const int32_t* __restrict__ colX,
     const T* __restrict__ valX, const T* __restrict__ q, const T* __restrict__ e, const V4<T>* __restrict__ m,
-    T* __restrict__ u) {
+    T* __restrict__ u, unsigned char* buf = nullptr) {
   T acc = stencil_row<T, P>(i, base, frac, U, N0, N1, N2, p0, p1, p2);
-  if constexpr (PMFEM_COR_VW == 8)
+  if constexpr (PMFEM_COR_VW == 8 && PIPE > 0)
+    acc += sell_dot8_pipe<PIPE>(cval, dcol, q + c0, cbase[t], coff[t >> 5] + 8 * (t & 31), clen[t], nc, buf);
+  else if constexpr (PMFEM_COR_VW == 8)
     acc += sell_dot8<(PMFEM_COR_G + 1) / 2>(cval, dcol, q + c0, cbase[t], coff[t >> 5] + 8 * (t & 31), clen[t], nc);
   else
     acc += sell_dot4<PMFEM_COR_G>(cval, dcol, q + c0, cbase[t], coff[t >> 5] + 4 * (t & 31), clen[t], nc);
