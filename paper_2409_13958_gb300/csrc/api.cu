@@ -136,6 +136,9 @@ int upload_sell(pmfem_t h, const SellMatrix& M, DevSell<T>& D, unsigned bf_comps
   if (!identity && (rc = upload(h, M.map.data(), M.map.size(), &D.map))) return rc;
   if ((rc = upload(h, M.len.data(), M.len.size(), &D.len))) return rc;
   if ((rc = upload(h, M.base.data(), M.base.size(), &D.base))) return rc;
+  // vector loads of a lane's step (up to 32 bytes) need chunk offsets in whole steps
+  for (int64_t o : M.off)
+    if (o % M.vw) return fail(h, ESTATE_, "internal: SELL chunk offset not a multiple of the vector width");
   if ((rc = upload(h, M.off.data(), M.off.size(), &D.off))) return rc;
   if (M.col16) {
     const int16_t* p16;

@@ -62,12 +62,13 @@ struct HostSell {
   std::vector<std::vector<float>> val;
   bool col16 = true;
   int64_t rows = 0;
+  int vw = 1;   // vector width of the cells' layout (the same for every cell)
 };
 
 // Append the rows of one cell's operator, starting at row row0 (a multiple of 32, after
 // the rows already present); map entries are shifted by map0.
 void append_sell(HostSell& G, const SellMatrix& M, int64_t row0, int64_t map0) {
-  if (G.val.empty()) G.val.resize(M.comps), G.comps = M.comps;
+  if (G.val.empty()) G.val.resize(M.comps), G.comps = M.comps, G.vw = M.vw;
   const int64_t pad_rows = row0 - G.rows;   // empty rows padding the previous cell
   for (int64_t r = 0; r < pad_rows; ++r) {
     G.map.push_back(-1);
@@ -340,6 +341,8 @@ int upload_hsell(pmfem_batch_t b, HostSell& H, DevSell<float>& D) {
   if ((rc = bupload(b, H.map.data(), H.map.size(), &D.map))) return rc;
   if ((rc = bupload(b, H.len.data(), H.len.size(), &D.len))) return rc;
   if ((rc = bupload(b, H.base.data(), H.base.size(), &D.base))) return rc;
+  for (int64_t o : H.off)
+    if (o % H.vw) return bfail(b, ESTATE_, "internal: SELL chunk offset not a multiple of the vector width");
   if ((rc = bupload(b, H.off.data(), H.off.size(), &D.off))) return rc;
   if (H.col16) {
     std::vector<int16_t> d16(H.delta.begin(), H.delta.end());
