@@ -29,14 +29,14 @@ constexpr int HVOX = HX * HY * HZ;                   // 540 voxels
 constexpr int WELEMS = 27 * 4 * 32 * 8;              // packed weights, bf16 elements
 constexpr int SMEM_W = WELEMS * 2;                   // 55296 B
 constexpr int SMEM_X = 4 * HVOX * 16;                // 34560 B
-// + mbarrier and TMEM address; the allocation is padded so that every descriptor this kernel
-// forms, read with its two byte offsets exchanged, would still stay inside the block's
-// shared memory (an A operand read that way reaches about 153 KB past s_x)
-constexpr int SMEM_TOTAL = 208 * 1024;
-// largest tap offset ((2 HY + 2) HX + 2) x 16 B, the half-K offset 2 x 540 x 16 B, then one K
-// step of 160 B and 15 row groups of 8640 B (the exchanged reading), plus one core matrix
-static_assert(SMEM_W + ((2 * HY + 2) * HX + 2) * 16 + 2 * HVOX * 16 + HX * 16 + 15 * HVOX * 16 + 128 <= SMEM_TOTAL,
-              "padding too small");
+// + mbarrier and TMEM address.  Every descriptor this kernel forms stays inside s_w and s_x:
+// the largest A read is the tap offset ((2 HY + 2) HX + 2) x 16 B, plus the half-K offset
+// 2 x 540 x 16 B, one more K core matrix (540 x 16 B), 15 row groups of 160 B and one core
+// matrix of 128 B, which is exactly SMEM_X; the largest B read ends exactly at SMEM_W.  At
+// about 88 KB two blocks share an SM, so one block's staging overlaps the other's MMAs.
+constexpr int SMEM_TOTAL = SMEM_W + SMEM_X + 128;
+static_assert(((2 * HY + 2) * HX + 2) * 16 + 2 * HVOX * 16 + HVOX * 16 + 15 * HX * 16 + 128 == SMEM_X, "A extent");
+static_assert(((26 * 4 + 2) * 32 + 32 + 3 * 8) * 16 + 128 == SMEM_W, "B extent");
 constexpr int kWaitIters = 1 << 20;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -71,6 +71,11 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
   return false;
 }
 
+// 16-byte global -> shared copy; the bytes past src_bytes (all 16 when it is 0) are zeros
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, uint32_t src_bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(dst), "l"(src), "r"(src_bytes) : "memory");
+}
+
 __device__ __forceinline__ int wrap_in(int i, int n, bool per, bool& inside) {
   inside = true;
   if (i < 0) {
@@ -91,7 +96,7 @@ __global__ void k_pack_w32(const float* __restrict__ W, __nv_bfloat16* __restric
   Wp[((tap * 4 + (ci >> 3)) * 32 + co) * 8 + (ci & 7)] = __float2bfloat16_rn(W[k]);
 }
 
-__global__ void __launch_bounds__(128, 1) k_conv32_tc(const __nv_bfloat16* __restrict__ in,
+__global__ void __launch_bounds__(128, 2) k_conv32_tc(const __nv_bfloat16* __restrict__ in,
                                                      const __nv_bfloat16* __restrict__ Wp,
                                                      const float* __restrict__ bias, __nv_bfloat16* __restrict__ out,
                                                      int X, int Y, int Z, bool px, bool py, bool pz, int act,
@@ -114,18 +119,23 @@ __global__ void __launch_bounds__(128, 1) k_conv32_tc(const __nv_bfloat16* __res
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)));
     asm volatile("fence.mbarrier_init.release.cluster;");
   }
+  // staging: every 16-byte piece is one cp.async, all in flight at once (a piece outside a
+  // non-periodic boundary is a zero fill: source size 0, nothing read)
   const uint4* wg = reinterpret_cast<const uint4*>(Wp);
-  for (int k = tid; k < SMEM_W / 16; k += blockDim.x) s_w[k] = wg[k];
+  for (int k = tid; k < SMEM_W / 16; k += blockDim.x) cp_async16(smem_u32(s_w + k), wg + k, 16);
   for (int k = tid; k < 4 * HVOX; k += blockDim.x) {
     const int h = k >> 2, cg = k & 3;
     const int hz = h / (HX * HY), hy = (h / HX) % HY, hx = h % HX;
     bool ix, iy, iz;
     const int gx = wrap_in(x0 + hx - 1, X, px, ix), gy = wrap_in(y0 + hy - 1, Y, py, iy);
     const int gz = wrap_in(z0 + hz - 1, Z, pz, iz);
-    uint4 v = make_uint4(0u, 0u, 0u, 0u);
-    if (ix && iy && iz) v = reinterpret_cast<const uint4*>(in + 32 * (gx + (int64_t)X * (gy + (int64_t)Y * gz)))[cg];
-    s_x[cg * HVOX + h] = v;
+    const bool inside = ix && iy && iz;
+    const uint4* src = reinterpret_cast<const uint4*>(in) +
+                       (inside ? 4 * (gx + (int64_t)X * (gy + (int64_t)Y * gz)) + cg : 0);
+    cp_async16(smem_u32(s_x + cg * HVOX + h), src, inside ? 16 : 0);
   }
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();

@@ -74,7 +74,7 @@ __global__ void __launch_bounds__(TILE) k_conv_fwd(const AIN* __restrict__ in, i
                                                    const float* __restrict__ b, AOUT* __restrict__ out, int X, int Y,
                                                    int Z, bool px, bool py, bool pz, float in_scale, float out_scale) {
   __shared__ float s_in[CK * HALO];
-  __shared__ float s_w[27 * CK * COUT];
+  __shared__ __align__(16) float s_w[27 * CK * COUT];
   const int ntx = X / TX, nty = Y / TY;
   const int tile = blockIdx.x;
   const int x0 = (tile % ntx) * TX, y0 = ((tile / ntx) % nty) * TY, z0 = (tile / (ntx * nty)) * TZ;
@@ -98,19 +98,87 @@ __global__ void __launch_bounds__(TILE) k_conv_fwd(const AIN* __restrict__ in, i
       for (int ci = 0; ci < CK; ++ci) {
         const float v = s_in[ci * HALO + h];
         const float* w = s_w + (tap * CK + ci) * COUT;
+        if constexpr (COUT % 4 == 0) {   // one 16-byte (broadcast) weight load per 4 FMAs
 #pragma unroll
-        for (int o = 0; o < COUT; ++o) acc[o] += v * w[o];
+          for (int o = 0; o < COUT; o += 4) {
+            const float4 w4 = *reinterpret_cast<const float4*>(w + o);
+            acc[o] += v * w4.x, acc[o + 1] += v * w4.y, acc[o + 2] += v * w4.z, acc[o + 3] += v * w4.w;
+          }
+        } else {
+#pragma unroll
+          for (int o = 0; o < COUT; ++o) acc[o] += v * w[o];
+        }
       }
     }
   }
   const int64_t plane = (int64_t)X * Y * Z;
   const int64_t vox = (x0 + lx) + (int64_t)X * ((y0 + ly) + (int64_t)Y * (z0 + lz));
+  if constexpr (CL_OUT && sizeof(AOUT) == 2 && COUT % 8 == 0) {   // channels-last bfloat16: 16-byte stores
 #pragma unroll
-  for (int o = 0; o < COUT; ++o) {
-    float z = acc[o];
-    if (ACT) z = z > 0.f ? z : kSlope * z;
-    st_act(out + (CL_OUT ? vox * COUT + o : (int64_t)o * plane + vox), z * out_scale);
+    for (int o = 0; o < COUT; o += 8) {
+      uint32_t w[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        float a = acc[o + 2 * j], c = acc[o + 2 * j + 1];
+        if (ACT) a = a > 0.f ? a : kSlope * a, c = c > 0.f ? c : kSlope * c;
+        const __nv_bfloat162 p2 = __floats2bfloat162_rn(a * out_scale, c * out_scale);
+        w[j] = *reinterpret_cast<const uint32_t*>(&p2);
+      }
+      *reinterpret_cast<uint4*>(out + vox * COUT + o) = make_uint4(w[0], w[1], w[2], w[3]);
+    }
+  } else {
+#pragma unroll
+    for (int o = 0; o < COUT; ++o) {
+      float z = acc[o];
+      if (ACT) z = z > 0.f ? z : kSlope * z;
+      st_act(out + (CL_OUT ? vox * COUT + o : (int64_t)o * plane + vox), z * out_scale);
+    }
   }
+}
+
+// Output layer (32 -> 1, no activation) on channels-last bfloat16 activations: the block's
+// halo with all 32 channels (600 voxels x 64 B) is staged with 16-byte loads, then each
+// thread sums 27 taps x 32 channels for its voxel.  W is [tap][ci] (one output channel).
+// Piece g of halo voxel h sits at 4 h + (g ^ ((h >> 1) & 3)): eight consecutive voxels then
+// fall in eight different 16-byte bank groups (unswizzled, the 64-byte voxel stride makes
+// the eight lanes of a phase collide four ways).
+__global__ void __launch_bounds__(TILE) k_conv_out_cl(const __nv_bfloat16* __restrict__ in, const float* __restrict__ W,
+                                                      const float* __restrict__ b, float* __restrict__ out, int X,
+                                                      int Y, int Z, bool px, bool py, bool pz, float out_scale) {
+  __shared__ uint4 s_in[HALO * 4];
+  __shared__ float4 s_w4[27 * 8];
+  float* s_w = reinterpret_cast<float*>(s_w4);
+  const int ntx = X / TX, nty = Y / TY;
+  const int tile = blockIdx.x;
+  const int x0 = (tile % ntx) * TX, y0 = ((tile / ntx) % nty) * TY, z0 = (tile / (ntx * nty)) * TZ;
+  for (int k = threadIdx.x; k < 27 * 32; k += blockDim.x) s_w[k] = W[k];
+  for (int k = threadIdx.x; k < HALO * 4; k += blockDim.x) {
+    const int h = k >> 2, g = k & 3;
+    const int hz = h / (HX * HY), hy = (h / HX) % HY, hx = h % HX;
+    bool ix, iy, iz;
+    const int gx = wrapc(x0 + hx - 1, X, px, ix), gy = wrapc(y0 + hy - 1, Y, py, iy), gz = wrapc(z0 + hz - 1, Z, pz, iz);
+    uint4 v = make_uint4(0u, 0u, 0u, 0u);
+    if (ix && iy && iz) v = reinterpret_cast<const uint4*>(in + 32 * (gx + (int64_t)X * (gy + (int64_t)Y * gz)))[g];
+    s_in[4 * h + (g ^ ((h >> 1) & 3))] = v;
+  }
+  __syncthreads();
+  const int lx = threadIdx.x % TX, ly = (threadIdx.x / TX) % TY, lz = threadIdx.x / (TX * TY);
+  float acc = b[0];
+#pragma unroll 1
+  for (int tap = 0; tap < 27; ++tap) {
+    const int dz = tap / 9, dy = (tap / 3) % 3, dx = tap % 3;
+    const int h = (lz + dz) * HX * HY + (ly + dy) * HX + lx + dx;
+#pragma unroll
+    for (int g = 0; g < 4; ++g) {
+      const uint4 v = s_in[4 * h + (g ^ ((h >> 1) & 3))];
+      const float4 wa = s_w4[8 * tap + 2 * g], wb = s_w4[8 * tap + 2 * g + 1];   // channels 8g .. 8g+7
+      acc += wa.x * __uint_as_float(v.x << 16) + wa.y * __uint_as_float(v.x & 0xffff0000u);
+      acc += wa.z * __uint_as_float(v.y << 16) + wa.w * __uint_as_float(v.y & 0xffff0000u);
+      acc += wb.x * __uint_as_float(v.z << 16) + wb.y * __uint_as_float(v.z & 0xffff0000u);
+      acc += wb.z * __uint_as_float(v.w << 16) + wb.w * __uint_as_float(v.w & 0xffff0000u);
+    }
+  }
+  out[(x0 + lx) + (int64_t)X * ((y0 + ly) + (int64_t)Y * (z0 + lz))] = acc * out_scale;
 }
 
 // g[c](v) *= act'(h[c](v)), read from the activation h (act keeps the sign of its argument).
@@ -272,8 +340,7 @@ void forward_t(SurrogateNet& n, const float* Q, float* U, cudaStream_t st) {
                                                                               pz, 1.f / n.sq, 1.f);
       conv32_tc(h0, n.Wp[0], n.b[1], h1, n.dims, n.periodic, true, n.tc_err, st);
       conv32_tc(h1, n.Wp[1], n.b[2], h2, n.dims, n.periodic, true, n.tc_err, st);
-      k_conv_fwd<8, 1, false, A, float, true, false><<<nt, TILE, 0, st>>>(h2, kNetC, n.W[3], n.b[3], U, X, Y, Z, px,
-                                                                           py, pz, 1.f, n.su);
+      k_conv_out_cl<<<nt, TILE, 0, st>>>(h2, n.W[3], n.b[3], U, X, Y, Z, px, py, pz, n.su);
       return;
     }
   }
