@@ -206,12 +206,17 @@ def alg_bytes(name: str, s: int, sz: dict, vs: dict | None = None) -> float:
     raise KeyError(name)
 
 
+# sources that decide what the field-path kernels read and write: the kernels, their row
+# functions and device types, and the layout builder (the tensor-core surrogate and the batch
+# path are not among them)
+FIELD_PATH_SOURCES = ("kernels.cu", "sell.cuh", "device.hpp", "internal.hpp", "layout.cpp")
+
+
 def src_hash() -> str:
     h = hashlib.sha1()
     d = os.path.join(ROOT, "paper_2409_13958_gb300", "csrc")
-    for f in sorted(os.listdir(d)):
-        if f.endswith((".cu", ".cpp", ".hpp")):
-            h.update(open(os.path.join(d, f), "rb").read())
+    for f in FIELD_PATH_SOURCES:
+        h.update(open(os.path.join(d, f), "rb").read())
     return h.hexdigest()[:12]
 
 

@@ -18,12 +18,10 @@ constexpr int kBlock = 256;
 #ifndef PMFEM_COR_G
 #define PMFEM_COR_G 4
 #endif
-// groups of 8 (projection) and of 4 (gradient + exchange) entries each lane keeps in flight
+// groups of 8 projection entries each lane keeps in flight (rows are short: about two groups;
+// two in flight measured no faster than one)
 #ifndef PMFEM_PRO_G
 #define PMFEM_PRO_G 1
-#endif
-#ifndef PMFEM_FIELD_G
-#define PMFEM_FIELD_G 1
 #endif
 
 template <typename T>
@@ -547,32 +545,7 @@ __device__ __forceinline__ void field_row(int64_t i, int64_t c0, int32_t nc, con
   const V4<T>* mc = m + c0;
   T ax = 0, ay = 0, az = 0;
   if (use_ms && use_ex) {
-    // PMFEM_FIELD_G groups of 4 entries in flight per lane (their loads issued together)
-    int g = 0;
-    for (; g + PMFEM_FIELD_G <= ng; g += PMFEM_FIELD_G, o += 128 * PMFEM_FIELD_G) {
-      int32_t c[PMFEM_FIELD_G][4];
-      T g0[PMFEM_FIELD_G][4], g1[PMFEM_FIELD_G][4], g2[PMFEM_FIELD_G][4], kk[PMFEM_FIELD_G][4];
-#pragma unroll
-      for (int f = 0; f < PMFEM_FIELD_G; ++f) {
-        ldc4(dcol + o + 128 * f, c[f]);
-        ldv4(gx + o + 128 * f, g0[f]);
-        ldv4(gy + o + 128 * f, g1[f]);
-        ldv4(gz + o + 128 * f, g2[f]);
-        ldv4(kp + o + 128 * f, kk[f]);
-      }
-#pragma unroll
-      for (int f = 0; f < PMFEM_FIELD_G; ++f)
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-          const int32_t col = col_of(b, c[f][k], nc);
-          const T du = __ldg(uc + col) - un;
-          const V4<T> mk = mc[col];
-          ax += g0[f][k] * du + kk[f][k] * (mk.x - mn.x);
-          ay += g1[f][k] * du + kk[f][k] * (mk.y - mn.y);
-          az += g2[f][k] * du + kk[f][k] * (mk.z - mn.z);
-        }
-    }
-    for (; g < ng; ++g, o += 128) {
+    for (int g = 0; g < ng; ++g, o += 128) {
       int32_t c[4];
       T g0[4], g1[4], g2[4], kk[4];
       ldc4(dcol + o, c);
