@@ -39,6 +39,8 @@ def _handle(kind):
         mesh, grid = meshgen.cube_cell(6, jitter=0.2, seed=63), (16, 16, 16)
     elif kind == "film16":      # 2D periodic film, grid 16 x 16 x 8 (tensor-core path, zero padding along z)
         mesh, grid = meshgen.film_cell(10, 10, 2, seed=64), (16, 16, 8)
+    elif kind == "film64":      # grid 64 x 64 x 8: 256 tensor-core tiles, more than one per SM
+        mesh, grid = meshgen.film_cell(10, 10, 2, seed=65), (64, 64, 8)
     else:                       # 2D periodic film, grid 16 x 8 x 8 with zero padding along z
         mesh, grid = meshgen.film_cell(10, 6, 2, seed=62), (16, 8, 8)
     h = Pmfem.create_mesh(mesh.xyz, mesh.tets, 8e5, 1.3e-11, 0.02)
@@ -54,9 +56,12 @@ def _rel(a, b):
 
 
 @pytest.mark.parametrize("kind,bf16,tol", [("cube", False, 1e-5), ("film", False, 1e-5), ("film", True, 2e-2),
-                                          ("cube16", True, 2e-2), ("film16", True, 2e-2), ("film16", False, 1e-5)])
+                                          ("cube16", True, 2e-2), ("film16", True, 2e-2), ("film16", False, 1e-5),
+                                          ("film64", True, 2e-2)])
 def test_forward_matches_oracle(kind, bf16, tol):
     h, mesh, dims, per = _handle(kind)
+    if kind == "film64":   # tensor-core tiles of 8 x 16 x 1 voxels: more tiles than persistent blocks
+        assert (dims[0] // 8) * (dims[1] // 16) * dims[2] > torch.cuda.get_device_properties(0).multi_processor_count
     params = S.init_params(C=32, seed=5)
     for k in range(1, 8, 2):
         params[k] = np.random.default_rng(10 + k).normal(0, 0.05, params[k].shape)
