@@ -235,8 +235,6 @@ int build_device(pmfem_t h, DevOps<T>& d) {
   d.q = (T*)p;
   if ((rc = dalloc(h, &p, s.Np * sizeof(T)))) return rc;
   d.e = (T*)p;
-  if ((rc = dalloc(h, &p, s.Np * sizeof(T)))) return rc;
-  d.u = (T*)p;
   if ((rc = dalloc(h, &p, ngrid * sizeof(T)))) return rc;
   d.grid = (T*)p;
   if ((rc = dalloc(h, &p, ncb * sizeof(C2)))) return rc;
@@ -769,7 +767,7 @@ size_t noalloc_need(const Setup& s) {
   const size_t np = (size_t)s.Np;
   const size_t G = (size_t)s.dims[0] * s.dims[1] * s.dims[2];
   const size_t ncb = (size_t)(s.fft[0] / 2 + 1) * s.fft[1] * s.fft[2];
-  return align256(np * sizeof(V4<T>)) + 3 * align256(np * sizeof(T)) + align256(G * sizeof(T)) +
+  return align256(np * sizeof(V4<T>)) + 2 * align256(np * sizeof(T)) + align256(G * sizeof(T)) +
          align256(ncb * sizeof(C2));
 }
 
@@ -787,8 +785,6 @@ void noalloc_eval(pmfem_t h, const DevOps<T>& d, unsigned char* base, const void
   x.q = (T*)(base + off);
   off += align256(np * sizeof(T));
   x.e = (T*)(base + off);
-  off += align256(np * sizeof(T));
-  x.u = (T*)(base + off);
   off += align256(np * sizeof(T));
   x.grid = (T*)(base + off);
   off += align256(G * sizeof(T));

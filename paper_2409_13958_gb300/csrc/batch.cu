@@ -139,7 +139,7 @@ struct pmfem_batch_state {
   float2* cbuf = nullptr;
   const float* ghat = nullptr;
   std::vector<FftGroup> groups;
-  float *q = nullptr, *e = nullptr, *u = nullptr;
+  float *q = nullptr, *e = nullptr;
   V4<float>* m = nullptr;     // state (node rows)
   V4<float>* mA = nullptr;
   V4<float>* mB = nullptr;
@@ -242,15 +242,14 @@ __global__ void __launch_bounds__(kBlock) kb_interp(
     const float* __restrict__ grid, const int32_t* __restrict__ clen, const int32_t* __restrict__ cbase,
     const int64_t* __restrict__ coff, const CT* __restrict__ dcol, const float* __restrict__ cval,
     const int32_t* __restrict__ rowptrX, const int32_t* __restrict__ colX, const float* __restrict__ valX,
-    const float* __restrict__ q, const float* __restrict__ e, const V4<float>* __restrict__ m,
-    float* __restrict__ u) {
+    const float* __restrict__ q, const float* __restrict__ e, const V4<float>* m, float* uw) {
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < rows;
        t += (int64_t)gridDim.x * blockDim.x) {
     const CellDev& c = cells[node_cell[t >> 5]];
     if (t - c.node_off >= c.Np) continue;
     interp_row<float, P, CT, float>(t, map[t], c.node_off, c.Np, sbase, frac, grid + c.grid_off, c.dims[0],
                                     c.dims[1], c.dims[2], c.periodic[0] != 0, c.periodic[1] != 0, c.periodic[2] != 0,
-                                    clen, cbase, coff, dcol, cval, rowptrX, colX, valX, q, e, m, u);
+                                    clen, cbase, coff, dcol, cval, rowptrX, colX, valX, q, e, m, uw);
   }
 }
 
@@ -260,7 +259,7 @@ __global__ void __launch_bounds__(kBlock) kb_field(int64_t rows, const int32_t* 
                                                   const int32_t* __restrict__ base, const int64_t* __restrict__ off,
                                                   const CT* __restrict__ dcol, const float* __restrict__ gx,
                                                   const float* __restrict__ gy, const float* __restrict__ gz,
-                                                  const float* __restrict__ kp, const float* __restrict__ u,
+                                                  const float* __restrict__ kp,
                                                   const V4<float>* __restrict__ m, const int32_t* __restrict__ uidx,
                                                   float* __restrict__ H, int use_ms, int use_ex, int use_ap,
                                                   V4<float>* __restrict__ m0, V4<float>* __restrict__ mnext,
@@ -271,7 +270,7 @@ __global__ void __launch_bounds__(kBlock) kb_field(int64_t rows, const int32_t* 
     const CellDev& c = cells[node_cell[t >> 5]];
     if (t - c.node_off >= c.Np) continue;
     const float hx = use_ap ? c.hap[0] : 0.f, hy = use_ap ? c.hap[1] : 0.f, hz = use_ap ? c.hap[2] : 0.f;
-    field_row<float, MODE, CT, float, float>(t, c.node_off, c.Np, len, base, off, dcol, gx, gy, gz, kp, u, m,
+    field_row<float, MODE, CT, float, float>(t, c.node_off, c.Np, len, base, off, dcol, gx, gy, gz, kp, m,
                                              MODE == 0 ? (int64_t)uidx[t] : 0, H, use_ms, use_ex, hx, hy, hz, m0,
                                              mnext, accb, cdt, bw, acc_init, dt6, c.gam, c.alpha, flag);
   }
@@ -482,8 +481,6 @@ int build_batch_device(pmfem_batch_t b) {
   b->q = (float*)p;
   if ((rc = balloc(b, &p, ss))) return rc;
   b->e = (float*)p;
-  if ((rc = balloc(b, &p, ss))) return rc;
-  b->u = (float*)p;
   if ((rc = balloc(b, &p, (size_t)grow * sizeof(float)))) return rc;
   b->grid = (float*)p;
   if ((rc = balloc(b, &p, (size_t)cb * sizeof(float2)))) return rc;
@@ -499,7 +496,6 @@ int build_batch_device(pmfem_batch_t b) {
   PMFEM_BCK(b, cudaMemset(b->flag, 0, sizeof(int)));
   PMFEM_BCK(b, cudaMemset(b->q, 0, ss));
   PMFEM_BCK(b, cudaMemset(b->e, 0, ss));
-  PMFEM_BCK(b, cudaMemset(b->u, 0, ss));
   b->dev_ready = true;
   return OK;
 }
@@ -569,7 +565,7 @@ void batch_eval(pmfem_batch_t b, const V4<float>* m, float* H, int comps, const 
       auto go = [&](auto kernel) {
         kernel<<<nb, kBlock, 0, st>>>(b->rows, b->node_cell, b->dtable, C.map, b->sbase, b->frac, b->grid, C.len,
                                       C.base, C.off, dcol, C.val[0], b->rowptrX, b->colX, b->valX, b->q, b->e, m,
-                                      b->u);
+                                      reinterpret_cast<float*>(const_cast<V4<float>*>(m)) + 3);   // u -> lane 3
       };
       switch (b->p) {
         case 2: go(kb_interp<3, CT>); break;
@@ -584,7 +580,7 @@ void batch_eval(pmfem_batch_t b, const V4<float>* m, float* H, int comps, const 
     using CT = std::remove_cv_t<std::remove_pointer_t<decltype(dcol)>>;
     auto go = [&](auto kernel) {
       kernel<<<nb, kBlock, 0, st>>>(b->rows, b->node_cell, b->dtable, A.len, A.base, A.off, dcol, A.val[6], A.val[7],
-                                    A.val[8], A.val[9], b->u, m, b->uidx, H, use_ms, use_ex, use_ap,
+                                    A.val[8], A.val[9], m, b->uidx, H, use_ms, use_ex, use_ap,
                                     (V4<float>*)rk.m0, (V4<float>*)rk.mnext, (V4<float>*)rk.acc, (float)rk.cdt,
                                     (float)rk.bw, rk.acc_init, (float)rk.dt6, b->flag);
     };

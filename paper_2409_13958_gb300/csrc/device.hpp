@@ -110,7 +110,6 @@ struct DevOps {
   // work buffers
   T* q = nullptr;
   T* e = nullptr;
-  T* u = nullptr;
   T* grid = nullptr;                              // N0 N1 N2 real (Q, then U)
   C2* cbuf = nullptr;                             // F2 x F1 x (F0/2+1) complex
   int* flag = nullptr;                            // device error word

@@ -122,7 +122,7 @@ __host__ __device__ constexpr int cor_pipe() {
       const int32_t *__restrict__ clen, const int32_t *__restrict__ cbase, const int64_t *__restrict__ coff,     \
       const CT *__restrict__ dcol, const VT *__restrict__ cval, const int32_t *__restrict__ rowptrX,             \
       const int32_t *__restrict__ colX, const T *__restrict__ valX, const T *__restrict__ q,                      \
-      const T *__restrict__ e, const V4<T> *__restrict__ m, T *__restrict__ u
+      const T *__restrict__ e, const V4<T> *m, T *uw
 #define PMFEM_INTERP_BODY                                                                                         \
   extern __shared__ __align__(16) unsigned char pipe_raw[];                                                      \
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;                                              \
@@ -130,7 +130,7 @@ __host__ __device__ constexpr int cor_pipe() {
   const int64_t i = map ? (int64_t)map[t] : t;                                                                    \
   interp_row<T, P, CT, VT, cor_pipe<VT>()>(                                                                      \
       t, i, 0, (int32_t)Np, base, frac, U, N0, N1, N2, p0, p1, p2, clen, cbase, coff, dcol, cval, rowptrX, colX,  \
-      valX, q, e, m, u, pipe_raw + (threadIdx.x >> 5) * (cor_pipe<VT>() * PipeStage<VT, CT>::BYTES));
+      valX, q, e, m, uw, pipe_raw + (threadIdx.x >> 5) * (cor_pipe<VT>() * PipeStage<VT, CT>::BYTES));
 template <typename T, int P, typename CT, typename VT>
 __global__ void __launch_bounds__(kBlock, PMFEM_INTERP_MINB) k_interp_capped(PMFEM_INTERP_PARAMS) {
   PMFEM_INTERP_BODY
@@ -150,22 +150,41 @@ constexpr auto interp_kernel() {
 }
 
 // ---------------------------------------------------------------- gradient + exchange + RK4
-template <typename T, int MODE, typename CT, typename VG, typename VK>
-__global__ void __launch_bounds__(kBlock) k_field(int64_t Np, const int32_t* __restrict__ len,
-                                                 const int32_t* __restrict__ base,
-                                                 const int64_t* __restrict__ off, const CT* __restrict__ dcol,
-                                                 const VG* __restrict__ gx, const VG* __restrict__ gy,
-                                                 const VG* __restrict__ gz, const VK* __restrict__ kp,
-                                                 const T* __restrict__ u, const V4<T>* __restrict__ m,
-                                                 const int32_t* __restrict__ perm, T* __restrict__ H, int use_ms,
-                                                 int use_ex, T hx, T hy, T hz, V4<T>* __restrict__ m0,
-                                                 V4<T>* __restrict__ mnext, V4<T>* __restrict__ accb, T cdt, T bw,
-                                                 int acc_init, T dt6, T gam, T alpha, int* flag) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= Np) return;
-  const int64_t uo = MODE == 0 ? (int64_t)perm[i] : 0;
-  field_row<T, MODE, CT, VG, VK>(i, 0, (int32_t)Np, len, base, off, dcol, gx, gy, gz, kp, u, m, uo, H, use_ms,
+// Two instances of the same body: with FP32 operator values the kernel asks for
+// PMFEM_FIELD_MINB resident blocks per SM (a register cap: measured 78 -> 72 us on the 1M-node
+// wire); with bfloat16 values (the cap measured 59 -> 62 us there) and FP64 the compiler chooses.
+#ifndef PMFEM_FIELD_MINB
+#define PMFEM_FIELD_MINB 5
+#endif
+#define PMFEM_FIELD_PARAMS                                                                                      \
+  int64_t Np, const int32_t *__restrict__ len, const int32_t *__restrict__ base, const int64_t *__restrict__ off, \
+      const CT *__restrict__ dcol, const VG *__restrict__ gx, const VG *__restrict__ gy,                          \
+      const VG *__restrict__ gz, const VK *__restrict__ kp, const V4<T> *__restrict__ m,                          \
+      const int32_t *__restrict__ perm, T *__restrict__ H, int use_ms, int use_ex, T hx, T hy, T hz,             \
+      V4<T> *__restrict__ m0, V4<T> *__restrict__ mnext, V4<T> *__restrict__ accb, T cdt, T bw, int acc_init,    \
+      T dt6, T gam, T alpha, int *flag
+#define PMFEM_FIELD_BODY                                                                                        \
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;                                            \
+  if (i >= Np) return;                                                                                          \
+  const int64_t uo = MODE == 0 ? (int64_t)perm[i] : 0;                                                          \
+  field_row<T, MODE, CT, VG, VK>(i, 0, (int32_t)Np, len, base, off, dcol, gx, gy, gz, kp, m, uo, H, use_ms,     \
                                  use_ex, hx, hy, hz, m0, mnext, accb, cdt, bw, acc_init, dt6, gam, alpha, flag);
+template <typename T, int MODE, typename CT, typename VG, typename VK>
+__global__ void __launch_bounds__(kBlock, PMFEM_FIELD_MINB) k_field_capped(PMFEM_FIELD_PARAMS) {
+  PMFEM_FIELD_BODY
+}
+template <typename T, int MODE, typename CT, typename VG, typename VK>
+__global__ void __launch_bounds__(kBlock) k_field(PMFEM_FIELD_PARAMS) {
+  PMFEM_FIELD_BODY
+}
+#undef PMFEM_FIELD_BODY
+#undef PMFEM_FIELD_PARAMS
+template <typename T, int MODE, typename CT, typename VG, typename VK>
+constexpr auto field_kernel() {
+  if constexpr (sizeof(T) == 4 && sizeof(VG) == 4 && sizeof(VK) == 4)
+    return k_field_capped<T, MODE, CT, VG, VK>;
+  else
+    return k_field<T, MODE, CT, VG, VK>;
 }
 
 inline unsigned blocks_for(int64_t threads) { return (unsigned)((threads + kBlock - 1) / kBlock); }
@@ -263,7 +282,7 @@ void launch_interp(const DevOps<T>& d, const V4<T>* m, cudaStream_t st) {
         kernel<<<nb, kBlock, sm, st>>>(d.Np, C.map, d.base, d.frac, d.grid, d.dims[0], d.dims[1], d.dims[2],
                                       d.periodic[0], d.periodic[1], d.periodic[2], C.len, C.base, C.off,
                                       (const CT*)C.delta, vals<VT>(C, 0), d.rowptrX, d.colX, d.valX, d.q, d.e, m,
-                                      d.u);
+                                      reinterpret_cast<T*>(const_cast<V4<T>*>(m)) + 3);   // u -> lane 3 of m
       };
       switch (d.p) {
         case 2: go(interp_kernel<T, 3, CT, VT>()); break;
@@ -295,16 +314,16 @@ void launch_field(const DevOps<T>& d, const V4<T>* m, T* H, int comps, double hx
         using VK = typename decltype(vk)::type;
         auto go = [&](auto kernel) {
           kernel<<<nb, kBlock, 0, st>>>(d.Np, A.len, A.base, A.off, (const CT*)A.delta, vals<VG>(A, 6),
-                                        vals<VG>(A, 7), vals<VG>(A, 8), vals<VK>(A, 9), d.u, m, d.perm, H, use_ms,
+                                        vals<VG>(A, 7), vals<VG>(A, 8), vals<VK>(A, 9), m, d.perm, H, use_ms,
                                         use_ex, ax, ay, az, m0, mn, acc, (T)rk.cdt, (T)rk.bw, rk.acc_init,
                                         (T)rk.dt6, (T)rk.gam, (T)rk.alpha, d.flag);
         };
         if (rk.mode == 0)
-          go(k_field<T, 0, CT, VG, VK>);
+          go(field_kernel<T, 0, CT, VG, VK>());
         else if (rk.mode == 1)
-          go(k_field<T, 1, CT, VG, VK>);
+          go(field_kernel<T, 1, CT, VG, VK>());
         else
-          go(k_field<T, 2, CT, VG, VK>);
+          go(field_kernel<T, 2, CT, VG, VK>());
       });
     });
   });

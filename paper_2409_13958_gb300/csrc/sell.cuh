@@ -484,7 +484,7 @@ __device__ __forceinline__ T stencil_row(int64_t i, const int32_t* __restrict__ 
 // Near-element entries of node i beyond the adjacency pattern (CSR, 3-vector values on M).
 template <typename T>
 __device__ __forceinline__ T extras_row(int64_t i, const int32_t* __restrict__ rowptrX, const int32_t* __restrict__ colX,
-                                        const T* __restrict__ valX, const V4<T>* __restrict__ m) {
+                                        const T* __restrict__ valX, const V4<T>* m) {
   T acc = 0;
   for (int32_t p = rowptrX[i]; p < rowptrX[i + 1]; ++p) {
     const V4<T> mk = m[colX[p]];
@@ -493,9 +493,11 @@ __device__ __forceinline__ T extras_row(int64_t i, const int32_t* __restrict__ r
   return acc;
 }
 
-// Potential of node i (SELL row t of the precorrection, stored with vector width 4): the
-// stencil (step 3), the point precorrection row (step 4), the near-element entries beyond the
-// adjacency pattern and the touching-element part e.
+// Potential of node i (SELL row t of the precorrection): the stencil (step 3), the point
+// precorrection row (step 4), the near-element entries beyond the adjacency pattern and the
+// touching-element part e.  The potential goes to the fourth (padding) lane of the node's
+// magnetisation 4-vector, uw = (T*)m + 3, so that the gradient pass gathers m and u of a
+// neighbour with one 16-byte load; this pass reads only the first three lanes of m.
 // PIPE > 0 streams the precorrection row through the warp's PIPE-stage shared-memory buffer
 // buf (sell_dot8_pipe; vector width 8 only); PIPE = 0 loads it into registers.
 template <typename T, int P, typename CT, typename VT, int PIPE = 0>
@@ -504,8 +506,8 @@ __device__ __forceinline__ void interp_row(
     const T* __restrict__ U, int N0, int N1, int N2, bool p0, bool p1, bool p2, const int32_t* __restrict__ clen,
     const int32_t* __restrict__ cbase, const int64_t* __restrict__ coff, const CT* __restrict__ dcol,
     const VT* __restrict__ cval, const int32_t* __restrict__ rowptrX, const int32_t* __restrict__ colX,
-    const T* __restrict__ valX, const T* __restrict__ q, const T* __restrict__ e, const V4<T>* __restrict__ m,
-    T* __restrict__ u, unsigned char* buf = nullptr) {
+    const T* __restrict__ valX, const T* __restrict__ q, const T* __restrict__ e, const V4<T>* m, T* uw,
+    unsigned char* buf = nullptr) {
   T acc = stencil_row<T, P>(i, base, frac, U, N0, N1, N2, p0, p1, p2);
   if constexpr (PMFEM_COR_VW == 8 && PIPE > 0)
     acc += sell_dot8_pipe<PIPE>(cval, dcol, q + c0, cbase[t], coff[t >> 5] + 8 * (t & 31), clen[t], nc, buf);
@@ -514,7 +516,7 @@ __device__ __forceinline__ void interp_row(
   else
     acc += sell_dot4<PMFEM_COR_G>(cval, dcol, q + c0, cbase[t], coff[t >> 5] + 4 * (t & 31), clen[t], nc);
   acc += extras_row<T>(i, rowptrX, colX, valX, m);
-  u[i] = acc + e[i];
+  uw[4 * i] = acc + e[i];
 }
 
 // ---------------------------------------------------------------- gradient + exchange + RK4
@@ -531,17 +533,16 @@ __device__ __forceinline__ void field_row(int64_t i, int64_t c0, int32_t nc, con
                                           const int32_t* __restrict__ base, const int64_t* __restrict__ off,
                                           const CT* __restrict__ dcol, const VG* __restrict__ gx,
                                           const VG* __restrict__ gy, const VG* __restrict__ gz,
-                                          const VK* __restrict__ kp, const T* __restrict__ u,
-                                          const V4<T>* __restrict__ m, int64_t uo, T* __restrict__ H, int use_ms,
+                                          const VK* __restrict__ kp, const V4<T>* __restrict__ m, int64_t uo,
+                                          T* __restrict__ H, int use_ms,
                                           int use_ex, T hx, T hy, T hz, V4<T>* __restrict__ m0,
                                           V4<T>* __restrict__ mnext, V4<T>* __restrict__ accb, T cdt, T bw,
                                           int acc_init, T dt6, T gam, T alpha, int* flag) {
   const int ng = (len[i] + 3) >> 2;
   const int32_t b = base[i];
   int64_t o = off[i >> 5] + 4 * (i & 31);
-  const V4<T> mn = m[i];
-  const T un = use_ms ? u[i] : T(0);
-  const T* uc = u + c0;
+  const V4<T> mn = m[i];           // (m, u) of node i: the potential sits in the fourth lane
+  const T un = use_ms ? mn.w : T(0);
   const V4<T>* mc = m + c0;
   T ax = 0, ay = 0, az = 0;
   if (use_ms && use_ex) {
@@ -555,9 +556,8 @@ __device__ __forceinline__ void field_row(int64_t i, int64_t c0, int32_t nc, con
       ldv4(kp + o, kk);
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
-        const int32_t col = col_of(b, c[k], nc);
-        const T du = __ldg(uc + col) - un;
-        const V4<T> mk = mc[col];
+        const V4<T> mk = mc[col_of(b, c[k], nc)];   // one 16-byte gather: m and u of the neighbour
+        const T du = mk.w - un;
         ax += g0[k] * du + kk[k] * (mk.x - mn.x);
         ay += g1[k] * du + kk[k] * (mk.y - mn.y);
         az += g2[k] * du + kk[k] * (mk.z - mn.z);
@@ -573,7 +573,7 @@ __device__ __forceinline__ void field_row(int64_t i, int64_t c0, int32_t nc, con
       ldv4(gz + o, g2);
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
-        const T du = __ldg(uc + col_of(b, c[k], nc)) - un;
+        const T du = mc[col_of(b, c[k], nc)].w - un;
         ax += g0[k] * du;
         ay += g1[k] * du;
         az += g2[k] * du;
