@@ -38,7 +38,7 @@ GRID = (128, 128, 256)
 P_ORDER, NEAR_BOXES, NEAR_ELEM = 3, 3, 0.0
 
 
-def parse():
+def parse(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=200)
@@ -51,10 +51,15 @@ def parse():
     ap.add_argument("--no-batch", action="store_true", help="skip the 64-cell batch leg")
     ap.add_argument("--no-surrogate", action="store_true", help="skip the learned-surrogate leg")
     ap.add_argument("--out", default=None, help="also write the JSON line to this file")
-    return ap.parse_args()
+    return ap.parse_args(argv)
 
 
 # ------------------------------------------------------------------ distributed plumbing
+def whole_job_value(world: int, units_per_rank: float, ms_slowest: float) -> float:
+    """Throughput of the whole job: the units every rank processed over the slowest rank's time."""
+    return world * units_per_rank / (ms_slowest * 1e-3)
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -63,14 +68,21 @@ def dist_env():
 
 
 class Dist:
-    def __init__(self, world, local):
+    """Replica bookkeeping across ranks: a barrier and the maximum of a per-rank time.  NCCL on
+    the GPUs (one rank per GPU); gloo on CPU tensors for the host-side tests."""
+
+    def __init__(self, world, local, backend: str = "nccl"):
         import torch
         self.world = world
         self.torch = torch
         self.pg = None
+        self.device = "cuda" if backend == "nccl" else "cpu"
         if world > 1:
             import torch.distributed as td
-            td.init_process_group("nccl", device_id=torch.device("cuda", local))
+            if backend == "nccl":
+                td.init_process_group("nccl", device_id=torch.device("cuda", local))
+            else:
+                td.init_process_group(backend)
             self.td = td
             self.pg = True
 
@@ -81,7 +93,7 @@ class Dist:
     def max(self, x: float) -> float:
         if not self.pg:
             return x
-        t = self.torch.tensor([x], dtype=self.torch.float64, device="cuda")
+        t = self.torch.tensor([x], dtype=self.torch.float64, device=self.device)
         self.td.all_reduce(t, op=self.td.ReduceOp.MAX)
         return float(t.item())
 
@@ -567,7 +579,7 @@ def run_native(args):
     dist.barrier()
     ck = clocks.stop()
     ms = dist.max(e0.elapsed_time(e1))
-    value = world * Np * 4 * args.steps / (ms * 1e-3)
+    value = whole_job_value(world, Np * 4 * args.steps, ms)
     # per-kernel durations: the same K steps again with a CUDA-event pair around every launch
     # on the launching stream (the library then launches kernel by kernel instead of replaying
     # the graph, so this pass is timed apart from the headline)
