@@ -205,10 +205,15 @@ def alg_bytes(name: str, s: int, sz: dict, vs: dict | None = None) -> float:
         return 2 * s * Hx * F1 * N2 + 2 * s * Hx * N1 * N2
     if name == "fft_x_inv":
         return 2 * s * Hx * N1 * N2 + s * G
+    if name == "interp_precorr" and sz.get("split"):   # the precorrection pass of the two-pass form:
+        # near-element row pointer, row map + len + base, values + column deltas, q once, e read, u written
+        return 4 * Np + 12 * Np + nc * (cb["precorrection"] + vs.get("precorrection", s)) + 3 * s * Np
     if name == "interp_precorr":               # stencil base + frac + near-element row pointer, grid once,
         # row map + len + base, values + column deltas, q once, e read, u written (into lane 3 of m)
         return ((12 + 3 * s + 4) * Np + s * G + 12 * Np + nc * (cb["precorrection"] + vs.get("precorrection", s))
                 + 3 * s * Np)
+    if name == "interp_stencil":               # stencil base + frac, grid once, u read and written
+        return (12 + 3 * s) * Np + s * G + 2 * s * Np
     if name == "gradient_exchange":            # gradient + exchange values, (m, u) 4-vectors once, RK4 stage state
         return 4 * Np + na * (cb["adjacency"] + 4 * s) + v4 * Np + 3.5 * v4 * Np
     if name == "permute":
@@ -662,6 +667,7 @@ def run_native(args):
 
     # roofline of the dominant kernel
     peak, peak_kind = measured_peaks()
+    sizes["split"] = prof.get("interp_stencil", (0, 0.0))[0] > 0   # two-pass interpolation
     per = {k: {"launches": c, "ms_total": t, "share": 0.0} for k, (c, t) in prof.items() if c}
     tot = sum(v["ms_total"] for k, v in per.items() if k != "grid_clear") or 1.0
     for k, v in per.items():
@@ -683,6 +689,8 @@ def run_native(args):
                    "step": "one RK4 LLG step = 4 field evaluations", "dt_s": dt,
                    "nnz_adjacency": sizes["nnz"], "nnz_precorrection": sizes["nnzC"], "device_layout": sizes["dev"],
                    "l2": "inputs larger than L2 (operator data streamed every evaluation)",
+                   "interpolation": ("two passes: precorrection on a second stream during projection + FFT, "
+                                     "then the stencil" if sizes.get("split") else "one fused pass after the FFT"),
                    "parallelism": f"replicas x{world}", "setup_s": round(t_setup, 1), "mesh_s": round(t_mesh, 1)},
         "clocks": ck,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": step_bytes, "d2h_bytes_per_step": step_bytes,

@@ -203,8 +203,11 @@ int pmfem_llg_step(pmfem_t h, double dt, int nsteps, void* stream);
  * for kernel ids 0..n-1, the launch counts and the summed event time in ms since the last
  * pmfem_profile(h, 1).  Ids: 0 charges, 1 projection, 2 FFT x forward, 3 FFT y forward,
  * 4 FFT z + spectral multiply, 5 FFT y inverse, 6 FFT x inverse, 7 interpolation +
- * precorrection, 8 gradient + exchange (+ RK4 stage), 9 grid clear, 10 permutation between
- * the C-ABI unknown order and the internal box-sorted order.
+ * precorrection (the precorrection alone where the two-pass form runs), 8 gradient + exchange
+ * (+ RK4 stage), 9 grid clear, 10 permutation between the C-ABI unknown order and the internal
+ * box-sorted order, 11 stencil of the grid potential added to the precorrected potential (the
+ * second pass of the two-pass form, in which the precorrection overlaps the projection and the
+ * FFT on a second stream; with timing on, every launch runs on the launching stream in order).
  */
 int pmfem_profile(pmfem_t h, int enable);
 int pmfem_profile_read(pmfem_t h, int64_t* counts, double* total_ms, int n);

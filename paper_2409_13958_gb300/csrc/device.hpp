@@ -50,7 +50,7 @@ struct alignas(4 * sizeof(T)) V4 {
 
 // Optional per-launch timing: the handle records a CUDA event pair around each kernel.
 enum KernelId : int { KID_CHARGES = 0, KID_ANTERP, KID_FFT_X_FWD, KID_FFT_Y_FWD, KID_FFT_Z_CONV, KID_FFT_Y_INV,
-                      KID_FFT_X_INV, KID_INTERP, KID_FIELD, KID_MEMSET, KID_PERM, KID_COUNT };
+                      KID_FFT_X_INV, KID_INTERP, KID_FIELD, KID_MEMSET, KID_PERM, KID_STENCIL, KID_COUNT };
 struct ProfHook {
   void (*fn)(void* ctx, int id, int phase, cudaStream_t st) = nullptr;
   void* ctx = nullptr;
@@ -156,6 +156,10 @@ struct FftArgs {
 };
 template <typename T> void launch_fft(const FftArgs<T>& a, const ProfHook& prof, cudaStream_t st);
 template <typename T> void launch_interp(const DevOps<T>& d, const V4<T>* m, cudaStream_t st);
+// the two halves of launch_interp: precorrection (+ near and touching elements) from q, m, e;
+// then the stencil of the grid potential added on top
+template <typename T> void launch_precorr(const DevOps<T>& d, const V4<T>* m, cudaStream_t st);
+template <typename T> void launch_stencil(const DevOps<T>& d, const V4<T>* m, cudaStream_t st);
 // mode 0 writes H in the C-ABI order (N' x 3); RK modes update internal 4-vector buffers
 template <typename T>
 void launch_field(const DevOps<T>& d, const V4<T>* m, T* H_user, int comps, double hx, double hy, double hz,

@@ -149,6 +149,54 @@ constexpr auto interp_kernel() {
     return k_interp<T, P, CT, VT>;
 }
 
+// ---------------------------------------------------------------- the two-pass form
+// Precorrection pass (one thread per precorrection row, as in the fused kernel, without the
+// stencil) and stencil pass (one thread per node in the internal order).
+#define PMFEM_PRECORR_PARAMS                                                                                    \
+  int64_t Np, const int32_t *__restrict__ map, const int32_t *__restrict__ clen,                               \
+      const int32_t *__restrict__ cbase, const int64_t *__restrict__ coff, const CT *__restrict__ dcol,           \
+      const VT *__restrict__ cval, const int32_t *__restrict__ rowptrX, const int32_t *__restrict__ colX,         \
+      const T *__restrict__ valX, const T *__restrict__ q, const T *__restrict__ e, const V4<T> *m, T *uw
+#define PMFEM_PRECORR_BODY                                                                                      \
+  extern __shared__ __align__(16) unsigned char pipe_raw[];                                                    \
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;                                            \
+  if (t >= Np) return;                                                                                          \
+  const int64_t i = map ? (int64_t)map[t] : t;                                                                  \
+  precorr_row<T, CT, VT, cor_pipe<VT>()>(t, i, 0, (int32_t)Np, clen, cbase, coff, dcol, cval, rowptrX, colX,   \
+                                         valX, q, e, m, uw,                                                     \
+                                         pipe_raw + (threadIdx.x >> 5) * (cor_pipe<VT>() * PipeStage<VT, CT>::BYTES));
+template <typename T, typename CT, typename VT>
+__global__ void __launch_bounds__(kBlock, PMFEM_INTERP_MINB) k_precorr_capped(PMFEM_PRECORR_PARAMS) {
+  PMFEM_PRECORR_BODY
+}
+template <typename T, typename CT, typename VT>
+__global__ void __launch_bounds__(kBlock) k_precorr(PMFEM_PRECORR_PARAMS) {
+  PMFEM_PRECORR_BODY
+}
+#undef PMFEM_PRECORR_BODY
+#undef PMFEM_PRECORR_PARAMS
+template <typename T, typename CT, typename VT>
+constexpr auto precorr_kernel() {
+  if constexpr (sizeof(T) == 4)
+    return k_precorr_capped<T, CT, VT>;
+  else
+    return k_precorr<T, CT, VT>;
+}
+
+#ifdef PMFEM_STENCIL_MINB
+#define PMFEM_STENCIL_LB __launch_bounds__(kBlock, PMFEM_STENCIL_MINB)
+#else
+#define PMFEM_STENCIL_LB __launch_bounds__(kBlock)
+#endif
+template <typename T, int P>
+__global__ void PMFEM_STENCIL_LB k_stencil(int64_t Np, const int32_t* __restrict__ base,
+                                                   const T* __restrict__ frac, const T* __restrict__ U, int N0,
+                                                   int N1, int N2, bool p0, bool p1, bool p2, T* uw) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= Np) return;
+  stencil_add_row<T, P>(i, base, frac, U, N0, N1, N2, p0, p1, p2, uw);
+}
+
 // ---------------------------------------------------------------- gradient + exchange + RK4
 // Two instances of the same body: with FP32 operator values the kernel asks for
 // PMFEM_FIELD_MINB resident blocks per SM (a register cap: measured 78 -> 72 us on the 1M-node
@@ -296,6 +344,44 @@ void launch_interp(const DevOps<T>& d, const V4<T>* m, cudaStream_t st) {
 }
 
 template <typename T>
+void launch_precorr(const DevOps<T>& d, const V4<T>* m, cudaStream_t st) {
+  const unsigned nb = blocks_for(d.Np);
+  const DevSell<T>& C = d.cor;
+  d.prof.begin(KID_INTERP, st);
+  with_ct(C, [&](auto ct) {
+    using CT = typename decltype(ct)::type;
+    with_vt<T>(C.bval[0] != nullptr, [&](auto vt) {
+      using VT = typename decltype(vt)::type;
+      const size_t sm = (size_t)(kBlock / 32) * cor_pipe<VT>() * PipeStage<VT, CT>::BYTES;
+      auto kernel = precorr_kernel<T, CT, VT>();
+      set_smem(kernel, sm);
+      kernel<<<nb, kBlock, sm, st>>>(d.Np, C.map, C.len, C.base, C.off, (const CT*)C.delta, vals<VT>(C, 0),
+                                    d.rowptrX, d.colX, d.valX, d.q, d.e, m,
+                                    reinterpret_cast<T*>(const_cast<V4<T>*>(m)) + 3);   // u -> lane 3 of m
+    });
+  });
+  d.prof.end(KID_INTERP, st);
+}
+
+template <typename T>
+void launch_stencil(const DevOps<T>& d, const V4<T>* m, cudaStream_t st) {
+  const unsigned nb = blocks_for(d.Np);
+  T* uw = reinterpret_cast<T*>(const_cast<V4<T>*>(m)) + 3;
+  d.prof.begin(KID_STENCIL, st);
+  auto go = [&](auto kernel) {
+    kernel<<<nb, kBlock, 0, st>>>(d.Np, d.base, d.frac, d.grid, d.dims[0], d.dims[1], d.dims[2], d.periodic[0],
+                                  d.periodic[1], d.periodic[2], uw);
+  };
+  switch (d.p) {
+    case 2: go(k_stencil<T, 3>); break;
+    case 3: go(k_stencil<T, 4>); break;
+    case 4: go(k_stencil<T, 5>); break;
+    default: go(k_stencil<T, 6>); break;
+  }
+  d.prof.end(KID_STENCIL, st);
+}
+
+template <typename T>
 void launch_field(const DevOps<T>& d, const V4<T>* m, T* H, int comps, double hx, double hy, double hz,
                   const RkArgs& rk, cudaStream_t st) {
   const DevSell<T>& A = d.adj;
@@ -336,6 +422,8 @@ void launch_field(const DevOps<T>& d, const V4<T>* m, T* H, int comps, double hx
   template void launch_charges<T>(const DevOps<T>&, const V4<T>*, cudaStream_t);                     \
   template void launch_anterp<T>(const DevOps<T>&, cudaStream_t);                                    \
   template void launch_interp<T>(const DevOps<T>&, const V4<T>*, cudaStream_t);                      \
+  template void launch_precorr<T>(const DevOps<T>&, const V4<T>*, cudaStream_t);                     \
+  template void launch_stencil<T>(const DevOps<T>&, const V4<T>*, cudaStream_t);                     \
   template void launch_field<T>(const DevOps<T>&, const V4<T>*, T*, int, double, double, double, const RkArgs&, \
                                 cudaStream_t);
 PMFEM_INSTANTIATE(double)

@@ -31,16 +31,18 @@ __device__ __forceinline__ T warp_sum(T v) {
   return v;
 }
 
-// Lagrange basis polynomial a (of the P nodes 0 .. P-1) at s.
-template <typename T, int P>
-__device__ __forceinline__ T lagrange1(T s, int a) {
-  T v = T(1);
-#pragma unroll
+// prod_{j != a} (a - j): the denominator of Lagrange basis polynomial a of the nodes 0 .. P-1
+// (an integer of magnitude at most 5! for P <= 6)
+template <int P>
+__host__ __device__ constexpr double lagrange_den(int a) {
+  double d = 1.0;
   for (int j = 0; j < P; ++j)
-    if (j != a) v *= (s - T(j)) / T(a - j);
-  return v;
+    if (j != a) d *= (double)(a - j);
+  return d;
 }
 
+// The P Lagrange basis polynomials of the nodes 0 .. P-1 at s: the product of (s - j) over
+// j != a times the compile-time reciprocal of its denominator (no division at run time).
 template <typename T, int P>
 __device__ __forceinline__ void lagrange(T s, T (&w)[P]) {
 #pragma unroll
@@ -48,8 +50,8 @@ __device__ __forceinline__ void lagrange(T s, T (&w)[P]) {
     T v = T(1);
 #pragma unroll
     for (int j = 0; j < P; ++j)
-      if (j != i) v *= (s - T(j)) / T(i - j);
-    w[i] = v;
+      if (j != i) v *= (s - T(j));
+    w[i] = v * T(1.0 / lagrange_den<P>(i));
   }
 }
 
@@ -517,6 +519,36 @@ __device__ __forceinline__ void interp_row(
     acc += sell_dot4<PMFEM_COR_G>(cval, dcol, q + c0, cbase[t], coff[t >> 5] + 4 * (t & 31), clen[t], nc);
   acc += extras_row<T>(i, rowptrX, colX, valX, m);
   uw[4 * i] = acc + e[i];
+}
+
+// The same potential in two passes, so that the precorrection (which needs only q, m and e)
+// can run while the projection and the FFT produce U: precorr_row writes the precorrection,
+// near-element and touching-element parts to lane 3 of m; stencil_add_row then adds the
+// stencil of U (step 3) for node i.
+template <typename T, typename CT, typename VT, int PIPE = 0>
+__device__ __forceinline__ void precorr_row(int64_t t, int64_t i, int64_t c0, int32_t nc,
+                                            const int32_t* __restrict__ clen, const int32_t* __restrict__ cbase,
+                                            const int64_t* __restrict__ coff, const CT* __restrict__ dcol,
+                                            const VT* __restrict__ cval, const int32_t* __restrict__ rowptrX,
+                                            const int32_t* __restrict__ colX, const T* __restrict__ valX,
+                                            const T* __restrict__ q, const T* __restrict__ e, const V4<T>* m, T* uw,
+                                            unsigned char* buf = nullptr) {
+  T acc;
+  if constexpr (PMFEM_COR_VW == 8 && PIPE > 0)
+    acc = sell_dot8_pipe<PIPE>(cval, dcol, q + c0, cbase[t], coff[t >> 5] + 8 * (t & 31), clen[t], nc, buf);
+  else if constexpr (PMFEM_COR_VW == 8)
+    acc = sell_dot8<(PMFEM_COR_G + 1) / 2>(cval, dcol, q + c0, cbase[t], coff[t >> 5] + 8 * (t & 31), clen[t], nc);
+  else
+    acc = sell_dot4<PMFEM_COR_G>(cval, dcol, q + c0, cbase[t], coff[t >> 5] + 4 * (t & 31), clen[t], nc);
+  acc += extras_row<T>(i, rowptrX, colX, valX, m);
+  uw[4 * i] = acc + e[i];
+}
+
+template <typename T, int P>
+__device__ __forceinline__ void stencil_add_row(int64_t i, const int32_t* __restrict__ base, const T* __restrict__ frac,
+                                                const T* __restrict__ U, int N0, int N1, int N2, bool p0, bool p1,
+                                                bool p2, T* uw) {
+  uw[4 * i] += stencil_row<T, P>(i, base, frac, U, N0, N1, N2, p0, p1, p2);
 }
 
 // ---------------------------------------------------------------- gradient + exchange + RK4

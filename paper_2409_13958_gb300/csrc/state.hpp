@@ -24,6 +24,10 @@ struct pmfem_state {
   bool dev_ready = false;
   int dev_prec = -1;
   cudaStream_t stream = nullptr;
+  // the precorrection runs on `side` while the projection and FFT run on the caller's stream:
+  // ev_fork (after the charges) and ev_join (after the precorrection) order the two
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   std::vector<void*> allocs;
   pmfem::DevOps<double> d64;
   pmfem::DevOps<float> d32;
