@@ -155,7 +155,10 @@ int pmfem_lca_map(pmfem_t h, int32_t* host_out);
  *   H      device, N' x 3 T, written in A/m (may not alias m)
  *   components  bitmask of PMFEM_EX | PMFEM_MS | PMFEM_AP
  * Enqueued on stream; a non-finite m sets a device flag reported as ENONFINITE by the
- * next pmfem_sync.
+ * next pmfem_sync.  In FP32 and BF16-split, the precorrection part of the magnetostatic
+ * field runs on a second stream of the handle, forked from stream after the charges and
+ * joined back into it before the stencil pass (CUDA events): the evaluation stays ordered on
+ * stream as a whole, and a graph capture on stream captures both branches.
  */
 int pmfem_field(pmfem_t h, const void* m, void* H, int components, void* stream);
 

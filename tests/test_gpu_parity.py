@@ -209,3 +209,40 @@ def test_nonfinite_input_is_reported():
     h.field(m, H)
     h.sync()                                   # the flag was cleared
     h.destroy()
+
+
+@pytest.mark.parametrize("prec", [1, 2])
+def test_second_stream_precorrection_is_ordered(prec):
+    """FP32 and BF16-split run the precorrection on a second stream, forked after the charges and
+    joined before the stencil pass.  With per-launch timing on, the same kernels run in order
+    on one stream; a missing or misplaced join would let the stencil or the gradient read a
+    stale potential, so the two must agree to rounding (the projection's few exception nodes
+    add by atomics, whose order may differ between runs), fields and an RK4 trajectory alike."""
+    mesh, ob, grid, p, nb, f = _problem("film_20x20x2")
+    h = _lib(mesh, grid, p, nb, f, prec)
+    m = torch.tensor(meshgen.m_tilted(ob.Np, 5.0, seed=3), dtype=torch.float32, device="cuda")
+    H_fork, H_order = torch.empty_like(m), torch.empty_like(m)
+    st = torch.cuda.Stream()
+    for _ in range(3):                       # repeated calls reuse the fork and join events
+        h.field(m, H_fork, stream=st)
+    h.profile(True)
+    h.field(m, H_order, stream=st)
+    h.profile_read()
+    h.profile(False)
+    h.sync()
+    assert _rel(H_fork.double().cpu().numpy(), H_order.double().cpu().numpy()) <= 1e-6
+    dt = 2e-14
+    out = []
+    for timing in (False, True):             # replayed graph (two streams) / launches in order
+        h.set_m(m)
+        h.profile(timing)
+        h.llg_step(dt, 3)
+        if timing:
+            h.profile_read()
+        h.profile(False)
+        mo = torch.empty_like(m)
+        h.get_m(mo)
+        h.sync()
+        out.append(mo)
+    assert _rel(out[0].double().cpu().numpy(), out[1].double().cpu().numpy()) <= 1e-6
+    h.destroy()
