@@ -119,9 +119,6 @@ struct pmfem_batch_state {
   // device
   bool dev_ready = false;
   cudaStream_t stream = nullptr;
-  // the precorrection pass runs on `side` during the projection and FFT (fork / join events)
-  cudaStream_t side = nullptr;
-  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   std::vector<void*> allocs;
   std::vector<CellDev> table;
   CellDev* dtable = nullptr;
@@ -238,12 +235,11 @@ __global__ void __launch_bounds__(kBlock) kb_project_exc(int64_t n, const int32_
   }
 }
 
-// Interpolation + precorrection in two passes (as for one mesh): the precorrection rows of
-// every cell, then the stencil of each cell's grid potential, node by node.
-template <typename CT>
-__global__ void __launch_bounds__(kBlock) kb_precorr(
+template <int P, typename CT>
+__global__ void __launch_bounds__(kBlock) kb_interp(
     int64_t rows, const int32_t* __restrict__ node_cell, const CellDev* __restrict__ cells,
-    const int32_t* __restrict__ map, const int32_t* __restrict__ clen, const int32_t* __restrict__ cbase,
+    const int32_t* __restrict__ map, const int32_t* __restrict__ sbase, const float* __restrict__ frac,
+    const float* __restrict__ grid, const int32_t* __restrict__ clen, const int32_t* __restrict__ cbase,
     const int64_t* __restrict__ coff, const CT* __restrict__ dcol, const float* __restrict__ cval,
     const int32_t* __restrict__ rowptrX, const int32_t* __restrict__ colX, const float* __restrict__ valX,
     const float* __restrict__ q, const float* __restrict__ e, const V4<float>* m, float* uw) {
@@ -251,22 +247,9 @@ __global__ void __launch_bounds__(kBlock) kb_precorr(
        t += (int64_t)gridDim.x * blockDim.x) {
     const CellDev& c = cells[node_cell[t >> 5]];
     if (t - c.node_off >= c.Np) continue;
-    precorr_row<float, CT, float>(t, map[t], c.node_off, c.Np, clen, cbase, coff, dcol, cval, rowptrX, colX,
-                                  valX, q, e, m, uw);
-  }
-}
-
-template <int P>
-__global__ void __launch_bounds__(kBlock) kb_stencil(int64_t rows, const int32_t* __restrict__ node_cell,
-                                                    const CellDev* __restrict__ cells,
-                                                    const int32_t* __restrict__ sbase, const float* __restrict__ frac,
-                                                    const float* __restrict__ grid, float* uw) {
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < rows;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const CellDev& c = cells[node_cell[i >> 5]];
-    if (i - c.node_off >= c.Np) continue;
-    stencil_add_row<float, P>(i, sbase, frac, grid + c.grid_off, c.dims[0], c.dims[1], c.dims[2],
-                              c.periodic[0] != 0, c.periodic[1] != 0, c.periodic[2] != 0, uw);
+    interp_row<float, P, CT, float>(t, map[t], c.node_off, c.Np, sbase, frac, grid + c.grid_off, c.dims[0],
+                                    c.dims[1], c.dims[2], c.periodic[0] != 0, c.periodic[1] != 0, c.periodic[2] != 0,
+                                    clen, cbase, coff, dcol, cval, rowptrX, colX, valX, q, e, m, uw);
   }
 }
 
@@ -521,9 +504,6 @@ int ensure_batch(pmfem_batch_t b) {
   if (b->dev_ready) return OK;
   free_batch_device(b);
   if (!b->stream) PMFEM_BCK(b, cudaStreamCreate(&b->stream));
-  if (!b->side) PMFEM_BCK(b, cudaStreamCreateWithFlags(&b->side, cudaStreamNonBlocking));
-  if (!b->ev_fork) PMFEM_BCK(b, cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming));
-  if (!b->ev_join) PMFEM_BCK(b, cudaEventCreateWithFlags(&b->ev_join, cudaEventDisableTiming));
   int dev = 0, sms = 0;
   PMFEM_BCK(b, cudaGetDevice(&dev));
   PMFEM_BCK(b, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
@@ -557,22 +537,6 @@ void batch_eval(pmfem_batch_t b, const V4<float>* m, float* H, int comps, const 
       kb_charges<CT><<<nb, kBlock, 0, st>>>(b->rows, b->node_cell, b->dtable, A.len, A.base, A.off, dcol, A.val[0],
                                             A.val[1], A.val[2], A.val[3], A.val[4], A.val[5], m, b->q, b->e);
     });
-    // the precorrection needs only q, m and e: it runs on the side stream during the
-    // projection and the FFT; the stencil pass after the FFT waits for it
-    float* uw = reinterpret_cast<float*>(const_cast<V4<float>*>(m)) + 3;   // u -> lane 3 of m
-    const DevSell<float>& C = b->cor;
-    const bool fork = b->side && b->ev_fork && b->ev_join;
-    cudaStream_t s2 = fork ? b->side : st;
-    if (fork) {
-      cudaEventRecord(b->ev_fork, st);
-      cudaStreamWaitEvent(s2, b->ev_fork, 0);
-    }
-    with_cols(C, [&](auto dcol) {
-      using CT = std::remove_cv_t<std::remove_pointer_t<decltype(dcol)>>;
-      kb_precorr<CT><<<nb, kBlock, 0, s2>>>(b->rows, b->node_cell, b->dtable, C.map, C.len, C.base, C.off, dcol,
-                                            C.val[0], b->rowptrX, b->colX, b->valX, b->q, b->e, m, uw);
-    });
-    if (fork) cudaEventRecord(b->ev_join, s2);
     const DevSell<float>& Pm = b->pro;
     with_cols(Pm, [&](auto dcol) {
       using CT = std::remove_cv_t<std::remove_pointer_t<decltype(dcol)>>;
@@ -595,16 +559,21 @@ void batch_eval(pmfem_batch_t b, const V4<float>* m, float* H, int comps, const 
       a.count = (unsigned)g.cells.size();
       launch_fft(a, ProfHook(), st);
     }
-    if (fork) cudaStreamWaitEvent(st, b->ev_join, 0);
-    auto go = [&](auto kernel) {
-      kernel<<<nb, kBlock, 0, st>>>(b->rows, b->node_cell, b->dtable, b->sbase, b->frac, b->grid, uw);
-    };
-    switch (b->p) {
-      case 2: go(kb_stencil<3>); break;
-      case 3: go(kb_stencil<4>); break;
-      case 4: go(kb_stencil<5>); break;
-      default: go(kb_stencil<6>); break;
-    }
+    const DevSell<float>& C = b->cor;
+    with_cols(C, [&](auto dcol) {
+      using CT = std::remove_cv_t<std::remove_pointer_t<decltype(dcol)>>;
+      auto go = [&](auto kernel) {
+        kernel<<<nb, kBlock, 0, st>>>(b->rows, b->node_cell, b->dtable, C.map, b->sbase, b->frac, b->grid, C.len,
+                                      C.base, C.off, dcol, C.val[0], b->rowptrX, b->colX, b->valX, b->q, b->e, m,
+                                      reinterpret_cast<float*>(const_cast<V4<float>*>(m)) + 3);   // u -> lane 3
+      };
+      switch (b->p) {
+        case 2: go(kb_interp<3, CT>); break;
+        case 3: go(kb_interp<4, CT>); break;
+        case 4: go(kb_interp<5, CT>); break;
+        default: go(kb_interp<6, CT>); break;
+      }
+    });
   }
   const int use_ms = (comps & PMFEM_MS) ? 1 : 0, use_ex = (comps & PMFEM_EX) ? 1 : 0, use_ap = (comps & PMFEM_AP) ? 1 : 0;
   with_cols(A, [&](auto dcol) {
@@ -702,9 +671,6 @@ int pmfem_batch_create(pmfem_batch_t* out, const pmfem_t* cells, int n) {
 int pmfem_batch_destroy(pmfem_batch_t b) {
   if (!b) return EINVAL_;
   free_batch_device(b);
-  if (b->ev_fork) cudaEventDestroy(b->ev_fork);
-  if (b->ev_join) cudaEventDestroy(b->ev_join);
-  if (b->side) cudaStreamDestroy(b->side);
   if (b->stream) cudaStreamDestroy(b->stream);
   delete b;
   return OK;
