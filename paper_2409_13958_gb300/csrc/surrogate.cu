@@ -152,15 +152,22 @@ __global__ void __launch_bounds__(TILE) k_conv_out_cl(const __nv_bfloat16* __res
   const int tile = blockIdx.x;
   const int x0 = (tile % ntx) * TX, y0 = ((tile / ntx) % nty) * TY, z0 = (tile / (ntx * nty)) * TZ;
   for (int k = threadIdx.x; k < 27 * 32; k += blockDim.x) s_w[k] = W[k];
+  // every 16-byte piece is one cp.async, all in flight at once (zero fill outside a
+  // non-periodic border: source size 0, nothing read)
   for (int k = threadIdx.x; k < HALO * 4; k += blockDim.x) {
     const int h = k >> 2, g = k & 3;
     const int hz = h / (HX * HY), hy = (h / HX) % HY, hx = h % HX;
     bool ix, iy, iz;
     const int gx = wrapc(x0 + hx - 1, X, px, ix), gy = wrapc(y0 + hy - 1, Y, py, iy), gz = wrapc(z0 + hz - 1, Z, pz, iz);
-    uint4 v = make_uint4(0u, 0u, 0u, 0u);
-    if (ix && iy && iz) v = reinterpret_cast<const uint4*>(in + 32 * (gx + (int64_t)X * (gy + (int64_t)Y * gz)))[g];
-    s_in[4 * h + (g ^ ((h >> 1) & 3))] = v;
+    const bool inside = ix && iy && iz;
+    const uint4* src = reinterpret_cast<const uint4*>(in) +
+                       (inside ? 4 * (gx + (int64_t)X * (gy + (int64_t)Y * gz)) + g : 0);
+    const uint32_t dst = (uint32_t)__cvta_generic_to_shared(s_in + 4 * h + (g ^ ((h >> 1) & 3)));
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(dst), "l"(src), "r"(inside ? 16u : 0u)
+                 : "memory");
   }
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
   __syncthreads();
   const int lx = threadIdx.x % TX, ly = (threadIdx.x / TX) % TY, lz = threadIdx.x / (TX * TY);
   float acc = b[0];
