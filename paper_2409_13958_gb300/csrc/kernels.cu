@@ -1,7 +1,8 @@
 // Field-evaluation kernels for sm_103a: charges (Eq. 14a) with the touching-element part
 // of Eq. 14c, projection onto the grid (BAIM step 1), interpolation plus precorrection
-// (steps 3 and 4), and the gradient (Eq. 14d) + exchange (Eq. 8) pass with the fused
-// RK4 stage update of the LLG equation (Eq. 2).
+// (steps 3 and 4: one fused kernel, or a precorrection pass that can run beside the
+// projection and FFT followed by a stencil pass), and the gradient (Eq. 14d) + exchange
+// (Eq. 8) pass with the fused RK4 stage update of the LLG equation (Eq. 2).
 //
 // Layout: unknowns in the internal box-sorted order (the C-ABI's m and H are permuted
 // at the boundary); sparse rows in SELL-32, one thread per row, so that at every step j
@@ -183,6 +184,8 @@ constexpr auto precorr_kernel() {
     return k_precorr<T, CT, VT>;
 }
 
+// PMFEM_STENCIL_MINB: optional register cap of the stencil pass (measured: 6 blocks per SM,
+// 40 registers, no faster than the compiler's choice, so unset by default)
 #ifdef PMFEM_STENCIL_MINB
 #define PMFEM_STENCIL_LB __launch_bounds__(kBlock, PMFEM_STENCIL_MINB)
 #else

@@ -14,7 +14,8 @@ namespace {
 
 constexpr int kBlock = 256;
 
-// values of a precorrection row each lane keeps in flight: 4 x PMFEM_COR_G
+// values of a precorrection row each lane keeps in flight: 4 x PMFEM_COR_G (vector width 4), or
+// 8 x (PMFEM_COR_G + 1) / 2 (vector width 8)
 #ifndef PMFEM_COR_G
 #define PMFEM_COR_G 4
 #endif
@@ -231,7 +232,8 @@ __device__ __forceinline__ void ldc8(const int32_t* p, int32_t (&c)[8]) {
 }
 
 // sell_dot for a SELL-32 operator stored eight values per lane and step (vector width 8):
-// group g of the lane at o0 + 256 g with o0 = off[c] + 8 lane; rows padded as for width 4.
+// group g of the lane at o0 + 256 g with o0 = off[c] + 8 lane; rows padded to whole groups
+// with value 0 and delta 0 (a valid column), so every group is read whole.
 template <int G, bool W = true, typename T, typename CT, typename VT>
 __device__ __forceinline__ T sell_dot8(const VT* __restrict__ val, const CT* __restrict__ dcol,
                                        const T* __restrict__ x, int32_t b, int64_t o0, int n, int32_t ncol) {
@@ -553,8 +555,8 @@ __device__ __forceinline__ void stencil_add_row(int64_t i, const int32_t* __rest
 
 // ---------------------------------------------------------------- gradient + exchange + RK4
 // Field of node i: gradient (Eq. 14d) and exchange (Eq. 8) over adjacency row i (vector
-// width 4, as in charges_row), plus the
-// applied field; then either the output (MODE 0, written to H[3 * uo] in the caller's
+// width 4, as in charges_row; the potential u of a node is the fourth lane of its m vector),
+// plus the applied field; then either the output (MODE 0, written to H[3 * uo] in the caller's
 // order) or the RK4 stage update of the LLG equation (Eq. 2; MODE 1 an intermediate stage,
 // MODE 2 the final combination with the renormalisation of Eq. 6 in FP64).
 // Both operators annihilate constants (rows of the gradient and of the Laplacian sum to
