@@ -31,6 +31,10 @@
  *     PMFEM_FP64 -> double; PMFEM_FP32 and PMFEM_BF16SPLIT -> float.
  *   - Set-up (create_mesh, set_aim, set_periodicity) runs on the host and does not touch
  *     the GPU; device buffers are allocated on the first call that needs them.
+ *   - A handle (and a batch) is used by one host thread at a time: its scratch buffers, its
+ *     second stream and its fork/join events are per handle, so two calls on one handle
+ *     must not overlap.  Different handles are independent (pmfem_field_noalloc excepted,
+ *     see there).
  */
 #ifndef PMFEM_H
 #define PMFEM_H
