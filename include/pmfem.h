@@ -174,15 +174,16 @@ int pmfem_field_host(pmfem_t h, const void* m_host, void* H_host, int components
  * pmfem_field without any allocation (the paper has no counterpart; this is a service for
  * callers that must not allocate device memory when they ask for a field: real-time loops
  * that forbid allocator calls, or hosts whose device memory belongs to a pooling
- * allocator).  Same arguments and same result as
- * pmfem_field; all scratch of the evaluation lives in one fixed 64 MiB device array
- * compiled into the library, which every GPU that loads the library keeps until the
- * process exits.  The call allocates nothing itself:
+ * allocator).  Same arguments and same result as pmfem_field; all scratch of the
+ * evaluation lives in one fixed 64 MiB device array compiled into the library.  The array
+ * is reserved on a device when the library's device code is loaded there (with CUDA's lazy
+ * module loading, at the latest when a handle's device data are first built on it) and is
+ * kept until the process exits.  The call allocates nothing itself:
  *   - the handle's operators must already be on the device at the current precision (one
- *     earlier pmfem_field or pmfem_set_m call); otherwise ESTATE;
+ *     earlier pmfem_field or pmfem_set_m call); otherwise ESTATE.  That earlier call also
+ *     looks up the array's device address (cudaGetSymbolAddress, in the context then
+ *     current), so pmfem_field_noalloc itself makes no CUDA call but its kernel launches;
  *   - a mesh and grid whose scratch exceeds 64 MiB give EINVAL (use pmfem_field);
- *   - the first call on a device looks up the array's address (cudaGetSymbolAddress) and
- *     should therefore come before any stream capture;
  *   - every call on a device shares the one array: calls that overlap on the GPU (other
  *     streams, other handles) race and must be serialised by the caller.  Nothing in the
  *     array needs to start at zero; it keeps whatever the last call left.

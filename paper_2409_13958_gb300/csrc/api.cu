@@ -57,6 +57,28 @@ void apply_prof(pmfem_t h) {
   h->d32.prof = hk;
 }
 
+// Fixed scratch of pmfem_field_noalloc (see the section of that entry point below): one
+// file-scope device array, reserved on a device when this library's device code is loaded
+// there, and kept until the process exits.
+constexpr size_t kNoAllocBytes = 64u << 20;   // 64 MiB of shared scratch per device
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+// In host code g_noalloc_scratch is only a host-side stand-in; the array's device address
+// comes from cudaGetSymbolAddress, in the context current now.  Called where the device data
+// of a handle are built (a path that may allocate: the lookup can load the module that holds
+// the array), so that pmfem_field_noalloc itself only reads the cached address.  A failed
+// lookup leaves nullptr and its message; pmfem_field_noalloc then reports it.
+void noalloc_lookup(pmfem_t h, std::string* why) {
+  void* p = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+  if (e != cudaSuccess || !p) {
+    if (e != cudaSuccess) cudaGetLastError();   // not sticky: clear it for the callers' next check
+    *why = std::string("cudaGetSymbolAddress of the no-alloc scratch failed: ") + cudaGetErrorString(e);
+    p = nullptr;
+  }
+  h->noalloc_base = p;
+}
+
 void free_device(pmfem_t h) {
   if (h->graph) cudaGraphExecDestroy(h->graph);
   h->graph = nullptr;
@@ -66,6 +88,7 @@ void free_device(pmfem_t h) {
   h->d32 = DevOps<float>();
   h->m = h->mA = h->mB = h->acc = h->mF = h->hin = h->hout = nullptr;
   h->flag = nullptr;
+  h->noalloc_base = nullptr;
   h->dev_ready = false;
   h->dev_prec = -1;
 }
@@ -272,6 +295,7 @@ int ensure_device(pmfem_t h) {
   }
   h->dev_prec = h->prec;
   h->dev_ready = true;
+  noalloc_lookup(h, &h->noalloc_why);
   apply_prof(h);
   return OK;
 }
@@ -784,13 +808,6 @@ int pmfem_folded_positions(pmfem_t h, double* out) {
 // ------------------------------------------------------------------------------------
 namespace {
 
-constexpr size_t kNoAllocBytes = 64u << 20;   // 64 MiB of shared scratch per device
-static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
-
-constexpr int kMaxDevices = 128;
-void* g_noalloc_ptr[kMaxDevices] = {};
-std::mutex g_noalloc_mutex;
-
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 // bytes of scratch one evaluation of this handle needs at precision T
@@ -844,23 +861,8 @@ extern "C" int pmfem_field_noalloc(pmfem_t h, const void* m, void* H, int compon
   if (!h->dev_ready || h->dev_prec != h->prec)
     return fail(h, ESTATE_, "pmfem_field_noalloc needs the operators on the device: make one pmfem_field (or "
                             "pmfem_set_m) call at this precision first");
-  int dev = 0;
-  PMFEM_CK(h, cudaGetDevice(&dev));
-  if (dev < 0 || dev >= kMaxDevices) return fail(h, EINVAL_, "device index out of range");
-  void* base = nullptr;
-  {
-    std::lock_guard<std::mutex> lk(g_noalloc_mutex);
-    if (!g_noalloc_ptr[dev]) {
-      // once per device, with that device current: the array's device address
-      void* p = nullptr;
-      cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-      if (e != cudaSuccess || !p)
-        return fail(h, ECUDA_, std::string("cudaGetSymbolAddress of the no-alloc scratch failed: ") +
-                                   cudaGetErrorString(e));
-      g_noalloc_ptr[dev] = p;
-    }
-    base = g_noalloc_ptr[dev];
-  }
+  void* base = h->noalloc_base;   // looked up when the device data were built
+  if (!base) return fail(h, ECUDA_, h->noalloc_why);
   cudaStream_t st = stream ? (cudaStream_t)stream : h->stream;
   if (h->dev_prec == PMFEM_FP64) noalloc_eval(h, h->d64, (unsigned char*)base, m, H, components, st);
   else noalloc_eval(h, h->d32, (unsigned char*)base, m, H, components, st);

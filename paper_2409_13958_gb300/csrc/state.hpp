@@ -39,6 +39,10 @@ struct pmfem_state {
   void* hin = nullptr;    // N' x 3 user-order staging for the host-buffer calls
   void* hout = nullptr;
   int* flag = nullptr;
+  // device address of the library's fixed scratch array for pmfem_field_noalloc, looked up
+  // whenever the device data are (re)built, in the context that holds them
+  void* noalloc_base = nullptr;
+  std::string noalloc_why;
   // per-launch timing (pmfem_profile)
   bool prof_on = false;
   std::vector<cudaEvent_t> ev_pool;

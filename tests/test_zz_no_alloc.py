@@ -33,14 +33,14 @@ def _handle(mesh, grid, prec):
     return h
 
 
-@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("prec", [0, 1, 2])
 def test_noalloc_matches_field_on_two_calls(prec):
     from paper_2409_13958_gb300 import PMFEM_ALL, PMFEM_MS, PMFEM_EX
     mesh = meshgen.film_cell(20, 20, 2)
     h = _handle(mesh, (32, 32, 8), prec)
     n = h.num_unknowns()
     dt = torch.float64 if prec == 0 else torch.float32
-    tol = 1e-12 if prec == 0 else 1e-6
+    tol = 1e-12 if prec == 0 else 1e-6     # same kernels on the same operators: rounding order only
     for call, (seed, comps) in enumerate(((3, PMFEM_ALL), (4, PMFEM_MS | PMFEM_EX))):
         m = torch.tensor(meshgen.m_random(n, seed=seed), dtype=dt, device="cuda")
         ref = torch.empty_like(m)
@@ -68,3 +68,21 @@ def test_noalloc_refuses_before_upload_and_beyond_its_size():
         big.field_noalloc(m, H)
     assert e.value.code == -1
     big.destroy()
+
+
+def test_noalloc_after_set_m_upload():
+    """The operators can reach the device through pmfem_set_m alone; the no-alloc call that
+    follows then agrees with pmfem_field called afterwards."""
+    from paper_2409_13958_gb300 import PMFEM_ALL
+    mesh = meshgen.film_cell(12, 10, 2, seed=3)
+    h = _handle(mesh, (16, 16, 8), 1)
+    n = h.num_unknowns()
+    m = torch.tensor(meshgen.m_random(n, seed=9), dtype=torch.float32, device="cuda")
+    h.set_m(m)                           # uploads the operators; no field evaluated yet
+    got = torch.full_like(m, float("nan"))
+    h.field_noalloc(m, got, PMFEM_ALL)
+    ref = torch.empty_like(m)
+    h.field(m, ref, PMFEM_ALL)
+    h.sync()
+    assert float((got - ref).norm() / ref.norm()) <= 1e-6
+    h.destroy()
