@@ -20,10 +20,14 @@ from .pgf import pgf, pgf_reg0
 
 
 def potential_direct(pos_f, q, periods, EM=None, observers=None, max_pairs=1_000_000, eta=None):
-    """4 pi u at the observers (all unknowns by default)."""
+    """4 pi u at the observers (all unknowns by default).
+
+    q may be (N,) or (N, k): k charge sets share every evaluation of G^p (EM then (N,) or
+    (N, k) alike)."""
     N = pos_f.shape[0]
     obs = np.arange(N) if observers is None else np.asarray(observers)
-    u = np.zeros(obs.size)
+    q = np.asarray(q, dtype=np.float64)
+    u = np.zeros((obs.size,) + q.shape[1:])
     R0 = pgf_reg0(periods, eta)
     B = max(1, max_pairs // N)
     for s in range(0, obs.size, B):

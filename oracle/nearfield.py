@@ -115,9 +115,18 @@ def near_sets(pos_f, xyz, tets, tri, lca, periods, r_E):
     return res
 
 
-def near_matrix(pos_f, xyz, tets, tri, lca, vol, grad, periods, n_unknowns, r_E, self_tol):
-    """E as three csr matrices (x, y, z components): 4 pi u += sum_d E[d] @ M[:, d]."""
+def near_matrix(pos_f, xyz, tets, tri, lca, vol, grad, periods, n_unknowns, r_E, self_tol, observers=None):
+    """E as three csr matrices (x, y, z components): 4 pi u += sum_d E[d] @ M[:, d].
+
+    observers (optional): only these rows are built (the others stay empty), for problems
+    too large to integrate every near placement; the kept rows are unchanged."""
     (nt, st, lt), (nf, sf, lf) = near_sets(pos_f, xyz, tets, tri, lca, periods, r_E)
+    if observers is not None:
+        keep_row = np.zeros(n_unknowns, bool)
+        keep_row[np.asarray(observers)] = True
+        kt, kf = keep_row[nt], keep_row[nf]
+        nt, st, lt = nt[kt], st[kt], lt[kt]
+        nf, sf, lf = nf[kf], sf[kf], lf[kf]
     rows, cols, vals = [], [], []
     # tetrahedra
     if nt.size:

@@ -27,7 +27,11 @@ GAMMA0 = ops.MU0 * GAMMA_E          # m/(A s)
 class OracleProblem:
     def __init__(self, xyz, tets, periods, Ms=8e5, A=1.3e-11, alpha=0.02, H_ap=(0.0, 0.0, 0.0),
                  grid=None, p=3, near_boxes=1, near_elem_factor=0.0, eta=None, build_paim=True,
-                 paim_observers=None):
+                 observers=None):
+        """observers (optional): the unknowns at which the potential is needed.  The
+        precorrection C and the near-element matrix E are then built for those rows only,
+        and both potentials (O1 and O2) are valid at those rows only; H_ms is valid at an
+        unknown whose adjacency neighbours are all observers."""
         self.xyz = np.asarray(xyz, dtype=np.float64)
         self.tets = np.asarray(tets, dtype=np.int64)
         self.periods = tuple(float(L) for L in periods)
@@ -45,13 +49,13 @@ class OracleProblem:
         self.r_E = near_elem_factor * self.mean_edge
         self.E, self.near_counts = near_matrix(self.pos_f, self.xyz, self.tets, self.tri, self.lca, self.vol,
                                                self.grad, self.periods, self.Np, self.r_E,
-                                               1e-6 * self.mean_edge)
+                                               1e-6 * self.mean_edge, observers)
         self.grid = None
         if grid is not None and build_paim:
             self.grid = AimGrid(self.pos_f, self.periods, grid, p)
             self.Ktab = self.grid.kernel_table(eta)
             self.Khat = np.fft.rfftn(self.Ktab).real
-            self.C = precorrection_matrix(self.grid, self.pos_f, near_boxes, paim_observers)
+            self.C = precorrection_matrix(self.grid, self.pos_f, near_boxes, observers)
             self.stencil_idx, self.stencil_w = self.grid.flat(self.pos_f)
 
     # ------------------------------------------------------------------ pieces

@@ -120,3 +120,56 @@ def test_fold_translation_invariance():
         Hs.append((pb.h_ms(m0, "direct"), pb.h_ms(m0, "paim")))
     assert np.linalg.norm(Hs[1][0] - Hs[0][0]) / np.linalg.norm(Hs[0][0]) < 1e-10
     assert np.linalg.norm(Hs[1][1] - Hs[0][1]) / np.linalg.norm(Hs[0][1]) < 5e-3
+
+
+def _o1_fields(pb, ms):
+    """O1 magnetostatic fields of several magnetisations, sharing the lattice sums."""
+    from oracle.direct import potential_direct
+    q = np.stack([pb.charges(m) for m in ms], 1)
+    em = np.stack([pb.EM(m) for m in ms], 1)
+    u = potential_direct(pb.pos_f, q, pb.periods, em, eta=pb.eta)
+    return [pb.h_ms_from_potential(u[:, i]) for i in range(len(ms))]
+
+
+@pytest.mark.slow
+def test_paim_method_error_vs_direct_1d_protruding():
+    """O2 against O1 on a 1D-periodic cell that protrudes past its period (fold of Eq. 18,
+    1D lattice sums of Eq. 15, box-near pairs through the periodic wrap of Eq. 17)."""
+    p = meshgen.prism_cell(5, 5, 8, jitter=0.15, seed=5)
+    xyz = p.xyz.copy()
+    xyz[:, 2] += 0.37 * p.periods[2] + 0.2 * xyz[:, 0]
+    mr = None
+    errs = {}
+    for nb in (1, 3):
+        pb = OracleProblem(xyz, p.tets, p.periods, grid=(16, 16, 32), near_boxes=nb)
+        if mr is None:
+            mr = meshgen.m_random(pb.Np, 3)
+            H1 = _o1_fields(pb, [mr])[0]
+        errs[nb] = np.linalg.norm(pb.h_ms(mr, "paim") - H1) / np.linalg.norm(H1)
+    assert errs[3] < 6e-3                 # measured 3.7e-3
+    assert errs[1] > 3 * errs[3]
+
+
+@pytest.mark.slow
+def test_sphere_lattice_closed_form_and_method_error():
+    """3D-periodic cubic lattice of spheres (radius 0.4 L, tin-foil reading of Eq. 15), O1:
+    for a uniform M along axis i the field averaged over the sphere is -(1 - f)/3 M
+    (self field -M/3, zero Lorentz sum of a cubic lattice, +f M/3 from the neutralising
+    background), f = 4 pi 0.4^3 / 3.  For any body the three averages add up to -(1 - f) Ms
+    with f the body's own volume fraction (the trace of the periodic demagnetising kernel
+    is delta - 1/V); here f is the faceted mesh's.  O2 against O1 on a random m."""
+    mesh = meshgen.sphere_lattice(target_nodes=800, seed=7)
+    pb = OracleProblem(mesh.xyz, mesh.tets, mesh.periods, grid=(32, 32, 32), near_boxes=3)
+    ms = [meshgen.m_uniform(pb.Np, np.eye(3)[d]) for d in range(3)] + [meshgen.m_random(pb.Np, 3)]
+    Hs = _o1_fields(pb, ms)
+    f = 4 * math.pi * 0.4 ** 3 / 3
+    f_mesh = pb.vol.sum() / np.prod(mesh.periods)
+    means = [(Hs[d][:, d] * pb.V).sum() / pb.V.sum() / pb.Ms for d in range(3)]
+    for d in range(3):
+        assert abs(means[d] + (1 - f) / 3) < 0.015 * (1 - f) / 3, (d, means[d])     # measured 0.46%
+    assert abs(sum(means) + (1 - f_mesh)) < 0.005 * (1 - f_mesh), sum(means)        # measured 0.24%
+    err = np.linalg.norm(pb.h_ms(ms[3], "paim") - Hs[3]) / np.linalg.norm(Hs[3])
+    assert err < 2e-3                                                                 # measured 7.8e-4
+    pb1 = OracleProblem(mesh.xyz, mesh.tets, mesh.periods, grid=(32, 32, 32), near_boxes=1)
+    err1 = np.linalg.norm(pb1.h_ms(ms[3], "paim") - Hs[3]) / np.linalg.norm(Hs[3])
+    assert err1 > 3 * err
