@@ -2,7 +2,7 @@
 
 Test infrastructure (see ``oracle/__init__``).
 
-These are the "exact integrals ... over the relevant elements" of Sec. 3.2 that
+These are the exact element integrals of Sec. 3.2 that
 replace the point-charge contributions of nearby sources (Eq. 14c).
 
 Triangle T with unit normal n, observer r, projection p = r - d n onto the plane.

@@ -15,8 +15,8 @@ observer n when
       including those reached through a periodic image), or
   (b) its centroid lies within r_E of the observer (periodic images included, as in
       Eq. 17 for the box search).
-Reading of Sec. 3.2 ("r_ER ... based on the tetrahedron size, i.e. the average edge
-length"): r_E = near_elem_factor * mean edge; factor 0 keeps only (a).
+Reading of Sec. 3.2, which ties the element radius to the tetrahedron size (the mean
+edge length): r_E = near_elem_factor * mean edge; factor 0 keeps only (a).
 
 For every near placement, 4 pi u_n gains  int_{s+l} G0(r_n - r') dens_s - sum_k q_k^s G0'(r_n - r_k - l)
 where G0'(0) = 0 (the self point is carried by R(0) in the lattice sum).  This is

@@ -11,7 +11,7 @@ ignores periodicity):
 Stencil of order p: t = (x - origin) / Delta; base = floor(t) - (p-1)/2 for odd p,
 round-half-down(t) - p/2 for even p; points base..base+p with 1D Lagrange weights,
 tensor product in 3D.  Projection (step 1) is the transpose of interpolation (step 3).
-Grid kernel (step 2, Sec. 3.2 "replace G0 with G^p"): K(d) = G^p(d Delta), K(0) = R(0).
+Grid kernel (step 2, Sec. 3.2: the periodic G^p takes the place of G0): K(d) = G^p(d Delta), K(0) = R(0).
 Precorrection (step 4, only G0 is corrected, Sec. 3.2): for every source image
 (k, l) whose box lies within Chebyshev distance near_boxes of the observer's box
 (periodic wrap gives the expanded regions of Eq. 17),

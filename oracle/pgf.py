@@ -3,7 +3,8 @@
 Test infrastructure (see ``oracle/__init__``).
 
 The lattice sums of Eq. 15 are evaluated by Ewald splitting of 1/r with the
-Gaussian parameter eta (the paper only says "exponentially convergent sums").
+Gaussian parameter eta (the paper names only a family of exponentially convergent
+sums, without details).
 Readings, since the paper fixes no neutralisation convention: the sums diverge (1D,
 2D) or are conditionally convergent (3D) for a non-neutral charge set, so the
 constant / k = 0 part is the one that makes the result independent of eta:

@@ -1,5 +1,5 @@
 // Periodic Green's function of Eq. 15 for k0 = 0 and G0 = 1/r, evaluated by Ewald-type
-// splitting (the paper computes it by "exponentially convergent sums"):
+// splitting (the paper names exponentially convergent sums without details):
 //   3D: sum_l erfc(eta|r+l|)/|r+l| + (4 pi/V) sum_{k!=0} e^{-k^2/4eta^2} cos(k.r)/k^2 - pi/(eta^2 V)
 //   2D: sum_l erfc(eta|r+l|)/|r+l| + (pi/A) sum_{k!=0} cos(k.rho)/k [e^{kz} erfc(k/2eta+eta z)
 //       + e^{-kz} erfc(k/2eta-eta z)] - (2 pi/A)[z erf(eta z) + e^{-eta^2 z^2}/(eta sqrt(pi))]
