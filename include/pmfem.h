@@ -247,6 +247,15 @@ int pmfem_operator_export(pmfem_t h, int which, int32_t* rowptr, int32_t* col, d
  */
 int pmfem_device_info(pmfem_t h, int64_t* out, int n);
 
+/*
+ * Wall-clock seconds of the set-up stages of the handle (host, n doubles; stages beyond 7
+ * read 0): out[0] PBC pairing and fold (Sec. 2.2, Eq. 18), out[1] periodized local operators
+ * (Eqs. 7-12, 14a, 14d), out[2] grid and stencils (Eq. 16), out[3] PGF spectrum (Eq. 15),
+ * out[4] near-element correction (Eq. 14c), out[5] point precorrection (BAIM step 4), all of
+ * the last pmfem_set_periodicity; out[6] device layout and upload of the last device build.
+ */
+int pmfem_setup_times(pmfem_t h, double* out, int n);
+
 /* Grid of Eq. 16 as set up: dims[3], fft[3], origin[3], delta[3] (host). */
 int pmfem_grid_info(pmfem_t h, int32_t* dims, int32_t* fft, double* origin, double* delta);
 /* PGF spectrum (Eq. 15 on the grid, transformed), reduced by symmetry:

@@ -68,6 +68,7 @@ SIGNATURES = {
     "pmfem_batch_get_m": (_c.c_int, [_vp, _vp, _vp]),
     "pmfem_batch_llg_step": (_c.c_int, [_vp, _dbl, _c.c_int, _vp]),
     "pmfem_batch_sync": (_c.c_int, [_vp]),
+    "pmfem_setup_times": (_c.c_int, [_vp, _vp, _c.c_int]),
     "pmfem_grid_info": (_c.c_int, [_vp, _vp, _vp, _vp, _vp]),
     "pmfem_export_spectrum": (_c.c_int, [_vp, _vp]),
     "pmfem_folded_positions": (_c.c_int, [_vp, _vp]),
@@ -275,6 +276,12 @@ class Pmfem:
         d["projection_exceptions"] = int(out[9])
         d["tile"] = (int(out[10]), int(out[11]))
         return d
+
+    def setup_times(self) -> dict:
+        out = np.zeros(7)
+        self._ck(self._lib.pmfem_setup_times(self.h, out.ctypes.data, 7))
+        keys = ("pairing", "operators", "grid", "spectrum", "near_elements", "precorrection", "device")
+        return dict(zip(keys, out.tolist()))
 
     def grid_info(self):
         dims = np.zeros(3, np.int32)

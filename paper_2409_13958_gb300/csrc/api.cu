@@ -1,4 +1,5 @@
 // C-ABI of libpmfem (declared in include/pmfem.h).
+#include <chrono>
 #include <cmath>
 #include <cstring>
 #include <mutex>
@@ -288,11 +289,13 @@ int ensure_device(pmfem_t h) {
   if (!h->side) PMFEM_CK(h, cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking));
   if (!h->ev_fork) PMFEM_CK(h, cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
   if (!h->ev_join) PMFEM_CK(h, cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
+  const auto t0 = std::chrono::steady_clock::now();
   int rc = (h->prec == PMFEM_FP64) ? build_device(h, h->d64) : build_device(h, h->d32);
   if (rc) {
     free_device(h);
     return rc;
   }
+  h->s.t_stage[6] = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   h->dev_prec = h->prec;
   h->dev_ready = true;
   noalloc_lookup(h, &h->noalloc_why);
@@ -763,6 +766,12 @@ int pmfem_device_info(pmfem_t h, int64_t* out, int n) {
   int rc = ensure_device(h);
   if (rc) return rc;
   for (int i = 0; i < n; ++i) out[i] = i < 12 ? h->dev_info[i] : 0;
+  return OK;
+}
+
+int pmfem_setup_times(pmfem_t h, double* out, int n) {
+  if (!h || !out || n <= 0) return EINVAL_;
+  for (int i = 0; i < n; ++i) out[i] = i < 7 ? h->s.t_stage[i] : 0.0;
   return OK;
 }
 

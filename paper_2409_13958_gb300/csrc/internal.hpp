@@ -76,6 +76,9 @@ struct Setup {
   std::vector<double> ghat;          // (F0/2+1)(F1/2+1)(F2/2+1), x fastest, unscaled
   std::vector<int32_t> box;          // Np x 3 grid box of each unknown (folded position)
   bool ready = false;
+  // ---- wall seconds of the set-up stages (pmfem_setup_times): pairing + fold, local
+  // operators, grid, PGF spectrum, near elements, point precorrection, device layout + upload
+  double t_stage[7] = {0, 0, 0, 0, 0, 0, 0};
 };
 
 // Device-side layout: unknowns re-ordered by grid box (z-major, then y, then x) so that

@@ -10,6 +10,7 @@
 // pattern when k is a neighbour of n (always so for touching elements), otherwise in a
 // separate sparse matrix.
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <map>
 #include <unordered_map>
@@ -221,12 +222,24 @@ int setup_near_elements(Setup& s, Error& err) {
 int run_setup(Setup& s, Error& err) {
   int rc;
   s.ready = false;
+  auto t0 = std::chrono::steady_clock::now();
+  auto lap = [&](int i) {
+    auto t1 = std::chrono::steady_clock::now();
+    s.t_stage[i] = std::chrono::duration<double>(t1 - t0).count();
+    t0 = t1;
+  };
   if ((rc = setup_pairing(s, err))) return rc;
+  lap(0);
   if ((rc = setup_operators(s, err))) return rc;
+  lap(1);
   if ((rc = setup_grid(s, err))) return rc;
+  lap(2);
   if ((rc = setup_spectrum(s, err))) return rc;
+  lap(3);
   if ((rc = setup_near_elements(s, err))) return rc;
+  lap(4);
   if ((rc = setup_precorrection(s, err))) return rc;
+  lap(5);
   s.ready = true;
   return OK;
 }
