@@ -246,3 +246,40 @@ def test_second_stream_precorrection_is_ordered(prec):
         out.append(mo)
     assert _rel(out[0].double().cpu().numpy(), out[1].double().cpu().numpy()) <= 1e-6
     h.destroy()
+
+
+LAYOUTS = {
+    # (tile rows, tile planes, sort window, column-delta bits)
+    "tiles4x2_window256_int32": (4, 2, 256, 32),
+    "tiles16x2_int32": (16, 2, 0, 32),
+    "tiles4x4_window64_int16": (4, 4, 64, 16),
+}
+
+
+@pytest.mark.parametrize("prec", [0, 1, 2])
+@pytest.mark.parametrize("layout", sorted(LAYOUTS))
+@pytest.mark.parametrize("name", ["prism_1d_protruding", "sphere_3d_nt", "film_20x20x2"])
+def test_field_parity_other_layouts(name, layout, prec):
+    """The same parity on other device layouts: other box-order tiles and sort windows, and the
+    32-bit column deltas (every operator then stores 32-bit deltas)."""
+    from paper_2409_13958_gb300 import PMFEM_ALL, PMFEM_MS
+    mesh, ob, grid, p, nb, f = _problem(name)
+    h = _lib(mesh, grid, p, nb, f, prec)
+    ty, tz, win, bits = LAYOUTS[layout]
+    h.set_layout(ty, tz, win, bits)
+    info = h.device_info()
+    assert info["tile"] == (ty, tz)
+    if bits == 32:
+        assert all(info[k]["col_bits"] == 32 for k in ("adjacency", "precorrection", "projection"))
+    dt = torch.float64 if prec == 0 else torch.float32
+    m = meshgen.m_random(ob.Np, seed=19)
+    m = m.astype(np.float32).astype(np.float64) if prec else m      # the same input on both sides
+    mt = torch.tensor(m, dtype=dt, device="cuda")
+    H = torch.empty_like(mt)
+    for comps, ref in ((PMFEM_MS, ob.h_ms(m, "paim")), (PMFEM_ALL, ob.h_eff(m, "paim"))):
+        H.fill_(float("nan"))
+        h.field(mt, H, comps)
+        h.sync()
+        err = _rel(H.double().cpu().numpy(), ref)
+        assert err <= TOL[prec], (name, layout, prec, comps, err)
+    h.destroy()
