@@ -21,7 +21,7 @@ import numpy as np
 
 __all__ = [
     "Mesh", "kuhn_box", "film_cell", "cube_cell", "prism_cell", "sphere_lattice",
-    "wire_cell", "batch_cells", "m_tilted", "m_random", "m_vortex", "m_uniform", "net_init",
+    "wire_cell", "batch_cells", "granular_cell", "m_tilted", "m_random", "m_vortex", "m_uniform", "net_init",
 ]
 
 
@@ -121,6 +121,49 @@ def prism_cell(nx=4, ny=4, nz=4, h=1e-9, jitter=0.15, seed=0) -> Mesh:
     """Square prism filling a 1D-periodic (z) cell; x and y are open."""
     xyz, tets = kuhn_box(nx, ny, nz, h, jitter=jitter, seed=seed)
     return Mesh(xyz, tets, (0.0, 0.0, nz * h), name=f"prism_{nx}x{ny}x{nz}")
+
+
+@dataclass
+class Grains:
+    """Seeded grain structure of a cell: the grain of every tetrahedron, per-grain random
+    orthonormal crystal axes (rows), anisotropy constants, and the exchange stiffness of every
+    tetrahedron (A inside grains, A_iex in the boundary layer)."""
+    tet_grain: np.ndarray     # (T,) int32
+    axes: np.ndarray          # (G, 3, 3)
+    K1: np.ndarray            # (G,) J/m^3
+    Ku: np.ndarray            # (G,) J/m^3
+    u: np.ndarray             # (G, 3) unit uniaxial axes
+    A_tet: np.ndarray         # (T,) J/m
+
+
+def granular_cell(n=8, h=1e-9, grains=6, K1=-4.5e3, Ku=0.0, A=1.3e-11, A_iex=0.2e-11, layer=0.6,
+                  jitter=0.15, seed=0):
+    """3D-periodic cube of n^3 Kuhn-split hexes with Voronoi grains of periodic seeds.
+
+    A tetrahedron belongs to the grain of the seed nearest (periodically) to its centroid; it is
+    in the boundary layer, with exchange stiffness A_iex, when the second-nearest seed is less
+    than layer * h farther away than the nearest.  Crystal axes are seeded random rotations.
+    Returns (Mesh, Grains)."""
+    mesh = cube_cell(n, h=h, jitter=jitter, seed=seed)
+    L = n * h
+    rng = np.random.default_rng(seed + 101)
+    seeds = rng.uniform(0, L, size=(grains, 3))
+    cen = mesh.xyz[mesh.tets].mean(axis=1)
+    d = cen[:, None, :] - seeds[None, :, :]
+    d -= np.round(d / L) * L
+    dist = np.linalg.norm(d, axis=2)
+    order = np.argsort(dist, axis=1)
+    tg = order[:, 0].astype(np.int32)
+    gap = dist[np.arange(dist.shape[0]), order[:, 1]] - dist[np.arange(dist.shape[0]), order[:, 0]]
+    A_tet = np.where(gap < layer * h, A_iex, A)
+    axes = np.empty((grains, 3, 3))
+    for g in range(grains):
+        q, r = np.linalg.qr(rng.normal(size=(3, 3)))
+        axes[g] = (q * np.sign(np.diag(r))[None, :]).T
+    u = rng.normal(size=(grains, 3))
+    u /= np.linalg.norm(u, axis=1, keepdims=True)
+    gr = Grains(tg, axes, np.full(grains, float(K1)), np.full(grains, float(Ku)), u, A_tet)
+    return mesh, gr
 
 
 def _fibonacci_sphere(n: int, R: float) -> np.ndarray:
