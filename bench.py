@@ -50,6 +50,10 @@ def parse(argv=None):
     ap.add_argument("--no-bf16", action="store_true", help="skip the BF16-split leg")
     ap.add_argument("--no-batch", action="store_true", help="skip the 64-cell batch leg")
     ap.add_argument("--no-surrogate", action="store_true", help="skip the learned-surrogate leg")
+    ap.add_argument("--no-host-setup", action="store_true",
+                    help="skip timing the host set-up beside the GPU set-up of the same mesh")
+    ap.add_argument("--no-cufft", action="store_true", help="skip the cuFFT convolution comparison")
+    ap.add_argument("--repeats", type=int, default=5, help="repeats of the timed steps for the median")
     ap.add_argument("--out", default=None, help="also write the JSON line to this file")
     return ap.parse_args(argv)
 
@@ -322,6 +326,91 @@ def run_reference(args):
     return 0
 
 
+# ------------------------------------------------------------------ comparisons beside the path
+def cufft_leg(h, stream, reps: int = 20):
+    """The FFT convolution of BAIM step 2 done by cuFFT (through torch.fft) on the same grid
+    and FFT shape, as the comparison baseline for the library's own five FFT passes: zero-pad
+    Q to the FFT shape, R2C, multiply by the real PGF spectrum, C2R, crop.  Times one
+    convolution with CUDA events on the launching stream."""
+    import torch
+    dims, fft, _, _ = h.grid_info()
+    N0, N1, N2 = (int(x) for x in dims)
+    F0, F1, F2 = (int(x) for x in fft)
+    g = torch.Generator(device="cuda").manual_seed(0)
+    Q = torch.randn((N2, N1, N0), device="cuda", dtype=torch.float32, generator=g)        # x fastest
+    Gh = torch.randn((F2, F1, F0 // 2 + 1), device="cuda", dtype=torch.float32, generator=g)
+
+    def conv():
+        S = torch.fft.rfftn(Q, s=(F2, F1, F0))
+        return torch.fft.irfftn(S * Gh, s=(F2, F1, F0))[:N2, :N1, :N0]
+
+    for _ in range(3):
+        conv()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(reps):
+        conv()
+    b.record(stream)
+    b.synchronize()
+    return {"us_per_convolution": 1e3 * a.elapsed_time(b) / reps, "fft": [F0, F1, F2], "grid": [N0, N1, N2],
+            "how": "torch.fft rfftn (zero-padded to the FFT shape) x real spectrum, irfftn, crop; FP32"}
+
+
+def _oracle_worker(args):
+    nodes, budget = args
+    ob, grid = oracle_sample(nodes)
+    n, el = time_oracle(ob, budget)
+    return ob.Np, n, el
+
+
+def cpu_baseline_leg(nodes: int = 6000, budget_s: float = 12.0):
+    """The oracle (O2, NumPy/SciPy FP64, as it stands) on a bounded sample of the wire: RK4
+    steps in one process (one core), and the same in one process per host core at once (all
+    cores; NumPy's FFT and sparse products are single-threaded, so processes are how the
+    oracle uses the host).  Processes are spawned, never forked, from this GPU process."""
+    import multiprocessing as mp
+    ob, grid = oracle_sample(nodes)
+    n1, el1 = time_oracle(ob, budget_s)
+    one = ob.Np * 4 * n1 / el1
+    cores = os.cpu_count() or 1
+    saved = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
+    for k in saved:
+        os.environ[k] = "1"
+    try:
+        with mp.get_context("spawn").Pool(cores) as pool:
+            res = pool.map(_oracle_worker, [(nodes, budget_s)] * cores)
+    finally:
+        for k, v in saved.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+    allv = sum(np_ * 4 * n / el for np_, n, el in res)
+    return {"value": allv, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"oracle O2 RK4 steps (NumPy/SciPy FP64) on a {ob.Np}-unknown wire of the same geometry, "
+                      f"grid {grid}, set-up excluded: {cores} processes at once, about {budget_s:.0f} s each "
+                      f"(value = their summed node-field-evals/s)",
+            "one_core": {"value": one, "cores": 1, "steps": n1, "seconds": round(el1, 2)}}
+
+
+def method_error_record():
+    """P-AIM (O2) against the direct definition (O1) on the wire geometry at the benchmark's
+    node-per-cell density and settings, as written by tests/golden/method_error_wire.py (an
+    oracle-only script)."""
+    p = os.path.join(ROOT, "tests", "golden", "method_error_wire.json")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p))
+    for r in d["o2"]:
+        if r["grid"] == d["grid"] and r["near_boxes"] == NEAR_BOXES and r["near_elem_factor"] == NEAR_ELEM:
+            return {"vortex_m": r["vortex_vs_O1_same_factor"], "random_m": r["random_vs_O1_same_factor"],
+                    "sample": f"{d['samples']} sampled unknowns of a {d['unknowns']}-unknown wire of the same geometry, "
+                              f"grid {d['grid']} (the benchmark's nodes per grid cell), p 3, near_boxes {NEAR_BOXES}",
+                    "source": "tests/golden/method_error_wire.json (oracle only)"}
+    return None
+
+
 # ------------------------------------------------------------------ GPU leg
 def bf16_leg(h, m0, dt, comps, H32, H64, stream, dist, world, Np, args):
     """BF16-split precision on the same workload: its speed, and its field error per term
@@ -539,11 +628,25 @@ def run_native(args):
     t0 = time.time()
     mesh = make_mesh(args.nodes)
     t_mesh = time.time() - t0
+    setup = {}
+    if not args.no_host_setup:
+        # the host set-up of the same mesh, timed for comparison (its handle is not used)
+        t0 = time.time()
+        hh = Pmfem.create_mesh(mesh.xyz, mesh.tets, MS, AEX, ALPHA)
+        hh.set_aim(*GRID, P_ORDER, NEAR_BOXES, NEAR_ELEM)
+        hh.set_periodicity(0.0, 0.0, WIRE["L"])
+        setup["host_s"] = round(time.time() - t0, 2)
+        setup["host_stages_s"] = {k: round(v, 3) for k, v in hh.setup_times().items() if k != "device"}
+        hh.destroy()
+        del hh
     t0 = time.time()
     h = Pmfem.create_mesh(mesh.xyz, mesh.tets, MS, AEX, ALPHA)
     h.set_aim(*GRID, P_ORDER, NEAR_BOXES, NEAR_ELEM)
+    h.set_setup_device(True)          # FP64 spectrum, near-element integrals, precorrection on the GPU
     h.set_periodicity(0.0, 0.0, WIRE["L"])
     t_setup = time.time() - t0
+    setup["gpu_s"] = round(t_setup, 2)
+    setup["gpu_stages_s"] = {k: round(v, 3) for k, v in h.setup_times().items() if k != "device"}
     Np = h.num_unknowns()
     pos = h.folded_positions()
     m0 = initial_m(pos)
@@ -585,6 +688,24 @@ def run_native(args):
     ck = clocks.stop()
     ms = dist.max(e0.elapsed_time(e1))
     value = whole_job_value(world, Np * 4 * args.steps, ms)
+    # the same timed region repeated (at least 25 steps = 100 evaluations each): the median of
+    # the repeats beside the headline
+    k_rep = max(25, args.steps)
+    rep_ms = []
+    for _ in range(max(0, args.repeats)):
+        torch.cuda.synchronize()
+        dist.barrier()
+        e0.record(stream)
+        for _ in range(k_rep):
+            h.llg_step(dt, 1, stream)
+        e1.record(stream)
+        e1.synchronize()
+        rep_ms.append(dist.max(e0.elapsed_time(e1)) / k_rep)
+    repeats = None
+    if rep_ms:
+        med = float(np.median(rep_ms))
+        repeats = {"steps_each": k_rep, "evaluations_each": 4 * k_rep, "ms_per_step": [round(x, 4) for x in rep_ms],
+                   "median_ms_per_step": med, "median_value": world * Np * 4 / (med * 1e-3)}
     # per-kernel durations: the same K steps again with a CUDA-event pair around every launch
     # on the launching stream (the library then launches kernel by kernel instead of replaying
     # the graph, so this pass is timed apart from the headline)
@@ -663,7 +784,30 @@ def run_native(args):
                 "fp32_rel_l2_same_input_by_term": rel_same}
         fp64["fp32_speedup"] = value / fp64["value"]
     bf16 = bf16_leg(h, m0, dt, comps, H32, H64 if fp64 else None, stream, dist, world, Np, args) if not args.no_bf16 else None
+    cufft = None
+    if not args.no_cufft:
+        h.set_precision(PMFEM_FP32)
+        cufft = cufft_leg(h, stream)
     h.destroy()
+
+    # field accuracy of the headline (FP32) path, stated beside the number: against the FP64 GPU
+    # path (which equals the oracle's P-AIM to 1e-10 in the tests), per term, on the benchmark's
+    # m and on an m both represent exactly; and the method's own error (P-AIM against the
+    # direct definition) from the oracle study of this geometry and density
+    accuracy = {"fp32_vs_fp64_by_term": fp64.get("fp32_rel_l2_by_term") if fp64 else None,
+                "fp32_vs_fp64_same_input_by_term": fp64.get("fp32_rel_l2_same_input_by_term") if fp64 else None,
+                "fp32_tolerance": 1e-5,
+                "bf16split_vs_fp64_by_term": (bf16 or {}).get("rel_l2_by_term"),
+                "bf16split_tolerance": 3e-3,
+                "method_rel_l2_vs_O1": method_error_record()}
+    if fp64:
+        over = {k: v for k, v in fp64["fp32_rel_l2_by_term"].items() if v > 1e-5}
+        accuracy["fp32_terms_above_tolerance"] = over
+    if cufft is not None:
+        n_eval = max(1, prof.get("charges", (1, 0.0))[0])
+        cufft["own_five_passes_us_per_evaluation"] = sum(1e3 * t for k, (c, t) in prof.items()
+                                                         if c and k.startswith("fft_")) / n_eval
+        cufft["own_vs_cufft"] = cufft["own_five_passes_us_per_evaluation"] / cufft["us_per_convolution"]
 
     # roofline of the dominant kernel
     peak, peak_kind = measured_peaks()
@@ -691,7 +835,8 @@ def run_native(args):
                    "l2": "inputs larger than L2 (operator data streamed every evaluation)",
                    "interpolation": ("two passes: precorrection on a second stream during projection + FFT, "
                                      "then the stencil" if sizes.get("split") else "one fused pass after the FFT"),
-                   "parallelism": f"replicas x{world}", "setup_s": round(t_setup, 1), "mesh_s": round(t_mesh, 1)},
+                   "parallelism": f"replicas x{world}", "setup_s": round(t_setup, 1), "mesh_s": round(t_mesh, 1),
+                   "setup": setup},
         "clocks": ck,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": step_bytes, "d2h_bytes_per_step": step_bytes,
                 "steps": k2},
@@ -701,8 +846,11 @@ def run_native(args):
                      "traffic": ncu_traffic(dom),
                      "timing": "mean launch duration, CUDA events on the launching stream, over the profiled "
                                "pass of the same K steps"},
+        "repeats": repeats,
+        "accuracy": accuracy,
         "fp64": fp64 or None,
         "bf16split": bf16,
+        "cufft": cufft,
         "kernels": per,
         "kernels_pass": "a second pass of the same K steps, launched kernel by kernel with a CUDA-event pair "
                         "around every launch; the headline pass replays each step's captured CUDA graph",
@@ -712,11 +860,7 @@ def run_native(args):
     if not args.no_surrogate:
         line["surrogate"] = surrogate_leg(args, dist, world)
     if rank == 0 and not args.no_cpu:
-        ob, grid = oracle_sample(6000)
-        n, el = time_oracle(ob, 15.0)
-        line["cpu_baseline"] = {"value": ob.Np * 4 * n / el, "unit": UNIT, "cores": cpu_cores_used(), "kind": "oracle",
-                                "sample": f"{n} oracle O2 RK4 steps (NumPy/SciPy FP64) on a {ob.Np}-unknown wire of "
-                                          f"the same geometry, grid {grid}; set-up excluded"}
+        line["cpu_baseline"] = cpu_baseline_leg()
     dist.close()
     if rank == 0:
         print(json.dumps(line))

@@ -57,6 +57,7 @@ typedef struct pmfem_state* pmfem_t;
 #define PMFEM_ENONFINITE -5   /* NaN/Inf met in an input or a result (device check)      */
 #define PMFEM_ETIMEOUT   -6   /* a bounded device wait ran out                          */
 #define PMFEM_ESTATE     -7   /* call out of order (e.g. field before set_periodicity)  */
+#define PMFEM_ENOCONV    -8   /* an iterative solve (Newton) did not converge            */
 
 /* precision modes */
 #define PMFEM_FP64      0
@@ -74,10 +75,11 @@ typedef struct pmfem_state* pmfem_t;
 #define PMFEM_BF16_EXCHANGE     16   /* periodized Laplacian of Eq. 8                       */
 
 /* field component bitmask for pmfem_field */
-#define PMFEM_EX 1
-#define PMFEM_MS 2
-#define PMFEM_AP 4
-#define PMFEM_ALL 7
+#define PMFEM_EX 1      /* exchange (Eqs. 7-12)                                                */
+#define PMFEM_MS 2      /* magnetostatic (Eq. 14)                                              */
+#define PMFEM_AP 4      /* applied field                                                        */
+#define PMFEM_AN 8      /* anisotropy (pmfem_set_anisotropy; zero when none is set)            */
+#define PMFEM_ALL 15
 
 /* Library version string and the last error message of a handle (never NULL). */
 const char* pmfem_version(void);
@@ -119,6 +121,46 @@ int pmfem_set_aim(pmfem_t h, int Nx, int Ny, int Nz, int order_p, int near_boxes
  * May be called again (with new periods) to redo the set-up.
  */
 int pmfem_set_periodicity(pmfem_t h, double L1, double L2, double L3);
+
+/*
+ * Local terms of Eq. 3 beyond exchange (the paper's granular example, Sec. 4.4: grains with
+ * their own crystal axes and a reduced exchange across grain boundaries).
+ *
+ * pmfem_set_exchange_per_tet: exchange stiffness of every tetrahedron, A_tet host T doubles
+ * [J/m] (>= 0), in place of the uniform A of pmfem_create_mesh: the exchange operator becomes
+ * -(2/(mu0 Ms)) V^-1 K_A with (K_A)_nk = sum_e A_e V_e grad(phi_n).grad(phi_k) (Eq. 8 with A
+ * inside the element sum; tetrahedra of a grain-boundary layer carry the inter-grain A_iex).
+ * NULL returns to the uniform A.  Takes effect at the next pmfem_set_periodicity.
+ *
+ * pmfem_set_anisotropy: the grain of every tetrahedron (tet_grain, host T int32 in
+ * [0, n_grains)) and per grain its crystal axes (axes, host n_grains x 9 doubles: three unit
+ * rows a1, a2, a3), cubic constant K1 [J/m^3] (host n_grains or NULL) and uniaxial constant Ku
+ * [J/m^3] with axis u (host n_grains and n_grains x 3, or both NULL).  With a_i = m . a_i the
+ * fields are -(2 K1/(mu0 Ms)) sum_i a_i (a_j^2 + a_k^2) a_i and (2 Ku/(mu0 Ms)) (m.u) u; the
+ * nodal field is the volume-weighted mean over the grains of the tetrahedra at the node (the
+ * energy lumped to the nodes).  It enters pmfem_field under PMFEM_AN (and PMFEM_ALL), the RK4
+ * and implicit steps (the implicit step's Jacobian leaves it out: its Newton iteration becomes
+ * a quasi-Newton iteration for it), in the field kernel's epilogue.  Batches ignore it.
+ * tet_grain NULL removes it.  Drops the handle's device data (the state m included); EINVAL
+ * for grains out of range, axes that are not unit rows, or non-finite constants.
+ */
+int pmfem_set_exchange_per_tet(pmfem_t h, const double* A_tet);
+int pmfem_set_anisotropy(pmfem_t h, const int32_t* tet_grain, int n_grains, const double* K1, const double* axes,
+                         const double* Ku, const double* u);
+
+/*
+ * Where pmfem_set_periodicity evaluates the FP64 set-up arithmetic that grows with the mesh
+ * and the grid (the paper does it once, in preprocessing, Sec. 4): use_gpu 0 (default) on
+ * the host's threads; 1 as CUDA kernels on the current device, in FP64, for the PGF spectrum
+ * (Eq. 15 by Ewald-type sums on the grid of Eq. 16, and its transform), the exact near-element
+ * integrals of Eq. 14c and the point precorrection of BAIM step 4 (Sec. 3.2).  Both evaluate
+ * the same formulas in the same order and agree to the rounding of the two sides' math
+ * libraries.  With 1, pmfem_set_periodicity allocates temporary device memory (freed before it
+ * returns), synchronises the device, and fails with ECUDA (no GPU) or ENOMEM.  Pairing, the
+ * local operators, the grid and the placement search stay on the host.  Takes effect at the
+ * next pmfem_set_periodicity.  EINVAL for other values.
+ */
+int pmfem_set_setup_device(pmfem_t h, int use_gpu);
 
 /*
  * Device layout tuning (no paper counterpart; it changes speed, not results beyond
@@ -203,6 +245,39 @@ int pmfem_get_m(pmfem_t h, void* m, void* stream);
  * the surrogate run the launches directly.  dt <= 0 or nsteps < 0 -> EINVAL.
  */
 int pmfem_llg_step(pmfem_t h, double dt, int nsteps, void* stream);
+
+/*
+ * Implicit midpoint steps of Eq. 2 with Newton-Krylov (the paper's way of integrating the
+ * discrete LLG system, Sec. 2.2 and Sec. 4: implicit schemes whose Newton iterations solve
+ * their linear systems with a preconditioned Krylov solver).  One step of size dt [s]:
+ *   y = m_n + dt f((m_n + y)/2),  f(m) = -g [m x H(m) + alpha m x (m x H(m))],
+ * g = gamma0 / (1 + alpha^2); the rule keeps |m| of every node (no renormalisation).  Newton
+ * starts from y = m_n; each Newton iteration solves J d = -R by restarted GMRES, right-
+ * preconditioned by 3x3 blocks per node (J with the field's linear part replaced by the
+ * exchange operator's own coefficient), where every product J v costs one evaluation of the
+ * field's linear part (the path of pmfem_field with PMFEM_EX | PMFEM_MS).  Works on the internal
+ * state (pmfem_set_m / pmfem_get_m) at the handle's precision; synchronises stream at every
+ * Krylov iteration (its scalars go to the host).
+ *   opts   may be NULL; zero fields take the defaults:
+ *            newton_tol  step converged when |d| <= newton_tol |y|   (1e-10 FP64, 1e-5 FP32)
+ *            krylov_tol  GMRES relative residual per Newton step       (1e-8 FP64, 1e-4 FP32)
+ *            restart     GMRES cycle length, 1..64                      (30)
+ *            max_newton  Newton iterations per step                     (20)
+ *            max_krylov  GMRES iterations per Newton iteration          (600)
+ *   stats  host int64[4] or NULL: Newton iterations, Krylov iterations, field evaluations,
+ *          steps completed (also on failure).
+ * ENOCONV when Newton does not converge: the state stays at the start of the failed step.
+ * EINVAL for dt <= 0, nsteps < 0, restart > 64 or a tolerance >= 1.
+ */
+typedef struct pmfem_implicit_opts {
+  double newton_tol;
+  double krylov_tol;
+  int restart;
+  int max_newton;
+  int max_krylov;
+} pmfem_implicit_opts;
+int pmfem_llg_step_implicit(pmfem_t h, double dt, int nsteps, const pmfem_implicit_opts* opts, int64_t* stats,
+                            void* stream);
 
 /*
  * Per-launch timing for measurement.  pmfem_profile(h, 1) starts recording a CUDA event

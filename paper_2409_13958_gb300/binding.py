@@ -12,11 +12,12 @@ import os
 import numpy as np
 
 PMFEM_FP64, PMFEM_FP32, PMFEM_BF16SPLIT = 0, 1, 2
-PMFEM_EX, PMFEM_MS, PMFEM_AP, PMFEM_ALL = 1, 2, 4, 7
+PMFEM_EX, PMFEM_MS, PMFEM_AP, PMFEM_AN, PMFEM_ALL = 1, 2, 4, 8, 15
 (PMFEM_BF16_PRECORRECTION, PMFEM_BF16_PROJECTION, PMFEM_BF16_CHARGES, PMFEM_BF16_GRADIENT,
  PMFEM_BF16_EXCHANGE) = 1, 2, 4, 8, 16
 
-_ERRORS = {-1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "EMESH", -5: "ENONFINITE", -6: "ETIMEOUT", -7: "ESTATE"}
+_ERRORS = {-1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "EMESH", -5: "ENONFINITE", -6: "ETIMEOUT", -7: "ESTATE",
+           -8: "ENOCONV"}
 
 _c = ctypes
 _vp, _i32, _i64, _dbl = _c.c_void_p, _c.c_int32, _c.c_int64, _c.c_double
@@ -30,6 +31,9 @@ SIGNATURES = {
     "pmfem_set_aim": (_c.c_int, [_vp, _c.c_int, _c.c_int, _c.c_int, _c.c_int, _c.c_int, _dbl]),
     "pmfem_set_periodicity": (_c.c_int, [_vp, _dbl, _dbl, _dbl]),
     "pmfem_set_layout": (_c.c_int, [_vp, _c.c_int, _c.c_int, _c.c_int, _c.c_int]),
+    "pmfem_set_setup_device": (_c.c_int, [_vp, _c.c_int]),
+    "pmfem_set_exchange_per_tet": (_c.c_int, [_vp, _vp]),
+    "pmfem_set_anisotropy": (_c.c_int, [_vp, _vp, _c.c_int, _vp, _vp, _vp, _vp]),
     "pmfem_set_precision": (_c.c_int, [_vp, _c.c_int]),
     "pmfem_set_bf16_operators": (_c.c_int, [_vp, _c.c_int]),
     "pmfem_set_applied_field": (_c.c_int, [_vp, _dbl, _dbl, _dbl]),
@@ -41,6 +45,7 @@ SIGNATURES = {
     "pmfem_set_m": (_c.c_int, [_vp, _vp, _vp]),
     "pmfem_get_m": (_c.c_int, [_vp, _vp, _vp]),
     "pmfem_llg_step": (_c.c_int, [_vp, _dbl, _c.c_int, _vp]),
+    "pmfem_llg_step_implicit": (_c.c_int, [_vp, _dbl, _c.c_int, _vp, _vp, _vp]),
     "pmfem_profile": (_c.c_int, [_vp, _c.c_int]),
     "pmfem_profile_read": (_c.c_int, [_vp, _vp, _vp, _c.c_int]),
     "pmfem_sync": (_c.c_int, [_vp]),
@@ -94,6 +99,12 @@ def load_library(path: str | None = None):
             f.argtypes = args
         _LIB = lib
     return _LIB
+
+
+class ImplicitOpts(ctypes.Structure):
+    """pmfem_implicit_opts (include/pmfem.h); zero fields select the defaults."""
+    _fields_ = [("newton_tol", ctypes.c_double), ("krylov_tol", ctypes.c_double), ("restart", ctypes.c_int),
+                ("max_newton", ctypes.c_int), ("max_krylov", ctypes.c_int)]
 
 
 class PmfemError(RuntimeError):
@@ -154,6 +165,26 @@ class Pmfem:
 
     def set_periodicity(self, L1=0.0, L2=0.0, L3=0.0):
         self._ck(self._lib.pmfem_set_periodicity(self.h, L1, L2, L3))
+
+    def set_exchange_per_tet(self, A_tet=None):
+        a = None if A_tet is None else np.ascontiguousarray(A_tet, dtype=np.float64)
+        self._ck(self._lib.pmfem_set_exchange_per_tet(self.h, None if a is None else a.ctypes.data))
+
+    def set_anisotropy(self, tet_grain=None, axes=None, K1=None, Ku=None, u=None):
+        if tet_grain is None:
+            self._ck(self._lib.pmfem_set_anisotropy(self.h, None, 0, None, None, None, None))
+            return
+        tg = np.ascontiguousarray(tet_grain, dtype=np.int32)
+        ax = np.ascontiguousarray(axes, dtype=np.float64).reshape(-1, 9)
+        k1 = None if K1 is None else np.ascontiguousarray(K1, dtype=np.float64)
+        ku = None if Ku is None else np.ascontiguousarray(Ku, dtype=np.float64)
+        uu = None if u is None else np.ascontiguousarray(u, dtype=np.float64).reshape(-1, 3)
+        addr = lambda x: None if x is None else x.ctypes.data
+        self._ck(self._lib.pmfem_set_anisotropy(self.h, tg.ctypes.data, ax.shape[0], addr(k1), ax.ctypes.data,
+                                                addr(ku), addr(uu)))
+
+    def set_setup_device(self, use_gpu: bool):
+        self._ck(self._lib.pmfem_set_setup_device(self.h, int(bool(use_gpu))))
 
     def set_layout(self, tile_y=0, tile_z=0, sort_window=0, col_bits=0):
         self._ck(self._lib.pmfem_set_layout(self.h, tile_y, tile_z, sort_window, col_bits))
@@ -231,6 +262,16 @@ class Pmfem:
         self._ck(self._lib.pmfem_surrogate_stats(self.h, out.ctypes.data))
         return {"steps": int(out[0]), "net_stages": int(out[1]), "judged_stages": int(out[2]),
                 "judged_rel_l2": float(out[3])}
+
+    def llg_step_implicit(self, dt: float, nsteps: int = 1, newton_tol: float = 0.0, krylov_tol: float = 0.0,
+                          restart: int = 0, max_newton: int = 0, max_krylov: int = 0, stream=None) -> dict:
+        """Implicit midpoint steps (Newton-GMRES); returns the iteration counts."""
+        o = ImplicitOpts(newton_tol, krylov_tol, restart, max_newton, max_krylov)
+        st = np.zeros(4, dtype=np.int64)
+        rc = self._lib.pmfem_llg_step_implicit(self.h, dt, nsteps, ctypes.byref(o), st.ctypes.data, _stream(stream))
+        out = {"newton": int(st[0]), "krylov": int(st[1]), "field_evals": int(st[2]), "steps": int(st[3])}
+        self._ck(rc)
+        return out
 
     def llg_step(self, dt: float, nsteps: int = 1, stream=None):
         self._ck(self._lib.pmfem_llg_step(self.h, dt, nsteps, _stream(stream)))

@@ -10,6 +10,7 @@
 #include "../../include/pmfem.h"
 #include "device.hpp"
 #include "internal.hpp"
+#include "implicit.hpp"
 #include "state.hpp"
 
 using namespace pmfem;
@@ -90,6 +91,9 @@ void free_device(pmfem_t h) {
   h->m = h->mA = h->mB = h->acc = h->mF = h->hin = h->hout = nullptr;
   h->flag = nullptr;
   h->noalloc_base = nullptr;
+  h->imp_vec.clear();
+  h->imp_pinv = h->imp_c = h->imp_red = nullptr;
+  h->imp_prec = -1;
   h->dev_ready = false;
   h->dev_prec = -1;
 }
@@ -211,6 +215,44 @@ int build_device(pmfem_t h, DevOps<T>& d) {
     d.periodic[a] = s.periodic[a];
   }
   if ((rc = upload(h, L.perm.data(), L.perm.size(), &d.perm))) return rc;
+  if (!s.tet_grain.empty()) {
+    // volume share of every grain at every unknown (lumped nodal quadrature), internal order
+    const int G = (int)(s.grain_tab.size() / kGrainTab);
+    std::vector<std::vector<std::pair<int32_t, double>>> gw(s.Np);
+    for (int64_t e = 0; e < s.T; ++e) {
+      double X[4][3], gr[4][3];
+      for (int a = 0; a < 4; ++a)
+        for (int c = 0; c < 3; ++c) X[a][c] = s.xyz[3 * (int64_t)s.tets[4 * e + a] + c];
+      const double q = 0.25 * tet_grads(X, gr);
+      for (int a = 0; a < 4; ++a) {
+        auto& v = gw[s.lca[s.tets[4 * e + a]]];
+        bool found = false;
+        for (auto& x : v)
+          if (x.first == s.tet_grain[e]) {
+            x.second += q;
+            found = true;
+          }
+        if (!found) v.push_back({s.tet_grain[e], q});
+      }
+    }
+    std::vector<int32_t> ptr(s.Np + 1, 0), grain;
+    std::vector<double> w;
+    for (int64_t i = 0; i < s.Np; ++i) {
+      const int32_t uo = L.perm[i];
+      double tot = 0;
+      for (auto& x : gw[uo]) tot += x.second;
+      for (auto& x : gw[uo]) {
+        grain.push_back(x.first);
+        w.push_back(x.second / tot);
+      }
+      ptr[i + 1] = (int32_t)grain.size();
+    }
+    (void)G;
+    if ((rc = upload(h, ptr.data(), ptr.size(), &d.loc.ptr))) return rc;
+    if ((rc = upload(h, grain.data(), grain.size(), &d.loc.grain))) return rc;
+    if ((rc = upload_conv<T>(h, w.data(), w.size(), 1, 0, 1.0, &d.loc.w))) return rc;
+    if ((rc = upload_conv<T>(h, s.grain_tab.data(), s.grain_tab.size(), 1, 0, 1.0, &d.loc.tab))) return rc;
+  }
   // BF16-split: component masks of the operators stored in bfloat16 (adjacency components
   // 0-2 W^q, 3-5 E, 6-8 gradient, 9 exchange)
   const int bo = (sizeof(T) == 4 && h->prec == PMFEM_BF16SPLIT) ? h->bf16_ops : 0;
@@ -373,6 +415,200 @@ int run_llg(pmfem_t h, DevOps<T>& d, double dt, int nsteps, cudaStream_t st) {
   return OK;
 }
 
+// ------------------------------------------------------------------------------------
+// Implicit midpoint LLG steps with Newton-GMRES (kernels and formulas in implicit.cu).
+// The vectors of a step live in the C-ABI order; every field evaluation goes through the
+// handle's own path (permute in, the evaluation of pmfem_field), with the applied field for
+// the residual and without it for the Jacobian's products (the field's linear part).
+// ------------------------------------------------------------------------------------
+struct ImpOpts {
+  double newton_tol, krylov_tol;
+  int restart, max_newton, max_krylov;
+};
+
+template <typename T>
+int run_implicit(pmfem_t h, DevOps<T>& d, double dt, int nsteps, const ImpOpts& o, int64_t stats[4],
+                 cudaStream_t st) {
+  const int64_t n = d.Np, len = 3 * n;
+  const int k = o.restart;
+  const double g = kMu0 * kGammaE / (1.0 + h->s.alpha * h->s.alpha), alpha = h->s.alpha;
+  // work vectors (device, allocated with the handle's device data; a longer cycle adds more)
+  const int nvec = 9 + (k + 1);
+  if ((int)h->imp_vec.size() < nvec || h->imp_prec != h->dev_prec) {
+    h->imp_vec.clear();
+    for (int i = 0; i < nvec; ++i) {
+      void* p;
+      int rc = dalloc(h, &p, (size_t)len * sizeof(T));
+      if (rc) return rc;
+      h->imp_vec.push_back(p);
+    }
+    void* p;
+    int rc;
+    if ((rc = dalloc(h, &p, (size_t)9 * n * sizeof(T)))) return rc;
+    h->imp_pinv = p;
+    if ((rc = dalloc(h, &p, (size_t)std::max<int64_t>(n, 1) * sizeof(T)))) return rc;
+    h->imp_c = p;
+    if ((rc = dalloc(h, &p, (size_t)(kImpBlocks + 1) * (kMaxKrylov + 1) * sizeof(double)))) return rc;
+    h->imp_red = p;
+    h->imp_prec = h->dev_prec;
+    // the exchange operator's own coefficient of every unknown (preconditioner blocks)
+    std::vector<T> c(n, (T)0);
+    for (int64_t u = 0; u < n; ++u)
+      for (int32_t q = h->s.rowptr[u]; q < h->s.rowptr[u + 1]; ++q)
+        if (h->s.col[q] == u) c[u] = (T)h->s.Kp[q];
+    PMFEM_CK(h, cudaMemcpy(h->imp_c, c.data(), n * sizeof(T), cudaMemcpyHostToDevice));
+  }
+  T* m0 = (T*)h->imp_vec[0];
+  T* y = (T*)h->imp_vec[1];
+  T* mb = (T*)h->imp_vec[2];
+  T* Hb = (T*)h->imp_vec[3];
+  T* R = (T*)h->imp_vec[4];
+  T* x = (T*)h->imp_vec[5];
+  T* z = (T*)h->imp_vec[6];
+  T* w = (T*)h->imp_vec[7];
+  T* Av = (T*)h->imp_vec[8];
+  T** V = (T**)&h->imp_vec[9];
+  T* Pinv = (T*)h->imp_pinv;
+  const T* cdiag = (const T*)h->imp_c;
+  double* red = (double*)h->imp_red;                         // partial sums, then results
+  double* dres = red + (size_t)kImpBlocks * (kMaxKrylov + 1);
+  const int nblk = (int)std::min<int64_t>(kImpBlocks, std::max<int64_t>(1, (len + 255) / 256));
+  RkArgs none;
+  auto eval = [&](const T* xin, T* H, int comps) {
+    launch_perm_in(d, xin, (V4<T>*)h->mF, st);
+    enqueue_eval(h, d, (const V4<T>*)h->mF, H, comps, none, st);
+    ++stats[2];
+  };
+  auto dots = [&](int cnt, T* const* vs, const T* wv, double* out) -> int {
+    VecList<T> L;
+    for (int j = 0; j < cnt; ++j) L.p[j] = vs[j];
+    imp_multidot(len, L, cnt, wv, red, nblk, dres, st);
+    PMFEM_CK(h, cudaMemcpyAsync(out, dres, cnt * sizeof(double), cudaMemcpyDeviceToHost, st));
+    PMFEM_CK(h, cudaStreamSynchronize(st));
+    return OK;
+  };
+  // wv = a wv + sum coef_j vs_j
+  auto combine = [&](int cnt, T* const* vs, const double* coef, double a, T* wv) -> int {
+    VecList<T> L;
+    for (int j = 0; j < cnt; ++j) L.p[j] = vs[j];
+    PMFEM_CK(h, cudaMemcpyAsync(dres, coef, cnt * sizeof(double), cudaMemcpyHostToDevice, st));
+    imp_combine(len, L, cnt, dres, a, wv, st);
+    PMFEM_CK(h, cudaStreamSynchronize(st));   // coef is a host array of the caller
+    return OK;
+  };
+  auto Jv = [&](T* v, T* out) {   // out = J v
+    eval(v, Av, PMFEM_EX | PMFEM_MS);
+    imp_jvp(n, (const T*)mb, (const T*)Hb, (const T*)Av, (const T*)v, dt, g, alpha, out, st);
+  };
+  int rc;
+  launch_perm_out(d, (const V4<T>*)h->m, m0, st);
+  for (int step = 0; step < nsteps; ++step) {
+    PMFEM_CK(h, cudaMemcpyAsync(y, m0, len * sizeof(T), cudaMemcpyDeviceToDevice, st));
+    bool conv = false;
+    for (int it = 0; it < o.max_newton && !conv; ++it) {
+      imp_mid(n, (const T*)m0, (const T*)y, mb, st);
+      eval(mb, Hb, PMFEM_ALL);
+      imp_residual(n, (const T*)m0, (const T*)y, (const T*)mb, (const T*)Hb, dt, g, alpha, R, st);
+      imp_blocks(n, (const T*)mb, (const T*)Hb, cdiag, dt, g, alpha, Pinv, st);
+      ++stats[0];
+      // GMRES on J x = -R, x0 = 0, right-preconditioned by the blocks, restarted every k
+      double one = 1.0, mone = -1.0, zero = 0.0;
+      (void)zero;
+      PMFEM_CK(h, cudaMemsetAsync(x, 0, len * sizeof(T), st));
+      double b2;
+      if ((rc = dots(1, &R, R, &b2))) return rc;
+      const double bnorm = std::sqrt(b2);
+      double beta = bnorm;
+      // r = -R into V[0] (scaled below)
+      if ((rc = combine(1, &R, &mone, 0.0, V[0]))) return rc;
+      int kits = 0;
+      while (beta > o.krylov_tol * bnorm && beta > 0 && kits < o.max_krylov) {
+        double inv = 1.0 / beta;
+        if ((rc = combine(1, &V[0], &inv, 0.0, V[0]))) return rc;
+        std::vector<double> Hm((size_t)(k + 1) * k, 0.0), cs(k), sn(k), gv(k + 1, 0.0);
+        gv[0] = beta;
+        int j = 0;
+        for (; j < k && kits < o.max_krylov; ++j) {
+          imp_apply_blocks(n, (const T*)Pinv, (const T*)V[j], z, st);
+          Jv(z, w);
+          ++kits;
+          ++stats[1];
+          std::vector<double> h1(j + 1), h2(j + 1);
+          if ((rc = dots(j + 1, V, w, h1.data()))) return rc;
+          for (auto& t : h1) t = -t;
+          if ((rc = combine(j + 1, V, h1.data(), 1.0, w))) return rc;
+          if ((rc = dots(j + 1, V, w, h2.data()))) return rc;   // second pass (classical Gram-Schmidt twice)
+          for (auto& t : h2) t = -t;
+          if ((rc = combine(j + 1, V, h2.data(), 1.0, w))) return rc;
+          for (int i = 0; i <= j; ++i) Hm[(size_t)i * k + j] = -(h1[i] + h2[i]);
+          double wn2;
+          if ((rc = dots(1, &w, w, &wn2))) return rc;
+          const double wn = std::sqrt(wn2);
+          Hm[(size_t)(j + 1) * k + j] = wn;
+          if (wn > 0) {
+            double iw = 1.0 / wn;
+            if ((rc = combine(1, &w, &iw, 0.0, V[j + 1]))) return rc;
+          }
+          // Givens rotations of column j
+          for (int i = 0; i < j; ++i) {
+            const double a = Hm[(size_t)i * k + j], b = Hm[(size_t)(i + 1) * k + j];
+            Hm[(size_t)i * k + j] = cs[i] * a + sn[i] * b;
+            Hm[(size_t)(i + 1) * k + j] = -sn[i] * a + cs[i] * b;
+          }
+          const double a = Hm[(size_t)j * k + j], b = Hm[(size_t)(j + 1) * k + j];
+          const double r = std::hypot(a, b);
+          cs[j] = r > 0 ? a / r : 1.0;
+          sn[j] = r > 0 ? b / r : 0.0;
+          Hm[(size_t)j * k + j] = r;
+          Hm[(size_t)(j + 1) * k + j] = 0.0;
+          gv[j + 1] = -sn[j] * gv[j];
+          gv[j] = cs[j] * gv[j];
+          beta = std::fabs(gv[j + 1]);
+          if (beta <= o.krylov_tol * bnorm || wn == 0) {
+            ++j;
+            break;
+          }
+        }
+        // x += P^-1 (V_{0..j-1} yv), yv from the triangular system
+        std::vector<double> yv(j, 0.0);
+        for (int i = j - 1; i >= 0; --i) {
+          double s2 = gv[i];
+          for (int l = i + 1; l < j; ++l) s2 -= Hm[(size_t)i * k + l] * yv[l];
+          yv[i] = Hm[(size_t)i * k + i] != 0 ? s2 / Hm[(size_t)i * k + i] : 0.0;
+        }
+        if ((rc = combine(j, V, yv.data(), 0.0, w))) return rc;
+        imp_apply_blocks(n, (const T*)Pinv, (const T*)w, z, st);
+        if ((rc = combine(1, &z, &one, 1.0, x))) return rc;
+        if (beta <= o.krylov_tol * bnorm || kits >= o.max_krylov) break;
+        // restart: r = -R - J x
+        Jv(x, w);
+        T* pair[2] = {R, w};
+        double cf[2] = {-1.0, -1.0};
+        if ((rc = combine(2, pair, cf, 0.0, V[0]))) return rc;
+        double r2;
+        if ((rc = dots(1, &V[0], V[0], &r2))) return rc;
+        beta = std::sqrt(r2);
+      }
+      // y += x; converged when |x| <= newton_tol |y|
+      if ((rc = combine(1, &x, &one, 1.0, y))) return rc;
+      double xx, yy;
+      if ((rc = dots(1, &x, x, &xx))) return rc;
+      if ((rc = dots(1, &y, y, &yy))) return rc;
+      if (!std::isfinite(xx) || !std::isfinite(yy))
+        return fail(h, ENONFINITE_, "implicit step: non-finite Newton iterate");
+      conv = std::sqrt(xx) <= o.newton_tol * std::sqrt(yy);
+    }
+    if (!conv) {
+      return fail(h, ENOCONV_, "implicit step " + std::to_string(step) + ": Newton did not converge in " +
+                                   std::to_string(o.max_newton) + " iterations (dt too large for this state?)");
+    }
+    PMFEM_CK(h, cudaMemcpyAsync(m0, y, len * sizeof(T), cudaMemcpyDeviceToDevice, st));
+    launch_perm_in(d, (const T*)m0, (V4<T>*)h->m, st);
+    ++stats[3];
+  }
+  return check_launch(h);
+}
+
 // RK4 steps with the surrogate: stage 1 runs the full P-AIM and keeps its grid charges Q1
 // and potential U1; stages 2-4 take U = U1 + net(Q - Q1) instead of the FFT convolution,
 // except on every sur_every-th step, where they run the full P-AIM and the network's
@@ -486,6 +722,64 @@ int pmfem_set_aim(pmfem_t h, int Nx, int Ny, int Nz, int order_p, int near_boxes
   return OK;
 }
 
+int pmfem_set_exchange_per_tet(pmfem_t h, const double* A_tet) {
+  if (!h) return EINVAL_;
+  if (!A_tet) {
+    h->s.A_tet.clear();
+    return OK;
+  }
+  for (int64_t e = 0; e < h->s.T; ++e)
+    if (!(A_tet[e] >= 0) || !std::isfinite(A_tet[e])) return fail(h, EINVAL_, "A_tet must be finite and >= 0");
+  h->s.A_tet.assign(A_tet, A_tet + h->s.T);
+  return OK;
+}
+
+int pmfem_set_anisotropy(pmfem_t h, const int32_t* tet_grain, int n_grains, const double* K1, const double* axes,
+                         const double* Ku, const double* u) {
+  if (!h) return EINVAL_;
+  free_device(h);
+  if (!tet_grain) {
+    h->s.tet_grain.clear();
+    h->s.grain_tab.clear();
+    return OK;
+  }
+  if (n_grains <= 0 || !axes || (!K1 && !Ku)) return fail(h, EINVAL_, "need n_grains > 0, axes and K1 or Ku");
+  if (Ku && !u) return fail(h, EINVAL_, "Ku needs the uniaxial axes u");
+  for (int64_t e = 0; e < h->s.T; ++e)
+    if (tet_grain[e] < 0 || tet_grain[e] >= n_grains) return fail(h, EINVAL_, "tet_grain outside [0, n_grains)");
+  const double sc = 2.0 / (kMu0 * h->s.Ms);
+  std::vector<double> tab((size_t)n_grains * kGrainTab, 0.0);
+  for (int g = 0; g < n_grains; ++g) {
+    double* P = &tab[(size_t)g * kGrainTab];
+    for (int r = 0; r < 3; ++r) {
+      const double* a = axes + 9 * g + 3 * r;
+      const double nr = std::sqrt(a[0] * a[0] + a[1] * a[1] + a[2] * a[2]);
+      if (!(std::fabs(nr - 1.0) < 1e-6)) return fail(h, EINVAL_, "grain axes must be unit rows");
+      for (int c = 0; c < 3; ++c) P[3 * r + c] = a[c];
+    }
+    P[9] = K1 ? -sc * K1[g] : 0.0;
+    if (Ku) {
+      const double* uu = u + 3 * g;
+      const double nr = std::sqrt(uu[0] * uu[0] + uu[1] * uu[1] + uu[2] * uu[2]);
+      if (!(nr > 0)) return fail(h, EINVAL_, "uniaxial axes must be non-zero");
+      for (int c = 0; c < 3; ++c) P[10 + c] = uu[c] / nr;
+      P[13] = sc * Ku[g];
+    }
+    for (int k = 0; k < kGrainTab; ++k)
+      if (!std::isfinite(P[k])) return fail(h, EINVAL_, "non-finite anisotropy parameter");
+  }
+  h->s.tet_grain.assign(tet_grain, tet_grain + h->s.T);
+  h->s.grain_tab.swap(tab);
+  return OK;
+}
+
+int pmfem_set_setup_device(pmfem_t h, int use_gpu) {
+  if (!h) return EINVAL_;
+  if (use_gpu != 0 && use_gpu != 1) return fail(h, EINVAL_, "use_gpu must be 0 (host) or 1 (GPU)");
+  h->s.setup_gpu = use_gpu == 1;
+  return OK;
+}
+
 int pmfem_set_layout(pmfem_t h, int tile_y, int tile_z, int sort_window, int col_bits) {
   if (!h) return EINVAL_;
   if (tile_y < 0 || tile_y > 64 || tile_z < 0 || tile_z > 64 || sort_window < 0 || sort_window > 65536)
@@ -562,7 +856,7 @@ int pmfem_lca_map(pmfem_t h, int32_t* out) {
 int pmfem_field(pmfem_t h, const void* m, void* H, int components, void* stream) {
   if (!h) return EINVAL_;
   if (!m || !H || m == H) return fail(h, EINVAL_, "m and H must be distinct device pointers");
-  if (components <= 0 || components > PMFEM_ALL) return fail(h, EINVAL_, "components must be a non-empty PMFEM_EX|MS|AP mask");
+  if (components <= 0 || components > PMFEM_ALL) return fail(h, EINVAL_, "components must be a non-empty PMFEM_EX|MS|AP|AN mask");
   int rc = ensure_device(h);
   if (rc) return rc;
   cudaStream_t st = stream ? (cudaStream_t)stream : h->stream;
@@ -658,6 +952,29 @@ int pmfem_llg_step(pmfem_t h, double dt, int nsteps, void* stream) {
   }
   for (int k = 0; k < nsteps; ++k) PMFEM_CK(h, cudaGraphLaunch(h->graph, st));
   return OK;
+}
+
+int pmfem_llg_step_implicit(pmfem_t h, double dt, int nsteps, const pmfem_implicit_opts* opts, int64_t* stats,
+                            void* stream) {
+  if (!h) return EINVAL_;
+  if (!(dt > 0) || !std::isfinite(dt) || nsteps < 0) return fail(h, EINVAL_, "need dt > 0 and nsteps >= 0");
+  int rc = ensure_device(h);
+  if (rc) return rc;
+  const bool f64 = h->dev_prec == PMFEM_FP64;
+  ImpOpts o;
+  o.newton_tol = opts && opts->newton_tol > 0 ? opts->newton_tol : (f64 ? 1e-10 : 1e-5);
+  o.krylov_tol = opts && opts->krylov_tol > 0 ? opts->krylov_tol : (f64 ? 1e-8 : 1e-4);
+  o.restart = opts && opts->restart > 0 ? opts->restart : 30;
+  o.max_newton = opts && opts->max_newton > 0 ? opts->max_newton : 20;
+  o.max_krylov = opts && opts->max_krylov > 0 ? opts->max_krylov : 600;
+  if (o.restart > kMaxKrylov) return fail(h, EINVAL_, "restart must be at most 64");
+  if (!(o.newton_tol < 1) || !(o.krylov_tol < 1)) return fail(h, EINVAL_, "tolerances must be below 1");
+  int64_t st4[4] = {0, 0, 0, 0};
+  cudaStream_t st = stream ? (cudaStream_t)stream : h->stream;
+  rc = f64 ? run_implicit(h, h->d64, dt, nsteps, o, st4, st) : run_implicit(h, h->d32, dt, nsteps, o, st4, st);
+  if (stats)
+    for (int i = 0; i < 4; ++i) stats[i] = st4[i];
+  return rc;
 }
 
 int pmfem_sync(pmfem_t h) {
@@ -860,7 +1177,7 @@ void noalloc_eval(pmfem_t h, const DevOps<T>& d, unsigned char* base, const void
 extern "C" int pmfem_field_noalloc(pmfem_t h, const void* m, void* H, int components, void* stream) {
   if (!h) return EINVAL_;
   if (!m || !H || m == H) return fail(h, EINVAL_, "m and H must be distinct device pointers");
-  if (components <= 0 || components > PMFEM_ALL) return fail(h, EINVAL_, "components must be a non-empty PMFEM_EX|MS|AP mask");
+  if (components <= 0 || components > PMFEM_ALL) return fail(h, EINVAL_, "components must be a non-empty PMFEM_EX|MS|AP|AN mask");
   if (!h->s.ready) return fail(h, ESTATE_, "call pmfem_set_periodicity first");
   const size_t need = h->prec == PMFEM_FP64 ? noalloc_need<double>(h->s) : noalloc_need<float>(h->s);
   if (need > kNoAllocBytes)

@@ -79,6 +79,18 @@ struct DevSell {
   const bf16_t* bval[10] = {};
 };
 
+// Local anisotropy terms (internal order): unknown i has grains grain[ptr[i] .. ptr[i+1]) with
+// volume shares w; grain g's row of tab holds its axes a1, a2, a3 (9), c1 = -2 K1 / (mu0 Ms),
+// the uniaxial axis u (3), cu = 2 Ku / (mu0 Ms) and two pads.  ptr null: no anisotropy.
+constexpr int kGrainTab = 16;
+template <typename T>
+struct LocalTerms {
+  const int32_t* ptr = nullptr;
+  const int32_t* grain = nullptr;
+  const T* w = nullptr;
+  const T* tab = nullptr;
+};
+
 // Operator values, grid set-up and work buffers of one precision, all device memory,
 // in the internal (box-sorted) order of the unknowns.
 template <typename T>
@@ -113,6 +125,7 @@ struct DevOps {
   T* grid = nullptr;                              // N0 N1 N2 real (Q, then U)
   C2* cbuf = nullptr;                             // F2 x F1 x (F0/2+1) complex
   int* flag = nullptr;                            // device error word
+  LocalTerms<T> loc;                              // anisotropy (PMFEM_AN), when set
   ProfHook prof;
 };
 

@@ -8,6 +8,8 @@
 #include <string>
 #include <vector>
 
+#include "setup_math.hpp"
+
 namespace pmfem {
 
 constexpr double kPi = 3.14159265358979323846;
@@ -15,7 +17,8 @@ constexpr double kMu0 = 4e-7 * kPi;
 
 // status codes (mirror of pmfem.h)
 enum Status : int { OK = 0, EINVAL_ = -1, ENOMEM_ = -2, ECUDA_ = -3, EMESH_ = -4,
-                    ENONFINITE_ = -5, ETIMEOUT_ = -6, ESTATE_ = -7 };
+                    ENONFINITE_ = -5, ETIMEOUT_ = -6, ESTATE_ = -7,
+                    ENOCONV_ = -8 };
 
 struct Error {
   int code = 0;
@@ -38,11 +41,19 @@ struct Setup {
   std::vector<double> xyz;      // N x 3
   std::vector<int32_t> tets;    // T x 4, positively oriented
   double Ms = 0, A = 0, alpha = 0;
+  std::vector<double> A_tet;    // T exchange stiffness per tetrahedron (empty: A everywhere)
+  // ---- anisotropy per grain (pmfem_set_anisotropy): grain of every tetrahedron and, per
+  // grain, axes a1 a2 a3 (9, rows), c1 = -2 K1/(mu0 Ms), u (3), cu = 2 Ku/(mu0 Ms), 2 pads
+  std::vector<int32_t> tet_grain;
+  std::vector<double> grain_tab;
   // ---- AIM settings (0 = default)
   int dims_req[3] = {0, 0, 0};
   int p = 3;
   int near_boxes = 3;
   double near_elem_factor = 0.0;
+  // ---- set-up on the GPU (pmfem_set_setup_device): PGF spectrum, near-element integrals and
+  // point precorrection evaluated by CUDA kernels in FP64 on the current device
+  bool setup_gpu = false;
   // ---- device layout tuning (0 = default)
   int tile_y = 0, tile_z = 0, sort_window = 0, col_bits = 0;
   // ---- periodicity
@@ -145,19 +156,40 @@ int setup_precorrection(Setup& s, Error& err);
 int setup_near_elements(Setup& s, Error& err);
 int run_setup(Setup& s, Error& err);
 
-// periodic Green's function of Eq. 15 (k0 = 0), Ewald-type evaluation
+// Near-element correction, as planned on the host: the sorted near placements of every row
+// and, for every vertex of a placement, its output slot (adjacency position, or nnz + the
+// index of an extra column); extra columns per row sorted.
+struct NearPlan {
+  std::vector<int64_t> pptr;   // Np + 1
+  std::vector<int64_t> elem;   // tet index, or T + boundary-triangle index
+  std::vector<int32_t> img;    // 3 per placement
+  std::vector<int64_t> dest;   // 4 per placement
+  std::vector<int64_t> xptr;   // Np + 1
+  std::vector<int32_t> xcol;
+};
+
+// GPU set-up stages (setup_gpu.cu), FP64 on the current device; each fills what its host
+// counterpart fills
+int spectrum_gpu(Setup& s, Error& err);                                             // s.ghat
+int near_eval_gpu(const Setup& s, const NearPlan& plan, std::vector<double>& out, Error& err);
+int precorrection_gpu(Setup& s, const std::vector<int32_t>& box, const std::vector<int64_t>& bptr,
+                      const std::vector<int32_t>& bl, const std::vector<double>& T0, int R, Error& err);   // s.C
+
+// periodic Green's function of Eq. 15 (k0 = 0), Ewald-type evaluation: the lattice's
+// parameters are built here (host); the evaluation itself is sm::pgf_eval (setup_math.hpp),
+// shared with the GPU set-up, which copies params() and kflat() to the device
 class PeriodicGreen {
  public:
   PeriodicGreen(const double L[3], double eta_scale = 1.0);
+  PeriodicGreen(const PeriodicGreen&) = delete;             // params() points into kflat_
+  PeriodicGreen& operator=(const PeriodicGreen&) = delete;
   double operator()(double x, double y, double z) const;  // r not on the lattice
   double reg0() const { return reg0_; }                     // lim (G^p - 1/r)
   int dim() const { return dim_; }
+  const sm::PgfParams& params() const { return P_; }
+  const std::vector<double>& kflat() const { return kflat_; }   // nk x (kx, ky, kz, coefficient)
  private:
-  double g3(double x, double y, double z) const;
-  double g2(double x, double y, double z) const;
-  double g1(double x, double y, double z) const;
-  double real_space(double x, double y, double z, bool skip_origin) const;
-  void min_image(double& x, double& y, double& z) const;
+  void fill_params();
   int dim_ = 0;
   int ax_[3] = {0, 1, 2};          // periodic axes first, then the open ones
   double L_[3] = {0, 0, 0};
@@ -167,6 +199,8 @@ class PeriodicGreen {
   std::vector<std::array<double, 4>> kvec_;   // (kx, ky, kz, coefficient)
   std::vector<double> gl_u_, gl_w_;           // Gauss-Legendre on [0, 1]
   double reg0_ = 0;
+  sm::PgfParams P_;
+  std::vector<double> kflat_;
 };
 
 // exact potential integrals (Sec. 3.2 near correction)

@@ -213,29 +213,30 @@ __global__ void PMFEM_STENCIL_LB k_stencil(int64_t Np, const int32_t* __restrict
       const VG *__restrict__ gz, const VK *__restrict__ kp, const V4<T> *__restrict__ m,                          \
       const int32_t *__restrict__ perm, T *__restrict__ H, int use_ms, int use_ex, T hx, T hy, T hz,             \
       V4<T> *__restrict__ m0, V4<T> *__restrict__ mnext, V4<T> *__restrict__ accb, T cdt, T bw, int acc_init,    \
-      T dt6, T gam, T alpha, int *flag
+      T dt6, T gam, T alpha, int *flag, LocalTerms<T> lt
 #define PMFEM_FIELD_BODY                                                                                        \
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;                                            \
   if (i >= Np) return;                                                                                          \
   const int64_t uo = MODE == 0 ? (int64_t)perm[i] : 0;                                                          \
-  field_row<T, MODE, CT, VG, VK>(i, 0, (int32_t)Np, len, base, off, dcol, gx, gy, gz, kp, m, uo, H, use_ms,     \
-                                 use_ex, hx, hy, hz, m0, mnext, accb, cdt, bw, acc_init, dt6, gam, alpha, flag);
-template <typename T, int MODE, typename CT, typename VG, typename VK>
+  field_row<T, MODE, CT, VG, VK, LOC>(i, 0, (int32_t)Np, len, base, off, dcol, gx, gy, gz, kp, m, uo, H, use_ms, \
+                                      use_ex, hx, hy, hz, m0, mnext, accb, cdt, bw, acc_init, dt6, gam, alpha, flag, \
+                                      lt);
+template <typename T, int MODE, typename CT, typename VG, typename VK, bool LOC>
 __global__ void __launch_bounds__(kBlock, PMFEM_FIELD_MINB) k_field_capped(PMFEM_FIELD_PARAMS) {
   PMFEM_FIELD_BODY
 }
-template <typename T, int MODE, typename CT, typename VG, typename VK>
+template <typename T, int MODE, typename CT, typename VG, typename VK, bool LOC>
 __global__ void __launch_bounds__(kBlock) k_field(PMFEM_FIELD_PARAMS) {
   PMFEM_FIELD_BODY
 }
 #undef PMFEM_FIELD_BODY
 #undef PMFEM_FIELD_PARAMS
-template <typename T, int MODE, typename CT, typename VG, typename VK>
+template <typename T, int MODE, typename CT, typename VG, typename VK, bool LOC>
 constexpr auto field_kernel() {
   if constexpr (sizeof(T) == 4 && sizeof(VG) == 4 && sizeof(VK) == 4)
-    return k_field_capped<T, MODE, CT, VG, VK>;
+    return k_field_capped<T, MODE, CT, VG, VK, LOC>;
   else
-    return k_field<T, MODE, CT, VG, VK>;
+    return k_field<T, MODE, CT, VG, VK, LOC>;
 }
 
 inline unsigned blocks_for(int64_t threads) { return (unsigned)((threads + kBlock - 1) / kBlock); }
@@ -390,6 +391,7 @@ void launch_field(const DevOps<T>& d, const V4<T>* m, T* H, int comps, double hx
   const DevSell<T>& A = d.adj;
   const unsigned nb = blocks_for(d.Np);
   const int use_ms = (comps & 2) ? 1 : 0, use_ex = (comps & 1) ? 1 : 0;
+  const bool loc = (comps & 8) && d.loc.ptr;
   const T ax = (comps & 4) ? (T)hx : T(0), ay = (comps & 4) ? (T)hy : T(0), az = (comps & 4) ? (T)hz : T(0);
   V4<T>* m0 = (V4<T>*)rk.m0;
   V4<T>* mn = (V4<T>*)rk.mnext;
@@ -405,14 +407,22 @@ void launch_field(const DevOps<T>& d, const V4<T>* m, T* H, int comps, double hx
           kernel<<<nb, kBlock, 0, st>>>(d.Np, A.len, A.base, A.off, (const CT*)A.delta, vals<VG>(A, 6),
                                         vals<VG>(A, 7), vals<VG>(A, 8), vals<VK>(A, 9), m, d.perm, H, use_ms,
                                         use_ex, ax, ay, az, m0, mn, acc, (T)rk.cdt, (T)rk.bw, rk.acc_init,
-                                        (T)rk.dt6, (T)rk.gam, (T)rk.alpha, d.flag);
+                                        (T)rk.dt6, (T)rk.gam, (T)rk.alpha, d.flag, d.loc);
         };
-        if (rk.mode == 0)
-          go(field_kernel<T, 0, CT, VG, VK>());
-        else if (rk.mode == 1)
-          go(field_kernel<T, 1, CT, VG, VK>());
-        else
-          go(field_kernel<T, 2, CT, VG, VK>());
+        if (loc) {
+          if (rk.mode == 0)
+            go(field_kernel<T, 0, CT, VG, VK, true>());
+          else if (rk.mode == 1)
+            go(field_kernel<T, 1, CT, VG, VK, true>());
+          else
+            go(field_kernel<T, 2, CT, VG, VK, true>());
+        } else if (rk.mode == 0) {
+          go(field_kernel<T, 0, CT, VG, VK, false>());
+        } else if (rk.mode == 1) {
+          go(field_kernel<T, 1, CT, VG, VK, false>());
+        } else {
+          go(field_kernel<T, 2, CT, VG, VK, false>());
+        }
       });
     });
   });

@@ -562,7 +562,7 @@ __device__ __forceinline__ void stencil_add_row(int64_t i, const int32_t* __rest
 // Both operators annihilate constants (rows of the gradient and of the Laplacian sum to
 // zero), so they act on differences to the row's own value: the same result in exact
 // arithmetic, without the cancellation of large terms in floating point.
-template <typename T, int MODE, typename CT, typename VG, typename VK>
+template <typename T, int MODE, typename CT, typename VG, typename VK, bool LOC = false>
 __device__ __forceinline__ void field_row(int64_t i, int64_t c0, int32_t nc, const int32_t* __restrict__ len,
                                           const int32_t* __restrict__ base, const int64_t* __restrict__ off,
                                           const CT* __restrict__ dcol, const VG* __restrict__ gx,
@@ -571,7 +571,8 @@ __device__ __forceinline__ void field_row(int64_t i, int64_t c0, int32_t nc, con
                                           T* __restrict__ H, int use_ms,
                                           int use_ex, T hx, T hy, T hz, V4<T>* __restrict__ m0,
                                           V4<T>* __restrict__ mnext, V4<T>* __restrict__ accb, T cdt, T bw,
-                                          int acc_init, T dt6, T gam, T alpha, int* flag) {
+                                          int acc_init, T dt6, T gam, T alpha, int* flag,
+                                          LocalTerms<T> lt = LocalTerms<T>()) {
   const int ng = (len[i] + 3) >> 2;
   const int32_t b = base[i];
   int64_t o = off[i >> 5] + 4 * (i & 31);
@@ -626,6 +627,23 @@ __device__ __forceinline__ void field_row(int64_t i, int64_t c0, int32_t nc, con
         ay += kk[k] * (mk.y - mn.y);
         az += kk[k] * (mk.z - mn.z);
       }
+    }
+  }
+  if constexpr (LOC) {
+    // anisotropy of the grains meeting at the node, weighted by their volume shares:
+    // cubic -(2 K1/(mu0 Ms)) sum_i a_i (a_j^2 + a_k^2) axis_i, uniaxial (2 Ku/(mu0 Ms)) (m.u) u
+    for (int32_t q = lt.ptr[i]; q < lt.ptr[i + 1]; ++q) {
+      const T* P = lt.tab + kGrainTab * lt.grain[q];
+      const T wq = lt.w[q];
+      const T a1 = mn.x * P[0] + mn.y * P[1] + mn.z * P[2];
+      const T a2 = mn.x * P[3] + mn.y * P[4] + mn.z * P[5];
+      const T a3 = mn.x * P[6] + mn.y * P[7] + mn.z * P[8];
+      const T s1 = a1 * a1, s2 = a2 * a2, s3 = a3 * a3;
+      const T f1 = P[9] * a1 * (s2 + s3), f2 = P[9] * a2 * (s1 + s3), f3 = P[9] * a3 * (s1 + s2);
+      const T mu = P[13] * (mn.x * P[10] + mn.y * P[11] + mn.z * P[12]);
+      ax += wq * (f1 * P[0] + f2 * P[3] + f3 * P[6] + mu * P[10]);
+      ay += wq * (f1 * P[1] + f2 * P[4] + f3 * P[7] + mu * P[11]);
+      az += wq * (f1 * P[2] + f2 * P[5] + f3 * P[8] + mu * P[12]);
     }
   }
   const T Hx = ax + hx, Hy = ay + hy, Hz = az + hz;

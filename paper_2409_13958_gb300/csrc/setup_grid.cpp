@@ -87,7 +87,7 @@ int setup_grid(Setup& s, Error& err) {
 }
 
 int setup_spectrum(Setup& s, Error& err) {
-  (void)err;
+  if (s.setup_gpu) return spectrum_gpu(s, err);
   PeriodicGreen G(s.L);
   int U[3], K[3];
   for (int a = 0; a < 3; ++a) {
@@ -142,18 +142,10 @@ int setup_spectrum(Setup& s, Error& err) {
   return OK;
 }
 
-static void lagrange(double sv, int p, double* w) {
-  for (int i = 0; i <= p; ++i) {
-    double v = 1.0;
-    for (int j = 0; j <= p; ++j)
-      if (j != i) v *= (sv - j) / (double)(i - j);
-    w[i] = v;
-  }
-}
+using sm::lagrange;
 
 int setup_precorrection(Setup& s, Error& err) {
-  (void)err;
-  const int nb = s.near_boxes, p = s.p, P = p + 1;
+  const int nb = s.near_boxes, p = s.p;
   const int64_t Np = s.Np;
   const int N0 = s.dims[0], N1 = s.dims[1], N2 = s.dims[2];
   // boxes and box -> unknown lists
@@ -185,11 +177,12 @@ int setup_precorrection(Setup& s, Error& err) {
         double r = std::sqrt(dx * dx + dy * dy + dz * dz);
         T0[(size_t)(x + R) + W * ((size_t)(y + R) + W * (size_t)(z + R))] = (x || y || z) ? 1.0 / r : 0.0;
       }
+  if (s.setup_gpu) return precorrection_gpu(s, box, bptr, bl, T0, R, err);
   std::vector<std::vector<std::pair<int32_t, double>>> rows(Np);
   const int dimN[3] = {N0, N1, N2};
   parallel_for(Np, [&](int64_t b, int64_t e) {
     std::vector<std::pair<int32_t, double>> acc;
-    double wn[3][6], wk[3][6], c[3][11];
+    double wn[3][6];
     for (int64_t n = b; n < e; ++n) {
       acc.clear();
       for (int a = 0; a < 3; ++a) lagrange(s.frac[3 * n + a], p, wn[a]);
@@ -213,36 +206,13 @@ int setup_precorrection(Setup& s, Error& err) {
             int64_t bi = lin(t[0], t[1], t[2]);
             for (int64_t q = bptr[bi]; q < bptr[bi + 1]; ++q) {
               const int32_t k = bl[q];
-              const double* rk = &s.pos_f[3 * (int64_t)k];
-              double val = 0;
-              if (!(k == n && !img[0] && !img[1] && !img[2])) {
-                double d0 = rn[0] - rk[0] - img[0] * s.L[0];
-                double d1 = rn[1] - rk[1] - img[1] * s.L[1];
-                double d2 = rn[2] - rk[2] - img[2] * s.L[2];
-                val = 1.0 / std::sqrt(d0 * d0 + d1 * d1 + d2 * d2);
-              }
-              // grid part: separable correlation of the two stencils, then the G0' table
-              int D[3];
-              for (int a = 0; a < 3; ++a) {
-                lagrange(s.frac[3 * (int64_t)k + a], p, wk[a]);
-                D[a] = s.base[3 * n + a] - s.base[3 * (int64_t)k + a] - (int)(img[a] * dimN[a]);
-                for (int i = 0; i < 2 * p + 1; ++i) c[a][i] = 0;
-                for (int i = 0; i < P; ++i)
-                  for (int j = 0; j < P; ++j) c[a][i - j + p] += wn[a][i] * wk[a][j];
-              }
-              double gsum = 0;
-              for (int tz = 0; tz <= 2 * p; ++tz) {
-                const size_t oz2 = (size_t)W * W * (size_t)(D[2] + tz - p + R);
-                double sy = 0;
-                for (int ty = 0; ty <= 2 * p; ++ty) {
-                  const size_t oy2 = oz2 + (size_t)W * (size_t)(D[1] + ty - p + R);
-                  double sx = 0;
-                  for (int tx = 0; tx <= 2 * p; ++tx) sx += c[0][tx] * T0[oy2 + (size_t)(D[0] + tx - p + R)];
-                  sy += c[1][ty] * sx;
-                }
-                gsum += c[2][tz] * sy;
-              }
-              acc.push_back({k, val - gsum});
+              int img3[3] = {(int)img[0], (int)img[1], (int)img[2]};
+              int Db[3];
+              for (int a = 0; a < 3; ++a) Db[a] = s.base[3 * n + a] - s.base[3 * (int64_t)k + a];
+              const bool self = k == n && !img[0] && !img[1] && !img[2];
+              const double v = sm::precorr_value(rn, &s.pos_f[3 * (int64_t)k], img3, s.L, Db, wn,
+                                                 &s.frac[3 * (int64_t)k], p, dimN, T0.data(), R, self);
+              acc.push_back({k, v});
             }
           }
       std::sort(acc.begin(), acc.end(), [](auto& x, auto& y) { return x.first < y.first; });

@@ -39,19 +39,7 @@ static inline void cross3(const double* a, const double* b, double* o) {
 static inline double dot3(const double* a, const double* b) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
 
 // Volume (signed) and gradients of the four barycentric coordinates.
-double tet_grads(const double X[4][3], double g[4][3]) {
-  double e1[3], e2[3], e3[3], c23[3], c31[3], c12[3];
-  sub3(X[1], X[0], e1); sub3(X[2], X[0], e2); sub3(X[3], X[0], e3);
-  cross3(e2, e3, c23); cross3(e3, e1, c31); cross3(e1, e2, c12);
-  double det = dot3(e1, c23);
-  for (int d = 0; d < 3; ++d) {
-    g[1][d] = c23[d] / det;
-    g[2][d] = c31[d] / det;
-    g[3][d] = c12[d] / det;
-    g[0][d] = -(g[1][d] + g[2][d] + g[3][d]);
-  }
-  return det / 6.0;
-}
+double tet_grads(const double X[4][3], double g[4][3]) { return sm::tet_grads(X, g); }
 
 static void load_tet(const Setup& s, int64_t e, double X[4][3]) {
   for (int i = 0; i < 4; ++i) {

@@ -86,16 +86,16 @@ int setup_near_elements(Setup& s, Error& err) {
     for (int d = 0; d < 3; ++d) span[d] = s.periodic[d] ? (int)std::ceil((hi[d] - lo[d]) / s.L[d]) + 2 : 0;
   }
 
+  // phase 1 (host): the near placements of every row, sorted, and for every vertex of a
+  // placement its output slot: the adjacency position when the vertex's unknown is a
+  // neighbour of the row, else a slot among the row's extra columns (sorted, after nnz)
   const int64_t nnz = s.rowptr[Np];
-  s.Ea.assign(3 * nnz, 0.0);
-  std::vector<std::vector<std::pair<int32_t, std::array<double, 3>>>> extra(Np);
+  std::vector<std::vector<Placement>> rows_pl(Np);
+  std::vector<std::vector<int32_t>> rows_x(Np);
   parallel_for(Np, [&](int64_t b, int64_t e) {
-    std::vector<Placement> pl;
-    std::map<int32_t, std::array<double, 3>> ext;
     for (int64_t n = b; n < e; ++n) {
       const double* rn = &s.pos_f[3 * n];
-      pl.clear();
-      ext.clear();
+      std::vector<Placement>& pl = rows_pl[n];
       // (a) elements with a vertex on the node
       for (int64_t t = ptr[n]; t < ptr[n + 1]; ++t) {
         int64_t slot = inc[t];
@@ -133,89 +133,96 @@ int setup_near_elements(Setup& s, Error& err) {
       }
       std::sort(pl.begin(), pl.end());
       pl.erase(std::unique(pl.begin(), pl.end()), pl.end());
-      auto add = [&](int32_t k, const double v[3]) {
-        const int32_t* cb = s.col.data() + s.rowptr[n];
-        const int32_t* ce = s.col.data() + s.rowptr[n + 1];
-        const int32_t* it = std::lower_bound(cb, ce, k);
-        if (it != ce && *it == k) {
-          int64_t pos = it - s.col.data();
-          for (int d = 0; d < 3; ++d) s.Ea[3 * pos + d] += v[d];
-        } else {
-          auto& a = ext[k];
-          for (int d = 0; d < 3; ++d) a[d] += v[d];
-        }
-      };
+      // columns outside the adjacency pattern (only elements found by the radius reach them)
+      std::vector<int32_t>& xc = rows_x[n];
+      const int32_t* cb = s.col.data() + s.rowptr[n];
+      const int32_t* ce = s.col.data() + s.rowptr[n + 1];
       for (const Placement& P : pl) {
-        double obs[3];
-        for (int d = 0; d < 3; ++d) obs[d] = rn[d] - P.img[d] * s.L[d];
-        if (P.elem < T) {
-          double X[4][3], g[4][3];
-          int32_t vid[4];
-          for (int i = 0; i < 4; ++i) {
-            vid[i] = s.tets[4 * P.elem + i];
-            for (int d = 0; d < 3; ++d) X[i][d] = s.xyz[3 * (int64_t)vid[i] + d];
-          }
-          double Ve = tet_grads(X, g);
-          double I = tet_potential(obs, X);
-          double Ppt = 0;
-          for (int i = 0; i < 4; ++i) {
-            double d0 = obs[0] - X[i][0], d1 = obs[1] - X[i][1], d2 = obs[2] - X[i][2];
-            double dist = std::sqrt(d0 * d0 + d1 * d1 + d2 * d2);
-            bool self = s.lca[vid[i]] == n && dist < self_tol;
-            if (!self) Ppt += 0.25 * Ve / dist;
-          }
-          const double coef = I - Ppt;
-          for (int j = 0; j < 4; ++j) {
-            double v[3] = {-g[j][0] * coef, -g[j][1] * coef, -g[j][2] * coef};
-            add(s.lca[vid[j]], v);
-          }
-        } else {
-          const int64_t f = P.elem - T;
-          int32_t vid[3];
-          double X[3][3];
-          for (int i = 0; i < 3; ++i) {
-            vid[i] = s.bfaces[3 * f + i];
-            for (int d = 0; d < 3; ++d) X[i][d] = s.xyz[3 * (int64_t)vid[i] + d];
-          }
-          double e1[3] = {X[1][0] - X[0][0], X[1][1] - X[0][1], X[1][2] - X[0][2]};
-          double e2[3] = {X[2][0] - X[0][0], X[2][1] - X[0][1], X[2][2] - X[0][2]};
-          double nn[3] = {e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2], e1[0] * e2[1] - e1[1] * e2[0]};
-          double a2 = std::sqrt(nn[0] * nn[0] + nn[1] * nn[1] + nn[2] * nn[2]);
-          double nrm[3] = {nn[0] / a2, nn[1] / a2, nn[2] / a2};
-          const double area = 0.5 * a2;
-          double Ij[3];
-          tri_hat_potentials(obs, X[0], X[1], X[2], Ij);
-          double G[3], Gs = 0;
-          for (int i = 0; i < 3; ++i) {
-            double d0 = obs[0] - X[i][0], d1 = obs[1] - X[i][1], d2 = obs[2] - X[i][2];
-            double dist = std::sqrt(d0 * d0 + d1 * d1 + d2 * d2);
-            bool self = s.lca[vid[i]] == n && dist < self_tol;
-            G[i] = self ? 0.0 : 1.0 / dist;
-            Gs += G[i];
-          }
-          for (int j = 0; j < 3; ++j) {
-            double coef = Ij[j] - area / 12.0 * (Gs + G[j]);
-            double v[3] = {nrm[0] * coef, nrm[1] * coef, nrm[2] * coef};
-            add(s.lca[vid[j]], v);
-          }
+        const int nv = P.elem < T ? 4 : 3;
+        for (int j = 0; j < nv; ++j) {
+          const int32_t v = P.elem < T ? s.tets[4 * P.elem + j] : s.bfaces[3 * (P.elem - T) + j];
+          const int32_t k = s.lca[v];
+          const int32_t* it = std::lower_bound(cb, ce, k);
+          if (!(it != ce && *it == k)) xc.push_back(k);
         }
       }
-      for (auto& kv : ext) extra[n].push_back({kv.first, kv.second});
+      std::sort(xc.begin(), xc.end());
+      xc.erase(std::unique(xc.begin(), xc.end()), xc.end());
     }
   }, 64);
+  NearPlan plan;
+  plan.pptr.assign(Np + 1, 0);
+  plan.xptr.assign(Np + 1, 0);
+  for (int64_t n = 0; n < Np; ++n) {
+    plan.pptr[n + 1] = plan.pptr[n] + (int64_t)rows_pl[n].size();
+    plan.xptr[n + 1] = plan.xptr[n] + (int64_t)rows_x[n].size();
+  }
+  const int64_t npl = plan.pptr[Np], nx = plan.xptr[Np];
+  plan.elem.resize(npl);
+  plan.img.resize(3 * npl);
+  plan.dest.assign(4 * npl, 0);
+  plan.xcol.resize(nx);
+  parallel_for(Np, [&](int64_t b, int64_t e) {
+    for (int64_t n = b; n < e; ++n) {
+      const int32_t* cb = s.col.data() + s.rowptr[n];
+      const int32_t* ce = s.col.data() + s.rowptr[n + 1];
+      const std::vector<int32_t>& xc = rows_x[n];
+      std::copy(xc.begin(), xc.end(), plan.xcol.begin() + plan.xptr[n]);
+      int64_t q = plan.pptr[n];
+      for (const Placement& P : rows_pl[n]) {
+        plan.elem[q] = P.elem;
+        for (int d = 0; d < 3; ++d) plan.img[3 * q + d] = P.img[d];
+        const int nv = P.elem < T ? 4 : 3;
+        for (int j = 0; j < nv; ++j) {
+          const int32_t v = P.elem < T ? s.tets[4 * P.elem + j] : s.bfaces[3 * (P.elem - T) + j];
+          const int32_t k = s.lca[v];
+          const int32_t* it = std::lower_bound(cb, ce, k);
+          if (it != ce && *it == k) {
+            plan.dest[4 * q + j] = (int64_t)(it - s.col.data());
+          } else {
+            const int64_t xi = std::lower_bound(xc.begin(), xc.end(), k) - xc.begin();
+            plan.dest[4 * q + j] = nnz + plan.xptr[n] + xi;
+          }
+        }
+        ++q;
+      }
+      std::vector<Placement>().swap(rows_pl[n]);
+      std::vector<int32_t>().swap(rows_x[n]);
+    }
+  }, 64);
+  // phase 2: the integrals, row by row (host threads, or one GPU thread per row), into
+  // 3 x (nnz + extra) values
+  sm::NearArgs A;
+  A.xyz = s.xyz.data();
+  A.tets = s.tets.data();
+  A.bfaces = s.bfaces.data();
+  A.lca = s.lca.data();
+  A.pos_f = s.pos_f.data();
+  for (int d = 0; d < 3; ++d) A.L[d] = s.periodic[d] ? s.L[d] : 0.0;
+  A.T = T;
+  A.self_tol = self_tol;
+  A.pptr = plan.pptr.data();
+  A.elem = plan.elem.data();
+  A.img = plan.img.data();
+  A.dest = plan.dest.data();
+  std::vector<double> out(3 * (size_t)(nnz + nx), 0.0);
+  if (s.setup_gpu) {
+    int rc = near_eval_gpu(s, plan, out, err);
+    if (rc) return rc;
+  } else {
+    parallel_for(Np, [&](int64_t b, int64_t e) {
+      for (int64_t n = b; n < e; ++n) sm::near_eval_row(A, n, out.data());
+    }, 64);
+  }
+  s.Ea.assign(out.begin(), out.begin() + 3 * nnz);
   for (auto& x : s.Ea) x *= s.Ms;
   s.Ex.rows = Np;
   s.Ex.comps = 3;
   s.Ex.rowptr.assign(Np + 1, 0);
-  for (int64_t n = 0; n < Np; ++n) s.Ex.rowptr[n + 1] = s.Ex.rowptr[n] + (int32_t)extra[n].size();
-  s.Ex.col.resize(s.Ex.rowptr[Np]);
-  s.Ex.vals.resize(3 * (size_t)s.Ex.rowptr[Np]);
-  for (int64_t n = 0; n < Np; ++n)
-    for (size_t i = 0; i < extra[n].size(); ++i) {
-      int64_t o = s.Ex.rowptr[n] + i;
-      s.Ex.col[o] = extra[n][i].first;
-      for (int d = 0; d < 3; ++d) s.Ex.vals[3 * o + d] = s.Ms * extra[n][i].second[d];
-    }
+  for (int64_t n = 0; n <= Np; ++n) s.Ex.rowptr[n] = (int32_t)plan.xptr[n];
+  s.Ex.col = plan.xcol;
+  s.Ex.vals.resize(3 * (size_t)nx);
+  for (int64_t i = 0; i < 3 * nx; ++i) s.Ex.vals[i] = s.Ms * out[3 * nnz + i];
   return OK;
 }
 

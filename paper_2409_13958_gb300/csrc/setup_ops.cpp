@@ -70,16 +70,18 @@ int setup_operators(Setup& s, Error& err) {
         load_tet(s, tet, X);
         double Ve = tet_grads(X, g);
         s.V[u] += 0.25 * Ve;
+        const double Ke = s.A_tet.empty() ? Ve : s.A_tet[tet] * Ve;   // stiffness inside the element sum
         for (int j = 0; j < 4; ++j) {
           int64_t pos = find(u, s.lca[s.tets[4 * tet + j]]);
-          K[pos] += Ve * (g[i][0] * g[j][0] + g[i][1] * g[j][1] + g[i][2] * g[j][2]);
+          K[pos] += Ke * (g[i][0] * g[j][0] + g[i][1] * g[j][1] + g[i][2] * g[j][2]);
           for (int d = 0; d < 3; ++d) W[3 * pos + d] += 0.25 * Ve * g[i][d];
         }
       }
     }
   });
   // scaled values used by the field kernels
-  const double cex = -2.0 * s.A / (kMu0 * s.Ms);
+  // H_ex = -(2 A/(mu0 Ms)) V^-1 K m; with a stiffness per tetrahedron A sits inside K
+  const double cex = s.A_tet.empty() ? -2.0 * s.A / (kMu0 * s.Ms) : -2.0 / (kMu0 * s.Ms);
   s.Kp.resize(nnz);
   s.Wq.resize(3 * nnz);
   s.Gr.resize(3 * nnz);

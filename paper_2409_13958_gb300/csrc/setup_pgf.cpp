@@ -10,42 +10,14 @@
 #include <cmath>
 
 #include "internal.hpp"
+#include "setup_math.hpp"
 
 namespace pmfem {
 
 namespace {
-constexpr double kCutReal = 6.3;   // erfc(6.3) ~ 1e-19
-constexpr double kCutSpec = 43.0;  // exp(-43) ~ 2e-19
-constexpr double kEuler = 0.57721566490153286061;
-
-// E1(x) for x >= 1 by the continued fraction of Abramowitz & Stegun 5.1.22 (modified Lentz)
-double expint_e1_cf(double x) {
-  const double tiny = 1e-300;
-  double b = x + 1.0, c = 1.0 / tiny, d = 1.0 / b, h = d;
-  for (int i = 1; i < 1000; ++i) {
-    double an = -(double)i * i;
-    b += 2.0;
-    d = 1.0 / (an * d + b);
-    c = b + an / c;
-    double del = c * d;
-    h *= del;
-    if (std::fabs(del - 1.0) < 1e-16) break;
-  }
-  return h * std::exp(-x);
-}
-
-// Ein(x) = int_0^x (1 - e^-t)/t dt: power series below 1, E1 + ln x + gamma above
-double ein(double x) {
-  if (x < 1.0) {
-    double term = x, acc = x;
-    for (int k = 2; k < 40; ++k) {
-      term = -term * x / k;
-      acc += term / k;
-    }
-    return acc;
-  }
-  return expint_e1_cf(x) + std::log(x) + kEuler;
-}
+using sm::kCutReal;
+using sm::kCutSpec;
+using sm::expint_e1_cf;
 
 // Gauss-Legendre nodes and weights on [0, 1] (Newton iteration on P_n)
 void gauss_legendre01(int n, std::vector<double>& u, std::vector<double>& w) {
@@ -125,10 +97,11 @@ PeriodicGreen::PeriodicGreen(const double L[3], double eta_scale) {
       if (kz * kz / (4 * eta_ * eta_) > kCutSpec) break;
       kvec_.push_back({kz, 0, 0, 2.0 / Lz});
     }
-    gauss_legendre01(48, gl_u_, gl_w_);
+    gauss_legendre01(sm::kGaussLegendre, gl_u_, gl_w_);
   }
+  fill_params();   // before the regular part, which evaluates the real-space sum
   // regular part at the origin
-  double r = real_space(0, 0, 0, true) - 2 * eta_ / std::sqrt(kPi);
+  double r = sm::pgf_real_space(P_, 0, 0, 0, true) - 2 * eta_ / std::sqrt(kPi);
   if (dim_ == 3) {
     const double V = L_[0] * L_[1] * L_[2];
     for (auto& kv : kvec_) r += kv[3];
@@ -143,79 +116,30 @@ PeriodicGreen::PeriodicGreen(const double L[3], double eta_scale) {
     for (auto& kv : kvec_) r += kv[3] * expint_e1_cf(kv[0] * kv[0] / (4 * eta_ * eta_));
   }
   reg0_ = r;
+  P_.reg0 = r;
 }
 
-void PeriodicGreen::min_image(double& x, double& y, double& z) const {
-  double* v[3] = {&x, &y, &z};
-  for (int a = 0; a < 3; ++a)
-    if (per_[a]) *v[a] -= std::nearbyint(*v[a] / L_[a]) * L_[a];
-}
-
-double PeriodicGreen::real_space(double x, double y, double z, bool skip_origin) const {
-  double acc = 0;
-  const double cut = kCutReal / eta_ + 1e-300;
-  for (int i = -nimg_[0]; i <= nimg_[0]; ++i)
-    for (int j = -nimg_[1]; j <= nimg_[1]; ++j)
-      for (int k = -nimg_[2]; k <= nimg_[2]; ++k) {
-        if (skip_origin && !i && !j && !k) continue;
-        double dx = x + i * L_[0], dy = y + j * L_[1], dz = z + k * L_[2];
-        double d = std::sqrt(dx * dx + dy * dy + dz * dz);
-        if (d > 1.5 * cut) continue;   // erfc below 1e-40
-        acc += std::erfc(eta_ * d) / d;
-      }
-  return acc;
-}
-
-double PeriodicGreen::g3(double x, double y, double z) const {
-  double acc = real_space(x, y, z, false);
-  for (auto& kv : kvec_) acc += kv[3] * std::cos(kv[0] * x + kv[1] * y + kv[2] * z);
-  return acc - kPi / (eta_ * eta_ * L_[0] * L_[1] * L_[2]);
-}
-
-double PeriodicGreen::g2(double x, double y, double z) const {
-  double r[3] = {x, y, z};
-  const double ra = r[ax_[0]], rb = r[ax_[1]], zz = r[ax_[2]];
-  const double Ar = L_[ax_[0]] * L_[ax_[1]];
-  double acc = real_space(x, y, z, false);
-  for (auto& kv : kvec_) {
-    double kk = kv[2];
-    double slab = 0;
-    for (int sgn = -1; sgn <= 1; sgn += 2) {
-      double a = kk / (2 * eta_) + sgn * eta_ * zz;
-      double t = std::erfc(a);
-      if (t > 0) slab += std::exp(sgn * kk * zz + std::log(t));
-    }
-    acc += kv[3] * std::cos(kv[0] * ra + kv[1] * rb) * slab;
+void PeriodicGreen::fill_params() {
+  P_ = sm::PgfParams();
+  P_.dim = dim_;
+  for (int a = 0; a < 3; ++a) {
+    P_.ax[a] = ax_[a];
+    P_.L[a] = L_[a];
+    P_.per[a] = per_[a] ? 1 : 0;
+    P_.nimg[a] = nimg_[a];
   }
-  acc -= 2 * kPi / Ar * (zz * std::erf(eta_ * zz) + std::exp(-eta_ * eta_ * zz * zz) / (eta_ * std::sqrt(kPi)));
-  return acc;
-}
-
-double PeriodicGreen::g1(double x, double y, double z) const {
-  double r[3] = {x, y, z};
-  const int a = ax_[0];
-  const double zz = r[a];
-  const double rho2 = x * x + y * y + z * z - zz * zz;
-  const double rho2c = rho2 > 0 ? rho2 : 0.0;
-  const double Lz = L_[a];
-  double acc = real_space(x, y, z, false);
-  acc += (2.0 * std::log(eta_) - ein(eta_ * eta_ * rho2c)) / Lz;
-  const double b = rho2c * eta_ * eta_;
-  for (auto& kv : kvec_) {
-    const double aa = kv[0] * kv[0] / (4 * eta_ * eta_);
-    double f = 0;
-    for (size_t i = 0; i < gl_u_.size(); ++i) f += gl_w_[i] * std::exp(-b * gl_u_[i] - aa / gl_u_[i]) / gl_u_[i];
-    acc += kv[3] * std::cos(kv[0] * zz) * f;
+  P_.eta = eta_;
+  kflat_.clear();
+  for (auto& kv : kvec_) kflat_.insert(kflat_.end(), kv.begin(), kv.end());
+  P_.nk = (int)kvec_.size();
+  P_.kvec = kflat_.data();
+  P_.ngl = (int)gl_u_.size();
+  for (int i = 0; i < P_.ngl; ++i) {
+    P_.gl_u[i] = gl_u_[i];
+    P_.gl_w[i] = gl_w_[i];
   }
-  return acc;
 }
 
-double PeriodicGreen::operator()(double x, double y, double z) const {
-  if (dim_ == 0) return 1.0 / std::sqrt(x * x + y * y + z * z);
-  min_image(x, y, z);
-  if (dim_ == 3) return g3(x, y, z);
-  if (dim_ == 2) return g2(x, y, z);
-  return g1(x, y, z);
-}
+double PeriodicGreen::operator()(double x, double y, double z) const { return sm::pgf_eval(P_, x, y, z); }
 
 }  // namespace pmfem

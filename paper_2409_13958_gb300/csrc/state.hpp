@@ -43,6 +43,13 @@ struct pmfem_state {
   // whenever the device data are (re)built, in the context that holds them
   void* noalloc_base = nullptr;
   std::string noalloc_why;
+  // implicit midpoint steps: work vectors (N' x 3), preconditioner blocks, exchange diagonal,
+  // reduction scratch; device memory of the handle (freed with the device data)
+  std::vector<void*> imp_vec;
+  void* imp_pinv = nullptr;
+  void* imp_c = nullptr;
+  void* imp_red = nullptr;
+  int imp_prec = -1;
   // per-launch timing (pmfem_profile)
   bool prof_on = false;
   std::vector<cudaEvent_t> ev_pool;

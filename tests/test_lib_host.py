@@ -224,3 +224,20 @@ def test_batch_create_checks_its_cells_and_gives_offsets():
         b.set_applied_field(3, 1.0, 0.0, 0.0)
     assert e.value.code == -1
     b.destroy()
+
+
+def test_setup_device_switch_rejects_bad_values():
+    import meshgen
+    from paper_2409_13958_gb300 import Pmfem, PmfemError
+    m = meshgen.film_cell(4, 4, 2)
+    h = Pmfem.create_mesh(m.xyz, m.tets, 8e5, 1.3e-11, 0.02)
+    for bad in (2, -1):
+        with pytest.raises(PmfemError) as e:
+            h._ck(h._lib.pmfem_set_setup_device(h.h, bad))
+        assert e.value.code == -1
+    h.set_setup_device(False)
+    h.set_periodicity(*m.periods)
+    t = h.setup_times()
+    assert set(t) == {"pairing", "operators", "grid", "spectrum", "near_elements", "precorrection", "device"}
+    assert t["precorrection"] >= 0 and t["device"] == 0.0
+    h.destroy()
