@@ -98,76 +98,122 @@ int setup_operators(Setup& s, Error& err) {
       }
   });
 
-  // true boundary faces: mapped vertex triples that occur once
+  // true boundary faces: mapped vertex triples that occur once.  Faces are bucketed by their
+  // smallest unknown (a counting sort), each bucket sorted on its own: the same order as one
+  // global sort by (a, b, c, ref), in parallel.
   struct F {
     int32_t a, b, c;
     int64_t ref;
   };
   static const int opp[4][3] = {{1, 2, 3}, {0, 3, 2}, {0, 1, 3}, {0, 2, 1}};
-  std::vector<F> faces(4 * T);
-  parallel_for(T, [&](int64_t b, int64_t e) {
-    for (int64_t t = b; t < e; ++t)
-      for (int f = 0; f < 4; ++f) {
-        int32_t m[3];
-        for (int j = 0; j < 3; ++j) m[j] = s.lca[s.tets[4 * t + opp[f][j]]];
-        std::sort(m, m + 3);
-        faces[4 * t + f] = {m[0], m[1], m[2], 4 * t + f};
-      }
-  });
-  std::sort(faces.begin(), faces.end(), [](const F& x, const F& y) {
-    if (x.a != y.a) return x.a < y.a;
-    if (x.b != y.b) return x.b < y.b;
-    if (x.c != y.c) return x.c < y.c;
-    return x.ref < y.ref;
-  });
-  s.bfaces.clear();
-  for (size_t i = 0; i < faces.size();) {
-    size_t j = i + 1;
-    while (j < faces.size() && faces[j].a == faces[i].a && faces[j].b == faces[i].b && faces[j].c == faces[i].c) ++j;
-    if (j - i == 1) {
-      int64_t t = faces[i].ref / 4;
-      int f = (int)(faces[i].ref % 4);
-      int32_t v[3];
-      for (int k = 0; k < 3; ++k) v[k] = s.tets[4 * t + opp[f][k]];
-      // outward with respect to the owning tetrahedron
-      double X[4][3];
-      load_tet(s, t, X);
-      double cen[3] = {0, 0, 0};
-      for (int k = 0; k < 4; ++k)
-        for (int d = 0; d < 3; ++d) cen[d] += 0.25 * X[k][d];
-      const double* pa = &s.xyz[3 * (int64_t)v[0]];
-      const double* pb = &s.xyz[3 * (int64_t)v[1]];
-      const double* pc = &s.xyz[3 * (int64_t)v[2]];
-      double e1[3] = {pb[0] - pa[0], pb[1] - pa[1], pb[2] - pa[2]};
-      double e2[3] = {pc[0] - pa[0], pc[1] - pa[1], pc[2] - pa[2]};
-      double n[3] = {e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2], e1[0] * e2[1] - e1[1] * e2[0]};
-      double out = n[0] * (pa[0] - cen[0]) + n[1] * (pa[1] - cen[1]) + n[2] * (pa[2] - cen[2]);
-      if (out < 0) std::swap(v[1], v[2]);
-      s.bfaces.insert(s.bfaces.end(), v, v + 3);
-    }
-    i = j;
+  std::vector<int64_t> fptr(Np + 1, 0);
+  auto face_key = [&](int64_t slot, int32_t m[3]) {
+    const int64_t t = slot / 4;
+    const int f = (int)(slot % 4);
+    for (int j = 0; j < 3; ++j) m[j] = s.lca[s.tets[4 * t + opp[f][j]]];
+    std::sort(m, m + 3);
+  };
+  for (int64_t i = 0; i < 4 * T; ++i) {
+    int32_t m[3];
+    face_key(i, m);
+    fptr[m[0] + 1]++;
   }
+  for (int64_t u = 0; u < Np; ++u) fptr[u + 1] += fptr[u];
+  std::vector<F> faces(4 * T);
+  {
+    std::vector<int64_t> fill(fptr.begin(), fptr.end() - 1);
+    for (int64_t i = 0; i < 4 * T; ++i) {
+      int32_t m[3];
+      face_key(i, m);
+      faces[fill[m[0]]++] = {m[0], m[1], m[2], i};
+    }
+  }
+  std::vector<std::vector<int32_t>> bf_rows(Np);
+  parallel_for(Np, [&](int64_t ub, int64_t ue) {
+    for (int64_t u = ub; u < ue; ++u) {
+      std::sort(faces.begin() + fptr[u], faces.begin() + fptr[u + 1], [](const F& x, const F& y) {
+        if (x.b != y.b) return x.b < y.b;
+        if (x.c != y.c) return x.c < y.c;
+        return x.ref < y.ref;
+      });
+      for (int64_t i = fptr[u]; i < fptr[u + 1];) {
+        int64_t j = i + 1;
+        while (j < fptr[u + 1] && faces[j].b == faces[i].b && faces[j].c == faces[i].c) ++j;
+        if (j - i == 1) {
+          const int64_t t = faces[i].ref / 4;
+          const int f = (int)(faces[i].ref % 4);
+          int32_t v[3];
+          for (int k = 0; k < 3; ++k) v[k] = s.tets[4 * t + opp[f][k]];
+          // outward with respect to the owning tetrahedron
+          double X[4][3];
+          load_tet(s, t, X);
+          double cen[3] = {0, 0, 0};
+          for (int k = 0; k < 4; ++k)
+            for (int d = 0; d < 3; ++d) cen[d] += 0.25 * X[k][d];
+          const double* pa = &s.xyz[3 * (int64_t)v[0]];
+          const double* pb = &s.xyz[3 * (int64_t)v[1]];
+          const double* pc = &s.xyz[3 * (int64_t)v[2]];
+          double e1[3] = {pb[0] - pa[0], pb[1] - pa[1], pb[2] - pa[2]};
+          double e2[3] = {pc[0] - pa[0], pc[1] - pa[1], pc[2] - pa[2]};
+          double n[3] = {e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2], e1[0] * e2[1] - e1[1] * e2[0]};
+          double out = n[0] * (pa[0] - cen[0]) + n[1] * (pa[1] - cen[1]) + n[2] * (pa[2] - cen[2]);
+          if (out < 0) std::swap(v[1], v[2]);
+          bf_rows[u].insert(bf_rows[u].end(), v, v + 3);
+        }
+        i = j;
+      }
+    }
+  }, 1024);
+  s.bfaces.clear();
+  for (int64_t u = 0; u < Np; ++u) s.bfaces.insert(s.bfaces.end(), bf_rows[u].begin(), bf_rows[u].end());
+  std::vector<F>().swap(faces);
 
-  // mean length of the unique edges of the original mesh
-  std::vector<uint64_t> edges;
-  edges.reserve(6 * T);
+  // mean length of the unique edges of the original mesh: edges bucketed by their smaller
+  // node, each bucket sorted and de-duplicated in parallel, lengths summed per bucket and the
+  // bucket sums added in node order
   static const int ep[6][2] = {{0, 1}, {0, 2}, {0, 3}, {1, 2}, {1, 3}, {2, 3}};
+  const int64_t N = s.N;
+  std::vector<int64_t> eptr(N + 1, 0);
   for (int64_t t = 0; t < T; ++t)
     for (int k = 0; k < 6; ++k) {
-      uint64_t a = (uint32_t)s.tets[4 * t + ep[k][0]], b = (uint32_t)s.tets[4 * t + ep[k][1]];
-      if (a > b) std::swap(a, b);
-      edges.push_back((a << 32) | b);
+      const int32_t a0 = s.tets[4 * t + ep[k][0]], b0 = s.tets[4 * t + ep[k][1]];
+      eptr[std::min(a0, b0) + 1]++;
     }
-  std::sort(edges.begin(), edges.end());
-  edges.erase(std::unique(edges.begin(), edges.end()), edges.end());
-  double acc = 0;
-  for (uint64_t e : edges) {
-    int64_t a = (int64_t)(e >> 32), b = (int64_t)(e & 0xffffffffu);
-    double d0 = s.xyz[3 * a] - s.xyz[3 * b], d1 = s.xyz[3 * a + 1] - s.xyz[3 * b + 1],
-           d2 = s.xyz[3 * a + 2] - s.xyz[3 * b + 2];
-    acc += std::sqrt(d0 * d0 + d1 * d1 + d2 * d2);
+  for (int64_t u = 0; u < N; ++u) eptr[u + 1] += eptr[u];
+  std::vector<int32_t> other(eptr[N]);
+  {
+    std::vector<int64_t> fill(eptr.begin(), eptr.end() - 1);
+    for (int64_t t = 0; t < T; ++t)
+      for (int k = 0; k < 6; ++k) {
+        const int32_t a0 = s.tets[4 * t + ep[k][0]], b0 = s.tets[4 * t + ep[k][1]];
+        other[fill[std::min(a0, b0)]++] = std::max(a0, b0);
+      }
   }
-  s.mean_edge = acc / (double)edges.size();
+  std::vector<double> bucket_len(N, 0.0);
+  std::vector<int64_t> bucket_cnt(N, 0);
+  parallel_for(N, [&](int64_t ub, int64_t ue) {
+    for (int64_t a = ub; a < ue; ++a) {
+      auto b0 = other.begin() + eptr[a], b1 = other.begin() + eptr[a + 1];
+      std::sort(b0, b1);
+      b1 = std::unique(b0, b1);
+      bucket_cnt[a] = b1 - b0;
+      double acc = 0;
+      for (auto it = b0; it != b1; ++it) {
+        const int64_t b = *it;
+        double d0 = s.xyz[3 * a] - s.xyz[3 * b], d1 = s.xyz[3 * a + 1] - s.xyz[3 * b + 1],
+               d2 = s.xyz[3 * a + 2] - s.xyz[3 * b + 2];
+        acc += std::sqrt(d0 * d0 + d1 * d1 + d2 * d2);
+      }
+      bucket_len[a] = acc;
+    }
+  }, 1024);
+  double acc = 0;
+  int64_t ne = 0;
+  for (int64_t a = 0; a < N; ++a) {
+    acc += bucket_len[a];
+    ne += bucket_cnt[a];
+  }
+  s.mean_edge = acc / (double)ne;
   return OK;
 }
 
