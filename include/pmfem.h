@@ -280,6 +280,27 @@ int pmfem_llg_step_implicit(pmfem_t h, double dt, int nsteps, const pmfem_implic
                             void* stream);
 
 /*
+ * Bloch-phase periodic Green's function (Eq. 15 with k0 != 0; Sec. 4.3 excites phase-shifted
+ * periodic sources): G_k(r) = sum_l e^{-j k0.l} / |r - l| over the lattice of the handle's
+ * periodic axes, k0 (host, 3 doubles, rad/m) along those axes and off their reciprocal lattice.
+ * With q~ = q e^{j k0.r} and the twisted kernel K~(d) = G_k(d) e^{j k0.d}, which is periodic
+ * and Hermitian, the potential of quasi-periodic sources is e^{-j k0.r} times the circular
+ * convolution of q~ with K~ on the grid of Eq. 16 (BAIM step 2; open axes zero-padded to 2N).
+ *
+ * pmfem_bloch_spectrum: the spectrum of K~ on the FFT grid, computed on the GPU in FP64 (Ewald
+ * sums as for k0 = 0, plus its discrete transform): out host fft[0] x fft[1] x fft[2] doubles,
+ * x fastest, unscaled; it is real (max_imag, host double or NULL, receives the largest
+ * imaginary part of the transform).  Synchronises the device.
+ * pmfem_bloch_convolve: U~ = the convolution of Q~ with K~ on the node grid, Q and U device
+ * dims[0] x dims[1] x dims[2] complex numbers (interleaved re, im) of the precision's type T,
+ * x fastest; enqueued on stream.  The spectrum of the last k0 is kept on the device.
+ * The transforms are separable discrete Fourier sums in FP64 accumulation (O(F) work per point
+ * and axis).  EINVAL for k0 off the periodic axes or on the reciprocal lattice.
+ */
+int pmfem_bloch_spectrum(pmfem_t h, const double* k0, double* out, double* max_imag);
+int pmfem_bloch_convolve(pmfem_t h, const double* k0, const void* Q, void* U, void* stream);
+
+/*
  * Per-launch timing for measurement.  pmfem_profile(h, 1) starts recording a CUDA event
  * pair around every kernel the handle launches (on the stream it launches on) and clears
  * the totals; 0 stops recording.  pmfem_profile_read synchronises the device and writes,

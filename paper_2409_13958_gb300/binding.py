@@ -74,6 +74,8 @@ SIGNATURES = {
     "pmfem_batch_llg_step": (_c.c_int, [_vp, _dbl, _c.c_int, _vp]),
     "pmfem_batch_sync": (_c.c_int, [_vp]),
     "pmfem_setup_times": (_c.c_int, [_vp, _vp, _c.c_int]),
+    "pmfem_bloch_spectrum": (_c.c_int, [_vp, _vp, _vp, _vp]),
+    "pmfem_bloch_convolve": (_c.c_int, [_vp, _vp, _vp, _vp, _vp]),
     "pmfem_grid_info": (_c.c_int, [_vp, _vp, _vp, _vp, _vp]),
     "pmfem_export_spectrum": (_c.c_int, [_vp, _vp]),
     "pmfem_folded_positions": (_c.c_int, [_vp, _vp]),
@@ -323,6 +325,20 @@ class Pmfem:
         self._ck(self._lib.pmfem_setup_times(self.h, out.ctypes.data, 7))
         keys = ("pairing", "operators", "grid", "spectrum", "near_elements", "precorrection", "device")
         return dict(zip(keys, out.tolist()))
+
+    def bloch_spectrum(self, k0):
+        """Real spectrum of the twisted Bloch kernel, shape (fft z, fft y, fft x), and the
+        largest imaginary part of the transform."""
+        dims, fft, _, _ = self.grid_info()
+        k = np.ascontiguousarray(k0, dtype=np.float64)
+        out = np.empty((fft[2], fft[1], fft[0]), dtype=np.float64)
+        mi = ctypes.c_double(0.0)
+        self._ck(self._lib.pmfem_bloch_spectrum(self.h, k.ctypes.data, out.ctypes.data, ctypes.byref(mi)))
+        return out, mi.value
+
+    def bloch_convolve(self, k0, Q, U, stream=None):
+        k = np.ascontiguousarray(k0, dtype=np.float64)
+        self._ck(self._lib.pmfem_bloch_convolve(self.h, k.ctypes.data, _addr(Q), _addr(U), _stream(stream)))
 
     def grid_info(self):
         dims = np.zeros(3, np.int32)

@@ -10,6 +10,7 @@
 #include "../../include/pmfem.h"
 #include "device.hpp"
 #include "internal.hpp"
+#include "bloch.hpp"
 #include "implicit.hpp"
 #include "state.hpp"
 
@@ -94,6 +95,9 @@ void free_device(pmfem_t h) {
   h->imp_vec.clear();
   h->imp_pinv = h->imp_c = h->imp_red = nullptr;
   h->imp_prec = -1;
+  h->bloch_spec = nullptr;
+  h->bloch_buf[0] = h->bloch_buf[1] = h->bloch_buf[2] = nullptr;
+  h->bloch_prec = -1;
   h->dev_ready = false;
   h->dev_prec = -1;
 }
@@ -975,6 +979,69 @@ int pmfem_llg_step_implicit(pmfem_t h, double dt, int nsteps, const pmfem_implic
   if (stats)
     for (int i = 0; i < 4; ++i) stats[i] = st4[i];
   return rc;
+}
+
+int pmfem_bloch_spectrum(pmfem_t h, const double* k0, double* out, double* max_imag) {
+  if (!h || !k0 || !out) return EINVAL_;
+  if (!h->s.ready) return fail(h, ESTATE_, "call pmfem_set_periodicity first");
+  const int64_t n = (int64_t)h->s.fft[0] * h->s.fft[1] * h->s.fft[2];
+  double* d = nullptr;
+  PMFEM_CK(h, cudaMalloc(&d, n * sizeof(double)));
+  Error err;
+  int rc = bloch_spectrum_device(h->s, k0, d, max_imag, err);
+  if (!rc) {
+    cudaError_t e = cudaMemcpy(out, d, n * sizeof(double), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) {
+      err = {ECUDA_, std::string("copy of the Bloch spectrum: ") + cudaGetErrorString(e)};
+      rc = ECUDA_;
+    }
+  }
+  cudaFree(d);
+  return rc ? fail(h, rc, err.msg) : OK;
+}
+
+int pmfem_bloch_convolve(pmfem_t h, const double* k0, const void* Q, void* U, void* stream) {
+  if (!h || !k0 || !Q || !U || Q == U) return fail(h, EINVAL_, "k0, Q and U are required and Q, U distinct");
+  int rc = ensure_device(h);
+  if (rc) return rc;
+  const int64_t n = (int64_t)h->s.fft[0] * h->s.fft[1] * h->s.fft[2];
+  const bool f64 = h->dev_prec == PMFEM_FP64;
+  const size_t es = f64 ? sizeof(double) : sizeof(float);
+  if (!h->bloch_spec || h->bloch_prec != h->dev_prec || h->bloch_k0[0] != k0[0] || h->bloch_k0[1] != k0[1] ||
+      h->bloch_k0[2] != k0[2]) {
+    if (!h->bloch_spec || h->bloch_prec != h->dev_prec) {
+      if ((rc = dalloc(h, &h->bloch_spec, n * es))) return rc;
+      for (int i = 0; i < 3; ++i)
+        if ((rc = dalloc(h, &h->bloch_buf[i], n * 2 * es))) return rc;
+    }
+    double* d = nullptr;
+    PMFEM_CK(h, cudaMalloc(&d, n * sizeof(double)));
+    Error err;
+    rc = bloch_spectrum_device(h->s, k0, d, nullptr, err);
+    if (!rc) {
+      if (f64) {
+        cudaMemcpy(h->bloch_spec, d, n * sizeof(double), cudaMemcpyDeviceToDevice);
+      } else {
+        std::vector<double> hs(n);
+        std::vector<float> hf(n);
+        cudaMemcpy(hs.data(), d, n * sizeof(double), cudaMemcpyDeviceToHost);
+        for (int64_t i = 0; i < n; ++i) hf[i] = (float)hs[i];
+        cudaMemcpy(h->bloch_spec, hf.data(), n * sizeof(float), cudaMemcpyHostToDevice);
+      }
+    }
+    cudaFree(d);
+    if (rc) return fail(h, rc, err.msg);
+    for (int a = 0; a < 3; ++a) h->bloch_k0[a] = k0[a];
+    h->bloch_prec = h->dev_prec;
+  }
+  cudaStream_t st = stream ? (cudaStream_t)stream : h->stream;
+  if (f64)
+    bloch_convolve_device<double>(h->s, (const double*)h->bloch_spec, Q, U, h->bloch_buf[0], h->bloch_buf[1],
+                                  h->bloch_buf[2], st);
+  else
+    bloch_convolve_device<float>(h->s, (const float*)h->bloch_spec, Q, U, h->bloch_buf[0], h->bloch_buf[1],
+                                 h->bloch_buf[2], st);
+  return check_launch(h);
 }
 
 int pmfem_sync(pmfem_t h) {

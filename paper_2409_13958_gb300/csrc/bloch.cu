@@ -1,0 +1,326 @@
+// Bloch-phase PGF (Eq. 15 with k0 != 0) on the GPU: the twisted grid kernel in FP64 by the
+// Ewald-type sums, its spectrum, and the grid convolution of BAIM step 2 for sources that repeat
+// with the phase e^{-j k0.l} (phase-shifted excitation, Sec. 4.3).
+//
+// With q~ = q e^{j k0.r} and K~(d) = G_k(d) e^{j k0.d}, which is periodic and Hermitian, the
+// quasi-periodic potential is e^{-j k0.r} times the circular convolution of q~ with K~ on the grid
+// of Eq. 16 (open axes zero-padded to 2N as for k0 = 0); the spectrum of a Hermitian kernel is
+// real.  The transforms here are separable discrete Fourier sums, O(F) per point and axis, in
+// FP64 accumulation: a direct path for this service, not the library's fast FFT.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <string>
+#include <vector>
+
+#include "../../include/pmfem.h"
+#include "bloch.hpp"
+#include "setup_math.hpp"
+
+namespace pmfem {
+namespace {
+
+constexpr int kB = 256;
+unsigned nblk(int64_t n) { return (unsigned)((n + kB - 1) / kB); }
+
+struct GridDesc {
+  int dims[3], fft[3], per[3];
+  double delta[3];
+};
+
+// signed offset of FFT index j along an axis; false where the open-axis layout holds zero
+__device__ __forceinline__ bool offset_of(const GridDesc& g, int a, int j, int* d) {
+  const int N = g.dims[a];
+  if (g.per[a]) {
+    *d = j <= N / 2 ? j : j - N;
+    return true;
+  }
+  if (j == N) return false;
+  *d = j < N ? j : j - 2 * N;
+  return true;
+}
+
+__global__ void k_bloch_table(sm::BlochParams P, GridDesc g, double r0re, double r0im, double2* __restrict__ out) {
+  const int64_t n = (int64_t)g.fft[0] * g.fft[1] * g.fft[2];
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int jx = (int)(i % g.fft[0]), jy = (int)((i / g.fft[0]) % g.fft[1]), jz = (int)(i / ((int64_t)g.fft[0] * g.fft[1]));
+  int dx, dy, dz;
+  if (!offset_of(g, 0, jx, &dx) || !offset_of(g, 1, jy, &dy) || !offset_of(g, 2, jz, &dz)) {
+    out[i] = make_double2(0.0, 0.0);
+    return;
+  }
+  if (!dx && !dy && !dz) {
+    out[i] = make_double2(r0re, r0im);
+    return;
+  }
+  const double x = dx * g.delta[0], y = dy * g.delta[1], z = dz * g.delta[2];
+  double re, im;
+  sm::bloch_eval(P, x, y, z, false, &re, &im);
+  const double ph = P.k0[0] * x + P.k0[1] * y + P.k0[2] * z;   // the twist e^{j k0.d}
+  const double c = cos(ph), s = sin(ph);
+  out[i] = make_double2(re * c - im * s, re * s + im * c);
+}
+
+template <typename C>
+__device__ __forceinline__ double re_of(const C& v) { return (double)v.x; }
+template <typename C>
+__device__ __forceinline__ double im_of(const C& v) { return (double)v.y; }
+
+// out[c, c_axis = k] = scale sum_d in[c, c_axis = d] e^{sign 2 pi i d k / F} over a shape S
+template <typename C>
+__global__ void k_dft_axis(const C* __restrict__ in, C* __restrict__ out, int S0, int S1, int S2, int axis, int sign,
+                           double scale) {
+  const int64_t n = (int64_t)S0 * S1 * S2;
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int c[3] = {(int)(i % S0), (int)((i / S0) % S1), (int)(i / ((int64_t)S0 * S1))};
+  const int F = axis == 0 ? S0 : axis == 1 ? S1 : S2;
+  const int k = c[axis];
+  const int64_t st = axis == 0 ? 1 : axis == 1 ? S0 : (int64_t)S0 * S1;
+  c[axis] = 0;
+  const int64_t base = c[0] + (int64_t)S0 * (c[1] + (int64_t)S1 * c[2]);
+  double ar = 0, ai = 0;
+  for (int d = 0; d < F; ++d) {
+    double s, co;
+    sincospi(2.0 * (double)(((int64_t)d * k) % F) / F, &s, &co);
+    s *= sign;
+    const C v = in[base + d * st];
+    ar += re_of(v) * co - im_of(v) * s;
+    ai += re_of(v) * s + im_of(v) * co;
+  }
+  using E = decltype(out[0].x);
+  out[i].x = (E)(scale * ar);
+  out[i].y = (E)(scale * ai);
+}
+
+template <typename C>
+__global__ void k_pad(const C* __restrict__ Q, C* __restrict__ buf, GridDesc g) {
+  const int64_t n = (int64_t)g.fft[0] * g.fft[1] * g.fft[2];
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int jx = (int)(i % g.fft[0]), jy = (int)((i / g.fft[0]) % g.fft[1]), jz = (int)(i / ((int64_t)g.fft[0] * g.fft[1]));
+  C v;
+  v.x = 0;
+  v.y = 0;
+  if (jx < g.dims[0] && jy < g.dims[1] && jz < g.dims[2]) v = Q[jx + (int64_t)g.dims[0] * (jy + (int64_t)g.dims[1] * jz)];
+  buf[i] = v;
+}
+
+template <typename C, typename T>
+__global__ void k_mul_real(C* __restrict__ buf, const T* __restrict__ spec, int64_t n) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  buf[i].x *= spec[i];
+  buf[i].y *= spec[i];
+}
+
+template <typename C>
+__global__ void k_crop(const C* __restrict__ buf, C* __restrict__ U, GridDesc g) {
+  const int64_t n = (int64_t)g.dims[0] * g.dims[1] * g.dims[2];
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int x = (int)(i % g.dims[0]), y = (int)((i / g.dims[0]) % g.dims[1]), z = (int)(i / ((int64_t)g.dims[0] * g.dims[1]));
+  U[i] = buf[x + (int64_t)g.fft[0] * (y + (int64_t)g.fft[1] * z)];
+}
+
+__global__ void k_real_part(const double2* __restrict__ in, double* __restrict__ re, double* __restrict__ im_abs,
+                            int64_t n) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  re[i] = in[i].x;
+  im_abs[i] = fabs(in[i].y);
+}
+
+GridDesc desc(const Setup& s) {
+  GridDesc g;
+  for (int a = 0; a < 3; ++a) {
+    g.dims[a] = s.dims[a];
+    g.fft[a] = s.fft[a];
+    g.per[a] = s.periodic[a] ? 1 : 0;
+    g.delta[a] = s.delta[a];
+  }
+  return g;
+}
+
+template <typename C>
+void dft3(const C* in, C* tmp, C* out, const GridDesc& g, int sign, double scale, cudaStream_t st) {
+  const int64_t n = (int64_t)g.fft[0] * g.fft[1] * g.fft[2];
+  k_dft_axis<C><<<nblk(n), kB, 0, st>>>(in, tmp, g.fft[0], g.fft[1], g.fft[2], 0, sign, 1.0);
+  k_dft_axis<C><<<nblk(n), kB, 0, st>>>(tmp, out, g.fft[0], g.fft[1], g.fft[2], 1, sign, 1.0);
+  k_dft_axis<C><<<nblk(n), kB, 0, st>>>(out, tmp, g.fft[0], g.fft[1], g.fft[2], 2, sign, scale);
+  cudaMemcpyAsync(out, tmp, n * sizeof(C), cudaMemcpyDeviceToDevice, st);
+}
+
+}  // namespace
+
+int bloch_params(const Setup& s, const double k0[3], sm::BlochParams& P, std::vector<double>& kv, Error& err) {
+  int dim = 0;
+  double prod = 1;
+  P = sm::BlochParams();
+  for (int a = 0; a < 3; ++a) {
+    P.L[a] = s.periodic[a] ? s.L[a] : 0.0;
+    if (s.periodic[a]) {
+      P.ax[dim++] = a;
+      prod *= s.L[a];
+    } else if (k0[a] != 0) {
+      err = {EINVAL_, "k0 must lie along the periodic axes"};
+      return EINVAL_;
+    }
+    P.k0[a] = k0[a];
+  }
+  if (dim == 0) {
+    err = {EINVAL_, "the Bloch-phase Green's function needs a periodic axis"};
+    return EINVAL_;
+  }
+  int k = dim;
+  for (int a = 0; a < 3; ++a)
+    if (!s.periodic[a]) P.ax[k++] = a;
+  P.dim = dim;
+  P.eta = std::sqrt(kPi) / std::pow(prod, 1.0 / dim);
+  // off the reciprocal lattice: no shifted wavevector may vanish
+  for (int a = 0; a < 3; ++a)
+    if (s.periodic[a]) {
+      const double f = k0[a] * s.L[a] / (2 * kPi);
+      if (std::fabs(f - std::nearbyint(f)) < 1e-9 && dim > 0) {
+        bool all = true;
+        for (int b = 0; b < 3; ++b)
+          if (s.periodic[b]) {
+            const double fb = k0[b] * s.L[b] / (2 * kPi);
+            all = all && std::fabs(fb - std::nearbyint(fb)) < 1e-9;
+          }
+        if (all) {
+          err = {EINVAL_, "k0 on the reciprocal lattice: use the k0 = 0 path"};
+          return EINVAL_;
+        }
+      }
+    }
+  for (int a = 0; a < 3; ++a) {
+    if (!s.periodic[a]) continue;
+    const double ext = 0.5 * s.L[a];   // table offsets reach half a period along a periodic axis
+    P.nimg[a] = (int)std::ceil((sm::kCutReal / P.eta + ext) / s.L[a]) + 1;
+  }
+  const double kmax = 2.0 * P.eta * std::sqrt(sm::kCutSpec);
+  int nr[3] = {0, 0, 0};
+  for (int a = 0; a < 3; ++a)
+    if (s.periodic[a]) nr[a] = (int)std::ceil((kmax + std::fabs(k0[a])) * s.L[a] / (2 * kPi)) + 1;
+  kv.clear();
+  double V = 1;
+  for (int a = 0; a < dim; ++a) V *= s.L[P.ax[a]];
+  for (int i = -nr[0]; i <= nr[0]; ++i)
+    for (int j = -nr[1]; j <= nr[1]; ++j)
+      for (int l = -nr[2]; l <= nr[2]; ++l) {
+        const int idx[3] = {i, j, l};
+        double g[3];
+        for (int a = 0; a < 3; ++a) g[a] = (s.periodic[a] ? 2 * kPi * idx[a] / s.L[a] : 0.0) + k0[a];
+        const double g2 = g[0] * g[0] + g[1] * g[1] + g[2] * g[2];
+        if (g2 / (4 * P.eta * P.eta) > sm::kCutSpec) continue;
+        double c;
+        if (dim == 3) c = 4 * kPi / V * std::exp(-g2 / (4 * P.eta * P.eta)) / g2;
+        else if (dim == 2) c = kPi / V / std::sqrt(g2);
+        else c = 1.0 / V;
+        kv.insert(kv.end(), {g[0], g[1], g[2], c});
+      }
+  P.nk = (int)(kv.size() / 4);
+  // 16-point Gauss-Legendre on [-1, 1] (Newton on P_16)
+  for (int i = 0; i < 16; ++i) {
+    double x = std::cos(kPi * (i + 0.75) / 16.5), dp = 1;
+    for (int it = 0; it < 100; ++it) {
+      double p0 = 1, p1 = x;
+      for (int kk = 2; kk <= 16; ++kk) {
+        const double p2 = ((2 * kk - 1) * x * p1 - (kk - 1) * p0) / kk;
+        p0 = p1;
+        p1 = p2;
+      }
+      dp = 16 * (x * p1 - p0) / (x * x - 1);
+      const double dx = p1 / dp;
+      x -= dx;
+      if (std::fabs(dx) < 1e-16) break;
+    }
+    P.gl_x[i] = x;
+    P.gl_w[i] = 2.0 / ((1 - x * x) * dp * dp);
+  }
+  return OK;
+}
+
+int bloch_spectrum_device(const Setup& s, const double k0[3], double* spec_dev, double* max_imag, Error& err) {
+  sm::BlochParams P;
+  std::vector<double> kv;
+  int rc = bloch_params(s, k0, P, kv, err);
+  if (rc) return rc;
+  const GridDesc g = desc(s);
+  const int64_t n = (int64_t)g.fft[0] * g.fft[1] * g.fft[2];
+  double* dkv = nullptr;
+  double2 *a = nullptr, *b = nullptr, *c = nullptr;
+  double* im = nullptr;
+  auto cleanup = [&]() {
+    cudaFree(dkv);
+    cudaFree(a);
+    cudaFree(b);
+    cudaFree(c);
+    cudaFree(im);
+  };
+  cudaError_t e = cudaMalloc(&dkv, std::max<size_t>(kv.size(), 4) * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&a, n * sizeof(double2));
+  if (e == cudaSuccess) e = cudaMalloc(&b, n * sizeof(double2));
+  if (e == cudaSuccess) e = cudaMalloc(&c, n * sizeof(double2));
+  if (e == cudaSuccess) e = cudaMalloc(&im, n * sizeof(double));
+  if (e == cudaSuccess && !kv.empty()) e = cudaMemcpy(dkv, kv.data(), kv.size() * sizeof(double), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    cleanup();
+    err = {ECUDA_, std::string("Bloch spectrum: ") + cudaGetErrorString(e)};
+    return ECUDA_;
+  }
+  P.kv = dkv;
+  // regular part at the origin: the image sum without l = 0, minus the Gaussian self term
+  double r0re = 0, r0im = 0;
+  {
+    std::vector<double> hk = kv;
+    sm::BlochParams Ph = P;
+    Ph.kv = hk.data();
+    sm::bloch_eval(Ph, 0, 0, 0, true, &r0re, &r0im);
+    r0re -= 2 * P.eta / std::sqrt(kPi);
+  }
+  k_bloch_table<<<nblk(n), kB>>>(P, g, r0re, r0im, a);
+  dft3<double2>(a, b, c, g, -1, 1.0, 0);
+  k_real_part<<<nblk(n), kB>>>(c, spec_dev, im, n);
+  e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  double mi = 0;
+  if (e == cudaSuccess && max_imag) {
+    std::vector<double> h(n);
+    e = cudaMemcpy(h.data(), im, n * sizeof(double), cudaMemcpyDeviceToHost);
+    for (double v : h) mi = std::max(mi, v);
+    *max_imag = mi;
+  }
+  cleanup();
+  if (e != cudaSuccess) {
+    err = {ECUDA_, std::string("Bloch spectrum kernels: ") + cudaGetErrorString(e)};
+    return ECUDA_;
+  }
+  return OK;
+}
+
+template <typename T>
+void bloch_convolve_device(const Setup& s, const T* spec, const void* Q, void* U, void* buf_a, void* buf_b,
+                           void* buf_c, cudaStream_t st) {
+  using C = typename std::conditional<sizeof(T) == 8, double2, float2>::type;
+  const GridDesc g = desc(s);
+  const int64_t n = (int64_t)g.fft[0] * g.fft[1] * g.fft[2];
+  const int64_t nn = (int64_t)g.dims[0] * g.dims[1] * g.dims[2];
+  C* a = (C*)buf_a;
+  C* b = (C*)buf_b;
+  C* c = (C*)buf_c;
+  k_pad<C><<<nblk(n), kB, 0, st>>>((const C*)Q, a, g);
+  dft3<C>(a, b, c, g, -1, 1.0, st);
+  k_mul_real<C, T><<<nblk(n), kB, 0, st>>>(c, spec, n);
+  dft3<C>(c, b, a, g, +1, 1.0 / (double)n, st);
+  k_crop<C><<<nblk(nn), kB, 0, st>>>(a, (C*)U, g);
+}
+
+template void bloch_convolve_device<double>(const Setup&, const double*, const void*, void*, void*, void*, void*,
+                                            cudaStream_t);
+template void bloch_convolve_device<float>(const Setup&, const float*, const void*, void*, void*, void*, void*,
+                                           cudaStream_t);
+
+}  // namespace pmfem

@@ -431,3 +431,85 @@ PMFEM_HD double precorr_value(const double* rn, const double* rk, const int img[
 
 }  // namespace sm
 }  // namespace pmfem
+
+namespace pmfem {
+namespace sm {
+
+// ------------------------------------------------------------------ Bloch-phase PGF
+// Eq. 15 with a phase per image, G_k(r) = sum_l e^{-j k0.l} / |r - l|, by Ewald splitting:
+// real-space images with their phases, then the smooth part summed over the shifted reciprocal
+// vectors g = G + k0 (kv rows: gx, gy, gz, coefficient): 3D coefficient (4 pi/V) e^{-g^2/4eta^2}/g^2;
+// 2D (pi/A)/|g| times the slab function of the open coordinate; 1D 1/L times
+// int_0^{eta^2} exp(-rho^2 s - g^2/4s) ds/s, summed with s = eta^2 e^{-t} by 16-point
+// Gauss-Legendre on unit panels of t (the rule stays accurate for the small |g| near k0).
+struct BlochParams {
+  int dim = 0;
+  int ax[3] = {0, 1, 2};
+  double L[3] = {0, 0, 0};
+  double k0[3] = {0, 0, 0};
+  double eta = 0;
+  int nimg[3] = {0, 0, 0};
+  int nk = 0;
+  const double* kv = nullptr;   // nk x 4
+  double gl_x[16] = {}, gl_w[16] = {};
+};
+
+PMFEM_HD double bloch_spectral_1d(double rho, double k, double eta, const double* glx, const double* glw) {
+  const double a = k * k / (4.0 * eta * eta), b = rho * rho * eta * eta;
+  const double T = a < 45.0 ? fmax(1.0, log(45.0 / a) + 1.0) : 1.0;
+  const int npan = (int)ceil(T);
+  double out = 0;
+  for (int p = 0; p < npan; ++p)
+    for (int i = 0; i < 16; ++i) {
+      const double t = p + 0.5 * (glx[i] + 1.0);
+      out += 0.5 * glw[i] * exp(-b * exp(-t) - a * exp(t));
+    }
+  return out;
+}
+
+// G_k(r); skip_origin drops the l = 0 image (for the regular part at r = 0)
+PMFEM_HD void bloch_eval(const BlochParams& P, double x, double y, double z, bool skip_origin, double* re,
+                         double* im) {
+  double sr = 0, si = 0;
+  const double cut = kCutReal / P.eta;
+  for (int i = -P.nimg[0]; i <= P.nimg[0]; ++i)
+    for (int j = -P.nimg[1]; j <= P.nimg[1]; ++j)
+      for (int k = -P.nimg[2]; k <= P.nimg[2]; ++k) {
+        if (skip_origin && !i && !j && !k) continue;
+        const double lx = i * P.L[0], ly = j * P.L[1], lz = k * P.L[2];
+        const double dx = x - lx, dy = y - ly, dz = z - lz;
+        const double d = sqrt(dx * dx + dy * dy + dz * dz);
+        if (d > 1.5 * cut) continue;
+        const double t = erfc(P.eta * d) / d;
+        const double ph = -(P.k0[0] * lx + P.k0[1] * ly + P.k0[2] * lz);
+        sr += t * cos(ph);
+        si += t * sin(ph);
+      }
+  const double r[3] = {x, y, z};
+  for (int q = 0; q < P.nk; ++q) {
+    const double* g = P.kv + 4 * q;
+    const double ph = -(g[0] * x + g[1] * y + g[2] * z);
+    double amp = g[3];
+    if (P.dim == 2) {
+      const double kk = sqrt(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
+      const double zz = r[P.ax[2]];
+      double slab = 0;
+      for (int sgn = -1; sgn <= 1; sgn += 2) {
+        const double e = erfc(kk / (2 * P.eta) + sgn * P.eta * zz);
+        if (e > 0) slab += exp(sgn * kk * zz + log(e));
+      }
+      amp *= slab;
+    } else if (P.dim == 1) {
+      const int a = P.ax[0];
+      const double rho2 = x * x + y * y + z * z - r[a] * r[a];
+      amp *= bloch_spectral_1d(sqrt(rho2 > 0 ? rho2 : 0.0), fabs(g[a]), P.eta, P.gl_x, P.gl_w);
+    }
+    sr += amp * cos(ph);
+    si += amp * sin(ph);
+  }
+  *re = sr;
+  *im = si;
+}
+
+}  // namespace sm
+}  // namespace pmfem

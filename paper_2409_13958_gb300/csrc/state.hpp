@@ -50,6 +50,12 @@ struct pmfem_state {
   void* imp_c = nullptr;
   void* imp_red = nullptr;
   int imp_prec = -1;
+  // Bloch-phase convolution: the spectrum of the last k0 (device, precision of the handle)
+  // and three complex scratch grids
+  void* bloch_spec = nullptr;
+  void* bloch_buf[3] = {nullptr, nullptr, nullptr};
+  double bloch_k0[3] = {0, 0, 0};
+  int bloch_prec = -1;
   // per-launch timing (pmfem_profile)
   bool prof_on = false;
   std::vector<cudaEvent_t> ev_pool;
