@@ -277,6 +277,8 @@ int build_device(pmfem_t h, DevOps<T>& d) {
   h->dev_info[10] = L.TY;
   h->dev_info[11] = L.TZ;
 
+  if ((rc = upload(h, L.bstart.data(), L.bstart.size(), &d.bstart))) return rc;
+  if ((rc = upload(h, L.regular.data(), L.regular.size(), &d.regular))) return rc;
   d.nx_exc = (int64_t)L.xnode.size();
   if ((rc = upload(h, L.xnode.data(), L.xnode.size(), &d.xnode))) return rc;
   if ((rc = upload(h, L.xgrid.data(), L.xgrid.size(), &d.xgrid))) return rc;

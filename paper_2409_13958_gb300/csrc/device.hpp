@@ -118,6 +118,10 @@ struct DevOps {
   const int32_t* base = nullptr;                  // Np x 3
   const T* frac = nullptr;                        // Np x 3
   const T* ghat = nullptr;                        // (F0/2+1)(F1/2+1)(F2/2+1), scaled by 1/(F0 F1 F2)
+  // box order for the projection with weights computed on the fly: first node of every box
+  // (boxes + 1, box-order index) and a flag per node whose stencil starts pl boxes below its box
+  const int32_t* bstart = nullptr;
+  const uint8_t* regular = nullptr;
   const C2* tw[3] = {nullptr, nullptr, nullptr};  // exp(-2 pi i j / F_a), j < F_a
   // work buffers
   T* q = nullptr;
