@@ -54,6 +54,10 @@ def parse(argv=None):
                     help="skip timing the host set-up beside the GPU set-up of the same mesh")
     ap.add_argument("--no-cufft", action="store_true", help="skip the cuFFT convolution comparison")
     ap.add_argument("--repeats", type=int, default=5, help="repeats of the timed steps for the median")
+    ap.add_argument("--sur-runs", type=int, default=20, help="trajectories that give the surrogate's training pairs")
+    ap.add_argument("--sur-steps", type=int, default=1000, help="RK4 steps per surrogate training trajectory")
+    ap.add_argument("--only", default=None, choices=["surrogate", "batch"],
+                    help="run one side leg alone and print its JSON object (diagnosis and profiling)")
     ap.add_argument("--out", default=None, help="also write the JSON line to this file")
     return ap.parse_args(argv)
 
@@ -542,51 +546,75 @@ def surrogate_leg(args, dist, world):
     dt = stable_dt(float(np.add.reduceat(np.abs(vals[:, 0]), rp[:-1]).max()))
     V = 64 ** 3
     st = torch.cuda.current_stream()   # every launch on one stream, ordered with the torch copies
-    runs, steps = 4, 16
-    Q = torch.empty((runs * steps, V), dtype=torch.float32, device="cuda")
-    U = torch.empty_like(Q)
+    # training pairs streamed run by run: each RK4 trajectory (seeded random m0) gives the grid
+    # charges Q and FFT potentials U of its states; their increments train the network in one
+    # pass and are then dropped; the last runs are held out
+    runs, steps = args.sur_runs, args.sur_steps
+    held_runs = max(1, runs // 10)
+    sq = su = None
+    losses = []
+    t_gen = t_train = 0.0
+    n_train = 0
+    held = []
     m = torch.empty((Np, 3), dtype=torch.float32, device="cuda")
-    k = 0
+    Q = torch.empty((steps, V), dtype=torch.float32, device="cuda")
+    U = torch.empty_like(Q)
     for r in range(runs):
+        t0 = time.time()
         m.copy_(torch.tensor(meshgen.m_random(Np, seed=100 + r), dtype=torch.float32))
         h.set_m(m, st)
-        for _ in range(steps):
+        for k in range(steps):
             h.get_m(m, st)
             h.grid_pair(m, Q[k], U[k], st)
             h.llg_step(dt, 1, st)
-            k += 1
-    torch.cuda.synchronize()
-    dQ = (Q.view(runs, steps, V)[:, 1:] - Q.view(runs, steps, V)[:, :-1]).reshape(-1, V).contiguous()
-    dU = (U.view(runs, steps, V)[:, 1:] - U.view(runs, steps, V)[:, :-1]).reshape(-1, V).contiguous()
+        dQ = (Q[1:] - Q[:-1]).contiguous()
+        dU = (U[1:] - U[:-1]).contiguous()
+        torch.cuda.synchronize()
+        t_gen += time.time() - t0
+        if r >= runs - held_runs:
+            held.append((dQ, dU))
+            continue
+        if sq is None:                  # scales from the first run's increments
+            sq, su = float(dQ.std()), float(dU.std())
+            h.surrogate_set_params(meshgen.net_init(32, seed=0), sq, su, act_bf16=True)
+        t0 = time.time()
+        losses += list(h.surrogate_train(dQ, dU, dQ.shape[0], epochs=1, batch=4, lr=1e-3, stream=st))
+        torch.cuda.synchronize()
+        t_train += time.time() - t0
+        n_train += dQ.shape[0]
+        del dQ, dU
     del Q, U
-    n_train = int(0.9 * dQ.shape[0])
-    sq, su = float(dQ[:n_train].std()), float(dU[:n_train].std())
-    h.surrogate_set_params(meshgen.net_init(32, seed=0), sq, su, act_bf16=True)
-    torch.cuda.synchronize()
-    t0 = time.time()
-    epochs = 5
-    losses = h.surrogate_train(dQ[:n_train], dU[:n_train], n_train, epochs=epochs, batch=4, lr=1e-3, stream=st)
-    torch.cuda.synchronize()
-    t_train = time.time() - t0
+    epochs = 1
     # held-out increments
     pred = torch.empty(V, dtype=torch.float32, device="cuda")
     num = den = 0.0
-    for j in range(n_train, dQ.shape[0]):
-        h.surrogate_apply(dQ[j], pred, st)
-        torch.cuda.synchronize()
-        num += float(((pred - dU[j]) ** 2).sum())
-        den += float((dU[j] ** 2).sum())
+    n_held = 0
+    for dQ, dU in held:
+        for j in range(0, dQ.shape[0], 7):     # every 7th held-out increment
+            h.surrogate_apply(dQ[j], pred, st)
+            torch.cuda.synchronize()
+            num += float(((pred - dU[j]) ** 2).sum())
+            den += float((dU[j] ** 2).sum())
+            n_held += 1
     held_out = math.sqrt(num / den) if den > 0 else float("nan")
+    trained = h.surrogate_get_params()
     # trajectories from a new state: plain FP32 against surrogate-assisted, the same steps
     m0 = torch.tensor(meshgen.m_random(Np, seed=119), dtype=torch.float32, device="cuda")
     nsteps = 20
     res = {}
-    for mode in ("plain", "surrogate"):
-        h.surrogate_enable(10 if mode == "surrogate" else 0)
+    stats = {}
+    # control: the same judged steps with the network's output held at zero (stages 2-4 keep the
+    # first stage's potential, U = U1), then with the trained network
+    for mode in ("plain", "frozen", "surrogate"):
+        if mode == "frozen":
+            h.surrogate_set_params(np.zeros_like(trained), sq, su, act_bf16=True)
+        elif mode == "surrogate":
+            h.surrogate_set_params(trained, sq, su, act_bf16=True)
+        h.surrogate_enable(10 if mode != "plain" else 0)
         h.set_m(m0, st)
         h.llg_step(dt, 1, st)          # warm-up
         h.set_m(m0, st)
-        h.surrogate_enable(10 if mode == "surrogate" else 0)
+        h.surrogate_enable(10 if mode != "plain" else 0)
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(st)
@@ -597,19 +625,24 @@ def surrogate_leg(args, dist, world):
         h.get_m(out, st)
         h.sync()
         res[mode] = (e0.elapsed_time(e1) / nsteps, out.double().cpu().numpy())
-        if mode == "surrogate":
-            stats = h.surrogate_stats()
+        if mode != "plain":
+            stats[mode] = h.surrogate_stats()
     h.surrogate_enable(0)
     h.destroy()
-    drift = float(np.linalg.norm(res["surrogate"][1] - res["plain"][1]) / np.linalg.norm(res["plain"][1] - m0.double().cpu().numpy()))
+    mp = m0.double().cpu().numpy()
+    drift = {k: float(np.linalg.norm(res[k][1] - res["plain"][1]) / np.linalg.norm(res["plain"][1] - mp))
+             for k in ("frozen", "surrogate")}
     return {"workload": "sphere-lattice-3d-periodic-200k, grid 64^3", "unknowns": Np, "precision": "fp32 weights and accumulation, bf16 activations",
-            "train_pairs": n_train, "held_out_pairs": int(dQ.shape[0] - n_train), "epochs": epochs,
+            "train_pairs": n_train, "held_out_pairs_evaluated": n_held, "epochs": epochs,
             "train_loss_first_last": [float(losses[0]), float(losses[-1])], "train_s": round(t_train, 2),
-            "held_out_rel_l2_dU": held_out, "judged": stats,
+            "pair_generation_s": round(t_gen, 2),
+            "held_out_rel_l2_dU": held_out, "judged": stats["surrogate"], "judged_frozen_control": stats["frozen"],
+            "judged_gain_over_frozen": stats["frozen"]["judged_rel_l2"] / max(stats["surrogate"]["judged_rel_l2"], 1e-300),
             "trajectory_drift_vs_plain": drift, "steps": nsteps, "every_k": 10,
-            "ms_per_step": {"plain": res["plain"][0], "surrogate": res["surrogate"][0]},
+            "ms_per_step": {"plain": res["plain"][0], "frozen": res["frozen"][0], "surrogate": res["surrogate"][0]},
             "speedup_vs_plain": res["plain"][0] / res["surrogate"][0], "setup_s": round(t_setup, 1),
-            "data": "pairs of this run's own RK4 trajectories, 4 runs x 16 steps (bounded sample)"}
+            "data": f"increments of this run's own RK4 trajectories, {runs} runs x {steps} steps (m0 seeds 100..), "
+                    f"streamed run by run, the last {held_runs} run(s) held out"}
 
 
 def run_native(args):
@@ -869,10 +902,27 @@ def run_native(args):
     return 0
 
 
+def run_only(args):
+    """One side leg alone (diagnosis, profiling); prints its JSON object."""
+    import torch
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = Dist(world, local)
+    import __graft_entry__
+    __graft_entry__.build()
+    out = surrogate_leg(args, dist, world) if args.only == "surrogate" else batch_leg(args, dist, world)
+    dist.close()
+    if rank == 0:
+        print(json.dumps(out))
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.only:
+        return run_only(args)
     return run_native(args)
 
 

@@ -344,6 +344,19 @@ int pmfem_operator_export(pmfem_t h, int which, int32_t* rowptr, int32_t* col, d
 int pmfem_device_info(pmfem_t h, int64_t* out, int n);
 
 /*
+ * Test and diagnosis hooks (no counterpart in the paper).
+ * pmfem_debug_fail_alloc: process-wide; after `after` more device allocations of the library
+ * succeed, every further one fails with ENOMEM without calling the CUDA allocator, so that the
+ * out-of-memory paths (and the clean-up of a partial device build) can be tested without
+ * exhausting a GPU.  -1 switches it off (the default); EINVAL below -1.
+ * pmfem_build_flags: bit 0 set in a PMFEM_CHECKS build, which checks every stored index of a
+ * device upload against its bounds on the device (a failure is reported by pmfem_sync as
+ * EINVAL) and clamps gathered indices into their vectors.
+ */
+int pmfem_debug_fail_alloc(int after);
+int pmfem_build_flags(void);
+
+/*
  * Wall-clock seconds of the set-up stages of the handle (host, n doubles; stages beyond 7
  * read 0): out[0] PBC pairing and fold (Sec. 2.2, Eq. 18), out[1] periodized local operators
  * (Eqs. 7-12, 14a, 14d), out[2] grid and stencils (Eq. 16), out[3] PGF spectrum (Eq. 15),

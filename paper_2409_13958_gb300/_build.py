@@ -29,15 +29,15 @@ def _sources():
     return srcs, headers
 
 
-def _stale(srcs, headers) -> bool:
-    if not os.path.exists(LIB):
+def _stale(lib, srcs, headers) -> bool:
+    if not os.path.exists(lib):
         return True
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return any(os.path.getmtime(f) > t for f in srcs + headers + [__file__])
 
 
-def _compile(src: str, extra: list[str]) -> str:
-    obj = os.path.join(BUILD, os.path.basename(src) + ".o")
+def _compile(src: str, extra: list[str], build_dir: str = BUILD) -> str:
+    obj = os.path.join(build_dir, os.path.basename(src) + ".o")
     if src.endswith(".cu"):
         cmd = [_nvcc(), *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE,
                *extra, "-c", src, "-o", obj]
@@ -50,22 +50,29 @@ def _compile(src: str, extra: list[str]) -> str:
     return obj
 
 
-def build(force: bool = False, extra_flags: list[str] | None = None) -> str:
-    """Compile every source under csrc/ and link libpmfem.so next to this file."""
+def build(force: bool = False, extra_flags: list[str] | None = None, variant: str | None = None) -> str:
+    """Compile every source under csrc/ and link libpmfem.so next to this file.  variant
+    "checks" builds the bounds-checked library libpmfem_checks.so (-DPMFEM_CHECKS=1) instead."""
     srcs, headers = _sources()
-    if not force and not _stale(srcs, headers):
-        return LIB
-    os.makedirs(BUILD, exist_ok=True)
+    lib = LIB if variant is None else os.path.join(PKG, f"libpmfem_{variant}.so")
+    build_dir = BUILD if variant is None else BUILD + "_" + variant
     extra = list(extra_flags or [])
+    if variant == "checks":
+        extra.append("-DPMFEM_CHECKS=1")
+    elif variant is not None:
+        raise ValueError(f"unknown build variant {variant}")
+    if not force and not _stale(lib, srcs, headers):
+        return lib
+    os.makedirs(build_dir, exist_ok=True)
     with ThreadPoolExecutor(max_workers=min(8, len(srcs))) as ex:
-        objs = list(ex.map(lambda s: _compile(s, extra), srcs))
-    tmp = LIB + ".tmp"
+        objs = list(ex.map(lambda s: _compile(s, extra, build_dir), srcs))
+    tmp = lib + ".tmp"
     cmd = [_nvcc(), *ARCH, "-shared", "-o", tmp, *objs, "-lpthread"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed: {' '.join(cmd)}\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":

@@ -74,6 +74,8 @@ SIGNATURES = {
     "pmfem_batch_llg_step": (_c.c_int, [_vp, _dbl, _c.c_int, _vp]),
     "pmfem_batch_sync": (_c.c_int, [_vp]),
     "pmfem_setup_times": (_c.c_int, [_vp, _vp, _c.c_int]),
+    "pmfem_debug_fail_alloc": (_c.c_int, [_c.c_int]),
+    "pmfem_build_flags": (_c.c_int, []),
     "pmfem_bloch_spectrum": (_c.c_int, [_vp, _vp, _vp, _vp]),
     "pmfem_bloch_convolve": (_c.c_int, [_vp, _vp, _vp, _vp, _vp]),
     "pmfem_grid_info": (_c.c_int, [_vp, _vp, _vp, _vp, _vp]),
@@ -86,21 +88,30 @@ _LIB = None
 LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libpmfem.so")
 
 
+def _open(p: str):
+    if not os.path.exists(p):
+        raise RuntimeError(f"{p} is missing: build it with __graft_entry__.build() "
+                           "(paper_2409_13958_gb300._build.build()); there is no CPU fallback")
+    lib = ctypes.CDLL(p)
+    for name, (res, args) in SIGNATURES.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    return lib
+
+
 def load_library(path: str | None = None):
     """Load libpmfem.so (raises when it has not been built; there is no fallback)."""
     global _LIB
     if _LIB is None:
-        p = path or LIB_PATH
-        if not os.path.exists(p):
-            raise RuntimeError(f"{p} is missing: build it with __graft_entry__.build() "
-                               "(paper_2409_13958_gb300._build.build()); there is no CPU fallback")
-        lib = ctypes.CDLL(p)
-        for name, (res, args) in SIGNATURES.items():
-            f = getattr(lib, name)
-            f.restype = res
-            f.argtypes = args
-        _LIB = lib
+        _LIB = _open(path or LIB_PATH)
     return _LIB
+
+
+def load_variant(path: str):
+    """Another build of the library (e.g. the bounds-checked one), for handles created with
+    Pmfem.create_mesh(..., lib=...)."""
+    return _open(path)
 
 
 class ImplicitOpts(ctypes.Structure):
@@ -140,8 +151,8 @@ def _stream(s) -> int | None:
 class Pmfem:
     """One periodic unit cell (a pmfem_t handle)."""
 
-    def __init__(self, handle):
-        self._lib = load_library()
+    def __init__(self, handle, lib=None):
+        self._lib = lib if lib is not None else load_library()
         self.h = handle
 
     def _ck(self, rc: int):
@@ -151,8 +162,8 @@ class Pmfem:
 
     # ------------------------------------------------------------------ set-up
     @classmethod
-    def create_mesh(cls, xyz, tets, Ms: float, A: float, alpha: float) -> "Pmfem":
-        lib = load_library()
+    def create_mesh(cls, xyz, tets, Ms: float, A: float, alpha: float, lib=None) -> "Pmfem":
+        lib = lib if lib is not None else load_library()
         xyz = np.ascontiguousarray(xyz, dtype=np.float64)
         tets = np.ascontiguousarray(tets, dtype=np.int32)
         h = _vp()
@@ -160,7 +171,7 @@ class Pmfem:
                                    tets.shape[0], Ms, A, alpha)
         if rc != 0:
             raise PmfemError(rc, lib.pmfem_last_error(None).decode())
-        return cls(h)
+        return cls(h, lib)
 
     def set_aim(self, Nx=0, Ny=0, Nz=0, order_p=0, near_boxes=0, near_elem_factor=0.0):
         self._ck(self._lib.pmfem_set_aim(self.h, Nx, Ny, Nz, order_p, near_boxes, near_elem_factor))

@@ -1,11 +1,14 @@
 // C-ABI of libpmfem (declared in include/pmfem.h).
 #include <chrono>
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <mutex>
 #include <new>
 #include <string>
 #include <vector>
+
+#include <nvtx3/nvToolsExt.h>
 
 #include "../../include/pmfem.h"
 #include "device.hpp"
@@ -15,6 +18,13 @@
 #include "state.hpp"
 
 using namespace pmfem;
+
+#ifndef PMFEM_NVTX
+#define PMFEM_NVTX 1
+#endif
+#ifndef PMFEM_CHECKS
+#define PMFEM_CHECKS 0
+#endif
 
 
 namespace {
@@ -102,9 +112,17 @@ void free_device(pmfem_t h) {
   h->dev_prec = -1;
 }
 
+// Test hook (pmfem_debug_fail_alloc): when >= 0, the number of device allocations still
+// allowed before dalloc reports ENOMEM without calling the allocator.
+std::atomic<int> g_fail_after{-1};
+
 int dalloc(pmfem_t h, void** p, size_t bytes) {
   *p = nullptr;
   if (bytes == 0) bytes = 16;
+  for (int left = g_fail_after.load(); left >= 0; left = g_fail_after.load()) {
+    if (left == 0) return fail(h, ENOMEM_, "device allocation refused by pmfem_debug_fail_alloc");
+    if (g_fail_after.compare_exchange_weak(left, left - 1)) break;
+  }
   cudaError_t e = cudaMalloc(p, bytes);
   if (e != cudaSuccess) {
     *p = nullptr;
@@ -277,8 +295,6 @@ int build_device(pmfem_t h, DevOps<T>& d) {
   h->dev_info[10] = L.TY;
   h->dev_info[11] = L.TZ;
 
-  if ((rc = upload(h, L.bstart.data(), L.bstart.size(), &d.bstart))) return rc;
-  if ((rc = upload(h, L.regular.data(), L.regular.size(), &d.regular))) return rc;
   d.nx_exc = (int64_t)L.xnode.size();
   if ((rc = upload(h, L.xnode.data(), L.xnode.size(), &d.xnode))) return rc;
   if ((rc = upload(h, L.xgrid.data(), L.xgrid.size(), &d.xgrid))) return rc;
@@ -325,6 +341,12 @@ int build_device(pmfem_t h, DevOps<T>& d) {
   d.flag = h->flag;
   PMFEM_CK(h, cudaMemset(h->flag, 0, sizeof(int)));
   PMFEM_CK(h, cudaMemset(h->m, 0, sv));
+  if (PMFEM_CHECKS) {
+    // bounds of every stored index, checked on the device before any kernel uses them;
+    // a failure is reported by the next pmfem_sync (EINVAL)
+    launch_layout_checks(d, h->stream);
+    PMFEM_CK(h, cudaStreamSynchronize(h->stream));
+  }
   return OK;
 }
 
@@ -361,9 +383,22 @@ int ensure_device(pmfem_t h) {
 #ifndef PMFEM_OVERLAP
 #define PMFEM_OVERLAP 1
 #endif
+// NVTX ranges around the stages of an evaluation (host-side enqueue; header-only NVTX 3, a no-op
+// unless a tool is attached)
+struct NvtxRange {
+  explicit NvtxRange(const char* name) {
+    if (PMFEM_NVTX) nvtxRangePushA(name);
+  }
+  ~NvtxRange() {
+    if (PMFEM_NVTX) nvtxRangePop();
+  }
+};
+
 template <typename T>
 void enqueue_eval(pmfem_t h, DevOps<T>& d, const V4<T>* m, T* H, int comps, const RkArgs& rk, cudaStream_t st) {
+  NvtxRange all("pmfem field evaluation");
   if (comps & PMFEM_MS) {
+    NvtxRange ms("pmfem magnetostatic: charges, precorrection, projection, FFT, stencil");
     launch_charges(d, m, st);
     if (PMFEM_OVERLAP && sizeof(T) == 4) {
       const bool fork = !h->prof_on && h->side && h->ev_fork && h->ev_join;
@@ -376,14 +411,15 @@ void enqueue_eval(pmfem_t h, DevOps<T>& d, const V4<T>* m, T* H, int comps, cons
       if (fork) cudaEventRecord(h->ev_join, s2);
       launch_anterp(d, st);
       launch_fft_conv(d, st);
+      launch_stencil(d, m, st);     // adds into the potential lane beside the precorrection
       if (fork) cudaStreamWaitEvent(st, h->ev_join, 0);
-      launch_stencil(d, m, st);
     } else {
       launch_anterp(d, st);
       launch_fft_conv(d, st);
       launch_interp(d, m, st);
     }
   }
+  NvtxRange fr("pmfem gradient + exchange + local terms");
   launch_field(d, m, H, comps, h->hap[0], h->hap[1], h->hap[2], rk, st);
 }
 
@@ -1054,7 +1090,7 @@ int pmfem_sync(pmfem_t h) {
   PMFEM_CK(h, cudaMemcpy(&flag, h->flag, sizeof(int), cudaMemcpyDeviceToHost));
   if (flag) {
     PMFEM_CK(h, cudaMemset(h->flag, 0, sizeof(int)));
-    if (flag & FLAG_LAYOUT) return fail(h, EINVAL_, "precorrection layout check failed on the device");
+    if (flag & FLAG_LAYOUT) return fail(h, EINVAL_, "device layout check failed (PMFEM_CHECKS build)");
     return fail(h, ENONFINITE_, (flag & FLAG_NONFINITE_IN) ? "non-finite magnetisation input"
                                                           : "non-finite field result");
   }
@@ -1154,6 +1190,14 @@ int pmfem_device_info(pmfem_t h, int64_t* out, int n) {
   for (int i = 0; i < n; ++i) out[i] = i < 12 ? h->dev_info[i] : 0;
   return OK;
 }
+
+int pmfem_debug_fail_alloc(int after) {
+  if (after < -1) return EINVAL_;
+  g_fail_after.store(after);
+  return OK;
+}
+
+int pmfem_build_flags(void) { return PMFEM_CHECKS ? 1 : 0; }
 
 int pmfem_setup_times(pmfem_t h, double* out, int n) {
   if (!h || !out || n <= 0) return EINVAL_;

@@ -118,10 +118,6 @@ struct DevOps {
   const int32_t* base = nullptr;                  // Np x 3
   const T* frac = nullptr;                        // Np x 3
   const T* ghat = nullptr;                        // (F0/2+1)(F1/2+1)(F2/2+1), scaled by 1/(F0 F1 F2)
-  // box order for the projection with weights computed on the fly: first node of every box
-  // (boxes + 1, box-order index) and a flag per node whose stencil starts pl boxes below its box
-  const int32_t* bstart = nullptr;
-  const uint8_t* regular = nullptr;
   const C2* tw[3] = {nullptr, nullptr, nullptr};  // exp(-2 pi i j / F_a), j < F_a
   // work buffers
   T* q = nullptr;
@@ -172,6 +168,10 @@ struct FftArgs {
   unsigned count = 1;
 };
 template <typename T> void launch_fft(const FftArgs<T>& a, const ProfHook& prof, cudaStream_t st);
+// PMFEM_CHECKS builds: every stored row base, column delta, row map, stencil base and projection
+// exception
+// checked against its bounds on the device (FLAG_LAYOUT in the error word on a failure)
+template <typename T> void launch_layout_checks(const DevOps<T>& d, cudaStream_t st);
 template <typename T> void launch_interp(const DevOps<T>& d, const V4<T>* m, cudaStream_t st);
 // the two halves of launch_interp: precorrection (+ near and touching elements) from q, m, e;
 // then the stencil of the grid potential added on top

@@ -130,7 +130,6 @@ struct Layout {
   SellMatrix adj;                    // 10 components: W^q (3), E (3), gradient (3), exchange
   SellMatrix cor;                    // point precorrection, rows length-sorted in windows
   SellMatrix pro;                    // projection P^T: rows = grid points
-  std::vector<uint8_t> regular;      // Np: 1 when the node's stencil starts pl boxes below its box
   std::vector<int32_t> xnode;        // projection exceptions: node, grid index, weight
   std::vector<int64_t> xgrid;
   std::vector<double> xw;

@@ -83,84 +83,6 @@ __global__ void __launch_bounds__(kBlock) k_project(int64_t G, int64_t Np, const
   project_row<T, CT, VT>(t, g, 0, (int32_t)Np, len, base, off, dcol, pw, q, grid);
 }
 
-// BAIM step 1 with the weights computed on the fly: grid point g gathers q_k w_kg over the
-// nodes whose stencil covers it.  Those are the nodes of the boxes g - pr .. g + pl along each
-// axis; in the box order the boxes of one (y, z) box row are contiguous along x, so each of the
-// (p+1)^2 rows is one node range (two across a periodic seam in x).  A node's weight is the
-// product of its three 1D Lagrange basis values at the grid point's offset from its stencil
-// base, so no weight or column is stored: the pass reads bstart, the nodes' q, base and frac
-// (cache-resident across neighbouring grid points) and writes the grid once.  Nodes whose
-// stencil is not aligned with their box are left to k_project_exc.
-// PMFEM_PROJECT_FLY 1: the projection computes its weights on the fly (k_project_fly) instead of
-// streaming the stored SELL operator (k_project); 0 keeps the stored operator.
-#ifndef PMFEM_PROJECT_FLY
-#define PMFEM_PROJECT_FLY 1
-#endif
-template <typename T, int P>
-__global__ void __launch_bounds__(kBlock) k_project_fly(int N0, int N1, int N2, int p0, int p1, int p2, int TY,
-                                                        int TZ, int pl, int pr, const int32_t* __restrict__ bstart,
-                                                        const uint8_t* __restrict__ regular,
-                                                        const int32_t* __restrict__ base, const T* __restrict__ frac,
-                                                        const T* __restrict__ q, T* __restrict__ grid) {
-  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (g >= (int64_t)N0 * N1 * N2) return;
-  const int gx = (int)(g % N0), gy = (int)((g / N0) % N1), gz = (int)(g / ((int64_t)N0 * N1));
-  const int nty = N1 / TY;
-  T acc = 0;
-  for (int bz = gz - pr; bz <= gz + pl; ++bz) {
-    int z = bz;
-    if (p2) z = z < 0 ? z + N2 : (z >= N2 ? z - N2 : z);
-    else if (z < 0 || z >= N2) continue;
-    for (int by = gy - pr; by <= gy + pl; ++by) {
-      int y = by;
-      if (p1) y = y < 0 ? y + N1 : (y >= N1 ? y - N1 : y);
-      else if (y < 0 || y >= N1) continue;
-      const int64_t rowb = ((((int64_t)(z / TZ) * nty + y / TY) * TZ + z % TZ) * TY + y % TY) * N0;
-      int lo = gx - pr, hi = gx + pl, lo2 = 0, hi2 = -1;
-      if (!p0) {
-        lo = max(lo, 0);
-        hi = min(hi, N0 - 1);
-      } else if (lo < 0) {
-        lo2 = lo + N0, hi2 = N0 - 1, lo = 0;
-      } else if (hi >= N0) {
-        lo2 = 0, hi2 = hi - N0, hi = N0 - 1;
-      }
-#pragma unroll
-      for (int sgm = 0; sgm < 2; ++sgm) {
-        const int a0 = sgm ? lo2 : lo, a1 = sgm ? hi2 : hi;
-        if (a0 > a1) continue;
-        const int32_t k0 = __ldg(bstart + rowb + a0), k1 = __ldg(bstart + rowb + a1 + 1);
-        for (int32_t k = k0; k < k1; ++k) {
-          if (!__ldg(regular + k)) continue;
-          int i0 = gx - __ldg(base + 3 * k), i1 = gy - __ldg(base + 3 * k + 1), i2 = gz - __ldg(base + 3 * k + 2);
-          if (p0) i0 = ((i0 % N0) + N0) % N0;
-          if (p1) i1 = ((i1 % N1) + N1) % N1;
-          if (p2) i2 = ((i2 % N2) + N2) % N2;
-          if ((unsigned)i0 >= (unsigned)P || (unsigned)i1 >= (unsigned)P || (unsigned)i2 >= (unsigned)P) continue;
-          const T s0 = __ldg(frac + 3 * k), s1 = __ldg(frac + 3 * k + 1), s2 = __ldg(frac + 3 * k + 2);
-          T w0 = T(1), w1 = T(1), w2 = T(1);
-#pragma unroll
-          for (int j = 0; j < P; ++j) {
-            w0 *= j == i0 ? T(1) : (s0 - T(j));
-            w1 *= j == i1 ? T(1) : (s1 - T(j));
-            w2 *= j == i2 ? T(1) : (s2 - T(j));
-          }
-          T id0 = 0, id1 = 0, id2 = 0;
-#pragma unroll
-          for (int j = 0; j < P; ++j) {
-            const T r = T(1.0 / lagrange_den<P>(j));
-            id0 = j == i0 ? r : id0;
-            id1 = j == i1 ? r : id1;
-            id2 = j == i2 ? r : id2;
-          }
-          acc += (w0 * id0) * (w1 * id1) * (w2 * id2) * __ldg(q + k);
-        }
-      }
-    }
-  }
-  grid[g] = acc;
-}
-
 // nodes whose stencil is not aligned with their box (rare rounding cases)
 template <typename T>
 __global__ void __launch_bounds__(kBlock) k_project_exc(int64_t n, const int32_t* __restrict__ node,
@@ -384,24 +306,6 @@ void launch_anterp(const DevOps<T>& d, cudaStream_t st) {
   const DevSell<T>& Pm = d.pro;
   d.prof.begin(KID_ANTERP, st);
   const int64_t G = Pm.rows;
-  if (PMFEM_PROJECT_FLY && d.bstart) {
-    const unsigned nbk = blocks_for(G);
-    const int pp[3] = {d.periodic[0] ? 1 : 0, d.periodic[1] ? 1 : 0, d.periodic[2] ? 1 : 0};
-    auto go = [&](auto kernel) {
-      kernel<<<nbk, kBlock, 0, st>>>(d.dims[0], d.dims[1], d.dims[2], pp[0], pp[1], pp[2], d.TY, d.TZ, d.pl, d.pr,
-                                     d.bstart, d.regular, d.base, d.frac, d.q, d.grid);
-    };
-    switch (d.p) {
-      case 2: go(k_project_fly<T, 3>); break;
-      case 3: go(k_project_fly<T, 4>); break;
-      case 4: go(k_project_fly<T, 5>); break;
-      default: go(k_project_fly<T, 6>); break;
-    }
-    if (d.nx_exc > 0)
-      k_project_exc<T><<<blocks_for(d.nx_exc), kBlock, 0, st>>>(d.nx_exc, d.xnode, d.xgrid, d.xw, d.q, d.grid);
-    d.prof.end(KID_ANTERP, st);
-    return;
-  }
   with_ct(Pm, [&](auto ct) {
     using CT = typename decltype(ct)::type;
     with_vt<T>(Pm.bval[0] != nullptr, [&](auto vt) {
@@ -525,7 +429,77 @@ void launch_field(const DevOps<T>& d, const V4<T>* m, T* H, int comps, double hx
   d.prof.end(KID_FIELD, st);
 }
 
+// ---------------------------------------------------------------- layout checks
+namespace {
+template <typename CT>
+__global__ void k_check_sell(int64_t rows, int64_t ncols, int vw, const int32_t* __restrict__ map,
+                             const int32_t* __restrict__ len, const int32_t* __restrict__ base,
+                             const int64_t* __restrict__ off, const CT* __restrict__ dcol, int* flag) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= rows) return;
+  bool bad = false;
+  if (map && (map[t] < 0 || map[t] >= rows)) bad = true;
+  const int64_t c = t >> 5, lane = t & 31;
+  const int64_t width = (off[c + 1] - off[c]) / 32;   // padded entries per lane of this chunk
+  const int32_t n = len[t], b = base[t];
+  if (n < 0 || n > width || (n > 0 && (b < 0 || b >= ncols))) bad = true;
+  for (int32_t j = 0; j < n && !bad; ++j) {
+    const int64_t o = off[c] + ((int64_t)(j / vw) * 32 + lane) * vw + j % vw;
+    const int64_t d = (int64_t)dcol[o];
+    if (d <= -ncols || d >= ncols) bad = true;
+  }
+  if (bad) atomicOr(flag, FLAG_LAYOUT);
+}
+
+// stencil bases inside the grid along open axes (so the stencil passes stay in the grid)
+__global__ void k_check_stencils(int64_t Np, const int32_t* __restrict__ base, int N0, int N1, int N2, int p0, int p1,
+                                 int p2, int P, int* flag) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= Np) return;
+  const int Nn[3] = {N0, N1, N2}, pp[3] = {p0, p1, p2};
+  bool bad = false;
+  for (int a = 0; a < 3; ++a)
+    if (!pp[a] && (base[3 * i + a] < 0 || base[3 * i + a] + P > Nn[a])) bad = true;
+  if (bad) atomicOr(flag, FLAG_LAYOUT);
+}
+
+// projection exceptions: node and grid indices in range
+__global__ void k_check_exceptions(int64_t n, int64_t Np, int64_t G, const int32_t* __restrict__ node,
+                                   const int64_t* __restrict__ gidx, int* flag) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  if (node[i] < 0 || node[i] >= Np || gidx[i] < 0 || gidx[i] >= G) atomicOr(flag, FLAG_LAYOUT);
+}
+
+template <typename T>
+void check_sell(const DevSell<T>& M, int64_t ncols, int vw, int* flag, cudaStream_t st) {
+  if (M.rows <= 0) return;
+  if (M.col16)
+    k_check_sell<int16_t><<<blocks_for(M.rows), kBlock, 0, st>>>(M.rows, ncols, vw, M.map, M.len, M.base, M.off,
+                                                                  (const int16_t*)M.delta, flag);
+  else
+    k_check_sell<int32_t><<<blocks_for(M.rows), kBlock, 0, st>>>(M.rows, ncols, vw, M.map, M.len, M.base, M.off,
+                                                                  (const int32_t*)M.delta, flag);
+}
+}  // namespace
+
+template <typename T>
+void launch_layout_checks(const DevOps<T>& d, cudaStream_t st) {
+  check_sell(d.adj, d.Np, 4, d.flag, st);
+  check_sell(d.cor, d.Np, PMFEM_COR_VW, d.flag, st);
+  check_sell(d.pro, d.Np, PMFEM_COR_VW, d.flag, st);
+  if (d.Np > 0)
+    k_check_stencils<<<blocks_for(d.Np), kBlock, 0, st>>>(d.Np, d.base, d.dims[0], d.dims[1], d.dims[2],
+                                                        d.periodic[0] ? 1 : 0, d.periodic[1] ? 1 : 0,
+                                                        d.periodic[2] ? 1 : 0, d.p + 1, d.flag);
+  if (d.nx_exc > 0)
+    k_check_exceptions<<<blocks_for(d.nx_exc), kBlock, 0, st>>>(d.nx_exc, d.Np,
+                                                                 (int64_t)d.dims[0] * d.dims[1] * d.dims[2],
+                                                                 d.xnode, d.xgrid, d.flag);
+}
+
 #define PMFEM_INSTANTIATE(T)                                                                          \
+  template void launch_layout_checks<T>(const DevOps<T>&, cudaStream_t);                             \
   template void launch_perm_in<T>(const DevOps<T>&, const T*, V4<T>*, cudaStream_t);                 \
   template void launch_perm_out<T>(const DevOps<T>&, const V4<T>*, T*, cudaStream_t);                \
   template void launch_charges<T>(const DevOps<T>&, const V4<T>*, cudaStream_t);                     \

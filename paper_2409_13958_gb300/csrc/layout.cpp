@@ -330,7 +330,6 @@ int build_layout(const Setup& s, Layout& L, Error& err) {
     for (int a = 0; a < 3; ++a) {
       const int d = L.base[3 * i + a] - (L.box[3 * i + a] - L.pl);
       if (!(d == 0 || (p % 2 == 0 && d == 1))) regular[i] = 0;
-  L.regular.assign(regular.begin(), regular.end());
     }
   auto for_pull = [&](int gx, int gy, int gz, auto&& fn) {
     for (int bz = gz - L.pr; bz <= gz + L.pl; ++bz) {

@@ -72,7 +72,12 @@ template <typename CT>
 __device__ __forceinline__ int32_t col_of(int32_t b, CT d, int32_t n) {
   int32_t c = b + (int32_t)d;
   c = c < 0 ? c + n : c;
-  return c >= n ? c - n : c;
+  c = c >= n ? c - n : c;
+#if defined(PMFEM_CHECKS) && PMFEM_CHECKS
+  c = (c < 0 || c >= n) ? 0 : c;   // checked builds never gather outside the vector (the layout
+                                   // checks report the bad index at upload)
+#endif
+  return c;
 }
 
 // Streaming load of a stored operator value, widened to the arithmetic type T.  Values are
@@ -543,14 +548,18 @@ __device__ __forceinline__ void precorr_row(int64_t t, int64_t i, int64_t c0, in
   else
     acc = sell_dot4<PMFEM_COR_G>(cval, dcol, q + c0, cbase[t], coff[t >> 5] + 4 * (t & 31), clen[t], nc);
   acc += extras_row<T>(i, rowptrX, colX, valX, m);
-  uw[4 * i] = acc + e[i];
+  atomicAdd(uw + 4 * i, acc + e[i]);
 }
 
+// The two halves add into lane 3 of m, which enters every evaluation at zero (the permutation
+// into the internal order and the RK stage updates write it so): the stencil pass can then run
+// as soon as the FFT is done, while the precorrection may still run on the other stream, and the
+// sum of the two adds is the same in either order (0 + a + b = 0 + b + a exactly).
 template <typename T, int P>
 __device__ __forceinline__ void stencil_add_row(int64_t i, const int32_t* __restrict__ base, const T* __restrict__ frac,
                                                 const T* __restrict__ U, int N0, int N1, int N2, bool p0, bool p1,
                                                 bool p2, T* uw) {
-  uw[4 * i] += stencil_row<T, P>(i, base, frac, U, N0, N1, N2, p0, p1, p2);
+  atomicAdd(uw + 4 * i, stencil_row<T, P>(i, base, frac, U, N0, N1, N2, p0, p1, p2));
 }
 
 // ---------------------------------------------------------------- gradient + exchange + RK4

@@ -241,3 +241,12 @@ def test_setup_device_switch_rejects_bad_values():
     assert set(t) == {"pairing", "operators", "grid", "spectrum", "near_elements", "precorrection", "device"}
     assert t["precorrection"] >= 0 and t["device"] == 0.0
     h.destroy()
+
+
+def test_debug_hooks_without_a_gpu():
+    from paper_2409_13958_gb300 import binding
+    lib = binding.load_library()
+    assert lib.pmfem_build_flags() == 0
+    assert lib.pmfem_debug_fail_alloc(-2) == -1
+    assert lib.pmfem_debug_fail_alloc(3) == 0
+    assert lib.pmfem_debug_fail_alloc(-1) == 0
