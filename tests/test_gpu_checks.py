@@ -66,6 +66,7 @@ def test_checked_build_passes_and_agrees(libs, name, prec):
         H = torch.empty_like(m)
         h.field(m, H, PMFEM_ALL)
         h.sync()                                # a failed layout check would raise EINVAL here
+        h.set_m(m)
         h.llg_step(1e-15, 2)
         h.sync()
         out.append(H.double().cpu().numpy())
