@@ -964,14 +964,16 @@ int pmfem_llg_step(pmfem_t h, double dt, int nsteps, void* stream) {
     if (h->graph) cudaGraphExecDestroy(h->graph);
     h->graph = nullptr;
     PMFEM_CK(h, cudaStreamSynchronize(st));
+    // (on the scratch input mF, not the state: these launches write the potential lane, which
+    // must enter every evaluation of the state at zero)
     if (h->dev_prec == PMFEM_FP64) {
       launch_fft_conv(h->d64, h->stream);
-      launch_interp(h->d64, (const V4<double>*)h->m, h->stream);
-      launch_precorr(h->d64, (const V4<double>*)h->m, h->stream);
+      launch_interp(h->d64, (const V4<double>*)h->mF, h->stream);
+      launch_precorr(h->d64, (const V4<double>*)h->mF, h->stream);
     } else {
       launch_fft_conv(h->d32, h->stream);
-      launch_interp(h->d32, (const V4<float>*)h->m, h->stream);
-      launch_precorr(h->d32, (const V4<float>*)h->m, h->stream);
+      launch_interp(h->d32, (const V4<float>*)h->mF, h->stream);
+      launch_precorr(h->d32, (const V4<float>*)h->mF, h->stream);
     }
     PMFEM_CK(h, cudaStreamSynchronize(h->stream));
     cudaStream_t cs;
