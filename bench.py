@@ -53,6 +53,7 @@ def parse(argv=None):
     ap.add_argument("--no-host-setup", action="store_true",
                     help="skip timing the host set-up beside the GPU set-up of the same mesh")
     ap.add_argument("--no-cufft", action="store_true", help="skip the cuFFT convolution comparison")
+    ap.add_argument("--no-implicit", action="store_true", help="skip the implicit midpoint leg")
     ap.add_argument("--repeats", type=int, default=5, help="repeats of the timed steps for the median")
     ap.add_argument("--sur-runs", type=int, default=20, help="trajectories that give the surrogate's training pairs")
     ap.add_argument("--sur-steps", type=int, default=1000, help="RK4 steps per surrogate training trajectory")
@@ -771,6 +772,28 @@ def run_native(args):
     e2e_value = world * Np * 4 * k2 / e2e_s
     step_bytes = Np * 3 * 4
 
+    # implicit midpoint steps (Newton-GMRES) on the same wire at 4x the RK4 step, from the
+    # state the RK4 steps reached: iteration counts and time per unit of simulated time
+    implicit = None
+    if not args.no_implicit:
+        m_imp = torch.empty((Np, 3), dtype=torch.float32, device="cuda")
+        h.get_m(m_imp, stream)
+        dti, ni = 4.0 * dt, 3
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        try:
+            stats = h.llg_step_implicit(dti, ni, stream=stream)
+            torch.cuda.synchronize()
+            el = time.perf_counter() - t0
+            implicit = {"dt_s": dti, "steps": ni, "rk4_dt_s": dt, **stats, "ms_per_step": 1e3 * el / ni,
+                        "krylov_per_newton": stats["krylov"] / max(stats["newton"], 1),
+                        "sim_time_per_s_vs_rk4": (dti / (el / ni)) / (dt / (ms / args.steps * 1e-3)),
+                        "scheme": "implicit midpoint, Newton from m_n, GMRES(30) with 3x3 node blocks, FP32, "
+                                  "newton_tol 1e-5, krylov_tol 1e-4"}
+        except Exception as exc:      # a non-converged Newton is reported, not fatal to the bench
+            implicit = {"dt_s": dti, "steps": ni, "error": str(exc)}
+        h.set_m(m_imp, stream)
+
     # accuracy and speed against the plain FP64 GPU path (whole field and each term)
     from paper_2409_13958_gb300 import PMFEM_EX, PMFEM_MS
     comps = {"all": PMFEM_ALL, "exchange": PMFEM_EX, "magnetostatic": PMFEM_MS}
@@ -884,6 +907,7 @@ def run_native(args):
                                "pass of the same K steps"},
         "repeats": repeats,
         "accuracy": accuracy,
+        "implicit": implicit,
         "fp64": fp64 or None,
         "bf16split": bf16,
         "cufft": cufft,
