@@ -57,7 +57,7 @@ def parse(argv=None):
     ap.add_argument("--repeats", type=int, default=5, help="repeats of the timed steps for the median")
     ap.add_argument("--sur-runs", type=int, default=20, help="trajectories that give the surrogate's training pairs")
     ap.add_argument("--sur-steps", type=int, default=1000, help="RK4 steps per surrogate training trajectory")
-    ap.add_argument("--only", default=None, choices=["surrogate", "batch"],
+    ap.add_argument("--only", default=None, choices=["surrogate", "surrogate_fwd", "batch"],
                     help="run one side leg alone and print its JSON object (diagnosis and profiling)")
     ap.add_argument("--out", default=None, help="also write the JSON line to this file")
     return ap.parse_args(argv)
@@ -524,6 +524,64 @@ def batch_leg(args, dist, world):
             "launch": "one captured CUDA graph per RK4 step, one launch per pass over all cells"}
 
 
+def surrogate_forward_timing(h, V, st, reps=50):
+    """The network's forward pass on the 64^3 grid: CUDA events around `reps` calls (the whole
+    forward), then a profiled pass with an event pair around each layer.  A 32 -> 32 layer is
+    V x 27 x 32 x 32 x 2 flops on the tensor cores."""
+    import torch
+    Qg = torch.randn(V, dtype=torch.float32, device="cuda", generator=torch.Generator(device="cuda").manual_seed(7))
+    Ug = torch.empty_like(Qg)
+    for _ in range(3):
+        h.surrogate_apply(Qg, Ug, st)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for _ in range(reps):
+        h.surrogate_apply(Qg, Ug, st)
+    e1.record(st)
+    e1.synchronize()
+    fwd_us = 1e3 * e0.elapsed_time(e1) / reps
+    h.profile(True)
+    for _ in range(reps):
+        h.surrogate_apply(Qg, Ug, st)
+    torch.cuda.synchronize()
+    prof = h.profile_read()
+    h.profile(False)
+    h.sync()
+    layers = {k: round(1e3 * t / c, 2) for k, (c, t) in prof.items() if c and k.startswith("surrogate")}
+    hid_us = layers.get("surrogate_hidden")
+    flop = V * 27 * 32 * 32 * 2
+    peak = None
+    pp = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(pp):
+        peak = float(json.load(open(pp))["bf16_tflops"])
+    out = {"forward_us": round(fwd_us, 2), "layers_us_per_launch": layers}
+    if hid_us:
+        tf = flop / (hid_us * 1e-6) / 1e12
+        out["hidden_layer"] = {"tflops": round(tf, 1), "flop_per_launch": flop,
+                               "frac_of_measured_bf16_burst": round(tf / peak, 3) if peak else None,
+                               "timing": "CUDA events around each launch, profiled pass, mean of both layers"}
+    return out
+
+
+def surrogate_forward_leg(args, dist, world):
+    """The forward pass alone, with He-normal weights (no training): the profiling workload of
+    the tensor-core layers (3D-periodic sphere lattice, grid 64^3, bfloat16 activations)."""
+    import torch
+    import meshgen
+    from paper_2409_13958_gb300 import Pmfem, PMFEM_FP32
+    mesh = meshgen.sphere_lattice(L=50e-9, R=20e-9, target_nodes=200_000, seed=0)
+    h = Pmfem.create_mesh(mesh.xyz, mesh.tets, MS, AEX, ALPHA)
+    h.set_aim(64, 64, 64, P_ORDER, NEAR_BOXES, NEAR_ELEM)
+    h.set_periodicity(*mesh.periods)
+    h.set_precision(PMFEM_FP32)
+    h.surrogate_set_params(meshgen.net_init(32, seed=1), 1.0, 1.0, act_bf16=True)
+    out = {"workload": "surrogate forward, sphere-lattice-3d-periodic-200k, grid 64^3, bf16 activations"}
+    out.update(surrogate_forward_timing(h, 64 ** 3, torch.cuda.current_stream()))
+    h.destroy()
+    return out
+
+
 def surrogate_leg(args, dist, world):
     """Learned surrogate of the FFT convolution on the 3D-periodic sphere lattice (~200k nodes,
     AIM grid 64^3, FP32).  Training pairs are increments (dQ, dU) of the grid charges and FFT
@@ -629,6 +687,7 @@ def surrogate_leg(args, dist, world):
         if mode != "plain":
             stats[mode] = h.surrogate_stats()
     h.surrogate_enable(0)
+    fwd = surrogate_forward_timing(h, V, st)
     h.destroy()
     mp = m0.double().cpu().numpy()
     drift = {k: float(np.linalg.norm(res[k][1] - res["plain"][1]) / np.linalg.norm(res["plain"][1] - mp))
@@ -642,6 +701,7 @@ def surrogate_leg(args, dist, world):
             "trajectory_drift_vs_plain": drift, "steps": nsteps, "every_k": 10,
             "ms_per_step": {"plain": res["plain"][0], "frozen": res["frozen"][0], "surrogate": res["surrogate"][0]},
             "speedup_vs_plain": res["plain"][0] / res["surrogate"][0], "setup_s": round(t_setup, 1),
+            "forward": fwd,
             "data": f"increments of this run's own RK4 trajectories, {runs} runs x {steps} steps (m0 seeds 100..), "
                     f"streamed run by run, the last {held_runs} run(s) held out"}
 
@@ -937,7 +997,8 @@ def run_only(args):
     dist = Dist(world, local)
     import __graft_entry__
     __graft_entry__.build()
-    out = surrogate_leg(args, dist, world) if args.only == "surrogate" else batch_leg(args, dist, world)
+    legs = {"surrogate": surrogate_leg, "surrogate_fwd": surrogate_forward_leg, "batch": batch_leg}
+    out = legs[args.only](args, dist, world)
     dist.close()
     if rank == 0:
         print(json.dumps(out))

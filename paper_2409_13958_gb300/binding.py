@@ -290,7 +290,8 @@ class Pmfem:
         self._ck(self._lib.pmfem_llg_step(self.h, dt, nsteps, _stream(stream)))
 
     KERNELS = ("charges", "projection", "fft_x_fwd", "fft_y_fwd", "fft_z_conv", "fft_y_inv", "fft_x_inv",
-               "interp_precorr", "gradient_exchange", "grid_clear", "permute", "interp_stencil")
+               "interp_precorr", "gradient_exchange", "grid_clear", "permute", "interp_stencil",
+               "surrogate_in", "surrogate_hidden", "surrogate_out")
 
     def profile(self, enable: bool = True):
         self._ck(self._lib.pmfem_profile(self.h, 1 if enable else 0))

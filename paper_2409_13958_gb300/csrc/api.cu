@@ -68,6 +68,7 @@ void apply_prof(pmfem_t h) {
   }
   h->d64.prof = hk;
   h->d32.prof = hk;
+  if (h->net) h->net->prof = hk;
 }
 
 // Fixed scratch of pmfem_field_noalloc (see the section of that entry point below): one
@@ -1352,6 +1353,7 @@ int pmfem_surrogate_set_params(pmfem_t h, const float* params, int64_t n, double
       h->net = nullptr;
       return fail(h, rc, msg);
     }
+    apply_prof(h);
   }
   SurrogateNet& net = *h->net;
   std::vector<float> dl;

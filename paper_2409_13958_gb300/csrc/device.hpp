@@ -50,7 +50,9 @@ struct alignas(4 * sizeof(T)) V4 {
 
 // Optional per-launch timing: the handle records a CUDA event pair around each kernel.
 enum KernelId : int { KID_CHARGES = 0, KID_ANTERP, KID_FFT_X_FWD, KID_FFT_Y_FWD, KID_FFT_Z_CONV, KID_FFT_Y_INV,
-                      KID_FFT_X_INV, KID_INTERP, KID_FIELD, KID_MEMSET, KID_PERM, KID_STENCIL, KID_COUNT };
+                      KID_FFT_X_INV, KID_INTERP, KID_FIELD, KID_MEMSET, KID_PERM, KID_STENCIL,
+                      // surrogate network: the 1 -> 32 layer, the two 32 -> 32 layers, the 32 -> 1 layer
+                      KID_SUR_IN, KID_SUR_HIDDEN, KID_SUR_OUT, KID_COUNT };
 struct ProfHook {
   void (*fn)(void* ctx, int id, int phase, cudaStream_t st) = nullptr;
   void* ctx = nullptr;

@@ -72,7 +72,8 @@ __device__ __forceinline__ void load_halo(float* s, const AIN* __restrict__ in, 
 template <int CK, int COUT, bool ACT, typename AIN, typename AOUT, bool CL_IN = false, bool CL_OUT = false>
 __global__ void __launch_bounds__(TILE) k_conv_fwd(const AIN* __restrict__ in, int Cin, const float* __restrict__ W,
                                                    const float* __restrict__ b, AOUT* __restrict__ out, int X, int Y,
-                                                   int Z, bool px, bool py, bool pz, float in_scale, float out_scale) {
+                                                   int Z, bool px, bool py, bool pz, float in_scale, float out_scale,
+                                                   AOUT* __restrict__ pout = nullptr) {
   __shared__ float s_in[CK * HALO];
   __shared__ __align__(16) float s_w[27 * CK * COUT];
   const int ntx = X / TX, nty = Y / TY;
@@ -114,6 +115,10 @@ __global__ void __launch_bounds__(TILE) k_conv_fwd(const AIN* __restrict__ in, i
   const int64_t plane = (int64_t)X * Y * Z;
   const int64_t vox = (x0 + lx) + (int64_t)X * ((y0 + ly) + (int64_t)Y * (z0 + lz));
   if constexpr (CL_OUT && sizeof(AOUT) == 2 && COUT % 8 == 0) {   // channels-last bfloat16: 16-byte stores
+    // (and, when pout is set, the same rows in the padded layout the tensor-core layer reads)
+    int64_t slot[8];
+    const int ns = pout ? pad_slots(x0 + lx, y0 + ly, z0 + lz, X, Y, Z, px, py, pz, slot) : 0;
+    const int64_t vp = (int64_t)(X + 2) * (Y + 2) * (Z + 2);   // voxels of one padded group plane
 #pragma unroll
     for (int o = 0; o < COUT; o += 8) {
       uint32_t w[4];
@@ -124,7 +129,9 @@ __global__ void __launch_bounds__(TILE) k_conv_fwd(const AIN* __restrict__ in, i
         const __nv_bfloat162 p2 = __floats2bfloat162_rn(a * out_scale, c * out_scale);
         w[j] = *reinterpret_cast<const uint32_t*>(&p2);
       }
-      *reinterpret_cast<uint4*>(out + vox * COUT + o) = make_uint4(w[0], w[1], w[2], w[3]);
+      const uint4 v = make_uint4(w[0], w[1], w[2], w[3]);
+      *reinterpret_cast<uint4*>(out + vox * COUT + o) = v;
+      for (int k = 0; k < ns; ++k) *reinterpret_cast<uint4*>(pout + ((o / 8) * vp + slot[k]) * 8) = v;
     }
   } else {
 #pragma unroll
@@ -343,18 +350,34 @@ void forward_t(SurrogateNet& n, const float* Q, float* U, cudaStream_t st) {
     if (n.tc) {   // channels-last activations, layers 1 and 2 on the tensor cores
       conv32_tc_pack(n.W[1], n.Wp[0], st);
       conv32_tc_pack(n.W[2], n.Wp[1], st);
+      n.prof.begin(KID_SUR_IN, st);
       k_conv_fwd<1, kNetC, true, float, A, false, true><<<nt, TILE, 0, st>>>(Q, 1, n.W[0], n.b[0], h0, X, Y, Z, px, py,
-                                                                              pz, 1.f / n.sq, 1.f);
-      conv32_tc(h0, n.Wp[0], n.b[1], h1, n.dims, n.periodic, true, n.tc_err, st);
-      conv32_tc(h1, n.Wp[1], n.b[2], h2, n.dims, n.periodic, true, n.tc_err, st);
+                                                                              pz, 1.f / n.sq, 1.f, (A*)n.hpad[0]);
+      n.prof.end(KID_SUR_IN, st);
+      n.prof.begin(KID_SUR_HIDDEN, st);
+      conv32_tc(n.tmap[0], n.Wp[0], n.b[1], h1, n.hpad[1], n.dims, n.periodic, true, n.tc_err, st);
+      n.prof.end(KID_SUR_HIDDEN, st);
+      n.prof.begin(KID_SUR_HIDDEN, st);
+      conv32_tc(n.tmap[1], n.Wp[1], n.b[2], h2, nullptr, n.dims, n.periodic, true, n.tc_err, st);
+      n.prof.end(KID_SUR_HIDDEN, st);
+      n.prof.begin(KID_SUR_OUT, st);
       k_conv_out_cl<<<nt, TILE, 0, st>>>(h2, n.W[3], n.b[3], U, X, Y, Z, px, py, pz, n.su);
+      n.prof.end(KID_SUR_OUT, st);
       return;
     }
   }
+  n.prof.begin(KID_SUR_IN, st);
   k_conv_fwd<1, kNetC, true, float, A><<<nt, TILE, 0, st>>>(Q, 1, n.W[0], n.b[0], h0, X, Y, Z, px, py, pz, 1.f / n.sq, 1.f);
+  n.prof.end(KID_SUR_IN, st);
+  n.prof.begin(KID_SUR_HIDDEN, st);
   k_conv_fwd<8, kNetC, true, A, A><<<nt, TILE, 0, st>>>(h0, kNetC, n.W[1], n.b[1], h1, X, Y, Z, px, py, pz, 1.f, 1.f);
+  n.prof.end(KID_SUR_HIDDEN, st);
+  n.prof.begin(KID_SUR_HIDDEN, st);
   k_conv_fwd<8, kNetC, true, A, A><<<nt, TILE, 0, st>>>(h1, kNetC, n.W[2], n.b[2], h2, X, Y, Z, px, py, pz, 1.f, 1.f);
+  n.prof.end(KID_SUR_HIDDEN, st);
+  n.prof.begin(KID_SUR_OUT, st);
   k_conv_fwd<8, 1, false, A, float><<<nt, TILE, 0, st>>>(h2, kNetC, n.W[3], n.b[3], U, X, Y, Z, px, py, pz, 1.f, n.su);
+  n.prof.end(KID_SUR_OUT, st);
 }
 
 // Backward pass: the input gradients run as convolutions with mirrored weights (planar FP32
@@ -459,13 +482,20 @@ int net_create(SurrogateNet& n, const int dims[3], const bool periodic[3], bool 
        alloc(&p, 2 * sizeof(double)) && ((n.loss = (double*)p), true) && alloc(&p, 2 * sizeof(double)) &&
        ((n.err = (double*)p), true);
   n.tc = bf16 && conv32_tc_fits(dims);
+  const size_t padb = (size_t)kNetC * 2 * (dims[0] + 2) * (dims[1] + 2) * (dims[2] + 2);
   if (ok && n.tc)
     ok = alloc(&n.Wp[0], 27 * kNetC * kNetC * 2) && alloc(&n.Wp[1], 27 * kNetC * kNetC * 2) &&
-         alloc(&p, sizeof(int)) && ((n.tc_err = (int*)p), true);
+         alloc(&p, sizeof(int)) && ((n.tc_err = (int*)p), true) && alloc(&n.hpad[0], padb) &&
+         alloc(&n.hpad[1], padb);
   if (!ok) {
     net_destroy(n);
     msg = "device allocation for the surrogate failed";
     return ENOMEM_;
+  }
+  if (n.tc && !(conv32_tc_tensor_map(n.hpad[0], dims, n.tmap[0]) && conv32_tc_tensor_map(n.hpad[1], dims, n.tmap[1]))) {
+    net_destroy(n);
+    msg = "tensor map of the surrogate's padded activations could not be encoded";
+    return ECUDA_;
   }
   for (int k = 0; k < 4; ++k) n.W[k] = n.P + net_layer_offset(k, false), n.b[k] = n.P + net_layer_offset(k, true);
   return OK;

@@ -7,6 +7,8 @@
 #include <string>
 #include <vector>
 
+#include "device.hpp"
+
 namespace pmfem {
 
 constexpr int kNetC = 32;   // hidden channels
@@ -43,12 +45,44 @@ struct SurrogateNet {
   bool tc = false;
   void* Wp[2] = {};           // packed bfloat16 weights of layers 1 and 2
   int* tc_err = nullptr;      // device: set when a tensor-core wait gave up
+  // inputs of the two tensor-core layers (h0, h1) once more in the padded layout their TMA
+  // loads read, and a tensor map of each
+  void* hpad[2] = {};
+  alignas(64) unsigned char tmap[2][128] = {};
+  ProfHook prof;              // per-layer CUDA-event timing of the forward pass (when enabled)
 };
 
 bool conv32_tc_fits(const int dims[3]);
 void conv32_tc_pack(const float* W, void* Wp, cudaStream_t st);
-void conv32_tc(const void* in, const void* Wp, const float* bias, void* out, const int dims[3], const bool per[3],
-               bool act, int* err, cudaStream_t st);
+// tensor map (128 bytes at tmap) of a padded channels-last bfloat16 buffer of the grid dims
+bool conv32_tc_tensor_map(const void* padded, const int dims[3], void* tmap);
+// out = act(bias + conv(in)) with in read through its tensor map (its padded copy); out
+// channels-last [V][32], and also written padded to pout when pout is not null
+void conv32_tc(const void* tmap, const void* Wp, const float* bias, void* out, void* pout, const int dims[3],
+               const bool per[3], bool act, int* err, cudaStream_t st);
+
+#ifdef __CUDACC__
+// Padded layout of a tensor-core layer's input: four planes of 8 bfloat16 channels, each of
+// (X + 2)(Y + 2)(Z + 2) voxels, [group][z][y][x][8], the outer layer holding periodic copies
+// along periodic axes and zeros along open ones.  pad_slots lists the padded voxels that hold
+// voxel (x, y, z): itself and, on a periodic border, its copies (up to 8 at a corner).
+__device__ __forceinline__ int pad_slots(int x, int y, int z, int X, int Y, int Z, bool px, bool py, bool pz,
+                                         int64_t slot[8]) {
+  int xs[2] = {x + 1, 0}, ys[2] = {y + 1, 0}, zs[2] = {z + 1, 0};
+  int nx = 1, ny = 1, nz = 1;
+  if (px && x == 0) xs[nx++] = X + 1;
+  else if (px && x == X - 1) xs[nx++] = 0;
+  if (py && y == 0) ys[ny++] = Y + 1;
+  else if (py && y == Y - 1) ys[ny++] = 0;
+  if (pz && z == 0) zs[nz++] = Z + 1;
+  else if (pz && z == Z - 1) zs[nz++] = 0;
+  int n = 0;
+  for (int c = 0; c < nz; ++c)
+    for (int b = 0; b < ny; ++b)
+      for (int a = 0; a < nx; ++a) slot[n++] = xs[a] + (int64_t)(X + 2) * (ys[b] + (int64_t)(Y + 2) * zs[c]);
+  return n;
+}
+#endif
 
 int64_t net_layer_offset(int layer, bool bias);                 // offset in the device layout
 int net_create(SurrogateNet& n, const int dims[3], const bool periodic[3], bool bf16, std::string& msg);

@@ -39,8 +39,10 @@ def _handle(kind):
         mesh, grid = meshgen.cube_cell(6, jitter=0.2, seed=63), (16, 16, 16)
     elif kind == "film16":      # 2D periodic film, grid 16 x 16 x 8 (tensor-core path, zero padding along z)
         mesh, grid = meshgen.film_cell(10, 10, 2, seed=64), (16, 16, 8)
-    elif kind == "film64":      # grid 64 x 64 x 8: 256 tensor-core tiles, more than one per SM
+    elif kind == "film64":      # grid 64 x 64 x 8: 128 tensor-core tiles, zero padding along z
         mesh, grid = meshgen.film_cell(10, 10, 2, seed=65), (64, 64, 8)
+    elif kind == "cube64x32":   # grid 64 x 64 x 32, 3D periodic: 512 tensor-core tiles
+        mesh, grid = meshgen.cube_cell(6, jitter=0.2, seed=66), (64, 64, 32)
     else:                       # 2D periodic film, grid 16 x 8 x 8 with zero padding along z
         mesh, grid = meshgen.film_cell(10, 6, 2, seed=62), (16, 8, 8)
     h = Pmfem.create_mesh(mesh.xyz, mesh.tets, 8e5, 1.3e-11, 0.02)
@@ -57,11 +59,14 @@ def _rel(a, b):
 
 @pytest.mark.parametrize("kind,bf16,tol", [("cube", False, 1e-5), ("film", False, 1e-5), ("film", True, 2e-2),
                                           ("cube16", True, 2e-2), ("film16", True, 2e-2), ("film16", False, 1e-5),
-                                          ("film64", True, 2e-2)])
+                                          ("film64", True, 2e-2), ("cube64x32", True, 2e-2)])
 def test_forward_matches_oracle(kind, bf16, tol):
     h, mesh, dims, per = _handle(kind)
-    if kind == "film64":   # tensor-core tiles of 8 x 16 x 1 voxels: more tiles than persistent blocks
-        assert (dims[0] // 8) * (dims[1] // 16) * dims[2] > torch.cuda.get_device_properties(0).multi_processor_count
+    if kind == "cube64x32":
+        # tensor-core tiles of 8 x 16 x 2 voxels, one persistent block per SM: at least three tiles
+        # per block, so that the three halo stages and the two accumulator pairs are reused
+        sms = torch.cuda.get_device_properties(0).multi_processor_count
+        assert (dims[0] // 8) * (dims[1] // 16) * (dims[2] // 2) >= 3 * sms
     params = S.init_params(C=32, seed=5)
     for k in range(1, 8, 2):
         params[k] = np.random.default_rng(10 + k).normal(0, 0.05, params[k].shape)
