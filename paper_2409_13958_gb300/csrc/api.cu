@@ -491,7 +491,7 @@ int run_implicit(pmfem_t h, DevOps<T>& d, double dt, int nsteps, const ImpOpts& 
     h->imp_pinv = p;
     if ((rc = dalloc(h, &p, (size_t)std::max<int64_t>(n, 1) * sizeof(T)))) return rc;
     h->imp_c = p;
-    if ((rc = dalloc(h, &p, (size_t)(kImpBlocks + 1) * (kMaxKrylov + 1) * sizeof(double)))) return rc;
+    if ((rc = dalloc(h, &p, (size_t)(kImpBlocks + 3) * (kMaxKrylov + 1) * sizeof(double)))) return rc;
     h->imp_red = p;
     h->imp_prec = h->dev_prec;
     // the exchange operator's own coefficient of every unknown (preconditioner blocks)
@@ -515,6 +515,11 @@ int run_implicit(pmfem_t h, DevOps<T>& d, double dt, int nsteps, const ImpOpts& 
   const T* cdiag = (const T*)h->imp_c;
   double* red = (double*)h->imp_red;                         // partial sums, then results
   double* dres = red + (size_t)kImpBlocks * (kMaxKrylov + 1);
+  // Arnoldi step results on the device: both Gram-Schmidt passes' coefficients and |w|^2
+  constexpr int K1 = kMaxKrylov + 1;
+  double* dA = dres + K1;
+  double* dB = dres + 2 * K1;
+  double* dC = dB + kMaxKrylov;   // (a cycle has at most kMaxKrylov columns: dB[0 .. j], j < kMaxKrylov)
   const int nblk = (int)std::min<int64_t>(kImpBlocks, std::max<int64_t>(1, (len + 255) / 256));
   RkArgs none;
   auto eval = [&](const T* xin, T* H, int comps) {
@@ -535,7 +540,7 @@ int run_implicit(pmfem_t h, DevOps<T>& d, double dt, int nsteps, const ImpOpts& 
     VecList<T> L;
     for (int j = 0; j < cnt; ++j) L.p[j] = vs[j];
     PMFEM_CK(h, cudaMemcpyAsync(dres, coef, cnt * sizeof(double), cudaMemcpyHostToDevice, st));
-    imp_combine(len, L, cnt, dres, a, wv, st);
+    imp_combine(len, L, cnt, dres, 1.0, a, wv, st);
     PMFEM_CK(h, cudaStreamSynchronize(st));   // coef is a host array of the caller
     return OK;
   };
@@ -543,6 +548,41 @@ int run_implicit(pmfem_t h, DevOps<T>& d, double dt, int nsteps, const ImpOpts& 
     eval(v, Av, PMFEM_EX | PMFEM_MS);
     imp_jvp(n, (const T*)mb, (const T*)Hb, (const T*)Av, (const T*)v, dt, g, alpha, out, st);
   };
+  // w = J z, the product of every Arnoldi step (fixed buffers), captured once per call as a CUDA
+  // graph (the evaluation's launches and its second-stream fork replayed in one launch); the
+  // eager launches run instead while per-launch timing is on
+  struct GraphGuard {
+    cudaGraphExec_t g = nullptr;
+    ~GraphGuard() {
+      if (g) cudaGraphExecDestroy(g);
+    }
+  } jvz;
+  if (!h->prof_on) {
+    cudaStream_t cs;
+    PMFEM_CK(h, cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    cudaGraph_t gr = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      launch_perm_in(d, (const T*)z, (V4<T>*)h->mF, cs);
+      enqueue_eval(h, d, (const V4<T>*)h->mF, Av, PMFEM_EX | PMFEM_MS, none, cs);
+      imp_jvp(n, (const T*)mb, (const T*)Hb, (const T*)Av, (const T*)z, dt, g, alpha, w, cs);
+      e = cudaStreamEndCapture(cs, &gr);
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&jvz.g, gr, 0);
+    if (gr) cudaGraphDestroy(gr);
+    cudaStreamDestroy(cs);
+    if (e != cudaSuccess) return fail(h, ECUDA_, std::string("implicit step: capture of J z failed: ") + cudaGetErrorString(e));
+  }
+  auto Jz = [&]() -> int {   // w = J z
+    if (!jvz.g) {
+      Jv(z, w);
+      return OK;
+    }
+    PMFEM_CK(h, cudaGraphLaunch(jvz.g, st));
+    ++stats[2];
+    return OK;
+  };
+  double hres[2 * K1];
   int rc;
   launch_perm_out(d, (const V4<T>*)h->m, m0, st);
   for (int step = 0; step < nsteps; ++step) {
@@ -573,25 +613,26 @@ int run_implicit(pmfem_t h, DevOps<T>& d, double dt, int nsteps, const ImpOpts& 
         int j = 0;
         for (; j < k && kits < o.max_krylov; ++j) {
           imp_apply_blocks(n, (const T*)Pinv, (const T*)V[j], z, st);
-          Jv(z, w);
+          if ((rc = Jz())) return rc;
           ++kits;
           ++stats[1];
-          std::vector<double> h1(j + 1), h2(j + 1);
-          if ((rc = dots(j + 1, V, w, h1.data()))) return rc;
-          for (auto& t : h1) t = -t;
-          if ((rc = combine(j + 1, V, h1.data(), 1.0, w))) return rc;
-          if ((rc = dots(j + 1, V, w, h2.data()))) return rc;   // second pass (classical Gram-Schmidt twice)
-          for (auto& t : h2) t = -t;
-          if ((rc = combine(j + 1, V, h2.data(), 1.0, w))) return rc;
-          for (int i = 0; i <= j; ++i) Hm[(size_t)i * k + j] = -(h1[i] + h2[i]);
-          double wn2;
-          if ((rc = dots(1, &w, w, &wn2))) return rc;
-          const double wn = std::sqrt(wn2);
+          // classical Gram-Schmidt twice and the normalisation, with the coefficients kept on
+          // the device between the passes; one copy back per step for the Hessenberg column
+          VecList<T> L;
+          for (int i = 0; i <= j; ++i) L.p[i] = V[i];
+          imp_multidot(len, L, j + 1, (const T*)w, red, nblk, dA, st);
+          imp_combine(len, L, j + 1, dA, -1.0, 1.0, w, st);
+          imp_multidot(len, L, j + 1, (const T*)w, red, nblk, dB, st);
+          imp_combine(len, L, j + 1, dB, -1.0, 1.0, w, st);
+          VecList<T> Lw;
+          Lw.p[0] = w;
+          imp_multidot(len, Lw, 1, (const T*)w, red, nblk, dC, st);
+          imp_scale_invnorm(len, (const T*)w, dC, V[j + 1], st);
+          PMFEM_CK(h, cudaMemcpyAsync(hres, dA, 2 * K1 * sizeof(double), cudaMemcpyDeviceToHost, st));
+          PMFEM_CK(h, cudaStreamSynchronize(st));
+          for (int i = 0; i <= j; ++i) Hm[(size_t)i * k + j] = hres[i] + hres[K1 + i];
+          const double wn = std::sqrt(std::max(hres[K1 + kMaxKrylov], 0.0));
           Hm[(size_t)(j + 1) * k + j] = wn;
-          if (wn > 0) {
-            double iw = 1.0 / wn;
-            if ((rc = combine(1, &w, &iw, 0.0, V[j + 1]))) return rc;
-          }
           // Givens rotations of column j
           for (int i = 0; i < j; ++i) {
             const double a = Hm[(size_t)i * k + j], b = Hm[(size_t)(i + 1) * k + j];

@@ -32,8 +32,12 @@ template <typename T> void imp_apply_blocks(int64_t n, const T* Pinv, const T* x
 template <typename T>
 void imp_multidot(int64_t len, const VecList<T>& V, int cnt, const T* w, double* partial, int nblocks, double* out,
                   cudaStream_t st);
-// w = a w + sum_j coef[j] V_j  (coef: cnt device doubles)
+// w = a w + csign sum_j coef[j] V_j  (coef: cnt device doubles, e.g. the output of imp_multidot)
 template <typename T>
-void imp_combine(int64_t len, const VecList<T>& V, int cnt, const double* coef, double a, T* w, cudaStream_t st);
+void imp_combine(int64_t len, const VecList<T>& V, int cnt, const double* coef, double csign, double a, T* w,
+                 cudaStream_t st);
+// out = w / sqrt(*n2), n2 a device scalar (zero when it is not positive)
+template <typename T>
+void imp_scale_invnorm(int64_t len, const T* w, const double* n2, T* out, cudaStream_t st);
 
 }  // namespace pmfem
