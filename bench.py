@@ -501,6 +501,18 @@ def batch_leg(args, dist, world):
     e1.synchronize()
     ms = dist.max(e0.elapsed_time(e1))
     b.sync()
+    # per-kernel durations: the same steps again, launch by launch, an event pair around each;
+    # algorithmic bytes summed over the cells (their own operators and grids)
+    b.profile(True)
+    b.llg_step(dt, k, stream)
+    torch.cuda.synchronize()
+    prof = b.profile_read()
+    b.profile(False)
+    cell_sizes = []
+    for h in hs:
+        dims, fft = h.grid_info()[:2]
+        cell_sizes.append({"Np": h.num_unknowns(), "dims": [int(x) for x in dims], "fft": [int(x) for x in fft],
+                           "dev": None, "h": h})
     single = 0.0
     for h in hs:
         mk = m[:h.num_unknowns()].contiguous()
@@ -514,11 +526,33 @@ def batch_leg(args, dist, world):
         single += f0.elapsed_time(f1) / 2
     tiles = b.tiles()
     b.destroy()
+    for cs in cell_sizes:             # device layouts exist once each cell has stepped on its own
+        cs["dev"] = cs.pop("h").device_info()
+    peak, peak_kind = measured_peaks()
+    kernels = {}
+    evals = prof["charges"][0]          # one charges launch per evaluation of all cells
+    for name, (c, t) in prof.items():
+        if not c:
+            continue
+        us = 1e3 * t / c
+        kernels[name] = {"launches": c, "us_per_launch": round(us, 1), "share": round(t / sum(
+            tt for cc, tt in prof.values()), 3)}
+        try:
+            # all cells' bytes per evaluation, over this kernel's launches per evaluation (the
+            # FFT passes launch once per group of cells with the same grid)
+            bytes_ = sum(alg_bytes(name, 4, cs) for cs in cell_sizes) * evals / c
+        except KeyError:
+            continue
+        kernels[name]["alg_gbs"] = round(bytes_ / (us * 1e-6) / 1e9, 1)
+        kernels[name]["frac_of_measured_copy"] = round(bytes_ / (us * 1e-6) / 1e9 / peak, 3)
     for h in hs:
         h.destroy()
     return {"workload": "batch-64-cells-hysteresis", "cells": 64, "unknowns": n,
             "value": world * n * 4 * k / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms / k, "steps": k,
             "one_by_one_ms_per_step": single, "batching_gain": single / (ms / k),
+            "kernels": kernels, "kernels_timing": "a second pass of the same steps, kernel by kernel, CUDA-event "
+                                                  "pairs on the launching stream; algorithmic bytes summed over the "
+                                                  "cells' own operators (fused interpolation + precorrection)",
             "dt_s": dt, "setup_s": round(t_setup, 1), "autotune_s": round(t_tune, 1),
             "tiles_used": sorted({f"{int(a)}x{int(c)}" for a, c in tiles}), "precision": "fp32",
             "launch": "one captured CUDA graph per RK4 step, one launch per pass over all cells"}

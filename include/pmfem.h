@@ -311,7 +311,9 @@ int pmfem_bloch_convolve(pmfem_t h, const double* k0, const void* Q, void* U, vo
  * (+ RK4 stage), 9 grid clear, 10 permutation between the C-ABI unknown order and the internal
  * box-sorted order, 11 stencil of the grid potential added to the precorrected potential (the
  * second pass of the two-pass form, in which the precorrection overlaps the projection and the
- * FFT on a second stream; with timing on, every launch runs on the launching stream in order).
+ * FFT on a second stream; with timing on, every launch runs on the launching stream in order),
+ * 12, 13, 14 the surrogate network's 1 -> 32, 32 -> 32 (both hidden layers) and 32 -> 1 layers
+ * (pmfem_surrogate_apply and the surrogate's RK stages).
  */
 int pmfem_profile(pmfem_t h, int enable);
 int pmfem_profile_read(pmfem_t h, int64_t* counts, double* total_ms, int n);
@@ -484,6 +486,15 @@ int pmfem_batch_llg_step(pmfem_batch_t b, double dt, int nsteps, void* stream);
 
 /* Waits for the device and reports a device error of the batch (ENONFINITE) like pmfem_sync. */
 int pmfem_batch_sync(pmfem_batch_t b);
+
+/*
+ * Per-launch timing of the batch's kernels, as pmfem_profile / pmfem_profile_read with the same
+ * kernel ids (the batch runs the fused interpolation + precorrection, id 7, and no stencil
+ * pass).  While timing is on, pmfem_batch_llg_step launches every kernel in order on its stream
+ * instead of replaying its captured step, so that each launch is timed alone.
+ */
+int pmfem_batch_profile(pmfem_batch_t b, int enable);
+int pmfem_batch_profile_read(pmfem_batch_t b, int64_t* counts, double* total_ms, int n);
 
 #ifdef __cplusplus
 }

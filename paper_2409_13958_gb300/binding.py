@@ -73,6 +73,8 @@ SIGNATURES = {
     "pmfem_batch_get_m": (_c.c_int, [_vp, _vp, _vp]),
     "pmfem_batch_llg_step": (_c.c_int, [_vp, _dbl, _c.c_int, _vp]),
     "pmfem_batch_sync": (_c.c_int, [_vp]),
+    "pmfem_batch_profile": (_c.c_int, [_vp, _c.c_int]),
+    "pmfem_batch_profile_read": (_c.c_int, [_vp, _vp, _vp, _c.c_int]),
     "pmfem_setup_times": (_c.c_int, [_vp, _vp, _c.c_int]),
     "pmfem_debug_fail_alloc": (_c.c_int, [_c.c_int]),
     "pmfem_build_flags": (_c.c_int, []),
@@ -464,6 +466,16 @@ class PmfemBatch:
 
     def llg_step(self, dt: float, nsteps: int = 1, stream=None):
         self._ck(self._lib.pmfem_batch_llg_step(self.b, dt, nsteps, _stream(stream)))
+
+    def profile(self, enable: bool = True):
+        self._ck(self._lib.pmfem_batch_profile(self.b, 1 if enable else 0))
+
+    def profile_read(self) -> dict:
+        n = len(Pmfem.KERNELS)
+        counts = np.zeros(n, dtype=np.int64)
+        ms = np.zeros(n, dtype=np.float64)
+        self._ck(self._lib.pmfem_batch_profile_read(self.b, counts.ctypes.data, ms.ctypes.data, n))
+        return {k: (int(c), float(t)) for k, c, t in zip(Pmfem.KERNELS, counts, ms)}
 
     def sync(self):
         self._ck(self._lib.pmfem_batch_sync(self.b))

@@ -150,6 +150,19 @@ struct pmfem_batch_state {
   // captured RK4 step
   cudaGraphExec_t graph = nullptr;
   double graph_dt = 0.0;
+  // per-launch timing (pmfem_batch_profile): an event pair around every kernel launch
+  bool prof_on = false;
+  std::vector<cudaEvent_t> ev_pool;
+  size_t ev_next = 0;
+  cudaEvent_t open_ev[pmfem::KID_COUNT] = {};
+  struct Rec {
+    int id;
+    cudaEvent_t a, b;
+  };
+  std::vector<Rec> recs;
+  int64_t prof_count[pmfem::KID_COUNT] = {};
+  double prof_ms[pmfem::KID_COUNT] = {};
+  pmfem::ProfHook prof;
 };
 
 namespace pmfem {
@@ -287,6 +300,21 @@ inline unsigned pblocks(const pmfem_batch_state* b, int64_t n) { return std::max
 namespace {
 
 const double kGammaE = 1.76085963023e11;   // electron gyromagnetic ratio, rad/(s T)
+
+void batch_prof_hook(void* ctx, int id, int phase, cudaStream_t st) {
+  pmfem_batch_t b = (pmfem_batch_t)ctx;
+  if (b->ev_next >= b->ev_pool.size()) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) return;
+    b->ev_pool.push_back(e);
+  }
+  cudaEvent_t e = b->ev_pool[b->ev_next++];
+  cudaEventRecord(e, st);
+  if (phase == 0)
+    b->open_ev[id] = e;
+  else
+    b->recs.push_back({id, b->open_ev[id], e});
+}
 
 int bfail(pmfem_batch_t b, int code, const std::string& msg) {
   b->err = {code, msg};
@@ -532,11 +560,14 @@ void batch_eval(pmfem_batch_t b, const V4<float>* m, float* H, int comps, const 
   const unsigned nb = pblocks(b, b->rows);
   const DevSell<float>& A = b->adj;
   if (comps & PMFEM_MS) {
+    b->prof.begin(KID_CHARGES, st);
     with_cols(A, [&](auto dcol) {
       using CT = std::remove_cv_t<std::remove_pointer_t<decltype(dcol)>>;
       kb_charges<CT><<<nb, kBlock, 0, st>>>(b->rows, b->node_cell, b->dtable, A.len, A.base, A.off, dcol, A.val[0],
                                             A.val[1], A.val[2], A.val[3], A.val[4], A.val[5], m, b->q, b->e);
     });
+    b->prof.end(KID_CHARGES, st);
+    b->prof.begin(KID_ANTERP, st);
     const DevSell<float>& Pm = b->pro;
     with_cols(Pm, [&](auto dcol) {
       using CT = std::remove_cv_t<std::remove_pointer_t<decltype(dcol)>>;
@@ -545,6 +576,7 @@ void batch_eval(pmfem_batch_t b, const V4<float>* m, float* H, int comps, const 
     });
     if (b->nx_exc > 0)
       kb_project_exc<<<pblocks(b, b->nx_exc), kBlock, 0, st>>>(b->nx_exc, b->xnode, b->xgrid, b->xw, b->q, b->grid);
+    b->prof.end(KID_ANTERP, st);
     for (const FftGroup& g : b->groups) {
       FftArgs<float> a;
       a.grid = b->grid;
@@ -557,8 +589,9 @@ void batch_eval(pmfem_batch_t b, const V4<float>* m, float* H, int comps, const 
       }
       a.boff = g.boff;
       a.count = (unsigned)g.cells.size();
-      launch_fft(a, ProfHook(), st);
+      launch_fft(a, b->prof, st);
     }
+    b->prof.begin(KID_INTERP, st);
     const DevSell<float>& C = b->cor;
     with_cols(C, [&](auto dcol) {
       using CT = std::remove_cv_t<std::remove_pointer_t<decltype(dcol)>>;
@@ -574,6 +607,7 @@ void batch_eval(pmfem_batch_t b, const V4<float>* m, float* H, int comps, const 
         default: go(kb_interp<6, CT>); break;
       }
     });
+    b->prof.end(KID_INTERP, st);
   }
   const int use_ms = (comps & PMFEM_MS) ? 1 : 0, use_ex = (comps & PMFEM_EX) ? 1 : 0, use_ap = (comps & PMFEM_AP) ? 1 : 0;
   with_cols(A, [&](auto dcol) {
@@ -584,12 +618,14 @@ void batch_eval(pmfem_batch_t b, const V4<float>* m, float* H, int comps, const 
                                     (V4<float>*)rk.m0, (V4<float>*)rk.mnext, (V4<float>*)rk.acc, (float)rk.cdt,
                                     (float)rk.bw, rk.acc_init, (float)rk.dt6, b->flag);
     };
+    b->prof.begin(KID_FIELD, st);
     if (rk.mode == 0)
       go(kb_field<0, CT>);
     else if (rk.mode == 1)
       go(kb_field<1, CT>);
     else
       go(kb_field<2, CT>);
+    b->prof.end(KID_FIELD, st);
   });
 }
 
@@ -668,8 +704,42 @@ int pmfem_batch_create(pmfem_batch_t* out, const pmfem_t* cells, int n) {
   return OK;
 }
 
+int pmfem_batch_profile(pmfem_batch_t b, int enable) {
+  if (!b) return EINVAL_;
+  b->prof_on = enable != 0;
+  b->recs.clear();
+  b->ev_next = 0;
+  for (int i = 0; i < KID_COUNT; ++i) b->prof_count[i] = 0, b->prof_ms[i] = 0;
+  if (b->prof_on) {
+    b->prof.fn = batch_prof_hook;
+    b->prof.ctx = b;
+  } else {
+    b->prof = ProfHook();
+  }
+  return OK;
+}
+
+int pmfem_batch_profile_read(pmfem_batch_t b, int64_t* counts, double* total_ms, int n) {
+  if (!b || !counts || !total_ms || n <= 0) return EINVAL_;
+  PMFEM_BCK(b, cudaDeviceSynchronize());
+  for (auto& r : b->recs) {
+    float ms = 0;
+    PMFEM_BCK(b, cudaEventElapsedTime(&ms, r.a, r.b));
+    b->prof_count[r.id] += 1;
+    b->prof_ms[r.id] += ms;
+  }
+  b->recs.clear();
+  b->ev_next = 0;
+  for (int i = 0; i < n; ++i) {
+    counts[i] = i < KID_COUNT ? b->prof_count[i] : 0;
+    total_ms[i] = i < KID_COUNT ? b->prof_ms[i] : 0.0;
+  }
+  return OK;
+}
+
 int pmfem_batch_destroy(pmfem_batch_t b) {
   if (!b) return EINVAL_;
+  for (cudaEvent_t e : b->ev_pool) cudaEventDestroy(e);
   free_batch_device(b);
   if (b->stream) cudaStreamDestroy(b->stream);
   delete b;
@@ -753,6 +823,11 @@ int pmfem_batch_llg_step(pmfem_batch_t b, double dt, int nsteps, void* stream) {
   if (rc) return rc;
   cudaStream_t st = stream ? (cudaStream_t)stream : b->stream;
   if (nsteps == 0) return OK;
+  if (b->prof_on) {   // launch by launch, each timed on the stream
+    for (int k = 0; k < nsteps; ++k) batch_rk_step(b, dt, st);
+    PMFEM_BCK(b, cudaGetLastError());
+    return OK;
+  }
   if (!b->graph || b->graph_dt != dt) {
     // the capture reads the state buffers by address only: order it after the caller's work
     PMFEM_BCK(b, cudaStreamSynchronize(st));

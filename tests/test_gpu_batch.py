@@ -149,3 +149,34 @@ def test_batch_autotune_picks_listed_tiles_and_keeps_the_field():
         assert any(ty == min(a, grid[1]) and tz == min(c, grid[2]) for a, c in allowed), (k, ty, tz)
     assert _rel(H1.double().cpu().numpy(), H0.double().cpu().numpy()) <= TOL_FP32
     b.destroy()
+
+
+def test_batch_profile_times_every_pass_and_keeps_the_trajectory():
+    """With per-launch timing on, the batch steps kernel by kernel (no graph): the same
+    trajectory as the replayed step, and a launch count per pass of every evaluation."""
+    cells, hs, b = _setup()
+    n = int(b.offsets()[-1])
+    m0 = torch.tensor(meshgen.m_random(n, seed=77), dtype=torch.float32, device="cuda")
+    dt = 2e-14
+    b.set_m(m0)
+    b.llg_step(dt, 2)          # replayed graph
+    ref = torch.empty_like(m0)
+    b.get_m(ref)
+    b.set_m(m0)
+    b.profile(True)
+    b.llg_step(dt, 2)          # launch by launch, timed
+    prof = b.profile_read()
+    b.profile(False)
+    got = torch.empty_like(m0)
+    b.get_m(got)
+    b.sync()
+    # the same kernels in the same order (the few atomics of the projection's exception nodes may
+    # sum in another order)
+    assert _rel(got.double().cpu().numpy(), ref.double().cpu().numpy()) <= TOL_SAME
+    evals = 2 * 4
+    for name in ("charges", "projection", "interp_precorr", "gradient_exchange"):
+        c, t = prof[name]
+        assert c == evals and t > 0, name
+    assert prof["fft_z_conv"][0] >= evals     # one per grid-shape group and evaluation
+    assert prof["interp_stencil"][0] == 0     # the batch runs the fused interpolation
+    b.destroy()
