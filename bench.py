@@ -202,8 +202,10 @@ def alg_bytes(name: str, s: int, sz: dict, vs: dict | None = None) -> float:
     v4 = 4 * s                                  # internal magnetisation 4-vector
     if name == "charges":                      # len, W^q and E values, m once, q and e written
         return 4 * Np + na * (cb["adjacency"] + 6 * s) + v4 * Np + 2 * s * Np
-    if name == "projection":                   # len + base per grid point, weights, q once, grid written
-        return 8 * G + npro * (cb["projection"] + s) + s * Np + s * G
+    if name == "projection":                   # grid cleared; map + len + base per row (grid points with
+        # entries), weights, q once, the rows' grid points written
+        R = dev["projection"].get("rows", G)
+        return s * G + 12 * R + npro * (cb["projection"] + s) + s * Np + s * R
     if name == "fft_x_fwd":
         return s * G + 2 * s * Hx * N1 * N2
     if name == "fft_y_fwd":

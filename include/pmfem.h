@@ -341,7 +341,8 @@ int pmfem_operator_export(pmfem_t h, int which, int32_t* rowptr, int32_t* col, d
  * Device layout facts (uploads the device data for the current precision if needed):
  * out[0..2] adjacency entries, padded SELL slots, column bits; out[3..5] the same for the
  * point precorrection; out[6..8] for the projection; out[9] projection exception entries;
- * out[10..11] box-order tile rows and planes.
+ * out[10..11] box-order tile rows and planes; out[12] rows of the projection (the grid points
+ * that some node projects to; the grid is cleared before each projection).
  */
 int pmfem_device_info(pmfem_t h, int64_t* out, int n);
 

@@ -325,13 +325,14 @@ class Pmfem:
         return rp, col, vals
 
     def device_info(self) -> dict:
-        out = np.zeros(12, dtype=np.int64)
-        self._ck(self._lib.pmfem_device_info(self.h, out.ctypes.data, 12))
+        out = np.zeros(13, dtype=np.int64)
+        self._ck(self._lib.pmfem_device_info(self.h, out.ctypes.data, 13))
         names = ("adjacency", "precorrection", "projection")
         d = {n: {"entries": int(out[3 * k]), "padded": int(out[3 * k + 1]), "col_bits": int(out[3 * k + 2])}
              for k, n in enumerate(names)}
         d["projection_exceptions"] = int(out[9])
         d["tile"] = (int(out[10]), int(out[11]))
+        d["projection"]["rows"] = int(out[12])
         return d
 
     def setup_times(self) -> dict:

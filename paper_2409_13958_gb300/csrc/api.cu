@@ -295,6 +295,7 @@ int build_device(pmfem_t h, DevOps<T>& d) {
   h->dev_info[9] = (int64_t)L.xnode.size();
   h->dev_info[10] = L.TY;
   h->dev_info[11] = L.TZ;
+  h->dev_info[12] = L.pro.rows;
 
   d.nx_exc = (int64_t)L.xnode.size();
   if ((rc = upload(h, L.xnode.data(), L.xnode.size(), &d.xnode))) return rc;
@@ -1231,7 +1232,7 @@ int pmfem_device_info(pmfem_t h, int64_t* out, int n) {
   if (!h || !out || n <= 0) return EINVAL_;
   int rc = ensure_device(h);
   if (rc) return rc;
-  for (int i = 0; i < n; ++i) out[i] = i < 12 ? h->dev_info[i] : 0;
+  for (int i = 0; i < n; ++i) out[i] = i < 13 ? h->dev_info[i] : 0;
   return OK;
 }
 

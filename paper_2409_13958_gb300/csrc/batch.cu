@@ -38,8 +38,10 @@ struct CellDev {
   int64_t node_off;   // first row of the cell in the padded node space (multiple of 32)
   int64_t user_off;   // first unknown of the cell in the caller's concatenated order
   int64_t grid_off;   // first point of the cell's grid in the concatenated grids (multiple of 32)
+  int64_t prow_off;   // first row of the cell's projection (its grid points with entries)
   int32_t Np;         // unknowns of the cell
   int32_t G;          // grid points of the cell
+  int32_t nprow;      // rows of the cell's projection
   int32_t dims[3];
   int32_t periodic[3];
   float hap[3];       // applied field, A/m
@@ -114,6 +116,7 @@ struct pmfem_batch_state {
   int p = 3;
   int64_t rows = 0;        // padded node space
   int64_t grows = 0;       // padded grid-point space
+  int64_t prows = 0;       // padded row space of the projection (grid points with entries)
   int64_t users = 0;       // sum of N'
   std::vector<int64_t> user_off;
   // device
@@ -123,7 +126,7 @@ struct pmfem_batch_state {
   std::vector<CellDev> table;
   CellDev* dtable = nullptr;
   const int32_t* node_cell = nullptr;   // per 32-row chunk of the node space
-  const int32_t* grid_cell = nullptr;   // per 32-row chunk of the grid-point space
+  const int32_t* grid_cell = nullptr;   // per 32-row chunk of the projection's row space
   const int32_t* uidx = nullptr;        // node row -> caller's unknown (global)
   DevSell<float> adj, cor, pro;
   const int32_t* sbase = nullptr;       // stencil base, 3 per node row
@@ -225,16 +228,16 @@ __global__ void __launch_bounds__(kBlock) kb_charges(int64_t rows, const int32_t
 }
 
 template <typename CT>
-__global__ void __launch_bounds__(kBlock) kb_project(int64_t grows, const int32_t* __restrict__ grid_cell,
+__global__ void __launch_bounds__(kBlock) kb_project(int64_t prows, const int32_t* __restrict__ grid_cell,
                                                     const CellDev* __restrict__ cells, const int32_t* __restrict__ map,
                                                     const int32_t* __restrict__ len, const int32_t* __restrict__ base,
                                                     const int64_t* __restrict__ off, const CT* __restrict__ dcol,
                                                     const float* __restrict__ pw, const float* __restrict__ q,
                                                     float* __restrict__ grid) {
-  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < grows;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < prows;
        t += (int64_t)gridDim.x * blockDim.x) {
     const CellDev& c = cells[grid_cell[t >> 5]];
-    if (t - c.grid_off >= c.G) continue;
+    if (t - c.prow_off >= c.nprow) continue;
     project_row<float, CT, float>(t, map[t], c.node_off, c.Np, len, base, off, dcol, pw, q, grid);
   }
 }
@@ -396,7 +399,7 @@ int build_batch_device(pmfem_batch_t b) {
   std::vector<int64_t> xgrid;
   std::map<std::vector<int>, int> gkey;
   std::vector<std::vector<int64_t>> goffs;
-  int64_t row = 0, grow = 0, user = 0, cb = 0, gh = 0;
+  int64_t row = 0, grow = 0, prow = 0, user = 0, cb = 0, gh = 0;
   b->user_off.assign(n + 1, 0);
   for (int c = 0; c < n; ++c) {
     const Setup& s = b->cells[c]->s;
@@ -412,6 +415,8 @@ int build_batch_device(pmfem_batch_t b) {
     d.grid_off = grow;
     d.Np = (int32_t)Np;
     d.G = (int32_t)G;
+    d.prow_off = prow;
+    d.nprow = (int32_t)L.pro.rows;
     for (int a = 0; a < 3; ++a) {
       d.dims[a] = s.dims[a];
       d.periodic[a] = s.periodic[a] ? 1 : 0;
@@ -421,7 +426,7 @@ int build_batch_device(pmfem_batch_t b) {
     d.alpha = (float)s.alpha;
     append_sell(adj, L.adj, row, row);
     append_sell(cor, L.cor, row, row);
-    append_sell(pro, L.pro, grow, grow);
+    append_sell(pro, L.pro, prow, grow);   // rows: the grid points with entries; map: grid points
     for (int64_t i = 0; i < 32 * nch; ++i) {
       const bool in = i < Np;
       uidx.push_back(in ? (int32_t)(user + L.perm[i]) : 0);
@@ -442,7 +447,8 @@ int build_batch_device(pmfem_batch_t b) {
       xw.push_back((float)L.xw[k]);
     }
     for (int64_t k = 0; k < nch; ++k) node_cell.push_back(c);
-    for (int64_t k = 0; k < gch; ++k) grid_cell.push_back(c);
+    const int64_t pch = (L.pro.rows + 31) / 32;
+    for (int64_t k = 0; k < pch; ++k) grid_cell.push_back(c);
     const double scale = 1.0 / ((double)s.fft[0] * s.fft[1] * s.fft[2]);
     for (double g : s.ghat) ghat.push_back((float)(g * scale));
     const std::vector<int> key{s.dims[0], s.dims[1], s.dims[2], s.fft[0], s.fft[1], s.fft[2]};
@@ -460,11 +466,13 @@ int build_batch_device(pmfem_batch_t b) {
     gh += (int64_t)s.ghat.size();
     row += 32 * nch;
     grow += 32 * gch;
+    prow += 32 * pch;
     user += Np;
     b->user_off[c + 1] = user;
   }
   b->rows = row;
   b->grows = grow;
+  b->prows = prow;
   b->users = user;
   int rc;
   if ((rc = upload_hsell(b, adj, b->adj))) return rc;
@@ -569,11 +577,14 @@ void batch_eval(pmfem_batch_t b, const V4<float>* m, float* H, int comps, const 
     b->prof.end(KID_CHARGES, st);
     b->prof.begin(KID_ANTERP, st);
     const DevSell<float>& Pm = b->pro;
-    with_cols(Pm, [&](auto dcol) {
-      using CT = std::remove_cv_t<std::remove_pointer_t<decltype(dcol)>>;
-      kb_project<CT><<<pblocks(b, b->grows), kBlock, 0, st>>>(b->grows, b->grid_cell, b->dtable, Pm.map, Pm.len,
-                                                           Pm.base, Pm.off, dcol, Pm.val[0], b->q, b->grid);
-    });
+    // a cell's projection may hold only its grid points with entries: then clear the grids first
+    if (b->prows < b->grows) cudaMemsetAsync(b->grid, 0, (size_t)b->grows * sizeof(float), st);
+    if (b->prows > 0)
+      with_cols(Pm, [&](auto dcol) {
+        using CT = std::remove_cv_t<std::remove_pointer_t<decltype(dcol)>>;
+        kb_project<CT><<<pblocks(b, b->prows), kBlock, 0, st>>>(b->prows, b->grid_cell, b->dtable, Pm.map, Pm.len,
+                                                             Pm.base, Pm.off, dcol, Pm.val[0], b->q, b->grid);
+      });
     if (b->nx_exc > 0)
       kb_project_exc<<<pblocks(b, b->nx_exc), kBlock, 0, st>>>(b->nx_exc, b->xnode, b->xgrid, b->xw, b->q, b->grid);
     b->prof.end(KID_ANTERP, st);

@@ -305,15 +305,18 @@ template <typename T>
 void launch_anterp(const DevOps<T>& d, cudaStream_t st) {
   const DevSell<T>& Pm = d.pro;
   d.prof.begin(KID_ANTERP, st);
-  const int64_t G = Pm.rows;
-  with_ct(Pm, [&](auto ct) {
-    using CT = typename decltype(ct)::type;
-    with_vt<T>(Pm.bval[0] != nullptr, [&](auto vt) {
-      using VT = typename decltype(vt)::type;
-      k_project<T, CT, VT><<<blocks_for(G), kBlock, 0, st>>>(G, d.Np, Pm.map, Pm.len, Pm.base, Pm.off,
-                                                              (const CT*)Pm.delta, vals<VT>(Pm, 0), d.q, d.grid);
+  // an operator that holds only the grid points some node projects to: clear the grid first
+  const int64_t G = Pm.rows, Ggrid = (int64_t)d.dims[0] * d.dims[1] * d.dims[2];
+  if (G < Ggrid) cudaMemsetAsync(d.grid, 0, (size_t)Ggrid * sizeof(T), st);
+  if (G > 0)
+    with_ct(Pm, [&](auto ct) {
+      using CT = typename decltype(ct)::type;
+      with_vt<T>(Pm.bval[0] != nullptr, [&](auto vt) {
+        using VT = typename decltype(vt)::type;
+        k_project<T, CT, VT><<<blocks_for(G), kBlock, 0, st>>>(G, d.Np, Pm.map, Pm.len, Pm.base, Pm.off,
+                                                                (const CT*)Pm.delta, vals<VT>(Pm, 0), d.q, d.grid);
+      });
     });
-  });
   if (d.nx_exc > 0)
     k_project_exc<T><<<blocks_for(d.nx_exc), kBlock, 0, st>>>(d.nx_exc, d.xnode, d.xgrid, d.xw, d.q, d.grid);
   d.prof.end(KID_ANTERP, st);
@@ -432,13 +435,13 @@ void launch_field(const DevOps<T>& d, const V4<T>* m, T* H, int comps, double hx
 // ---------------------------------------------------------------- layout checks
 namespace {
 template <typename CT>
-__global__ void k_check_sell(int64_t rows, int64_t ncols, int vw, const int32_t* __restrict__ map,
+__global__ void k_check_sell(int64_t rows, int64_t map_lim, int64_t ncols, int vw, const int32_t* __restrict__ map,
                              const int32_t* __restrict__ len, const int32_t* __restrict__ base,
                              const int64_t* __restrict__ off, const CT* __restrict__ dcol, int* flag) {
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= rows) return;
   bool bad = false;
-  if (map && (map[t] < 0 || map[t] >= rows)) bad = true;
+  if (map && (map[t] < 0 || map[t] >= map_lim)) bad = true;
   const int64_t c = t >> 5, lane = t & 31;
   const int64_t width = (off[c + 1] - off[c]) / 32;   // padded entries per lane of this chunk
   const int32_t n = len[t], b = base[t];
@@ -471,23 +474,25 @@ __global__ void k_check_exceptions(int64_t n, int64_t Np, int64_t G, const int32
   if (node[i] < 0 || node[i] >= Np || gidx[i] < 0 || gidx[i] >= G) atomicOr(flag, FLAG_LAYOUT);
 }
 
+// map_lim: the rows the map points into (the operator's own rows, or the grid points for the
+// projection, whose rows are only the grid points with entries)
 template <typename T>
-void check_sell(const DevSell<T>& M, int64_t ncols, int vw, int* flag, cudaStream_t st) {
+void check_sell(const DevSell<T>& M, int64_t map_lim, int64_t ncols, int vw, int* flag, cudaStream_t st) {
   if (M.rows <= 0) return;
   if (M.col16)
-    k_check_sell<int16_t><<<blocks_for(M.rows), kBlock, 0, st>>>(M.rows, ncols, vw, M.map, M.len, M.base, M.off,
-                                                                  (const int16_t*)M.delta, flag);
+    k_check_sell<int16_t><<<blocks_for(M.rows), kBlock, 0, st>>>(M.rows, map_lim, ncols, vw, M.map, M.len, M.base,
+                                                                  M.off, (const int16_t*)M.delta, flag);
   else
-    k_check_sell<int32_t><<<blocks_for(M.rows), kBlock, 0, st>>>(M.rows, ncols, vw, M.map, M.len, M.base, M.off,
-                                                                  (const int32_t*)M.delta, flag);
+    k_check_sell<int32_t><<<blocks_for(M.rows), kBlock, 0, st>>>(M.rows, map_lim, ncols, vw, M.map, M.len, M.base,
+                                                                  M.off, (const int32_t*)M.delta, flag);
 }
 }  // namespace
 
 template <typename T>
 void launch_layout_checks(const DevOps<T>& d, cudaStream_t st) {
-  check_sell(d.adj, d.Np, 4, d.flag, st);
-  check_sell(d.cor, d.Np, PMFEM_COR_VW, d.flag, st);
-  check_sell(d.pro, d.Np, PMFEM_COR_VW, d.flag, st);
+  check_sell(d.adj, d.adj.rows, d.Np, 4, d.flag, st);
+  check_sell(d.cor, d.cor.rows, d.Np, PMFEM_COR_VW, d.flag, st);
+  check_sell(d.pro, (int64_t)d.dims[0] * d.dims[1] * d.dims[2], d.Np, PMFEM_COR_VW, d.flag, st);
   if (d.Np > 0)
     k_check_stencils<<<blocks_for(d.Np), kBlock, 0, st>>>(d.Np, d.base, d.dims[0], d.dims[1], d.dims[2],
                                                         d.periodic[0] ? 1 : 0, d.periodic[1] ? 1 : 0,

@@ -88,8 +88,8 @@ int64_t centre_deltas(const int32_t* cols, int64_t len, int32_t ref, int64_t n, 
 void build_sell(SellMatrix& M, int64_t rows, int comps, int sigma, int col_bits, int64_t ncols, int vw,
                 const std::function<int64_t(int64_t)>& len,
                 const std::function<int32_t(int64_t)>& base,
-                const std::function<void(int64_t, const std::function<void(int32_t, const double*)>&)>& fill) {
-  M.rows = rows;
+                const std::function<void(int64_t, const std::function<void(int32_t, const double*)>&)>& fill,
+                bool drop_empty = false) {
   M.comps = comps;
   M.vw = vw;
   std::vector<int64_t> rl(rows);
@@ -103,6 +103,19 @@ void build_sell(SellMatrix& M, int64_t rows, int comps, int sigma, int col_bits,
       const int64_t w1 = std::min(rows, w0 + sigma);
       std::stable_sort(M.map.begin() + w0, M.map.begin() + w1, [&](int32_t a, int32_t b) { return rl[a] > rl[b]; });
     }
+  // drop_empty: when at least half of the rows have no entries, they are left out (the caller
+  // zeroes their results); otherwise every row stays (and writes its zero itself)
+  int64_t nempty = 0;
+  if (drop_empty)
+    for (int64_t r = 0; r < rows; ++r) nempty += rl[r] == 0;
+  if (drop_empty && 2 * nempty >= rows && nempty > 0) {
+    int64_t k = 0;
+    for (int64_t t = 0; t < rows; ++t)
+      if (rl[M.map[t]] > 0) M.map[k++] = M.map[t];
+    M.map.resize(k);
+    rows = k;
+  }
+  M.rows = rows;
   const int64_t nch = (rows + 31) / 32;
   M.len.resize(rows);
   M.base.resize(rows);
@@ -358,6 +371,9 @@ int build_layout(const Setup& s, Layout& L, Error& err) {
     gc[2] = (int)(g / ((int64_t)N[0] * N[1]));
   };
   const int64_t G = (int64_t)N[0] * N[1] * N[2];
+  // the grid points no node projects to (the padding of open axes, the space around the body) are
+  // left out of the projection's rows when they are at least half of the grid (thin films): the
+  // grid is then cleared before each projection instead
   build_sell(L.pro, G, 1, s.sort_window > 0 ? s.sort_window : 1024, s.col_bits, Np, PMFEM_COR_VW,
              [&](int64_t g) {
                int gc[3];
@@ -385,7 +401,8 @@ int build_layout(const Setup& s, Layout& L, Error& err) {
                    put((int32_t)k, &w);
                  }
                });
-             });
+             },
+             true);
   L.xnode.clear();
   L.xgrid.clear();
   L.xw.clear();

@@ -66,7 +66,7 @@ struct pmfem_state {
   cudaEvent_t open_ev[pmfem::KID_COUNT] = {};
   int64_t prof_count[pmfem::KID_COUNT] = {};
   double prof_ms[pmfem::KID_COUNT] = {};
-  int64_t dev_info[12] = {};   // layout facts of the current device upload
+  int64_t dev_info[13] = {};   // layout facts of the current device upload
   // one RK4 step captured as a CUDA graph (pmfem_llg_step without timing or surrogate)
   cudaGraphExec_t graph = nullptr;
   double graph_dt = 0.0;

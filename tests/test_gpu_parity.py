@@ -43,6 +43,9 @@ CASES = {
                    (16, 16, 16), 3, 2, 0.0),
     "film_p2_near_radius": (lambda: meshgen.film_cell(9, 7, 3, seed=8), (16, 16, 16), 2, 2, 1.0),
     "film_p5": (lambda: meshgen.film_cell(9, 7, 3, seed=9), (16, 16, 16), 5, 2, 0.0),
+    # a thin film under a tall grid: most grid points receive no charge (the projection then
+    # keeps only the grid points with entries and the grid is cleared first)
+    "film_thin_tall_grid": (lambda: meshgen.film_cell(10, 10, 1, seed=13), (16, 16, 32), 3, 2, 0.0),
 }
 
 _cache = {}
@@ -310,3 +313,29 @@ def test_film_rk4_trajectory_200_steps_fp64():
     assert _rel(got, m) <= 1e-8, _rel(got, m)
     assert _rel(m, m0) > 1e-3
     h.destroy()
+
+
+def test_projection_leaves_out_empty_grid_points_of_thin_films():
+    """The projection's rows are the grid points some node projects to when at least half of the
+    grid is empty (a thin film's z padding), the grid being cleared before each projection;
+    otherwise every grid point is a row.  Every case's field is pinned to the oracle by
+    test_field_parity; here: each case follows the rule, both forms occur among the cases, and a
+    field evaluated twice (the second time over a grid that still holds the previous potential)
+    is unchanged."""
+    from paper_2409_13958_gb300 import PMFEM_FP32, PMFEM_MS
+    forms = set()
+    for name in sorted(CASES):
+        mesh, ob, grid, p, nb, f = _problem(name)
+        h = _lib(mesh, grid, p, nb, f, PMFEM_FP32)
+        G = int(np.prod(h.grid_info()[0]))
+        rows = h.device_info()["projection"]["rows"]
+        assert rows == G or 2 * rows <= G, (name, rows, G)
+        forms.add(rows < G)
+        m = torch.tensor(meshgen.m_random(ob.Np, seed=12), dtype=torch.float32, device="cuda")
+        H1, H2 = torch.empty_like(m), torch.empty_like(m)
+        h.field(m, H1, PMFEM_MS)
+        h.field(m, H2, PMFEM_MS)
+        h.sync()
+        assert _rel(H2.double().cpu().numpy(), H1.double().cpu().numpy()) <= 1e-6, name
+        h.destroy()
+    assert forms == {True, False}
