@@ -54,10 +54,11 @@ def parse(argv=None):
                     help="skip timing the host set-up beside the GPU set-up of the same mesh")
     ap.add_argument("--no-cufft", action="store_true", help="skip the cuFFT convolution comparison")
     ap.add_argument("--no-implicit", action="store_true", help="skip the implicit midpoint leg")
+    ap.add_argument("--no-lattice", action="store_true", help="skip the sphere-lattice FP32 vs FP64 leg")
     ap.add_argument("--repeats", type=int, default=5, help="repeats of the timed steps for the median")
     ap.add_argument("--sur-runs", type=int, default=20, help="trajectories that give the surrogate's training pairs")
     ap.add_argument("--sur-steps", type=int, default=1000, help="RK4 steps per surrogate training trajectory")
-    ap.add_argument("--only", default=None, choices=["surrogate", "surrogate_fwd", "batch"],
+    ap.add_argument("--only", default=None, choices=["surrogate", "surrogate_fwd", "batch", "lattice"],
                     help="run one side leg alone and print its JSON object (diagnosis and profiling)")
     ap.add_argument("--out", default=None, help="also write the JSON line to this file")
     return ap.parse_args(argv)
@@ -560,6 +561,97 @@ def batch_leg(args, dist, world):
             "launch": "one captured CUDA graph per RK4 step, one launch per pass over all cells"}
 
 
+_LATTICE = {}
+
+
+def lattice_mesh():
+    """The 3D-periodic sphere lattice (period 50 nm, sphere radius 20 nm, ~200k nodes, seed 0),
+    built once per process (the lattice and surrogate legs share it)."""
+    import meshgen
+    if "mesh" not in _LATTICE:
+        _LATTICE["mesh"] = meshgen.sphere_lattice(L=50e-9, R=20e-9, target_nodes=200_000, seed=0)
+    return _LATTICE["mesh"]
+
+
+def lattice_leg(args, dist, world):
+    """FP32 against FP64 on the sphere lattice (grid 64^3, p = 3, near_boxes = 3): the same random
+    unit m, 1000 RK4 steps in each precision (replayed graphs), the field of the first state per
+    term, and the trajectories' deviation after 10, 100 and 1000 steps.  A control separates the
+    arithmetic from the input: FP64 once more from m rounded to FP32 (the FP32 path's input)."""
+    import torch
+    import meshgen
+    from paper_2409_13958_gb300 import Pmfem, PMFEM_FP32, PMFEM_FP64, PMFEM_MS, PMFEM_EX
+    t0 = time.time()
+    mesh = lattice_mesh()
+    t_mesh = time.time() - t0
+    stream = torch.cuda.current_stream()
+    out, traj, fields = {}, {}, {}
+    segments = (10, 90, 900)
+    for prec, name in ((PMFEM_FP64, "fp64"), (PMFEM_FP64, "fp64_from_fp32_input"), (PMFEM_FP32, "fp32")):
+        t0 = time.time()
+        h = Pmfem.create_mesh(mesh.xyz, mesh.tets, MS, AEX, ALPHA)
+        h.set_aim(64, 64, 64, P_ORDER, NEAR_BOXES, NEAR_ELEM)
+        h.set_periodicity(*mesh.periods)
+        h.set_setup_device(True)
+        h.set_precision(prec)
+        Np = h.num_unknowns()
+        if "dt" not in out:
+            rp, col, vals = h.operator_export(0)
+            out["dt"] = stable_dt(float(np.add.reduceat(np.abs(vals[:, 0]), rp[:-1]).max()))
+            out["m0"] = meshgen.m_random(Np, seed=41)
+        dt = out["dt"]
+        m0 = out["m0"] if name == "fp64" else out["m0"].astype(np.float32).astype(np.float64)
+        dty = torch.float64 if prec == PMFEM_FP64 else torch.float32
+        m = torch.tensor(m0, dtype=dty, device="cuda")
+        if name != "fp64_from_fp32_input":
+            H = torch.empty_like(m)
+            fields[name] = {}
+            for comps, key in ((PMFEM_MS, "ms"), (PMFEM_EX, "ex")):
+                h.field(m, H, comps, stream)
+                torch.cuda.synchronize()
+                fields[name][key] = H.double().cpu().numpy()
+        h.set_m(m, stream)
+        h.llg_step(dt, 1, stream)        # capture
+        h.set_m(m, stream)
+        torch.cuda.synchronize()
+        traj[name] = []
+        ms = 0.0
+        for k in segments:
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            h.llg_step(dt, k, stream)
+            e1.record(stream)
+            e1.synchronize()
+            ms += dist.max(e0.elapsed_time(e1))
+            h.get_m(m, stream)
+            torch.cuda.synchronize()
+            traj[name].append(m.double().cpu().numpy())
+        h.sync()
+        steps = sum(segments)
+        if name != "fp64_from_fp32_input":
+            out[name] = {"ms_per_step": ms / steps, "value": world * Np * 4 * steps / (ms * 1e-3),
+                         "setup_s": round(time.time() - t0 - ms * 1e-3, 1)}
+        h.destroy()
+    m0 = out.pop("m0")
+
+    def dev(a, b):
+        return [float(np.linalg.norm(x - y) / np.linalg.norm(y - m0)) for x, y in zip(traj[a], traj[b])]
+
+    rel = {k: float(np.linalg.norm(fields["fp32"][k] - fields["fp64"][k]) / np.linalg.norm(fields["fp64"][k]))
+           for k in ("ms", "ex")}
+    return {"workload": "sphere-lattice-3d-periodic-200k, grid 64^3", "unknowns": int(m0.shape[0]),
+            "steps": sum(segments), "dt_s": out.pop("dt"), "fp64": out["fp64"], "fp32": out["fp32"],
+            "fp32_speedup": out["fp64"]["ms_per_step"] / out["fp32"]["ms_per_step"],
+            "field_rel_l2_fp32_vs_fp64": rel,
+            "trajectory_deviation_after_steps": [10, 100, 1000],
+            "fp32_vs_fp64": dev("fp32", "fp64"),
+            "fp64_from_fp32_rounded_input_vs_fp64": dev("fp64_from_fp32_input", "fp64"),
+            "deviation": "|m_a - m_b| / |m_b - m0| over all nodes",
+            "max_norm_error_fp32": float(np.abs(np.linalg.norm(traj["fp32"][-1], axis=1) - 1).max()),
+            "mesh_s": round(t_mesh, 1),
+            "oracle": "the same geometry against the oracle's P-AIM on sampled unknowns: tests/test_gpu_lattice.py"}
+
+
 def surrogate_forward_timing(h, V, st, reps=50):
     """The network's forward pass on the 64^3 grid: CUDA events around `reps` calls (the whole
     forward), then a profiled pass with an event pair around each layer.  A 32 -> 32 layer is
@@ -606,7 +698,7 @@ def surrogate_forward_leg(args, dist, world):
     import torch
     import meshgen
     from paper_2409_13958_gb300 import Pmfem, PMFEM_FP32
-    mesh = meshgen.sphere_lattice(L=50e-9, R=20e-9, target_nodes=200_000, seed=0)
+    mesh = lattice_mesh()
     h = Pmfem.create_mesh(mesh.xyz, mesh.tets, MS, AEX, ALPHA)
     h.set_aim(64, 64, 64, P_ORDER, NEAR_BOXES, NEAR_ELEM)
     h.set_periodicity(*mesh.periods)
@@ -630,7 +722,7 @@ def surrogate_leg(args, dist, world):
     import meshgen
     from paper_2409_13958_gb300 import Pmfem, PMFEM_FP32
     t0 = time.time()
-    mesh = meshgen.sphere_lattice(L=50e-9, R=20e-9, target_nodes=200_000, seed=0)
+    mesh = lattice_mesh()
     h = Pmfem.create_mesh(mesh.xyz, mesh.tets, MS, AEX, ALPHA)
     h.set_aim(64, 64, 64, P_ORDER, NEAR_BOXES, NEAR_ELEM)
     h.set_periodicity(*mesh.periods)
@@ -1013,6 +1105,8 @@ def run_native(args):
     }
     if not args.no_batch:
         line["batch"] = batch_leg(args, dist, world)
+    if not args.no_lattice:
+        line["lattice"] = lattice_leg(args, dist, world)
     if not args.no_surrogate:
         line["surrogate"] = surrogate_leg(args, dist, world)
     if rank == 0 and not args.no_cpu:
@@ -1033,7 +1127,8 @@ def run_only(args):
     dist = Dist(world, local)
     import __graft_entry__
     __graft_entry__.build()
-    legs = {"surrogate": surrogate_leg, "surrogate_fwd": surrogate_forward_leg, "batch": batch_leg}
+    legs = {"surrogate": surrogate_leg, "surrogate_fwd": surrogate_forward_leg, "batch": batch_leg,
+            "lattice": lattice_leg}
     out = legs[args.only](args, dist, world)
     dist.close()
     if rank == 0:
