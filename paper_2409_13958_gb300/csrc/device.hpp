@@ -48,6 +48,43 @@ struct alignas(4 * sizeof(T)) V4 {
   T x, y, z, w;
 };
 
+// Programmatic dependent launch on the evaluation's main stream (PMFEM_PDL 1): each kernel of
+// the chain is launched with programmatic stream serialisation, so that it is launched while the
+// previous kernel's last blocks run; it waits (griddepcontrol.wait: the previous grid complete,
+// its writes visible) before it reads or writes anything, and lets its own successor launch as
+// soon as each of its blocks has started.  Without the attribute both instructions do nothing.
+// Measured on the 1M-node wire (replayed RK4 graphs): FP32 2.456 -> 2.451 ms per step,
+// BF16-split 1.89e9 -> 1.93e9 node-field-evals/s, FP64 2.32e8 -> 2.30e8.
+#ifndef PMFEM_PDL
+#define PMFEM_PDL 1
+#endif
+#ifdef __CUDACC__
+__device__ __forceinline__ void pdl_enter() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+#endif
+template <typename... KArgs, typename... Args>
+inline void launch_k(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st, Args... args) {
+  if (PMFEM_PDL) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, kernel, ((KArgs)args)...);
+  } else {
+#ifdef __CUDACC__
+    kernel<<<grid, block, smem, st>>>(((KArgs)args)...);
+#endif
+  }
+}
+
 // Optional per-launch timing: the handle records a CUDA event pair around each kernel.
 enum KernelId : int { KID_CHARGES = 0, KID_ANTERP, KID_FFT_X_FWD, KID_FFT_Y_FWD, KID_FFT_Z_CONV, KID_FFT_Y_INV,
                       KID_FFT_X_INV, KID_INTERP, KID_FIELD, KID_MEMSET, KID_PERM, KID_STENCIL,

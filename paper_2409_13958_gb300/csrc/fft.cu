@@ -220,6 +220,7 @@ __global__ void __launch_bounds__(LB * Fac<F>::R2) k_fft_x_fwd(const T* __restri
                                                              int N1, int N2, int F1, const C2* __restrict__ tw,
                                                              const int64_t* __restrict__ boff) {
   using FF = Fac<F>;
+  pdl_enter();
   if (boff) {   // batched: blockIdx.y selects the mesh, boff its (grid, spectrum buffer) offsets
     Q += boff[3 * blockIdx.y];
     cb += boff[3 * blockIdx.y + 1];
@@ -257,6 +258,7 @@ __global__ void PMFEM_FFT_Y_LB(LB * Fac<F>::R2) k_fft_y(C2* __restrict__ cb, int
                                                          const C2* __restrict__ tw, const int64_t* __restrict__ boff,
                                                          int nz) {
   using FF = Fac<F>;
+  pdl_enter();
   if (boff) cb += boff[3 * blockIdx.y + 1];
   extern __shared__ unsigned char smem_raw[];
   C2* S = reinterpret_cast<C2*>(smem_raw);
@@ -295,6 +297,7 @@ __global__ void PMFEM_FFT_Z_LB(LB * Fac<F>::R2) k_fft_z_conv(C2* __restrict__ cb
                                                               const T* __restrict__ ghat, const C2* __restrict__ tw,
                                                               const int64_t* __restrict__ boff) {
   using FF = Fac<F>;
+  pdl_enter();
   if (boff) {
     cb += boff[3 * blockIdx.y + 1];
     ghat += boff[3 * blockIdx.y + 2];
@@ -339,6 +342,7 @@ __global__ void __launch_bounds__(LB * Fac<F>::R2) k_fft_x_inv(const C2* __restr
                                                              int N1, int N2, int F1, const C2* __restrict__ tw,
                                                              const int64_t* __restrict__ boff) {
   using FF = Fac<F>;
+  pdl_enter();
   if (boff) {
     U += boff[3 * blockIdx.y];
     cb += boff[3 * blockIdx.y + 1];
@@ -408,14 +412,14 @@ struct Passes {
     const int64_t nl = (int64_t)d.dims[1] * d.dims[2];
     const size_t sm = smem(LBX);
     set_smem(k_fft_x_fwd<T, C2, F, LBX>, sm);
-    k_fft_x_fwd<T, C2, F, LBX><<<dim3((unsigned)((nl + LBX - 1) / LBX), d.count), LBX * FF::R2, sm, st>>>(
+    launch_k(k_fft_x_fwd<T, C2, F, LBX>, dim3((unsigned)((nl + LBX - 1) / LBX), d.count), LBX * FF::R2, sm, st,
         d.grid, d.cbuf, d.dims[0], d.dims[1], d.dims[2], d.fft[1], d.tw[0], d.boff);
   }
   static void x_inv(const FftArgs<T>& d, cudaStream_t st) {
     const int64_t nl = (int64_t)d.dims[1] * d.dims[2];
     const size_t sm = smem(LBX);
     set_smem(k_fft_x_inv<T, C2, F, LBX>, sm);
-    k_fft_x_inv<T, C2, F, LBX><<<dim3((unsigned)((nl + LBX - 1) / LBX), d.count), LBX * FF::R2, sm, st>>>(
+    launch_k(k_fft_x_inv<T, C2, F, LBX>, dim3((unsigned)((nl + LBX - 1) / LBX), d.count), LBX * FF::R2, sm, st,
         d.cbuf, d.grid, d.dims[0], d.dims[1], d.dims[2], d.fft[1], d.tw[0], d.boff);
   }
   static void y(const FftArgs<T>& d, bool inv, cudaStream_t st) {
@@ -424,11 +428,11 @@ struct Passes {
     const size_t sm = smem(LBS);
     if (!inv) {
       set_smem(k_fft_y<C2, F, LBS, false>, sm);
-      k_fft_y<C2, F, LBS, false><<<dim3(nb, d.count), LBS * FF::R2, sm, st>>>(d.cbuf, Hx, d.dims[1], F, d.tw[1],
+      launch_k(k_fft_y<C2, F, LBS, false>, dim3(nb, d.count), LBS * FF::R2, sm, st, d.cbuf, Hx, d.dims[1], F, d.tw[1],
                                                                                d.boff, d.dims[2]);
     } else {
       set_smem(k_fft_y<C2, F, LBS, true>, sm);
-      k_fft_y<C2, F, LBS, true><<<dim3(nb, d.count), LBS * FF::R2, sm, st>>>(d.cbuf, Hx, F, d.dims[1], d.tw[1],
+      launch_k(k_fft_y<C2, F, LBS, true>, dim3(nb, d.count), LBS * FF::R2, sm, st, d.cbuf, Hx, F, d.dims[1], d.tw[1],
                                                                               d.boff, d.dims[2]);
     }
   }
@@ -437,7 +441,7 @@ struct Passes {
     const unsigned nb = strided_blocks<true>(Hx, LBZ, d.fft[1]);
     const size_t sm = smem(LBZ);
     set_smem(k_fft_z_conv<T, C2, F, LBZ>, sm);
-    k_fft_z_conv<T, C2, F, LBZ><<<dim3(nb, d.count), LBZ * FF::R2, sm, st>>>(d.cbuf, Hx, d.fft[1], d.dims[2],
+    launch_k(k_fft_z_conv<T, C2, F, LBZ>, dim3(nb, d.count), LBZ * FF::R2, sm, st, d.cbuf, Hx, d.fft[1], d.dims[2],
                                                                              d.ghat, d.tw[2], d.boff);
   }
 };

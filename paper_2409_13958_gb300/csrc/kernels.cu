@@ -63,6 +63,7 @@ __global__ void PMFEM_CHARGES_LB k_charges(int64_t Np, const int32_t* __restrict
                                                    const VT* __restrict__ wz, const VT* __restrict__ ex,
                                                    const VT* __restrict__ ey, const VT* __restrict__ ez,
                                                    const V4<T>* __restrict__ m, T* __restrict__ q, T* __restrict__ e) {
+  pdl_enter();
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= Np) return;
   charges_row<T, CT, VT>(i, 0, (int32_t)Np, len, base, off, dcol, wx, wy, wz, ex, ey, ez, m, q, e);
@@ -77,6 +78,7 @@ __global__ void __launch_bounds__(kBlock) k_project(int64_t G, int64_t Np, const
                                                    const int64_t* __restrict__ off, const CT* __restrict__ dcol,
                                                    const VT* __restrict__ pw, const T* __restrict__ q,
                                                    T* __restrict__ grid) {
+  pdl_enter();
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= G) return;
   const int64_t g = map ? (int64_t)map[t] : t;
@@ -88,6 +90,7 @@ template <typename T>
 __global__ void __launch_bounds__(kBlock) k_project_exc(int64_t n, const int32_t* __restrict__ node,
                                                        const int64_t* __restrict__ gidx, const T* __restrict__ w,
                                                        const T* __restrict__ q, T* __restrict__ grid) {
+  pdl_enter();
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= n) return;
   atomicAdd(grid + gidx[t], w[t] * q[node[t]]);
@@ -126,6 +129,7 @@ __host__ __device__ constexpr int cor_pipe() {
       const T *__restrict__ e, const V4<T> *m, T *uw
 #define PMFEM_INTERP_BODY                                                                                         \
   extern __shared__ __align__(16) unsigned char pipe_raw[];                                                      \
+  pdl_enter();                                                                                                    \
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;                                              \
   if (t >= Np) return;                                                                                            \
   const int64_t i = map ? (int64_t)map[t] : t;                                                                    \
@@ -160,6 +164,7 @@ constexpr auto interp_kernel() {
       const T *__restrict__ valX, const T *__restrict__ q, const T *__restrict__ e, const V4<T> *m, T *uw
 #define PMFEM_PRECORR_BODY                                                                                      \
   extern __shared__ __align__(16) unsigned char pipe_raw[];                                                    \
+  pdl_enter();                                                                                                  \
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;                                            \
   if (t >= Np) return;                                                                                          \
   const int64_t i = map ? (int64_t)map[t] : t;                                                                  \
@@ -195,6 +200,7 @@ template <typename T, int P>
 __global__ void PMFEM_STENCIL_LB k_stencil(int64_t Np, const int32_t* __restrict__ base,
                                                    const T* __restrict__ frac, const T* __restrict__ U, int N0,
                                                    int N1, int N2, bool p0, bool p1, bool p2, T* uw) {
+  pdl_enter();
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= Np) return;
   stencil_add_row<T, P>(i, base, frac, U, N0, N1, N2, p0, p1, p2, uw);
@@ -215,6 +221,7 @@ __global__ void PMFEM_STENCIL_LB k_stencil(int64_t Np, const int32_t* __restrict
       V4<T> *__restrict__ m0, V4<T> *__restrict__ mnext, V4<T> *__restrict__ accb, T cdt, T bw, int acc_init,    \
       T dt6, T gam, T alpha, int *flag, LocalTerms<T> lt
 #define PMFEM_FIELD_BODY                                                                                        \
+  pdl_enter();                                                                                                  \
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;                                            \
   if (i >= Np) return;                                                                                          \
   const int64_t uo = MODE == 0 ? (int64_t)perm[i] : 0;                                                          \
@@ -293,7 +300,7 @@ void launch_charges(const DevOps<T>& d, const V4<T>* m, cudaStream_t st) {
     using CT = typename decltype(ct)::type;
     with_vt<T>(A.bval[0] != nullptr, [&](auto vt) {
       using VT = typename decltype(vt)::type;
-      k_charges<T, CT, VT><<<blocks_for(d.Np), kBlock, 0, st>>>(
+      launch_k(k_charges<T, CT, VT>, blocks_for(d.Np), kBlock, 0, st, 
           d.Np, A.len, A.base, A.off, (const CT*)A.delta, vals<VT>(A, 0), vals<VT>(A, 1), vals<VT>(A, 2),
           vals<VT>(A, 3), vals<VT>(A, 4), vals<VT>(A, 5), m, d.q, d.e);
     });
@@ -313,12 +320,12 @@ void launch_anterp(const DevOps<T>& d, cudaStream_t st) {
       using CT = typename decltype(ct)::type;
       with_vt<T>(Pm.bval[0] != nullptr, [&](auto vt) {
         using VT = typename decltype(vt)::type;
-        k_project<T, CT, VT><<<blocks_for(G), kBlock, 0, st>>>(G, d.Np, Pm.map, Pm.len, Pm.base, Pm.off,
+        launch_k(k_project<T, CT, VT>, blocks_for(G), kBlock, 0, st, G, d.Np, Pm.map, Pm.len, Pm.base, Pm.off,
                                                                 (const CT*)Pm.delta, vals<VT>(Pm, 0), d.q, d.grid);
       });
     });
   if (d.nx_exc > 0)
-    k_project_exc<T><<<blocks_for(d.nx_exc), kBlock, 0, st>>>(d.nx_exc, d.xnode, d.xgrid, d.xw, d.q, d.grid);
+    launch_k(k_project_exc<T>, blocks_for(d.nx_exc), kBlock, 0, st, d.nx_exc, d.xnode, d.xgrid, d.xw, d.q, d.grid);
   d.prof.end(KID_ANTERP, st);
 }
 
@@ -334,7 +341,7 @@ void launch_interp(const DevOps<T>& d, const V4<T>* m, cudaStream_t st) {
       const size_t sm = (size_t)(kBlock / 32) * cor_pipe<VT>() * PipeStage<VT, CT>::BYTES;
       auto go = [&](auto kernel) {
         set_smem(kernel, sm);
-        kernel<<<nb, kBlock, sm, st>>>(d.Np, C.map, d.base, d.frac, d.grid, d.dims[0], d.dims[1], d.dims[2],
+        launch_k(kernel, nb, kBlock, sm, st, d.Np, C.map, d.base, d.frac, d.grid, d.dims[0], d.dims[1], d.dims[2],
                                       d.periodic[0], d.periodic[1], d.periodic[2], C.len, C.base, C.off,
                                       (const CT*)C.delta, vals<VT>(C, 0), d.rowptrX, d.colX, d.valX, d.q, d.e, m,
                                       reinterpret_cast<T*>(const_cast<V4<T>*>(m)) + 3);   // u -> lane 3 of m
@@ -376,7 +383,7 @@ void launch_stencil(const DevOps<T>& d, const V4<T>* m, cudaStream_t st) {
   T* uw = reinterpret_cast<T*>(const_cast<V4<T>*>(m)) + 3;
   d.prof.begin(KID_STENCIL, st);
   auto go = [&](auto kernel) {
-    kernel<<<nb, kBlock, 0, st>>>(d.Np, d.base, d.frac, d.grid, d.dims[0], d.dims[1], d.dims[2], d.periodic[0],
+    launch_k(kernel, nb, kBlock, 0, st, d.Np, d.base, d.frac, d.grid, d.dims[0], d.dims[1], d.dims[2], d.periodic[0],
                                   d.periodic[1], d.periodic[2], uw);
   };
   switch (d.p) {
@@ -407,7 +414,7 @@ void launch_field(const DevOps<T>& d, const V4<T>* m, T* H, int comps, double hx
       with_vt<T>(A.bval[9] != nullptr, [&](auto vk) {
         using VK = typename decltype(vk)::type;
         auto go = [&](auto kernel) {
-          kernel<<<nb, kBlock, 0, st>>>(d.Np, A.len, A.base, A.off, (const CT*)A.delta, vals<VG>(A, 6),
+          launch_k(kernel, nb, kBlock, 0, st, d.Np, A.len, A.base, A.off, (const CT*)A.delta, vals<VG>(A, 6),
                                         vals<VG>(A, 7), vals<VG>(A, 8), vals<VK>(A, 9), m, d.perm, H, use_ms,
                                         use_ex, ax, ay, az, m0, mn, acc, (T)rk.cdt, (T)rk.bw, rk.acc_init,
                                         (T)rk.dt6, (T)rk.gam, (T)rk.alpha, d.flag, d.loc);
