@@ -310,8 +310,8 @@ int pmfem_bloch_convolve(pmfem_t h, const double* k0, const void* Q, void* U, vo
  * precorrection (the precorrection alone where the two-pass form runs), 8 gradient + exchange
  * (+ RK4 stage), 9 grid clear, 10 permutation between the C-ABI unknown order and the internal
  * box-sorted order, 11 stencil of the grid potential added to the precorrected potential (the
- * second pass of the two-pass form, in which the precorrection overlaps the projection and the
- * FFT on a second stream; with timing on, every launch runs on the launching stream in order),
+ * second pass of the two-pass form, in which the precorrection runs on a second stream beside the
+ * projection and the FFT; with timing on, every launch runs on the launching stream in order),
  * 12, 13, 14 the surrogate network's 1 -> 32, 32 -> 32 (both hidden layers) and 32 -> 1 layers
  * (pmfem_surrogate_apply and the surrogate's RK stages).
  */

@@ -376,9 +376,11 @@ int ensure_device(pmfem_t h) {
 }
 
 // PMFEM_OVERLAP 1: in FP32 and BF16-split, the precorrection (which needs only q, m and e) runs
-// on the handle's side stream while the projection and the FFT produce the grid potential on
-// st; the stencil of that potential is then added in a second, light pass (measured on the
-// 1M-node wire: 644 -> 620 us per evaluation in FP32, 559 -> 532 in BF16-split).  FP64 keeps
+// on the handle's side stream, ordered only after the charges, while the projection and the FFT
+// produce the grid potential on st (each of these kernels fills the GPU, so the block scheduler
+// overlaps them at kernel boundaries); the stencil of that potential is then added in a second,
+// light pass (measured on the 1M-node wire: 644 -> 620 us per evaluation in FP32, 559 -> 532 in
+// BF16-split).  FP64 keeps
 // the fused kernel: its stencil alone takes 367 us on GB300's narrow FP64 units, work that the
 // fused kernel hides under the precorrection's memory latency.  0: fused everywhere.  With
 // per-launch timing on, the passes run in order on st, so that each launch is timed alone.
