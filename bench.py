@@ -55,10 +55,12 @@ def parse(argv=None):
     ap.add_argument("--no-cufft", action="store_true", help="skip the cuFFT convolution comparison")
     ap.add_argument("--no-implicit", action="store_true", help="skip the implicit midpoint leg")
     ap.add_argument("--no-lattice", action="store_true", help="skip the sphere-lattice FP32 vs FP64 leg")
+    ap.add_argument("--no-local-terms", action="store_true", help="skip the anisotropy + grain-boundary exchange leg")
+    ap.add_argument("--no-bloch", action="store_true", help="skip the Bloch-phase convolution leg")
     ap.add_argument("--repeats", type=int, default=5, help="repeats of the timed steps for the median")
     ap.add_argument("--sur-runs", type=int, default=20, help="trajectories that give the surrogate's training pairs")
     ap.add_argument("--sur-steps", type=int, default=1000, help="RK4 steps per surrogate training trajectory")
-    ap.add_argument("--only", default=None, choices=["surrogate", "surrogate_fwd", "batch", "lattice"],
+    ap.add_argument("--only", default=None, choices=["surrogate", "surrogate_fwd", "batch", "lattice", "local_terms", "bloch"],
                     help="run one side leg alone and print its JSON object (diagnosis and profiling)")
     ap.add_argument("--out", default=None, help="also write the JSON line to this file")
     return ap.parse_args(argv)
@@ -652,6 +654,150 @@ def lattice_leg(args, dist, world):
             "oracle": "the same geometry against the oracle's P-AIM on sampled unknowns: tests/test_gpu_lattice.py"}
 
 
+def _median_step_ms(h, dt, stream, steps=50, repeats=3):
+    """Median over `repeats` of the CUDA-event time of `steps` replayed RK4 steps, per step."""
+    import torch
+    out = []
+    for _ in range(repeats):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        h.llg_step(dt, steps, stream)
+        e1.record(stream)
+        e1.synchronize()
+        out.append(e0.elapsed_time(e1) / steps)
+    return float(np.median(out))
+
+
+def _field_kernel_ms(h, dt, stream, steps=10):
+    """Mean event time of one launch of the gradient + exchange (+ local terms, + RK4 stage)
+    kernel over `steps` profiled RK4 steps."""
+    h.profile(True)
+    h.llg_step(dt, steps, stream)
+    h.sync()
+    n, ms = h.profile_read()["gradient_exchange"]
+    h.profile(False)
+    return ms / max(n, 1)
+
+
+def mean_tet_size(mesh) -> float:
+    """Edge of the cube whose volume is six times the mean tetrahedron volume."""
+    x = mesh.xyz[mesh.tets]
+    v = np.abs(np.einsum("ij,ij->i", x[:, 1] - x[:, 0], np.cross(x[:, 2] - x[:, 0], x[:, 3] - x[:, 0]))) / 6
+    return float((6 * v.mean()) ** (1 / 3))
+
+
+def local_terms_leg(args, dist, world, mesh=None, grains=64):
+    """Anisotropy and grain-boundary exchange (the local terms) on the benchmark wire, FP32: RK4
+    steps (replayed graphs) of the plain handle against a handle with cubic anisotropy of 64
+    seeded Voronoi grains (K1 = -4.5e3 J/m^3, random axes) and an exchange stiffness per
+    tetrahedron (A_iex = 0.2e-11 J/m in the grain-boundary layer), same mesh, grid and step; and
+    the field kernel's launch time in each, where the local terms are fused into its epilogue."""
+    import torch
+    import meshgen
+    from paper_2409_13958_gb300 import Pmfem, PMFEM_FP32
+    if mesh is None:
+        mesh = make_mesh(args.nodes)
+    grid_used = GRID if args.nodes == 1_000_000 else scaled_grid(args.nodes)
+    t0 = time.time()
+    hs = mean_tet_size(mesh)
+    gr = meshgen.voronoi_grains(mesh, grains, hs, K1=-4.5e3, A=AEX, A_iex=0.2e-11, layer=0.6, seed=3)
+    t_grains = time.time() - t0
+    stream = torch.cuda.current_stream()
+    out, dt = {}, None
+    for name in ("plain", "local_terms"):
+        h = Pmfem.create_mesh(mesh.xyz, mesh.tets, MS, AEX, ALPHA)
+        h.set_aim(*grid_used, P_ORDER, NEAR_BOXES, NEAR_ELEM)
+        h.set_setup_device(True)
+        if name == "local_terms":
+            h.set_exchange_per_tet(gr.A_tet)
+        h.set_periodicity(0.0, 0.0, WIRE["L"])
+        if dt is None:
+            rp, col, vals = h.operator_export(0)
+            dt = stable_dt(float(np.add.reduceat(np.abs(vals[:, 0]), rp[:-1]).max()))
+        if name == "local_terms":
+            h.set_anisotropy(gr.tet_grain, gr.axes.reshape(-1, 9), K1=gr.K1)
+        h.set_precision(PMFEM_FP32)
+        Np = h.num_unknowns()
+        m = torch.tensor(initial_m(h.folded_positions()), dtype=torch.float32, device="cuda")
+        h.set_m(m, stream)
+        h.llg_step(dt, 3, stream)         # capture + warm-up
+        torch.cuda.synchronize()
+        ms = dist.max(_median_step_ms(h, dt, stream))
+        out[name] = {"ms_per_step": ms, "value": world * Np * 4 / (ms * 1e-3),
+                     "field_kernel_ms": _field_kernel_ms(h, dt, stream)}
+        h.get_m(m, stream)
+        h.sync()
+        mm = m.double().cpu().numpy()
+        out[name]["max_norm_error"] = float(np.abs(np.linalg.norm(mm, axis=1) - 1).max())
+        h.destroy()
+    return {"workload": f"wire-1d-periodic-protruding-{args.nodes // 1000}k, grid {'x'.join(map(str, grid_used))}",
+            "precision": "fp32", "grains": grains, "K1_J_m3": -4.5e3, "A_iex_J_m": 0.2e-11,
+            "boundary_layer_fraction": float((gr.A_tet < AEX).mean()), "grains_s": round(t_grains, 1),
+            "plain": out["plain"], "local_terms": out["local_terms"],
+            "step_overhead": out["local_terms"]["ms_per_step"] / out["plain"]["ms_per_step"] - 1.0,
+            "field_kernel_overhead": out["local_terms"]["field_kernel_ms"] / out["plain"]["field_kernel_ms"] - 1.0,
+            "timing": "median of 3 x 50 replayed RK4 steps; field kernel: event pairs over 10 profiled steps",
+            "oracle": "tests/test_gpu_local_terms.py (granular cell against oracle/local_terms.py)"}
+
+
+def bloch_leg(args, dist, world, mesh=None, reps=20):
+    """BAIM step 2 with the Bloch-phase PGF (k0 = 0.3 2 pi / L along the wire's axis) on the
+    benchmark wire's grid, FP32 and FP64: the set-up of the twisted kernel's spectrum (Ewald sums
+    and its FP64 transform, once per k0) and the grid convolution of a quasi-periodic complex
+    source (five line-transform passes), each convolution timed with CUDA events.  The bytes are
+    those of the five passes: complex grid rows read and written once per pass, the real
+    spectrum once."""
+    import torch
+    from paper_2409_13958_gb300 import Pmfem, PMFEM_FP32, PMFEM_FP64
+    if mesh is None:
+        mesh = make_mesh(args.nodes)
+    grid_used = GRID if args.nodes == 1_000_000 else scaled_grid(args.nodes)
+    h = Pmfem.create_mesh(mesh.xyz, mesh.tets, MS, AEX, ALPHA)
+    h.set_aim(*grid_used, P_ORDER, NEAR_BOXES, NEAR_ELEM)
+    h.set_setup_device(True)
+    h.set_periodicity(0.0, 0.0, WIRE["L"])
+    dims, fft, _, _ = h.grid_info()
+    N0, N1, N2 = (int(x) for x in dims)
+    F0, F1, F2 = (int(x) for x in fft)
+    k0 = np.array([0.0, 0.0, 0.3 * 2 * math.pi / WIRE["L"]])
+    stream = torch.cuda.current_stream()
+    g = torch.Generator(device="cuda").manual_seed(5)
+    res = {}
+    for prec, name, ct in ((PMFEM_FP32, "fp32", torch.complex64), (PMFEM_FP64, "fp64", torch.complex128)):
+        h.set_precision(prec)
+        Q = torch.randn((N2, N1, N0), dtype=ct, device="cuda", generator=g)
+        U = torch.empty_like(Q)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        h.bloch_convolve(k0, Q, U, stream)      # the spectrum of this k0 is set up here
+        torch.cuda.synchronize()
+        first_s = time.perf_counter() - t0
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            h.bloch_convolve(k0, Q, U, stream)
+        e1.record(stream)
+        e1.synchronize()
+        ms = dist.max(e0.elapsed_time(e1) / reps)
+        h.sync()
+        c = 16 if prec == PMFEM_FP64 else 8             # bytes of a complex value
+        r = c // 2                                       # bytes of a spectrum value
+        nq, nx, ny, nf = N0 * N1 * N2, F0 * N1 * N2, F0 * F1 * N2, F0 * F1 * F2
+        passes = c * (nq + nx) * 2 + c * (nx + ny) * 2 + c * 2 * ny + r * nf
+        res[name] = {"ms_per_convolution": ms, "spectrum_setup_s": round(first_s - ms * 1e-3, 3),
+                     "bytes_per_convolution": passes, "achieved_gbs": passes / (ms * 1e-3) / 1e9,
+                     "finite": bool(torch.isfinite(torch.view_as_real(U)).all())}
+    h.destroy()
+    peak, kind = measured_peaks()
+    for v in res.values():
+        v["frac_hbm"] = v["achieved_gbs"] / peak
+        v["peak"] = f"{peak:.1f} GB/s ({kind})"
+    return {"workload": f"wire-1d-periodic-protruding-{args.nodes // 1000}k grid {N0}x{N1}x{N2}, FFT {F0}x{F1}x{F2}",
+            "k0_per_m": k0.tolist(), "fp32": res["fp32"], "fp64": res["fp64"], "reps": reps,
+            "oracle": "tests/test_gpu_bloch.py (spectrum and convolution against oracle/bloch.py)"}
+
+
 def surrogate_forward_timing(h, V, st, reps=50):
     """The network's forward pass on the 64^3 grid: CUDA events around `reps` calls (the whole
     forward), then a profiled pass with an event pair around each layer.  A 32 -> 32 layer is
@@ -1107,6 +1253,10 @@ def run_native(args):
         line["batch"] = batch_leg(args, dist, world)
     if not args.no_lattice:
         line["lattice"] = lattice_leg(args, dist, world)
+    if not args.no_local_terms:
+        line["local_terms"] = local_terms_leg(args, dist, world, mesh)
+    if not args.no_bloch:
+        line["bloch"] = bloch_leg(args, dist, world, mesh)
     if not args.no_surrogate:
         line["surrogate"] = surrogate_leg(args, dist, world)
     if rank == 0 and not args.no_cpu:
@@ -1128,7 +1278,7 @@ def run_only(args):
     import __graft_entry__
     __graft_entry__.build()
     legs = {"surrogate": surrogate_leg, "surrogate_fwd": surrogate_forward_leg, "batch": batch_leg,
-            "lattice": lattice_leg}
+            "lattice": lattice_leg, "local_terms": local_terms_leg, "bloch": bloch_leg}
     out = legs[args.only](args, dist, world)
     dist.close()
     if rank == 0:

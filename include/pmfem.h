@@ -294,8 +294,12 @@ int pmfem_llg_step_implicit(pmfem_t h, double dt, int nsteps, const pmfem_implic
  * pmfem_bloch_convolve: U~ = the convolution of Q~ with K~ on the node grid, Q and U device
  * dims[0] x dims[1] x dims[2] complex numbers (interleaved re, im) of the precision's type T,
  * x fastest; enqueued on stream.  The spectrum of the last k0 is kept on the device.
- * The transforms are separable discrete Fourier sums in FP64 accumulation (O(F) work per point
- * and axis).  EINVAL for k0 off the periodic axes or on the reciprocal lattice.
+ * The transforms are the radix-2 line transforms of BAIM step 2, complex to complex over the full
+ * FFT grid (the twisted kernel's spectrum is real but not even): FP64 for the spectrum, the
+ * precision's type T for the convolution, O(log F) work per point and axis.  The first call for
+ * a k0 (or after a precision change) sets up that spectrum and synchronises the device; later
+ * calls with the same k0 only enqueue the five passes.  EINVAL for k0 off the periodic axes or on
+ * the reciprocal lattice.
  */
 int pmfem_bloch_spectrum(pmfem_t h, const double* k0, double* out, double* max_imag);
 int pmfem_bloch_convolve(pmfem_t h, const double* k0, const void* Q, void* U, void* stream);

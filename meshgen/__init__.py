@@ -21,7 +21,7 @@ import numpy as np
 
 __all__ = [
     "Mesh", "kuhn_box", "film_cell", "cube_cell", "prism_cell", "sphere_lattice",
-    "wire_cell", "batch_cells", "granular_cell", "m_tilted", "m_random", "m_vortex", "m_uniform", "net_init",
+    "wire_cell", "batch_cells", "granular_cell", "voronoi_grains", "m_tilted", "m_random", "m_vortex", "m_uniform", "net_init",
 ]
 
 
@@ -164,6 +164,35 @@ def granular_cell(n=8, h=1e-9, grains=6, K1=-4.5e3, Ku=0.0, A=1.3e-11, A_iex=0.2
     u /= np.linalg.norm(u, axis=1, keepdims=True)
     gr = Grains(tg, axes, np.full(grains, float(K1)), np.full(grains, float(Ku)), u, A_tet)
     return mesh, gr
+
+
+def voronoi_grains(mesh: Mesh, grains: int, h: float, K1=-4.5e3, Ku=0.0, A=1.3e-11, A_iex=0.2e-11, layer=0.6,
+                   seed=0) -> Grains:
+    """Voronoi grains of seeded points over any mesh, periodic along its periodic axes: a
+    tetrahedron belongs to the grain of the seed nearest (with the seeds' periodic images) to its
+    centroid, and to the boundary layer (exchange stiffness A_iex) when the second-nearest seed is
+    less than layer * h farther away.  Crystal axes are seeded random rotations."""
+    from scipy.spatial import cKDTree
+    rng = np.random.default_rng(seed + 101)
+    lo, hi = mesh.xyz.min(axis=0), mesh.xyz.max(axis=0)
+    seeds = lo + rng.uniform(0, 1, size=(grains, 3)) * (hi - lo)
+    shifts = [np.zeros(3)]
+    for a in range(3):
+        if mesh.periods[a] > 0:
+            shifts = [s + d * mesh.periods[a] * np.eye(3)[a] for s in shifts for d in (-1, 0, 1)]
+    pts = np.concatenate([seeds + s for s in shifts])
+    owner = np.tile(np.arange(grains), len(shifts))
+    cen = mesh.xyz[mesh.tets].mean(axis=1)
+    dist, idx = cKDTree(pts).query(cen, k=2)
+    tg = owner[idx[:, 0]].astype(np.int32)
+    A_tet = np.where(dist[:, 1] - dist[:, 0] < layer * h, A_iex, A)
+    axes = np.empty((grains, 3, 3))
+    for g in range(grains):
+        q, r = np.linalg.qr(rng.normal(size=(3, 3)))
+        axes[g] = (q * np.sign(np.diag(r))[None, :]).T
+    u = rng.normal(size=(grains, 3))
+    u /= np.linalg.norm(u, axis=1, keepdims=True)
+    return Grains(tg, axes, np.full(grains, float(K1)), np.full(grains, float(Ku)), u, A_tet)
 
 
 def _fibonacci_sphere(n: int, R: float) -> np.ndarray:

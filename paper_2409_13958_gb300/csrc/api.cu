@@ -1096,8 +1096,7 @@ int pmfem_bloch_convolve(pmfem_t h, const double* k0, const void* Q, void* U, vo
       h->bloch_k0[2] != k0[2]) {
     if (!h->bloch_spec || h->bloch_prec != h->dev_prec) {
       if ((rc = dalloc(h, &h->bloch_spec, n * es))) return rc;
-      for (int i = 0; i < 3; ++i)
-        if ((rc = dalloc(h, &h->bloch_buf[i], n * 2 * es))) return rc;
+      if ((rc = dalloc(h, &h->bloch_buf[0], n * 2 * es))) return rc;
     }
     double* d = nullptr;
     PMFEM_CK(h, cudaMalloc(&d, n * sizeof(double)));
@@ -1120,12 +1119,13 @@ int pmfem_bloch_convolve(pmfem_t h, const double* k0, const void* Q, void* U, vo
     h->bloch_prec = h->dev_prec;
   }
   cudaStream_t st = stream ? (cudaStream_t)stream : h->stream;
-  if (f64)
-    bloch_convolve_device<double>(h->s, (const double*)h->bloch_spec, Q, U, h->bloch_buf[0], h->bloch_buf[1],
-                                  h->bloch_buf[2], st);
-  else
-    bloch_convolve_device<float>(h->s, (const float*)h->bloch_spec, Q, U, h->bloch_buf[0], h->bloch_buf[1],
-                                 h->bloch_buf[2], st);
+  if (f64) {
+    const void* tw[3] = {h->d64.tw[0], h->d64.tw[1], h->d64.tw[2]};
+    bloch_convolve_device<double>(h->s, (const double*)h->bloch_spec, Q, U, h->bloch_buf[0], tw, st);
+  } else {
+    const void* tw[3] = {h->d32.tw[0], h->d32.tw[1], h->d32.tw[2]};
+    bloch_convolve_device<float>(h->s, (const float*)h->bloch_spec, Q, U, h->bloch_buf[0], tw, st);
+  }
   return check_launch(h);
 }
 

@@ -5,8 +5,9 @@
 // With q~ = q e^{j k0.r} and K~(d) = G_k(d) e^{j k0.d}, which is periodic and Hermitian, the
 // quasi-periodic potential is e^{-j k0.r} times the circular convolution of q~ with K~ on the grid
 // of Eq. 16 (open axes zero-padded to 2N as for k0 = 0); the spectrum of a Hermitian kernel is
-// real.  The transforms here are separable discrete Fourier sums, O(F) per point and axis, in
-// FP64 accumulation: a direct path for this service, not the library's fast FFT.
+// real but, unlike the k0 = 0 spectrum, not even, so it is kept on the full FFT grid.  Both
+// transforms (the FP64 one of the kernel table and the convolution's, in the precision's type)
+// run the radix-2 line transforms of the k0 = 0 path in fft.cu, complex to complex.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -62,68 +63,6 @@ __global__ void k_bloch_table(sm::BlochParams P, GridDesc g, double r0re, double
   out[i] = make_double2(re * c - im * s, re * s + im * c);
 }
 
-template <typename C>
-__device__ __forceinline__ double re_of(const C& v) { return (double)v.x; }
-template <typename C>
-__device__ __forceinline__ double im_of(const C& v) { return (double)v.y; }
-
-// out[c, c_axis = k] = scale sum_d in[c, c_axis = d] e^{sign 2 pi i d k / F} over a shape S
-template <typename C>
-__global__ void k_dft_axis(const C* __restrict__ in, C* __restrict__ out, int S0, int S1, int S2, int axis, int sign,
-                           double scale) {
-  const int64_t n = (int64_t)S0 * S1 * S2;
-  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  int c[3] = {(int)(i % S0), (int)((i / S0) % S1), (int)(i / ((int64_t)S0 * S1))};
-  const int F = axis == 0 ? S0 : axis == 1 ? S1 : S2;
-  const int k = c[axis];
-  const int64_t st = axis == 0 ? 1 : axis == 1 ? S0 : (int64_t)S0 * S1;
-  c[axis] = 0;
-  const int64_t base = c[0] + (int64_t)S0 * (c[1] + (int64_t)S1 * c[2]);
-  double ar = 0, ai = 0;
-  for (int d = 0; d < F; ++d) {
-    double s, co;
-    sincospi(2.0 * (double)(((int64_t)d * k) % F) / F, &s, &co);
-    s *= sign;
-    const C v = in[base + d * st];
-    ar += re_of(v) * co - im_of(v) * s;
-    ai += re_of(v) * s + im_of(v) * co;
-  }
-  using E = decltype(out[0].x);
-  out[i].x = (E)(scale * ar);
-  out[i].y = (E)(scale * ai);
-}
-
-template <typename C>
-__global__ void k_pad(const C* __restrict__ Q, C* __restrict__ buf, GridDesc g) {
-  const int64_t n = (int64_t)g.fft[0] * g.fft[1] * g.fft[2];
-  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  const int jx = (int)(i % g.fft[0]), jy = (int)((i / g.fft[0]) % g.fft[1]), jz = (int)(i / ((int64_t)g.fft[0] * g.fft[1]));
-  C v;
-  v.x = 0;
-  v.y = 0;
-  if (jx < g.dims[0] && jy < g.dims[1] && jz < g.dims[2]) v = Q[jx + (int64_t)g.dims[0] * (jy + (int64_t)g.dims[1] * jz)];
-  buf[i] = v;
-}
-
-template <typename C, typename T>
-__global__ void k_mul_real(C* __restrict__ buf, const T* __restrict__ spec, int64_t n) {
-  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  buf[i].x *= spec[i];
-  buf[i].y *= spec[i];
-}
-
-template <typename C>
-__global__ void k_crop(const C* __restrict__ buf, C* __restrict__ U, GridDesc g) {
-  const int64_t n = (int64_t)g.dims[0] * g.dims[1] * g.dims[2];
-  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  const int x = (int)(i % g.dims[0]), y = (int)((i / g.dims[0]) % g.dims[1]), z = (int)(i / ((int64_t)g.dims[0] * g.dims[1]));
-  U[i] = buf[x + (int64_t)g.fft[0] * (y + (int64_t)g.fft[1] * z)];
-}
-
 __global__ void k_real_part(const double2* __restrict__ in, double* __restrict__ re, double* __restrict__ im_abs,
                             int64_t n) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -141,15 +80,6 @@ GridDesc desc(const Setup& s) {
     g.delta[a] = s.delta[a];
   }
   return g;
-}
-
-template <typename C>
-void dft3(const C* in, C* tmp, C* out, const GridDesc& g, int sign, double scale, cudaStream_t st) {
-  const int64_t n = (int64_t)g.fft[0] * g.fft[1] * g.fft[2];
-  k_dft_axis<C><<<nblk(n), kB, 0, st>>>(in, tmp, g.fft[0], g.fft[1], g.fft[2], 0, sign, 1.0);
-  k_dft_axis<C><<<nblk(n), kB, 0, st>>>(tmp, out, g.fft[0], g.fft[1], g.fft[2], 1, sign, 1.0);
-  k_dft_axis<C><<<nblk(n), kB, 0, st>>>(out, tmp, g.fft[0], g.fft[1], g.fft[2], 2, sign, scale);
-  cudaMemcpyAsync(out, tmp, n * sizeof(C), cudaMemcpyDeviceToDevice, st);
 }
 
 }  // namespace
@@ -251,21 +181,26 @@ int bloch_spectrum_device(const Setup& s, const double k0[3], double* spec_dev, 
   const GridDesc g = desc(s);
   const int64_t n = (int64_t)g.fft[0] * g.fft[1] * g.fft[2];
   double* dkv = nullptr;
-  double2 *a = nullptr, *b = nullptr, *c = nullptr;
+  double2* a = nullptr;
   double* im = nullptr;
+  double2* tw[3] = {nullptr, nullptr, nullptr};
   auto cleanup = [&]() {
     cudaFree(dkv);
     cudaFree(a);
-    cudaFree(b);
-    cudaFree(c);
     cudaFree(im);
+    for (double2* t : tw) cudaFree(t);
   };
   cudaError_t e = cudaMalloc(&dkv, std::max<size_t>(kv.size(), 4) * sizeof(double));
   if (e == cudaSuccess) e = cudaMalloc(&a, n * sizeof(double2));
-  if (e == cudaSuccess) e = cudaMalloc(&b, n * sizeof(double2));
-  if (e == cudaSuccess) e = cudaMalloc(&c, n * sizeof(double2));
   if (e == cudaSuccess) e = cudaMalloc(&im, n * sizeof(double));
   if (e == cudaSuccess && !kv.empty()) e = cudaMemcpy(dkv, kv.data(), kv.size() * sizeof(double), cudaMemcpyHostToDevice);
+  for (int ax = 0; ax < 3 && e == cudaSuccess; ++ax) {   // exp(-2 pi i j / F) in FP64
+    const int F = g.fft[ax];
+    std::vector<double2> t(F);
+    for (int j = 0; j < F; ++j) t[j] = make_double2(std::cos(2.0 * kPi * j / F), -std::sin(2.0 * kPi * j / F));
+    e = cudaMalloc(&tw[ax], F * sizeof(double2));
+    if (e == cudaSuccess) e = cudaMemcpy(tw[ax], t.data(), F * sizeof(double2), cudaMemcpyHostToDevice);
+  }
   if (e != cudaSuccess) {
     cleanup();
     err = {ECUDA_, std::string("Bloch spectrum: ") + cudaGetErrorString(e)};
@@ -282,8 +217,9 @@ int bloch_spectrum_device(const Setup& s, const double k0[3], double* spec_dev, 
     r0re -= 2 * P.eta / std::sqrt(kPi);
   }
   k_bloch_table<<<nblk(n), kB>>>(P, g, r0re, r0im, a);
-  dft3<double2>(a, b, c, g, -1, 1.0, 0);
-  k_real_part<<<nblk(n), kB>>>(c, spec_dev, im, n);
+  const double2* twc[3] = {tw[0], tw[1], tw[2]};
+  launch_fft3_forward_f64(a, g.fft, twc, 0);
+  k_real_part<<<nblk(n), kB>>>(a, spec_dev, im, n);
   e = cudaGetLastError();
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
   double mi = 0;
@@ -302,25 +238,17 @@ int bloch_spectrum_device(const Setup& s, const double k0[3], double* spec_dev, 
 }
 
 template <typename T>
-void bloch_convolve_device(const Setup& s, const T* spec, const void* Q, void* U, void* buf_a, void* buf_b,
-                           void* buf_c, cudaStream_t st) {
+void bloch_convolve_device(const Setup& s, const T* spec, const void* Q, void* U, void* buf,
+                           const void* const tw[3], cudaStream_t st) {
   using C = typename std::conditional<sizeof(T) == 8, double2, float2>::type;
   const GridDesc g = desc(s);
-  const int64_t n = (int64_t)g.fft[0] * g.fft[1] * g.fft[2];
-  const int64_t nn = (int64_t)g.dims[0] * g.dims[1] * g.dims[2];
-  C* a = (C*)buf_a;
-  C* b = (C*)buf_b;
-  C* c = (C*)buf_c;
-  k_pad<C><<<nblk(n), kB, 0, st>>>((const C*)Q, a, g);
-  dft3<C>(a, b, c, g, -1, 1.0, st);
-  k_mul_real<C, T><<<nblk(n), kB, 0, st>>>(c, spec, n);
-  dft3<C>(c, b, a, g, +1, 1.0 / (double)n, st);
-  k_crop<C><<<nblk(nn), kB, 0, st>>>(a, (C*)U, g);
+  const C* twc[3] = {(const C*)tw[0], (const C*)tw[1], (const C*)tw[2]};
+  launch_bloch_fft_conv<T, C>((const C*)Q, (C*)U, (C*)buf, spec, g.dims, g.fft, twc, st);
 }
 
-template void bloch_convolve_device<double>(const Setup&, const double*, const void*, void*, void*, void*, void*,
-                                            cudaStream_t);
-template void bloch_convolve_device<float>(const Setup&, const float*, const void*, void*, void*, void*, void*,
-                                           cudaStream_t);
+template void bloch_convolve_device<double>(const Setup&, const double*, const void*, void*, void*,
+                                            const void* const*, cudaStream_t);
+template void bloch_convolve_device<float>(const Setup&, const float*, const void*, void*, void*,
+                                           const void* const*, cudaStream_t);
 
 }  // namespace pmfem

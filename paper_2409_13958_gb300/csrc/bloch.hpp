@@ -18,9 +18,20 @@ int bloch_params(const Setup& s, const double k0[3], sm::BlochParams& P, std::ve
 // unscaled) and the largest |imaginary part| of the transform (zero up to rounding)
 int bloch_spectrum_device(const Setup& s, const double k0[3], double* spec_dev, double* max_imag, Error& err);
 // U~ = IFFT(spec FFT(pad(Q~))) cropped to the node grid; Q, U complex interleaved N0 N1 N2 of T;
-// buf_a/b/c complex scratch of F0 F1 F2 elements each
+// buf complex scratch of F0 F1 F2 elements; tw[a] = exp(-2 pi i j / F_a) in T (the handle's tables)
 template <typename T>
-void bloch_convolve_device(const Setup& s, const T* spec, const void* Q, void* U, void* buf_a, void* buf_b,
-                           void* buf_c, cudaStream_t st);
+void bloch_convolve_device(const Setup& s, const T* spec, const void* Q, void* U, void* buf,
+                           const void* const tw[3], cudaStream_t st);
+
+// fft.cu: BAIM step 2 for the twisted kernel with the line transforms of the k0 = 0 path, complex
+// to complex over the full FFT grid (five passes: x forward on the populated rows, y forward on
+// the populated planes, z forward + multiply by the full real spectrum + z inverse, y inverse, x
+// inverse scaled by 1 / (F0 F1 F2)); Q, U complex N0 N1 N2 (x fastest), cb complex scratch of
+// F0 F1 F2 elements (never cleared: zero inputs are not read), spec F0 F1 F2 (x fastest, unscaled)
+template <typename T, typename C2>
+void launch_bloch_fft_conv(const C2* Q, C2* U, C2* cb, const T* spec, const int dims[3], const int fft[3],
+                           const C2* const tw[3], cudaStream_t st);
+// fft.cu: in-place forward transform of a complex F0 F1 F2 grid (x fastest) in FP64
+void launch_fft3_forward_f64(double2* buf, const int fft[3], const double2* const tw[3], cudaStream_t st);
 
 }  // namespace pmfem

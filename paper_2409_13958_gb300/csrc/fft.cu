@@ -20,6 +20,7 @@
 #include <set>
 #include <utility>
 
+#include "bloch.hpp"
 #include "device.hpp"
 
 namespace pmfem {
@@ -292,7 +293,9 @@ __global__ void PMFEM_FFT_Y_LB(LB * Fac<F>::R2) k_fft_y(C2* __restrict__ cb, int
 }
 
 // ---------------------------------------------------------------- pass 3: z convolution
-template <typename T, typename C2, int F, int LB>
+// FULL: the spectrum is the full F0 x F1 x F2 grid (x fastest, Hx = F0 columns), as for the
+// twisted Bloch kernel, which is real but not even; otherwise the PGF spectrum reduced by symmetry.
+template <typename T, typename C2, int F, int LB, bool FULL = false>
 __global__ void PMFEM_FFT_Z_LB(LB * Fac<F>::R2) k_fft_z_conv(C2* __restrict__ cb, int Hx, int F1, int N2,
                                                               const T* __restrict__ ghat, const C2* __restrict__ tw,
                                                               const int64_t* __restrict__ boff) {
@@ -308,24 +311,24 @@ __global__ void PMFEM_FFT_Z_LB(LB * Fac<F>::R2) k_fft_z_conv(C2* __restrict__ cb
   thread_line<true, LB, FF::R2>(l, j);
   int kx, ky;
   bool ok;
-  strided_line<true>(Hx, LB, F1, l, kx, ky, ok);
+  strided_line<!FULL>(Hx, LB, F1, l, kx, ky, ok);
   if (!ok) kx = 0, ky = 0;
   const int64_t zs = (int64_t)Hx * F1;
   C2* col = cb + (int64_t)Hx * ky + kx;
   auto ld = [&](int, int idx) -> C2 { return (ok && idx < N2) ? col[zs * idx] : C2{0, 0}; };
   C2 X[FF::IPT][FF::R2];
   line_forward<F, LB, true>(S, tw, ld, l, j, X);
-  // spectral multiply by the real, even PGF spectrum (reduced by symmetry in every axis)
+  // spectral multiply by the real PGF spectrum (reduced by symmetry in every axis unless FULL)
   const int H1 = F1 / 2 + 1;
-  const int iy = ky <= F1 - ky ? ky : F1 - ky;
+  const int iy = FULL ? ky : (ky <= F1 - ky ? ky : F1 - ky);
   const T* g = ghat + (ok ? kx : 0) + (int64_t)Hx * iy;
-  const int64_t gs = (int64_t)Hx * H1;
+  const int64_t gs = (int64_t)Hx * (FULL ? F1 : H1);
 #pragma unroll
   for (int i = 0; i < FF::IPT; ++i)
 #pragma unroll
     for (int k2 = 0; k2 < FF::R2; ++k2) {
       const int kz = j + FF::R2 * i + FF::R1 * k2;
-      const int iz = kz <= F - kz ? kz : F - kz;
+      const int iz = FULL ? kz : (kz <= F - kz ? kz : F - kz);
       const T gv = ok ? __ldg(&g[gs * iz]) : T(0);
       X[i][k2].x *= gv;
       X[i][k2].y *= gv;
@@ -379,6 +382,55 @@ __global__ void __launch_bounds__(LB * Fac<F>::R2) k_fft_x_inv(const C2* __restr
     if (ok && idx < N0) out[idx] = v.x;
   };
   line_inverse<F, LB, false>(S, tw, st, l, j, X);
+}
+
+// ---------------------------------------------------------------- complex x lines
+// Lines along x of a complex grid (the Bloch convolution and the FP64 transform of its kernel
+// table): line L = y + ny z reads src[ss_y y + ss_z z + idx] for idx < n_in (zero beyond) and
+// writes dst[ds_y y + ds_z z + k] for k < n_out, times scale; forward, or inverse (INV).  src may
+// be dst when the strides agree: a line is read whole before any of it is written.
+template <typename C2, int F, int LB, bool INV>
+__global__ void __launch_bounds__(LB * Fac<F>::R2) k_cfft_x(const C2* src, C2* dst, int ny, int nz, int64_t ss_y,
+                                                          int64_t ss_z, int64_t ds_y, int64_t ds_z, int n_in,
+                                                          int n_out, double scale, const C2* __restrict__ tw) {
+  using FF = Fac<F>;
+  using E = decltype(C2::x);
+  pdl_enter();
+  extern __shared__ unsigned char smem_raw[];
+  C2* S = reinterpret_cast<C2*>(smem_raw);
+  int l, j;
+  thread_line<false, LB, FF::R2>(l, j);
+  const int64_t L = (int64_t)blockIdx.x * LB + l;
+  const bool ok = L < (int64_t)ny * nz;
+  const int64_t yy = ok ? L % ny : 0, zz = ok ? L / ny : 0;
+  const C2* in = src + ss_y * yy + ss_z * zz;
+  C2* out = dst + ds_y * yy + ds_z * zz;
+  const E sc = (E)scale;
+  C2 X[FF::IPT][FF::R2];
+  if (!INV) {
+    auto ld = [&](int, int idx) -> C2 { return (ok && idx < n_in) ? in[idx] : C2{0, 0}; };
+    line_forward<F, LB, false>(S, tw, ld, l, j, X);
+    if (!ok) return;
+#pragma unroll
+    for (int i = 0; i < FF::IPT; ++i)
+#pragma unroll
+      for (int k2 = 0; k2 < FF::R2; ++k2) {
+        const int k = j + FF::R2 * i + FF::R1 * k2;
+        if (k < n_out) out[k] = C2{X[i][k2].x * sc, X[i][k2].y * sc};
+      }
+  } else {
+#pragma unroll
+    for (int i = 0; i < FF::IPT; ++i)
+#pragma unroll
+      for (int k2 = 0; k2 < FF::R2; ++k2) {
+        const int k = j + FF::R2 * i + FF::R1 * k2;
+        X[i][k2] = (ok && k < n_in) ? in[k] : C2{0, 0};
+      }
+    auto st = [&](int, int idx, C2 v) {
+      if (ok && idx < n_out) out[idx] = C2{v.x * sc, v.y * sc};
+    };
+    line_inverse<F, LB, false>(S, tw, st, l, j, X);
+  }
 }
 
 // Line counts per block (measured on the 256^3 transform of the 1M-node wire): the y passes
@@ -435,6 +487,45 @@ struct Passes {
       launch_k(k_fft_y<C2, F, LBS, true>, dim3(nb, d.count), LBS * FF::R2, sm, st, d.cbuf, Hx, F, d.dims[1], d.tw[1],
                                                                               d.boff, d.dims[2]);
     }
+  }
+  // complex lines along x (k_cfft_x)
+  static void cx(const C2* src, C2* dst, int ny, int nz, int64_t ssy, int64_t ssz, int64_t dsy, int64_t dsz, int n_in,
+                 int n_out, double scale, bool inv, const C2* tw, cudaStream_t st) {
+    const int64_t nl = (int64_t)ny * nz;
+    const dim3 grid((unsigned)((nl + LBX - 1) / LBX));
+    const size_t sm = smem(LBX);
+    if (!inv) {
+      set_smem(k_cfft_x<C2, F, LBX, false>, sm);
+      launch_k(k_cfft_x<C2, F, LBX, false>, grid, LBX * FF::R2, sm, st, src, dst, ny, nz, ssy, ssz, dsy, dsz, n_in,
+               n_out, scale, tw);
+    } else {
+      set_smem(k_cfft_x<C2, F, LBX, true>, sm);
+      launch_k(k_cfft_x<C2, F, LBX, true>, grid, LBX * FF::R2, sm, st, src, dst, ny, nz, ssy, ssz, dsy, dsz, n_in,
+               n_out, scale, tw);
+    }
+  }
+  // strided lines of length F over Hx adjacent columns in each of nz planes (plane stride Hx F):
+  // the y pass of a complex grid, or the z pass of a whole grid as Hx = F0 F1, nz = 1
+  static void cy(C2* cb, int Hx, int n_in, int n_out, int nz, bool inv, const C2* tw, cudaStream_t st) {
+    const unsigned nb = strided_blocks<false>(Hx, LBS, nz);
+    const size_t sm = smem(LBS);
+    if (!inv) {
+      set_smem(k_fft_y<C2, F, LBS, false>, sm);
+      launch_k(k_fft_y<C2, F, LBS, false>, dim3(nb), LBS * FF::R2, sm, st, cb, Hx, n_in, n_out, tw,
+               (const int64_t*)nullptr, nz);
+    } else {
+      set_smem(k_fft_y<C2, F, LBS, true>, sm);
+      launch_k(k_fft_y<C2, F, LBS, true>, dim3(nb), LBS * FF::R2, sm, st, cb, Hx, n_in, n_out, tw,
+               (const int64_t*)nullptr, nz);
+    }
+  }
+  // z forward, multiply by the full real spectrum, z inverse, on the Hx = F0 columns of F1 rows
+  static void cz_conv(C2* cb, int F0, int F1, int N2, const T* spec, const C2* tw, cudaStream_t st) {
+    const unsigned nb = strided_blocks<false>(F0, LBZ, F1);
+    const size_t sm = smem(LBZ);
+    set_smem(k_fft_z_conv<T, C2, F, LBZ, true>, sm);
+    launch_k(k_fft_z_conv<T, C2, F, LBZ, true>, dim3(nb), LBZ * FF::R2, sm, st, cb, F0, F1, N2, spec, tw,
+             (const int64_t*)nullptr);
   }
   static void z(const FftArgs<T>& d, cudaStream_t st) {
     const int Hx = d.fft[0] / 2 + 1;
@@ -494,6 +585,38 @@ void launch_fft_conv(const DevOps<T>& d, cudaStream_t st) {
   launch_fft(a, d.prof, st);
 }
 
+template <typename T, typename C2>
+void launch_bloch_fft_conv(const C2* Q, C2* U, C2* cb, const T* spec, const int dims[3], const int fft[3],
+                           const C2* const tw[3], cudaStream_t st) {
+  const int N0 = dims[0], N1 = dims[1], N2 = dims[2];
+  const int F0 = fft[0], F1 = fft[1], F2 = fft[2];
+  const int64_t row = F0, plane = (int64_t)F0 * F1;
+  // 1. x forward on the populated rows (y < N1, z < N2), inputs beyond N0 zero
+  PMFEM_FFT_DISPATCH(F0, cx(Q, cb, N1, N2, N0, (int64_t)N0 * N1, row, plane, N0, F0, 1.0, false, tw[0], st));
+  // 2. y forward on the populated planes (inputs beyond N1 zero)
+  PMFEM_FFT_DISPATCH(F1, cy(cb, F0, N1, F1, N2, false, tw[1], st));
+  // 3. z forward (inputs beyond N2 zero), times the spectrum, z inverse, keep z < N2
+  PMFEM_FFT_DISPATCH(F2, cz_conv(cb, F0, F1, N2, spec, tw[2], st));
+  // 4. y inverse on the kept planes, keep y < N1
+  PMFEM_FFT_DISPATCH(F1, cy(cb, F0, F1, N1, N2, true, tw[1], st));
+  // 5. x inverse on the kept rows, keep x < N0, scaled by 1 / (F0 F1 F2)
+  PMFEM_FFT_DISPATCH(F0, cx(cb, U, N1, N2, row, plane, N0, (int64_t)N0 * N1, F0, N0,
+                            1.0 / ((double)F0 * F1 * F2), true, tw[0], st));
+}
+
+void launch_fft3_forward_f64(double2* buf, const int fft[3], const double2* const tw[3], cudaStream_t st) {
+  using T = double;
+  const int F0 = fft[0], F1 = fft[1], F2 = fft[2];
+  const int64_t plane = (int64_t)F0 * F1;
+  PMFEM_FFT_DISPATCH(F0, cx(buf, buf, F1, F2, F0, plane, F0, plane, F0, F0, 1.0, false, tw[0], st));
+  PMFEM_FFT_DISPATCH(F1, cy(buf, F0, F1, F1, F2, false, tw[1], st));
+  PMFEM_FFT_DISPATCH(F2, cy(buf, F0 * F1, F2, F2, 1, false, tw[2], st));
+}
+
+template void launch_bloch_fft_conv<double, double2>(const double2*, double2*, double2*, const double*, const int*,
+                                                     const int*, const double2* const*, cudaStream_t);
+template void launch_bloch_fft_conv<float, float2>(const float2*, float2*, float2*, const float*, const int*,
+                                                   const int*, const float2* const*, cudaStream_t);
 template void launch_fft_conv<double>(const DevOps<double>&, cudaStream_t);
 template void launch_fft_conv<float>(const DevOps<float>&, cudaStream_t);
 template void launch_fft<float>(const FftArgs<float>&, const ProfHook&, cudaStream_t);

@@ -1,6 +1,7 @@
 """Bloch-phase PGF on the GPU (pmfem_bloch_spectrum, pmfem_bloch_convolve) against the oracle
 (oracle/bloch.py): the FP64 spectrum of the twisted grid kernel, and the grid convolution of
-quasi-periodic sources in FP64 (1e-11) and FP32 (1e-5), on 1D-, 2D- and 3D-periodic cells."""
+quasi-periodic sources in FP64 (1e-11) and FP32 (1e-5), on 1D-, 2D- and 3D-periodic cells, with
+FFT lengths from 8 to 256."""
 import math
 
 import numpy as np
@@ -30,7 +31,25 @@ def _cube():
     return c, (8, 8, 8), np.array([0.1, 0.25, -0.4]) * 2 * math.pi / L
 
 
-CASES = {"prism_1d": _prism, "film_2d": _film, "cube_3d": _cube}
+def _prism_long():
+    p = meshgen.prism_cell(4, 4, 32, jitter=0.15, seed=6)
+    return p, (8, 8, 256), np.array([0.0, 0.0, -0.29 * 2 * math.pi / p.periods[2]])
+
+
+def _prism_wide():
+    p = meshgen.prism_cell(8, 8, 16, jitter=0.15, seed=5)
+    return p, (32, 32, 64), np.array([0.0, 0.0, 0.37 * 2 * math.pi / p.periods[2]])
+
+
+def _film_wide():
+    f = meshgen.film_cell(12, 10, 3, seed=4)
+    return f, (64, 64, 16), np.array([0.21 * 2 * math.pi / f.periods[0], -0.33 * 2 * math.pi / f.periods[1], 0.0])
+
+
+# the small cells, and grids of 16-256 points per axis (FFT lengths 16 to 256: every two-factor
+# shape of the line transform from 4 x 4 to 16 x 16, several blocks per pass)
+CASES = {"prism_1d": _prism, "film_2d": _film, "cube_3d": _cube, "prism_1d_long": _prism_long,
+         "prism_1d_wide": _prism_wide, "film_2d_wide": _film_wide}
 
 
 @pytest.fixture(scope="module", autouse=True)
