@@ -471,10 +471,47 @@ __device__ __forceinline__ T stencil_row(int64_t i, const int32_t* __restrict__ 
   lagrange<T, P>(frac[3 * i + 1], w1);
   lagrange<T, P>(frac[3 * i + 2], w2);
   const int b0 = base[3 * i], b1 = base[3 * i + 1], b2 = base[3 * i + 2];
+  T acc = 0;
+  if constexpr (sizeof(T) == 4) {
+    // FP32 grid, x taps inside one row (no periodic wrap along x): each row's P taps come from
+    // the 16-byte-aligned chunks that hold them (one or two loads instead of P), weighted by the
+    // x weights shifted to the taps' offset o within the first chunk.  A chunk is loaded only if
+    // it holds a tap, so with N0 a multiple of 4 no load leaves the row.
+    if (b0 >= 0 && b0 + P <= N0 && (N0 & 3) == 0) {
+      constexpr int NCH = (P + 6) / 4;    // chunks that can hold taps o .. o + P - 1 for o < 4
+      const int o = b0 & 3;
+      const int nch = (o + P + 3) >> 2;   // chunks that do
+      T ws[4 * NCH];
+#pragma unroll
+      for (int k = 0; k < 4 * NCH; ++k) {
+        T v = 0;
+#pragma unroll
+        for (int a = 0; a < P; ++a) v = (k == o + a) ? w0[a] : v;
+        ws[k] = v;
+      }
+#pragma unroll
+      for (int c = 0; c < P; ++c) {
+        const int64_t zo = (int64_t)N1 * wrap(b2 + c, N2, p2);
+#pragma unroll
+        for (int b = 0; b < P; ++b) {
+          const float4* rowp = reinterpret_cast<const float4*>(U + (int64_t)N0 * (wrap(b1 + b, N1, p1) + zo) + (b0 - o));
+          T s = 0;
+#pragma unroll
+          for (int h = 0; h < NCH; ++h) {
+            if (h == 0 || h < nch) {
+              const float4 v = __ldg(rowp + h);
+              s += ws[4 * h] * v.x + ws[4 * h + 1] * v.y + ws[4 * h + 2] * v.z + ws[4 * h + 3] * v.w;
+            }
+          }
+          acc += w2[c] * w1[b] * s;
+        }
+      }
+      return acc;
+    }
+  }
   int ix[P];
 #pragma unroll
   for (int a = 0; a < P; ++a) ix[a] = wrap(b0 + a, N0, p0);
-  T acc = 0;
 #pragma unroll
   for (int c = 0; c < P; ++c) {
     const int64_t zo = (int64_t)N1 * wrap(b2 + c, N2, p2);
