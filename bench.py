@@ -741,6 +741,17 @@ def local_terms_leg(args, dist, world, mesh=None, grains=64):
             "oracle": "tests/test_gpu_local_terms.py (granular cell against oracle/local_terms.py)"}
 
 
+def bloch_pass_bytes(dims, fft, s: int) -> int:
+    """Bytes of one Bloch convolution's five passes with s-byte reals: x forward reads the N0 N1 N2
+    complex sources and writes F0 N1 N2 values, y forward reads those and writes F0 F1 N2, the z
+    pass reads and writes F0 F1 N2 and reads the F0 F1 F2 real spectrum, then the inverse y and x
+    passes mirror the forward ones."""
+    (N0, N1, N2), (F0, F1, F2) = dims, fft
+    c = 2 * s
+    nq, nx, ny, nf = N0 * N1 * N2, F0 * N1 * N2, F0 * F1 * N2, F0 * F1 * F2
+    return c * (nq + nx) * 2 + c * (nx + ny) * 2 + c * 2 * ny + s * nf
+
+
 def bloch_leg(args, dist, world, mesh=None, reps=20):
     """BAIM step 2 with the Bloch-phase PGF (k0 = 0.3 2 pi / L along the wire's axis) on the
     benchmark wire's grid, FP32 and FP64: the set-up of the twisted kernel's spectrum (Ewald sums
@@ -781,10 +792,7 @@ def bloch_leg(args, dist, world, mesh=None, reps=20):
         e1.synchronize()
         ms = dist.max(e0.elapsed_time(e1) / reps)
         h.sync()
-        c = 16 if prec == PMFEM_FP64 else 8             # bytes of a complex value
-        r = c // 2                                       # bytes of a spectrum value
-        nq, nx, ny, nf = N0 * N1 * N2, F0 * N1 * N2, F0 * F1 * N2, F0 * F1 * F2
-        passes = c * (nq + nx) * 2 + c * (nx + ny) * 2 + c * 2 * ny + r * nf
+        passes = bloch_pass_bytes((N0, N1, N2), (F0, F1, F2), 8 if prec == PMFEM_FP64 else 4)
         res[name] = {"ms_per_convolution": ms, "spectrum_setup_s": round(first_s - ms * 1e-3, 3),
                      "bytes_per_convolution": passes, "achieved_gbs": passes / (ms * 1e-3) / 1e9,
                      "finite": bool(torch.isfinite(torch.view_as_real(U)).all())}

@@ -142,7 +142,7 @@ def granular_cell(n=8, h=1e-9, grains=6, K1=-4.5e3, Ku=0.0, A=1.3e-11, A_iex=0.2
 
     A tetrahedron belongs to the grain of the seed nearest (periodically) to its centroid; it is
     in the boundary layer, with exchange stiffness A_iex, when the second-nearest seed is less
-    than layer * h farther away than the nearest.  Crystal axes are seeded random rotations.
+    than layer * h farther away than the nearest.  Crystal axes are seeded random orthonormal frames.
     Returns (Mesh, Grains)."""
     mesh = cube_cell(n, h=h, jitter=jitter, seed=seed)
     L = n * h
@@ -171,7 +171,7 @@ def voronoi_grains(mesh: Mesh, grains: int, h: float, K1=-4.5e3, Ku=0.0, A=1.3e-
     """Voronoi grains of seeded points over any mesh, periodic along its periodic axes: a
     tetrahedron belongs to the grain of the seed nearest (with the seeds' periodic images) to its
     centroid, and to the boundary layer (exchange stiffness A_iex) when the second-nearest seed is
-    less than layer * h farther away.  Crystal axes are seeded random rotations."""
+    less than layer * h farther away.  Crystal axes are seeded random orthonormal frames."""
     from scipy.spatial import cKDTree
     rng = np.random.default_rng(seed + 101)
     lo, hi = mesh.xyz.min(axis=0), mesh.xyz.max(axis=0)

@@ -31,3 +31,14 @@ def test_field_pass_reads_m_and_u_as_one_vector():
     Np, na = sz["Np"], sz["dev"]["adjacency"]["entries"]
     # row length + gradient and exchange values with deltas + (m, u) 4-vectors + RK4 stage state
     assert bench.alg_bytes("gradient_exchange", 4, sz) == 4 * Np + na * (2 + 16) + 16 * Np + 3.5 * 16 * Np
+
+
+def test_bloch_pass_bytes_count_each_pass_once():
+    # wire grid 128 x 128 x 256 with FFT 256^3: x passes 2 x (4.19M + 8.39M) complex values,
+    # y passes 2 x (8.39M + 16.8M), z pass 2 x 16.8M complex and the 16.8M-value real spectrum
+    n = bench.bloch_pass_bytes((128, 128, 256), (256, 256, 256), 4)
+    assert n == 939_524_096
+    assert bench.bloch_pass_bytes((128, 128, 256), (256, 256, 256), 8) == 2 * n
+    # a fully periodic grid (no padding): each of the five passes reads and writes the whole grid
+    # once (8 B per complex value), and the z pass reads the spectrum (4 B per point)
+    assert bench.bloch_pass_bytes((8, 8, 8), (8, 8, 8), 4) == 512 * (5 * 2 * 8 + 4)
