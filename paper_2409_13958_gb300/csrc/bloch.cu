@@ -41,26 +41,76 @@ __device__ __forceinline__ bool offset_of(const GridDesc& g, int a, int j, int* 
   return true;
 }
 
-__global__ void k_bloch_table(sm::BlochParams P, GridDesc g, double r0re, double r0im, double2* __restrict__ out) {
+// Spectral amplitudes that do not depend on the position along the periodic axes, tabulated once
+// per spectrum: in 1D per (term q, transverse offset t = jb + F_b jc over the two open axes
+// b = ax[1], c = ax[2]); in 2D per (q, open-axis index t = jc, c = ax[2]).  amp[q nt + t]; zero
+// where the open-axis layout holds no offset.
+__global__ void k_bloch_amp(sm::BlochParams P, GridDesc g, int nt, double* __restrict__ amp) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= (int64_t)P.nk * nt) return;
+  const int q = (int)(i / nt), t = (int)(i % nt);
+  double r[3] = {0.0, 0.0, 0.0};
+  if (P.dim == 1) {
+    const int b = P.ax[1], c = P.ax[2];
+    int db, dc;
+    if (!offset_of(g, b, t % g.fft[b], &db) || !offset_of(g, c, t / g.fft[b], &dc)) {
+      amp[i] = 0.0;
+      return;
+    }
+    r[b] = db * g.delta[b];
+    r[c] = dc * g.delta[c];
+  } else {
+    const int c = P.ax[2];
+    int dc;
+    if (!offset_of(g, c, t, &dc)) {
+      amp[i] = 0.0;
+      return;
+    }
+    r[c] = dc * g.delta[c];
+  }
+  amp[i] = sm::bloch_term_amp(P, q, r[0], r[1], r[2]);
+}
+
+// The twisted kernel K~(d) = G_k(d) e^{j k0.d} at every FFT-grid offset.  K~(-d) is the conjugate
+// of K~(d), and the offset of index j along an axis is minus that of F - j (mod F), so the thread
+// of the smaller of two mirrored linear indices computes both; self-mirrored indices compute
+// themselves.  amp: the tabulated amplitudes (1D, 2D) or null (3D: the coefficients themselves).
+__global__ void k_bloch_table(sm::BlochParams P, GridDesc g, double r0re, double r0im, const double* __restrict__ amp,
+                              int nt, double2* __restrict__ out) {
   const int64_t n = (int64_t)g.fft[0] * g.fft[1] * g.fft[2];
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= n) return;
-  const int jx = (int)(i % g.fft[0]), jy = (int)((i / g.fft[0]) % g.fft[1]), jz = (int)(i / ((int64_t)g.fft[0] * g.fft[1]));
+  const int j[3] = {(int)(i % g.fft[0]), (int)((i / g.fft[0]) % g.fft[1]), (int)(i / ((int64_t)g.fft[0] * g.fft[1]))};
+  int mj[3];
+  for (int a = 0; a < 3; ++a) mj[a] = j[a] ? g.fft[a] - j[a] : 0;
+  const int64_t im = mj[0] + (int64_t)g.fft[0] * (mj[1] + (int64_t)g.fft[1] * mj[2]);
+  if (im < i) return;
   int dx, dy, dz;
-  if (!offset_of(g, 0, jx, &dx) || !offset_of(g, 1, jy, &dy) || !offset_of(g, 2, jz, &dz)) {
-    out[i] = make_double2(0.0, 0.0);
-    return;
+  double2 v = make_double2(0.0, 0.0);
+  if (!offset_of(g, 0, j[0], &dx) || !offset_of(g, 1, j[1], &dy) || !offset_of(g, 2, j[2], &dz)) {
+    // no offset here, nor at the mirror
+  } else if (!dx && !dy && !dz) {
+    v = make_double2(r0re, r0im);
+  } else {
+    const double x = dx * g.delta[0], y = dy * g.delta[1], z = dz * g.delta[2];
+    double re, imv;
+    sm::bloch_real_part(P, x, y, z, false, &re, &imv);
+    int t = 0;
+    if (P.dim == 1) t = j[P.ax[1]] + g.fft[P.ax[1]] * j[P.ax[2]];
+    else if (P.dim == 2) t = j[P.ax[2]];
+    for (int q = 0; q < P.nk; ++q) {
+      const double* gv = P.kv + 4 * q;
+      const double ph = -(gv[0] * x + gv[1] * y + gv[2] * z);
+      const double a = amp ? amp[(int64_t)q * nt + t] : gv[3];
+      re += a * cos(ph);
+      imv += a * sin(ph);
+    }
+    const double ph = P.k0[0] * x + P.k0[1] * y + P.k0[2] * z;   // the twist e^{j k0.d}
+    const double c = cos(ph), s = sin(ph);
+    v = make_double2(re * c - imv * s, re * s + imv * c);
   }
-  if (!dx && !dy && !dz) {
-    out[i] = make_double2(r0re, r0im);
-    return;
-  }
-  const double x = dx * g.delta[0], y = dy * g.delta[1], z = dz * g.delta[2];
-  double re, im;
-  sm::bloch_eval(P, x, y, z, false, &re, &im);
-  const double ph = P.k0[0] * x + P.k0[1] * y + P.k0[2] * z;   // the twist e^{j k0.d}
-  const double c = cos(ph), s = sin(ph);
-  out[i] = make_double2(re * c - im * s, re * s + im * c);
+  out[i] = v;
+  if (im != i) out[im] = make_double2(v.x, -v.y);
 }
 
 __global__ void k_real_part(const double2* __restrict__ in, double* __restrict__ re, double* __restrict__ im_abs,
@@ -183,14 +233,20 @@ int bloch_spectrum_device(const Setup& s, const double k0[3], double* spec_dev, 
   double* dkv = nullptr;
   double2* a = nullptr;
   double* im = nullptr;
+  double* amp = nullptr;
   double2* tw[3] = {nullptr, nullptr, nullptr};
   auto cleanup = [&]() {
     cudaFree(dkv);
     cudaFree(a);
     cudaFree(im);
+    cudaFree(amp);
     for (double2* t : tw) cudaFree(t);
   };
+  // amplitude table: 1D per (term, transverse offset), 2D per (term, open index), 3D none
+  const int nt = P.dim == 1 ? g.fft[P.ax[1]] * g.fft[P.ax[2]] : P.dim == 2 ? g.fft[P.ax[2]] : 0;
+  const int64_t namp = (int64_t)P.nk * nt;
   cudaError_t e = cudaMalloc(&dkv, std::max<size_t>(kv.size(), 4) * sizeof(double));
+  if (e == cudaSuccess && namp > 0) e = cudaMalloc(&amp, namp * sizeof(double));
   if (e == cudaSuccess) e = cudaMalloc(&a, n * sizeof(double2));
   if (e == cudaSuccess) e = cudaMalloc(&im, n * sizeof(double));
   if (e == cudaSuccess && !kv.empty()) e = cudaMemcpy(dkv, kv.data(), kv.size() * sizeof(double), cudaMemcpyHostToDevice);
@@ -216,7 +272,8 @@ int bloch_spectrum_device(const Setup& s, const double k0[3], double* spec_dev, 
     sm::bloch_eval(Ph, 0, 0, 0, true, &r0re, &r0im);
     r0re -= 2 * P.eta / std::sqrt(kPi);
   }
-  k_bloch_table<<<nblk(n), kB>>>(P, g, r0re, r0im, a);
+  if (namp > 0) k_bloch_amp<<<nblk(namp), kB>>>(P, g, nt, amp);
+  k_bloch_table<<<nblk(n), kB>>>(P, g, r0re, r0im, amp, nt, a);
   const double2* twc[3] = {tw[0], tw[1], tw[2]};
   launch_fft3_forward_f64(a, g.fft, twc, 0);
   k_real_part<<<nblk(n), kB>>>(a, spec_dev, im, n);

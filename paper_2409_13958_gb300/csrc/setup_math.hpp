@@ -467,9 +467,10 @@ PMFEM_HD double bloch_spectral_1d(double rho, double k, double eta, const double
   return out;
 }
 
-// G_k(r); skip_origin drops the l = 0 image (for the regular part at r = 0)
-PMFEM_HD void bloch_eval(const BlochParams& P, double x, double y, double z, bool skip_origin, double* re,
-                         double* im) {
+// Real-space part of G_k(r): the images within reach of erfc, each with its phase; skip_origin
+// drops the l = 0 image (for the regular part at r = 0)
+PMFEM_HD void bloch_real_part(const BlochParams& P, double x, double y, double z, bool skip_origin, double* re,
+                              double* im) {
   double sr = 0, si = 0;
   const double cut = kCutReal / P.eta;
   for (int i = -P.nimg[0]; i <= P.nimg[0]; ++i)
@@ -485,25 +486,43 @@ PMFEM_HD void bloch_eval(const BlochParams& P, double x, double y, double z, boo
         sr += t * cos(ph);
         si += t * sin(ph);
       }
+  *re = sr;
+  *im = si;
+}
+
+// Amplitude of spectral term q at r, without its phase e^{-j g.r}: the coefficient times, in 2D,
+// the slab function of the open coordinate and, in 1D, the radial integral at the distance from
+// the lattice axis.  It depends on r only through that coordinate (2D) or distance (1D).
+PMFEM_HD double bloch_term_amp(const BlochParams& P, int q, double x, double y, double z) {
   const double r[3] = {x, y, z};
+  const double* g = P.kv + 4 * q;
+  double amp = g[3];
+  if (P.dim == 2) {
+    const double kk = sqrt(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
+    const double zz = r[P.ax[2]];
+    double slab = 0;
+    for (int sgn = -1; sgn <= 1; sgn += 2) {
+      const double e = erfc(kk / (2 * P.eta) + sgn * P.eta * zz);
+      if (e > 0) slab += exp(sgn * kk * zz + log(e));
+    }
+    amp *= slab;
+  } else if (P.dim == 1) {
+    const int a = P.ax[0];
+    const double rho2 = x * x + y * y + z * z - r[a] * r[a];
+    amp *= bloch_spectral_1d(sqrt(rho2 > 0 ? rho2 : 0.0), fabs(g[a]), P.eta, P.gl_x, P.gl_w);
+  }
+  return amp;
+}
+
+// G_k(r) = real-space part + sum over the shifted reciprocal vectors of amplitude x e^{-j g.r}
+PMFEM_HD void bloch_eval(const BlochParams& P, double x, double y, double z, bool skip_origin, double* re,
+                         double* im) {
+  double sr, si;
+  bloch_real_part(P, x, y, z, skip_origin, &sr, &si);
   for (int q = 0; q < P.nk; ++q) {
     const double* g = P.kv + 4 * q;
     const double ph = -(g[0] * x + g[1] * y + g[2] * z);
-    double amp = g[3];
-    if (P.dim == 2) {
-      const double kk = sqrt(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
-      const double zz = r[P.ax[2]];
-      double slab = 0;
-      for (int sgn = -1; sgn <= 1; sgn += 2) {
-        const double e = erfc(kk / (2 * P.eta) + sgn * P.eta * zz);
-        if (e > 0) slab += exp(sgn * kk * zz + log(e));
-      }
-      amp *= slab;
-    } else if (P.dim == 1) {
-      const int a = P.ax[0];
-      const double rho2 = x * x + y * y + z * z - r[a] * r[a];
-      amp *= bloch_spectral_1d(sqrt(rho2 > 0 ? rho2 : 0.0), fabs(g[a]), P.eta, P.gl_x, P.gl_w);
-    }
+    const double amp = bloch_term_amp(P, q, x, y, z);
     sr += amp * cos(ph);
     si += amp * sin(ph);
   }
