@@ -990,6 +990,20 @@ def surrogate_leg(args, dist, world):
                     f"streamed run by run, the last {held_runs} run(s) held out"}
 
 
+def side_leg(world: int, fn, *a):
+    """A side leg's JSON object.  On one rank a leg that raises is recorded as {"error": ...} (the
+    traceback goes to stderr) so that the headline line is still printed; with several ranks the
+    exception propagates, since the other ranks would otherwise wait in the leg's collectives."""
+    if world > 1:
+        return fn(*a)
+    try:
+        return fn(*a)
+    except Exception as e:   # noqa: BLE001 - any failure of a side leg is reported in its place
+        import traceback
+        traceback.print_exc(file=sys.stderr)
+        return {"error": f"{type(e).__name__}: {e}"}
+
+
 def run_native(args):
     import torch
     from paper_2409_13958_gb300 import Pmfem, PMFEM_FP32, PMFEM_FP64, PMFEM_ALL
@@ -1260,17 +1274,17 @@ def run_native(args):
                         "around every launch; the headline pass replays each step's captured CUDA graph",
     }
     if not args.no_batch:
-        line["batch"] = batch_leg(args, dist, world)
+        line["batch"] = side_leg(world, batch_leg, args, dist, world)
     if not args.no_lattice:
-        line["lattice"] = lattice_leg(args, dist, world)
+        line["lattice"] = side_leg(world, lattice_leg, args, dist, world)
     if not args.no_local_terms:
-        line["local_terms"] = local_terms_leg(args, dist, world, mesh)
+        line["local_terms"] = side_leg(world, local_terms_leg, args, dist, world, mesh)
     if not args.no_bloch:
-        line["bloch"] = bloch_leg(args, dist, world, mesh)
+        line["bloch"] = side_leg(world, bloch_leg, args, dist, world, mesh)
     if not args.no_surrogate:
-        line["surrogate"] = surrogate_leg(args, dist, world)
+        line["surrogate"] = side_leg(world, surrogate_leg, args, dist, world)
     if rank == 0 and not args.no_cpu:
-        line["cpu_baseline"] = cpu_baseline_leg()
+        line["cpu_baseline"] = side_leg(1, cpu_baseline_leg)
     dist.close()
     if rank == 0:
         print(json.dumps(line))

@@ -59,3 +59,17 @@ def test_two_gloo_ranks_take_the_max_time_and_sum_the_units():
         assert slowest == 15.0                     # the max over both ranks, on every rank
         assert value == pytest.approx(2 * 1000 / 15e-3)
         assert ref_rc == 0
+
+
+def test_a_failing_side_leg_is_recorded_on_one_rank_and_raised_on_several():
+    import bench
+
+    def leg(x):
+        if x < 0:
+            raise ValueError("negative")
+        return {"x": x}
+
+    assert bench.side_leg(1, leg, 2) == {"x": 2}
+    assert bench.side_leg(1, leg, -1) == {"error": "ValueError: negative"}
+    with pytest.raises(ValueError):
+        bench.side_leg(2, leg, -1)
