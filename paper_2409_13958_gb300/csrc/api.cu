@@ -1069,10 +1069,15 @@ int pmfem_llg_step_implicit(pmfem_t h, double dt, int nsteps, const pmfem_implic
 int pmfem_bloch_spectrum(pmfem_t h, const double* k0, double* out, double* max_imag) {
   if (!h || !k0 || !out) return EINVAL_;
   if (!h->s.ready) return fail(h, ESTATE_, "call pmfem_set_periodicity first");
+  Error err;
+  {   // k0 checked before any device allocation
+    sm::BlochParams P;
+    std::vector<double> kv;
+    if (int rc = bloch_params(h->s, k0, P, kv, err)) return fail(h, rc, err.msg);
+  }
   const int64_t n = (int64_t)h->s.fft[0] * h->s.fft[1] * h->s.fft[2];
   double* d = nullptr;
   PMFEM_CK(h, cudaMalloc(&d, n * sizeof(double)));
-  Error err;
   int rc = bloch_spectrum_device(h->s, k0, d, max_imag, err);
   if (!rc) {
     cudaError_t e = cudaMemcpy(out, d, n * sizeof(double), cudaMemcpyDeviceToHost);
@@ -1087,6 +1092,13 @@ int pmfem_bloch_spectrum(pmfem_t h, const double* k0, double* out, double* max_i
 
 int pmfem_bloch_convolve(pmfem_t h, const double* k0, const void* Q, void* U, void* stream) {
   if (!h || !k0 || !Q || !U || Q == U) return fail(h, EINVAL_, "k0, Q and U are required and Q, U distinct");
+  if (!h->s.ready) return fail(h, ESTATE_, "call pmfem_set_periodicity first");
+  {   // k0 checked before the device data are built
+    sm::BlochParams P;
+    std::vector<double> kv;
+    Error err;
+    if (int rc = bloch_params(h->s, k0, P, kv, err)) return fail(h, rc, err.msg);
+  }
   int rc = ensure_device(h);
   if (rc) return rc;
   const int64_t n = (int64_t)h->s.fft[0] * h->s.fft[1] * h->s.fft[2];

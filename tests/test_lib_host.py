@@ -250,3 +250,48 @@ def test_debug_hooks_without_a_gpu():
     assert lib.pmfem_debug_fail_alloc(-2) == -1
     assert lib.pmfem_debug_fail_alloc(3) == 0
     assert lib.pmfem_debug_fail_alloc(-1) == 0
+
+
+def test_local_terms_and_bloch_inputs_are_checked_without_a_gpu():
+    """Invalid anisotropy, stiffness and Bloch inputs are refused on the host (EINVAL), and a Bloch
+    call before the set-up with ESTATE, before any device work."""
+    mesh, gr = meshgen.granular_cell(n=4, grains=3, seed=1)
+    h = B.Pmfem.create_mesh(mesh.xyz, mesh.tets, 8e5, 1.3e-11, 0.02)
+    h.set_aim(8, 8, 8, 3, 2, 0.0)
+    k_lat = np.array([2 * np.pi / mesh.periods[0], 0.0, 0.0])      # on the reciprocal lattice
+    with pytest.raises(B.PmfemError) as e:
+        h.bloch_spectrum(0.3 * k_lat)
+    assert e.value.code == -7
+    for bad in (-1.0, np.nan):
+        A = gr.A_tet.copy()
+        A[3] = bad
+        with pytest.raises(B.PmfemError) as e:
+            h.set_exchange_per_tet(A)
+        assert e.value.code == -1
+    axes = gr.axes.reshape(-1, 9)
+    tg = gr.tet_grain.copy()
+    tg[0] = 3                                                       # only grains 0..2 exist
+    cases = [dict(tet_grain=tg, axes=axes, K1=gr.K1),
+             dict(tet_grain=gr.tet_grain, axes=2 * axes, K1=gr.K1),   # axes not unit rows
+             dict(tet_grain=gr.tet_grain, axes=axes, Ku=np.ones(3)),  # Ku without u
+             dict(tet_grain=gr.tet_grain, axes=axes)]                 # neither K1 nor Ku
+    for kw in cases:
+        with pytest.raises(B.PmfemError) as e:
+            h.set_anisotropy(**kw)
+        assert e.value.code == -1
+    h.set_exchange_per_tet(gr.A_tet)
+    h.set_periodicity(*mesh.periods)
+    h.set_anisotropy(gr.tet_grain, axes, K1=gr.K1)
+    with pytest.raises(B.PmfemError) as e:
+        h.bloch_spectrum(k_lat)
+    assert e.value.code == -1
+    with pytest.raises(B.PmfemError) as e:
+        h.bloch_convolve(k_lat, 1 << 20, 2 << 20)
+    assert e.value.code == -1
+    film = meshgen.film_cell(4, 4, 2)
+    f = B.Pmfem.create_mesh(film.xyz, film.tets, 8e5, 1.3e-11, 0.02)
+    f.set_aim(8, 8, 8, 3, 2, 0.0)
+    f.set_periodicity(*film.periods)
+    with pytest.raises(B.PmfemError) as e:                          # k0 along the open axis
+        f.bloch_convolve(np.array([0.0, 0.0, 1e8]), 1 << 20, 2 << 20)
+    assert e.value.code == -1
