@@ -141,8 +141,9 @@ int pmfem_set_periodicity(pmfem_t h, double L1, double L2, double L3);
  * energy lumped to the nodes).  It enters pmfem_field under PMFEM_AN (and PMFEM_ALL), the RK4
  * and implicit steps (the implicit step's Jacobian leaves it out: its Newton iteration becomes
  * a quasi-Newton iteration for it), in the field kernel's epilogue.  Batches ignore it.
- * tet_grain NULL removes it.  Drops the handle's device data (the state m included); EINVAL
- * for grains out of range, axes that are not unit rows, or non-finite constants.
+ * tet_grain NULL removes it.  An accepted call drops the handle's device data (the state m
+ * included); EINVAL, with the handle unchanged, for grains out of range, axes that are not unit
+ * rows, Ku without u, neither K1 nor Ku, or non-finite constants.
  */
 int pmfem_set_exchange_per_tet(pmfem_t h, const double* A_tet);
 int pmfem_set_anisotropy(pmfem_t h, const int32_t* tet_grain, int n_grains, const double* K1, const double* axes,

@@ -824,8 +824,8 @@ int pmfem_set_exchange_per_tet(pmfem_t h, const double* A_tet) {
 int pmfem_set_anisotropy(pmfem_t h, const int32_t* tet_grain, int n_grains, const double* K1, const double* axes,
                          const double* Ku, const double* u) {
   if (!h) return EINVAL_;
-  free_device(h);
   if (!tet_grain) {
+    free_device(h);
     h->s.tet_grain.clear();
     h->s.grain_tab.clear();
     return OK;
@@ -855,6 +855,7 @@ int pmfem_set_anisotropy(pmfem_t h, const int32_t* tet_grain, int n_grains, cons
     for (int k = 0; k < kGrainTab; ++k)
       if (!std::isfinite(P[k])) return fail(h, EINVAL_, "non-finite anisotropy parameter");
   }
+  free_device(h);   // only an accepted change drops the device data
   h->s.tet_grain.assign(tet_grain, tet_grain + h->s.T);
   h->s.grain_tab.swap(tab);
   return OK;
