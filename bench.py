@@ -1273,16 +1273,21 @@ def run_native(args):
         "kernels_pass": "a second pass of the same K steps, launched kernel by kernel with a CUDA-event pair "
                         "around every launch; the headline pass replays each step's captured CUDA graph",
     }
-    if not args.no_batch:
+    # the side legs' workloads are the same on every replica: with N > 1 (a scaling run, which
+    # holds all N GPUs) they are left to the N = 1 run
+    side = world == 1
+    if side and not args.no_batch:
         line["batch"] = side_leg(world, batch_leg, args, dist, world)
-    if not args.no_lattice:
+    if side and not args.no_lattice:
         line["lattice"] = side_leg(world, lattice_leg, args, dist, world)
-    if not args.no_local_terms:
+    if side and not args.no_local_terms:
         line["local_terms"] = side_leg(world, local_terms_leg, args, dist, world, mesh)
-    if not args.no_bloch:
+    if side and not args.no_bloch:
         line["bloch"] = side_leg(world, bloch_leg, args, dist, world, mesh)
-    if not args.no_surrogate:
+    if side and not args.no_surrogate:
         line["surrogate"] = side_leg(world, surrogate_leg, args, dist, world)
+    if not side:
+        line["side_legs"] = "batch, lattice, local terms, Bloch and surrogate legs run with N = 1 only"
     if rank == 0 and not args.no_cpu:
         line["cpu_baseline"] = side_leg(1, cpu_baseline_leg)
     dist.close()
