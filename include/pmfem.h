@@ -300,7 +300,7 @@ int pmfem_llg_step_implicit(pmfem_t h, double dt, int nsteps, const pmfem_implic
  * precision's type T for the convolution, O(log F) work per point and axis.  The first call for
  * a k0 (or after a precision change) sets up that spectrum and synchronises the device; later
  * calls with the same k0 only enqueue the five passes.  EINVAL for k0 off the periodic axes or on
- * the reciprocal lattice.
+ * the reciprocal lattice, checked before any device work; ESTATE before pmfem_set_periodicity.
  */
 int pmfem_bloch_spectrum(pmfem_t h, const double* k0, double* out, double* max_imag);
 int pmfem_bloch_convolve(pmfem_t h, const double* k0, const void* Q, void* U, void* stream);
