@@ -295,3 +295,22 @@ def test_local_terms_and_bloch_inputs_are_checked_without_a_gpu():
     with pytest.raises(B.PmfemError) as e:                          # k0 along the open axis
         f.bloch_convolve(np.array([0.0, 0.0, 1e8]), 1 << 20, 2 << 20)
     assert e.value.code == -1
+
+
+def test_host_exchange_with_a_stiffness_per_tet_matches_oracle():
+    """The stored exchange operator with a grain-boundary stiffness layer (A inside the element
+    sum) equals the oracle's K_A scaled by -2/(mu0 Ms V_n), on the granular 3D-periodic cell."""
+    from oracle import local_terms as LT
+    mesh, gr = meshgen.granular_cell(n=5, grains=4, seed=2)
+    Ms = 8e5
+    h = B.Pmfem.create_mesh(mesh.xyz, mesh.tets, Ms, 1.3e-11, 0.02)
+    h.set_aim(8, 8, 8, 3, 2, 0.0)
+    h.set_exchange_per_tet(gr.A_tet)
+    h.set_periodicity(*mesh.periods)
+    ob = OracleProblem(mesh.xyz, mesh.tets, mesh.periods, Ms=Ms, A=1.3e-11, grid=(8, 8, 8), p=3, near_boxes=2)
+    KA = LT.exchange_matrix_per_tet(ob.xyz, ob.tets, ob.lca, ob.Np, gr.A_tet)
+    ref = sp.csr_matrix(-(2.0 / (4e-7 * math.pi * Ms)) * sp.diags(1 / ob.V) @ KA)
+    rp, col, v = h.operator_export(0)
+    ok, err = _close(_csr(rp, col, v[:, 0], ob.Np), ref, 1e-12)
+    assert ok, err
+    assert 0 < (gr.A_tet < 1.3e-11).mean() < 1      # the layer is there and is not everything
